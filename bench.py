@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the Langevin nanoparticle-aggregation step on GB300.
+
+Workload: the 250000-NP three-type droplet (diameters 1/1.5/3 sigma, fractions
+0.6/0.3/0.1, charges 0/+0.5/-0.5, all-pairs Coulomb + cell-list LJ at
+2.5 sigma_ab, R 200 -> 60 sigma, kT = 1), synthetic seeded initial state.  One
+step = cell binning, cell-list LJ, all-pairs Coulomb, and the fused
+integrator (radius law, interface spring, drag, Philox noise, update).
+
+Prints one JSON line: pair-interactions/s (N(N-1) per step) as `value`, with
+particle-steps/s, the roofline of the all-pairs kernel (FP32 CUDA-core ALU),
+an end-to-end figure through the C ABI with host buffers, the FP64 CPU oracle
+timed on a bounded sample, and the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s & particle-steps/s at N=2.5e5; ensemble droplets/s vs plain"
+UNIT = "pair-interactions/s"
+FLOPS_PER_PAIR = 17  # Coulomb pair: 3 sub, 5 for r^2, 2 for r^-3, 1 for q_j, 6 accumulate
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=250000, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _scenario(n, seed):
+    import workloads as wl
+    sc = wl.config3(kT=1.0, seed=seed)
+    return wl.scaled(sc, n) if n != sc.n else sc
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+
+
+def _oracle_sample(sc, x, types, seconds, max_rows=None):
+    """Time the FP64 oracle's pair + external forces on sampled rows of the workload.
+    Rows grow until one call takes about `seconds`."""
+    import numpy as np
+    import oracle
+    sig = [t.sigma for t in sc.types]
+    eps = [t.eps for t in sc.types]
+    q = [t.charge for t in sc.types]
+    rows = 256
+    rng = np.random.default_rng(1)
+    while True:
+        sel = rng.choice(sc.n, rows, replace=False)
+        t0 = time.perf_counter()
+        oracle.pair_forces(x, types, sig, eps, q, sc.bjerrum, lj_cut=sc.lj_cut,
+                           lj=True, coulomb=True, sel=sel)
+        oracle.external_forces(sc, x[sel], types[sel], 0.0)
+        dt = time.perf_counter() - t0
+        if dt >= seconds or rows >= sc.n or (max_rows and rows >= max_rows):
+            return rows, dt
+        rows = min(sc.n, int(rows * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
+
+
+def _omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import workloads as wl
+    import oracle
+    oracle.build()
+    sc = _scenario(a.n, 0)
+    types, x, _ = wl.initial_state(sc)
+    import numpy as np
+    rows, _ = _oracle_sample(sc, x, types, 3.0)
+    sig = [t.sigma for t in sc.types]
+    eps = [t.eps for t in sc.types]
+    q = [t.charge for t in sc.types]
+    times = []
+    for k in range(a.warmup + a.steps):
+        sel = np.random.default_rng(100 + k).choice(sc.n, rows, replace=False)
+        t0 = time.perf_counter()
+        oracle.pair_forces(x, types, sig, eps, q, sc.bjerrum, lj_cut=sc.lj_cut, sel=sel)
+        oracle.external_forces(sc, x[sel], types[sel], 0.0)
+        dt = time.perf_counter() - t0
+        if k >= a.warmup:
+            times.append(dt)
+    t = sum(times)
+    pairs = rows * (sc.n - 1) * a.steps
+    val = pairs / t
+    sample = (f"FP64 oracle pair+external forces of {rows} sampled rows of the "
+              f"{sc.n}-NP workload per step (all {sc.n - 1} partners each)")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+           "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": sc.name, "n_particles": sc.n, "rows_per_step": rows},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": _omp_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
+# Clocks sampled during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _traffic_from_profile(kernel_src):
+    """dram bytes per launch recorded by the committed ncu summary, if it was taken
+    on the current all-pairs source (else null)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "allpairs_paper_scale250000.md")
+    try:
+        txt = open(path).read()
+        src = open(kernel_src, "rb").read()
+    except OSError:
+        return None
+    h = hashlib.sha256(src).hexdigest()[:16]
+    m_h = re.search(r"source sha256\[:16\]:\s*([0-9a-f]{16})", txt)
+    m_t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    if m_h and m_t and m_h.group(1) == h:
+        return float(m_t.group(1))
+    return None
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2501_04456_gb300 import build as _b
+    _b.build()
+    import paper_2501_04456_gb300 as P
+    import workloads as wl
+
+    sc = _scenario(a.n, rank)  # weak scaling: every rank runs its own droplet
+    types, x, v = wl.initial_state(sc)
+    n = sc.n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    sim = P.Sim(sc, x, v, types, stream=stream)
+    sim.profile(True)
+    info = P.npsim_device_info()
+    cfg = sim.allpairs_config()
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    clocks.start()
+    time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    ap_ms = []
+    int_ms = []
+    cell_ms = []
+    t_wall0 = time.perf_counter()
+    for k in range(a.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+        kt, _ = sim.kernel_times()
+        ap_ms.append(kt["allpairs"])
+        int_ms.append(kt["integrate"])
+        cell_ms.append(kt["cell_build"] + kt["cell_lj"])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    launches = a.steps * (1 + sim.launches_per_step())
+    sim.close()
+
+    pairs_per_step = n * (n - 1)
+    value = world * pairs_per_step / (step_ms * 1e-3)
+    psteps = world * n / (step_ms * 1e-3)
+
+    # roofline of the dominant kernel (all-pairs, FP32 CUDA-core ALU)
+    peaks = _peaks()
+    max_mhz = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    peak_tflops = info["sm_count"] * 128 * 2 * max_mhz * 1e6 / 1e12
+    ap_avg = sum(ap_ms) / len(ap_ms)
+    achieved = FLOPS_PER_PAIR * pairs_per_step / (ap_avg * 1e-3) / 1e12
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2501_04456_gb300", "csrc",
+                                                 "allpairs.cu"))
+
+    # end to end through the C ABI with host buffers: create from host arrays,
+    # then per step one step and a device->host read of the positions
+    e2e = None
+    if rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = P.Sim(sc, x, v, types, stream=stream)
+        for _ in range(a.steps):
+            s2.step(1)
+            P.npsim_get_state(s2.h, n)
+        s2.close()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = (x.nbytes + v.nbytes + types.nbytes) / a.steps
+        d2h = 3 * 3 * 8 * n  # x, v and F as float64 per step
+        e2e = {"value": world * pairs_per_step * a.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "includes": "create (upload, initial forces) + per step npsim_step(1) and "
+                           "npsim_get_state to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import oracle
+        oracle.build()
+        rows, dt = _oracle_sample(sc, x, types, a.cpu_seconds)
+        cpu = {"value": rows * (n - 1) / dt, "unit": UNIT, "cores": _omp_threads(),
+               "kind": "oracle",
+               "sample": f"FP64 oracle pair+external forces of {rows} random rows of the "
+                         f"{n}-NP workload (all {n - 1} partners each), {dt:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pair math, f64 accumulation and integration",
+            "data": "synthetic (seeded placement in the droplet, Maxwell velocities)",
+            "config": {"workload": sc.name, "n_particles": n, "types": 3,
+                       "forces": "all-pairs Coulomb + cell-list LJ 2.5 sigma_ab",
+                       "l2": "flushed (256 MiB write) before every timed step, outside "
+                             "the step's events",
+                       "allpairs_launch": cfg, "parallelism": f"replicas{world}"},
+            "particle_steps_per_s": psteps,
+            "wall_s_timed_loop": t_wall,
+            "kernel_ms": {"allpairs": ap_avg, "integrate": sum(int_ms) / len(int_ms),
+                          "cell_list": sum(cell_ms) / len(cell_ms)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": traffic,
+                         "peak_basis": f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x "
+                                       f"{max_mhz:.0f} MHz (max SM clock)",
+                         "frac_at_sampled_clock": (achieved / (peak_tflops * clk["sm_mhz"] /
+                                                               max_mhz)) if clk else None},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * npsim.h -- C ABI of the GB300 (sm_103a) Langevin-dynamics nanoparticle
+ * aggregation library.
+ *
+ * The library advances N nanoparticles (NPs) of up to NPSIM_MAX_TYPES types
+ * inside an evaporating or condensing droplet, following the six-step loop of
+ * arXiv 2501.04456 Sec. 2.2: (i) binning into cells, (ii) Lennard-Jones and
+ * Coulomb pair forces, (iii) the droplet radius, (iv) the interface (surface
+ * tension) force, (v) gravity, viscosity and centrifugal force, (vi) the
+ * velocity and position update with Brownian noise.  All compute runs in the
+ * library's CUDA kernels; this header uses only plain C types.
+ *
+ * Units are reduced: length = sigma of the reference NP, energy = kT_ref = 1.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: NPSIM_OK (0) or a negative NPSIM_ERR_* code.  Nothing aborts,
+ *    traps or exits; npsim_last_error() gives a message for the calling thread.
+ *  - Host arrays of positions, velocities and forces are row-major n x 3
+ *    float64 ("xyz xyz ...").  Types are int32 in [0, n_types).
+ *  - The caller owns every buffer it passes; the library copies what it keeps.
+ *    The library owns the simulation object and its device memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    queued on it; functions that return host data synchronise it.
+ *  - A simulation object may be used by one host thread at a time.
+ */
+#ifndef NPSIM_H
+#define NPSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NPSIM_MAX_TYPES 8
+#define NPSIM_MAX_SCALES 32
+
+enum {
+    NPSIM_OK = 0,
+    NPSIM_ERR_INVALID_ARG = -1, /* bad size, pointer, type index or parameter */
+    NPSIM_ERR_CUDA = -2,        /* a CUDA runtime call failed (message says which) */
+    NPSIM_ERR_NONFINITE = -3,   /* a position became NaN/Inf during npsim_step */
+    NPSIM_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    NPSIM_ERR_OOM = -5,         /* device allocation failed */
+    NPSIM_ERR_IO = -6,          /* checkpoint file could not be written or read */
+    NPSIM_ERR_NO_DEVICE = -7    /* no CUDA device, or not an sm_103 device */
+};
+
+/* Per-type NP properties (Sec. 2.1: "radius, mass, charge"; a spring constant of
+ * the interface per NP type; friction from Stokes' law). */
+typedef struct {
+    double sigma;  /* diameter; LJ length of the like pair; radius = sigma/2 */
+    double eps;    /* LJ well depth of the like pair */
+    double mass;
+    double charge; /* in units of the elementary charge */
+    double gamma;  /* Langevin friction rate (1/time): drag force = -mass*gamma*v */
+    double k_wall; /* interface spring constant */
+} npsim_type_t;
+
+/* Scenario parameters. */
+typedef struct {
+    int32_t n_types;    /* 1 .. NPSIM_MAX_TYPES */
+    int32_t rot_mode;   /* centrifugal force: 0 none, 1 rotation about z, 2 isotropic */
+    int32_t lj_mode;    /* LJ: 0 off, 1 inside the all-pairs kernel, 2 cell list */
+    int32_t coulomb;    /* 1: all-pairs Coulomb (not truncated), 0: off */
+    int32_t wall;       /* 1: interface spring on, 0: off (bulk liquid) */
+    int32_t integrator; /* 0: BAOAB Langevin, 1: overdamped (Brownian dynamics) */
+    uint64_t seed;      /* Philox key of the noise */
+    double dt;          /* time step */
+    double kT;          /* temperature of the noise */
+    double R0;          /* droplet radius at t = 0 */
+    double k_evap;      /* radius-square law R(t)^2 = R0^2 - k_evap*t */
+    double g;           /* gravity along -z: force -mass*g */
+    double omega;       /* rotation rate of the centrifugal force */
+    double bjerrum;     /* Coulomb prefactor C: U = C q_a q_b / r */
+    double lj_cut;      /* LJ cutoff in units of sigma_ab (2.5 typical) */
+    const double *eps_override; /* n_types x n_types LJ eps matrix, or NULL for
+                                   Lorentz-Berthelot eps_ab = sqrt(eps_a eps_b) */
+} npsim_params_t;
+
+typedef struct npsim_sim *npsim_sim_t;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *npsim_last_error(void);
+
+/* Library version string and the device it runs on.  sm_count/clock_khz may be NULL. */
+int npsim_device_info(int *sm_count, int *clock_khz, int *cc_major, int *cc_minor);
+
+/*
+ * Create a simulation of n NPs (Sec. 2.1: NPs "initially randomly distributed in
+ * a sphere"; the caller supplies the initial state so that runs are
+ * reproducible).  x0: n x 3 positions; v0: n x 3 velocities or NULL (zero);
+ * type: n type indices.  Pair parameters follow Lorentz-Berthelot mixing,
+ * sigma_ab = (sigma_a + sigma_b)/2, unless params->eps_override is set
+ * (Table 1 prints such a matrix).  The initial total force F(x0, t=0) is
+ * computed before returning.  On success *out owns device memory until
+ * npsim_destroy.  Errors: INVALID_ARG (n < 1, n > 2^31-1, bad type index,
+ * non-positive mass/sigma/dt), OOM, CUDA, NO_DEVICE.
+ */
+int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_t n,
+                 const double *x0, const double *v0, const int32_t *type,
+                 void *stream, npsim_sim_t *out);
+
+/* Release the object and its device memory (NULL is ignored). */
+void npsim_destroy(npsim_sim_t sim);
+
+/*
+ * Advance n_steps steps of the loop of Sec. 2.2 (steps i-vi): cell binning (if
+ * lj_mode == 2), pair forces, R(t) by the radius-square law, interface spring,
+ * gravity, centrifugal force and the Langevin update with Philox4x32-10 noise
+ * keyed by (seed) and counted by (particle, step, 0).  Steps are replayed from
+ * captured CUDA graphs.  Returns after one device-to-host read of the error
+ * word: NONFINITE if any position became non-finite, TIMEOUT if a bounded wait
+ * expired.  n_steps = 0 is a no-op.
+ */
+int npsim_step(npsim_sim_t sim, int64_t n_steps);
+
+/* Copy the state to host arrays (any may be NULL): x, v (n x 3), F (n x 3 total
+ * force at x and the current time), *step (steps taken since t = 0). */
+int npsim_get_state(npsim_sim_t sim, double *x, double *v, double *F, int64_t *step);
+
+/* Replace the state (x required, v may be NULL = zero) and set the step counter;
+ * recomputes F at the new positions. */
+int npsim_set_state(npsim_sim_t sim, const double *x, const double *v, int64_t step);
+
+/* Forces at the current state into host F (n x 3).  what = 0: total force (pair +
+ * external, the one the integrator uses); 1: pair forces only (step ii);
+ * 2: LJ only; 3: Coulomb only. */
+int npsim_forces(npsim_sim_t sim, int what, double *F);
+
+/* Float32 mirror of the positions (x, y, z, charge) into a caller-owned device
+ * buffer of 4*n floats on the simulation's stream (no host synchronisation). */
+int npsim_positions_device(npsim_sim_t sim, float *dev_xyzq);
+
+/* Statistics of Sec. 3 at the current state. */
+typedef struct {
+    double r_max;       /* RDF range (bins cover [0, r_max)) */
+    int32_t n_bins;     /* RDF bins (> 0) */
+    int32_t radial_bins;/* bins of the radial concentration over [0, R(t)) (0 = skip) */
+    int32_t boxcount;   /* 1: compute the box-counting dimension */
+    int32_t max_scales; /* box-counting scales d*2^k, k < max_scales (<= NPSIM_MAX_SCALES) */
+} npsim_stats_cfg_t;
+
+typedef struct {
+    double R;        /* droplet radius R(t) */
+    double d_mean;   /* number-mean NP diameter */
+    double Rg;       /* radius of gyration (Eqs. Rg, r0) */
+    double Df_rg;    /* D_f from the fractal equation (Eq. N, k_f = 1.593) */
+    double Df_box;   /* box-counting D_f (NaN if fewer than two scales fit) */
+    double center[3];/* centre of mass r0 */
+    int32_t n_scales;
+    int32_t pad_;
+    int64_t nbox[NPSIM_MAX_SCALES];
+} npsim_stats_t;
+
+/*
+ * RDF of Sec. 3.2, g(r) = sum_i (psi_i(r)/N) / ((N-1) dV_r / V) with V the
+ * droplet volume 4 pi R(t)^3 / 3: pair counts (ordered pairs, int64[n_bins])
+ * and g (float64[n_bins]); the radial concentration C_NPs about the droplet
+ * centre (Sec. 3.2) into radial_counts/radial_c (int64/float64[radial_bins],
+ * both may be NULL); R_g and D_f by the fractal equation (Sec. 3.1); the
+ * box-counting D_f.  Pair distances and box indices are computed in float64.
+ */
+int npsim_stats(npsim_sim_t sim, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
+                double *rdf_g, int64_t *radial_counts, double *radial_c,
+                npsim_stats_t *out);
+
+/* Checkpoint (Sec. 2.2: "stopped and restarted with different parameters from
+ * the saved NPs configuration"): positions, velocities, types, step counter and
+ * parameters.  npsim_load creates a new object; params_override (or NULL)
+ * replaces the saved scenario parameters, types_override likewise. */
+int npsim_save(npsim_sim_t sim, const char *path);
+int npsim_load(const char *path, const npsim_type_t *types_override,
+               const npsim_params_t *params_override, void *stream, npsim_sim_t *out);
+
+/* Test hook: n_blocks Philox4x32-10 blocks computed on the device, block b with
+ * counter (ctr[0] + b (carry into ctr[1]), ctr[1], ctr[2], ctr[3]) and key
+ * (seed low word, seed high word), copied to host out[4*n_blocks]. */
+int npsim_philox(uint64_t seed, const uint32_t ctr[4], int64_t n_blocks, uint32_t *out);
+
+/* Test hook: the three standard normals per particle that step `step` uses
+ * (Box-Muller on Philox counter (i, step, 0)), n x 3 into host out. */
+int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out);
+
+/* Kernel-launch configuration of the all-pairs kernel chosen by the autotuner
+ * (block threads, i per thread, j-tile length, grid size). */
+int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j_tile,
+                          int *grid);
+
+/* Kernel launches per step in a long run (pair kernels + cell-list kernels + one
+ * integrator pass); npsim_step adds one integrator launch per graph chunk. */
+int npsim_launches_per_step(npsim_sim_t sim, int *launches);
+
+/* Steps per captured CUDA graph (npsim_step replays ceil(n / chunk) graphs). */
+int npsim_chunk_steps(npsim_sim_t sim, int *chunk);
+
+/*
+ * Per-kernel timing.  enable = 1 re-captures the step graphs with CUDA event
+ * records around the kernels of every step (all-pairs forces, cell-list
+ * build, cell-list LJ, integrator); enable = 0 removes them.  After an
+ * npsim_step, npsim_kernel_times writes the mean duration in milliseconds of
+ * each of the four groups over the steps of the last replayed graph chunk
+ * (0 for groups this scenario does not launch) and the number of steps
+ * averaged.  ms must hold 4 doubles.
+ */
+int npsim_profile(npsim_sim_t sim, int enable);
+int npsim_kernel_times(npsim_sim_t sim, double *ms, int *samples);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NPSIM_H */

@@ -1,0 +1,375 @@
+"""Python binding of libnpsim, the GB300 (sm_103a) Langevin-dynamics library for
+nanoparticle aggregation in an evaporating droplet (arXiv 2501.04456).
+
+Argument marshalling only: every function here has the name of the C entry point
+it calls (include/npsim.h) and converts numpy arrays to the C layouts; all
+computation runs in the library's CUDA kernels.  There is no CPU fallback: if
+``libnpsim.so`` has not been built, every call raises ``RuntimeError``.
+
+PyTorch is optional and used only for streams and device buffers: a ``stream``
+argument may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer or None
+(None = torch's current stream when torch sees a GPU, else the default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnpsim.so")
+MAX_TYPES = 8
+MAX_SCALES = 32
+
+NPSIM_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NONFINITE", -4: "TIMEOUT", -5: "OOM",
+          -6: "IO", -7: "NO_DEVICE"}
+
+
+class NpsimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"npsim error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class npsim_type_t(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("eps", C.c_double), ("mass", C.c_double),
+                ("charge", C.c_double), ("gamma", C.c_double), ("k_wall", C.c_double)]
+
+
+class npsim_params_t(C.Structure):
+    _fields_ = [("n_types", C.c_int32), ("rot_mode", C.c_int32), ("lj_mode", C.c_int32),
+                ("coulomb", C.c_int32), ("wall", C.c_int32), ("integrator", C.c_int32),
+                ("seed", C.c_uint64), ("dt", C.c_double), ("kT", C.c_double),
+                ("R0", C.c_double), ("k_evap", C.c_double), ("g", C.c_double),
+                ("omega", C.c_double), ("bjerrum", C.c_double), ("lj_cut", C.c_double),
+                ("eps_override", C.POINTER(C.c_double))]
+
+
+class npsim_stats_cfg_t(C.Structure):
+    _fields_ = [("r_max", C.c_double), ("n_bins", C.c_int32), ("radial_bins", C.c_int32),
+                ("boxcount", C.c_int32), ("max_scales", C.c_int32)]
+
+
+class npsim_stats_t(C.Structure):
+    _fields_ = [("R", C.c_double), ("d_mean", C.c_double), ("Rg", C.c_double),
+                ("Df_rg", C.c_double), ("Df_box", C.c_double), ("center", C.c_double * 3),
+                ("n_scales", C.c_int32), ("pad_", C.c_int32),
+                ("nbox", C.c_int64 * MAX_SCALES)]
+
+
+_lock = threading.Lock()
+_lib = None
+_d = C.POINTER(C.c_double)
+_i64 = C.POINTER(C.c_int64)
+_i32 = C.POINTER(C.c_int32)
+_u32 = C.POINTER(C.c_uint32)
+_h = C.c_void_p
+
+
+def lib():
+    """The loaded libnpsim.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_2501_04456_gb300.build` (needs nvcc, sm_103a)")
+            L = C.CDLL(LIB_PATH)
+            L.npsim_last_error.restype = C.c_char_p
+            L.npsim_device_info.argtypes = [_i32, _i32, _i32, _i32]
+            L.npsim_create.argtypes = [C.POINTER(npsim_type_t), C.POINTER(npsim_params_t),
+                                       C.c_int64, _d, _d, _i32, C.c_void_p,
+                                       C.POINTER(_h)]
+            L.npsim_destroy.argtypes = [_h]
+            L.npsim_destroy.restype = None
+            L.npsim_step.argtypes = [_h, C.c_int64]
+            L.npsim_get_state.argtypes = [_h, _d, _d, _d, _i64]
+            L.npsim_set_state.argtypes = [_h, _d, _d, C.c_int64]
+            L.npsim_forces.argtypes = [_h, C.c_int, _d]
+            L.npsim_positions_device.argtypes = [_h, C.c_void_p]
+            L.npsim_stats.argtypes = [_h, C.POINTER(npsim_stats_cfg_t), _i64, _d, _i64, _d,
+                                      C.POINTER(npsim_stats_t)]
+            L.npsim_save.argtypes = [_h, C.c_char_p]
+            L.npsim_load.argtypes = [C.c_char_p, C.POINTER(npsim_type_t),
+                                     C.POINTER(npsim_params_t), C.c_void_p, C.POINTER(_h)]
+            L.npsim_philox.argtypes = [C.c_uint64, _u32, C.c_int64, _u32]
+            L.npsim_normals.argtypes = [C.c_uint64, C.c_int64, C.c_int64, _d]
+            L.npsim_allpairs_config.argtypes = [_h, _i32, _i32, _i32, _i32]
+            L.npsim_launches_per_step.argtypes = [_h, _i32]
+            L.npsim_chunk_steps.argtypes = [_h, _i32]
+            L.npsim_profile.argtypes = [_h, C.c_int]
+            L.npsim_kernel_times.argtypes = [_h, _d, _i32]
+            _lib = L
+        return _lib
+
+
+def npsim_last_error() -> str:
+    return lib().npsim_last_error().decode()
+
+
+def _check(rc):
+    if rc != NPSIM_OK:
+        raise NpsimError(rc, npsim_last_error())
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _aos(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, 3)
+    if n is not None and a.shape[0] != n:
+        raise ValueError(f"expected {n} x 3 array, got {a.shape}")
+    return a
+
+
+# --------------------------------------------------------------------------
+# Scenario marshalling (duck-typed: any object with the fields of the C structs)
+
+
+def types_from(specs):
+    arr = (npsim_type_t * MAX_TYPES)()
+    for k, t in enumerate(specs):
+        arr[k] = npsim_type_t(t.sigma, t.eps, t.mass, t.charge, t.gamma, t.k_wall)
+    return arr
+
+
+def params_from(sc):
+    """npsim_params_t from a scenario object (n_types taken from sc.types)."""
+    p = npsim_params_t()
+    p.n_types = len(sc.types)
+    p.rot_mode = sc.rot_mode
+    p.lj_mode = sc.lj_mode
+    p.coulomb = int(bool(sc.coulomb))
+    p.wall = int(bool(sc.wall))
+    p.integrator = sc.integrator
+    p.seed = sc.seed
+    p.dt, p.kT, p.R0, p.k_evap = sc.dt, sc.kT, sc.R0, sc.k_evap
+    p.g, p.omega, p.bjerrum, p.lj_cut = sc.g, sc.omega, sc.bjerrum, sc.lj_cut
+    ov = getattr(sc, "eps_override", None)
+    if ov is not None:
+        ov = np.ascontiguousarray(ov, dtype=np.float64).ravel()
+        p._keep = ov
+        p.eps_override = _p(ov, C.c_double)
+    return p
+
+
+# --------------------------------------------------------------------------
+# Entry points
+
+
+def npsim_device_info():
+    a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().npsim_device_info(C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return {"sm_count": a.value, "clock_khz": b.value, "cc": (c.value, d.value)}
+
+
+def npsim_create(types, params, x0, v0, type, stream=None):
+    x0 = _aos(x0)
+    n = x0.shape[0]
+    v0 = None if v0 is None else _aos(v0, n)
+    ty = np.ascontiguousarray(type, dtype=np.int32)
+    if ty.shape != (n,):
+        raise ValueError("type must have one entry per particle")
+    h = _h()
+    _check(lib().npsim_create(types, C.byref(params), n, _p(x0, C.c_double),
+                              None if v0 is None else _p(v0, C.c_double),
+                              _p(ty, C.c_int32), _stream_handle(stream), C.byref(h)))
+    return h
+
+
+def npsim_destroy(h):
+    lib().npsim_destroy(h)
+
+
+def npsim_step(h, n_steps):
+    _check(lib().npsim_step(h, int(n_steps)))
+
+
+def npsim_get_state(h, n):
+    x = np.empty((n, 3))
+    v = np.empty((n, 3))
+    F = np.empty((n, 3))
+    st = C.c_int64()
+    _check(lib().npsim_get_state(h, _p(x, C.c_double), _p(v, C.c_double),
+                                 _p(F, C.c_double), C.byref(st)))
+    return x, v, F, st.value
+
+
+def npsim_set_state(h, x, v=None, step=0):
+    x = _aos(x)
+    v = None if v is None else _aos(v, x.shape[0])
+    _check(lib().npsim_set_state(h, _p(x, C.c_double),
+                                 None if v is None else _p(v, C.c_double), int(step)))
+
+
+def npsim_forces(h, n, what=0):
+    F = np.empty((n, 3))
+    _check(lib().npsim_forces(h, int(what), _p(F, C.c_double)))
+    return F
+
+
+def npsim_positions_device(h, dev_ptr):
+    _check(lib().npsim_positions_device(h, C.c_void_p(int(dev_ptr))))
+
+
+def npsim_stats(h, r_max=10.0, n_bins=128, radial_bins=0, boxcount=True,
+                max_scales=MAX_SCALES):
+    cfg = npsim_stats_cfg_t(r_max, n_bins, radial_bins, int(boxcount), max_scales)
+    counts = np.zeros(max(n_bins, 1), np.int64)
+    g = np.zeros(max(n_bins, 1))
+    rc_ = np.zeros(max(radial_bins, 1), np.int64)
+    rcc = np.zeros(max(radial_bins, 1))
+    out = npsim_stats_t()
+    _check(lib().npsim_stats(h, C.byref(cfg), _p(counts, C.c_int64), _p(g, C.c_double),
+                             _p(rc_, C.c_int64) if radial_bins else None,
+                             _p(rcc, C.c_double) if radial_bins else None, C.byref(out)))
+    ns = out.n_scales
+    return {"R": out.R, "d_mean": out.d_mean, "Rg": out.Rg, "Df_rg": out.Df_rg,
+            "Df_box": out.Df_box, "center": np.array(out.center[:]),
+            "nbox": np.array(out.nbox[:ns], np.int64),
+            "rdf_counts": counts[:n_bins], "rdf_g": g[:n_bins],
+            "radial_counts": rc_[:radial_bins], "radial_c": rcc[:radial_bins]}
+
+
+def npsim_save(h, path):
+    _check(lib().npsim_save(h, os.fsencode(path)))
+
+
+def npsim_load(path, types=None, params=None, stream=None):
+    h = _h()
+    _check(lib().npsim_load(os.fsencode(path), types,
+                            None if params is None else C.byref(params),
+                            _stream_handle(stream), C.byref(h)))
+    return h
+
+
+def npsim_philox(seed, ctr, n_blocks):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    out = np.zeros((n_blocks, 4), np.uint32)
+    _check(lib().npsim_philox(C.c_uint64(seed), _p(c, C.c_uint32), n_blocks,
+                              _p(out, C.c_uint32)))
+    return out
+
+
+def npsim_normals(seed, step, n):
+    out = np.zeros((n, 3))
+    _check(lib().npsim_normals(C.c_uint64(seed), int(step), int(n), _p(out, C.c_double)))
+    return out
+
+
+def npsim_allpairs_config(h):
+    a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().npsim_allpairs_config(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return {"block": a.value, "i_per_thread": b.value, "j_tile": c.value, "grid": d.value}
+
+
+def npsim_launches_per_step(h):
+    a = C.c_int32()
+    _check(lib().npsim_launches_per_step(h, C.byref(a)))
+    return a.value
+
+
+def npsim_chunk_steps(h):
+    a = C.c_int32()
+    _check(lib().npsim_chunk_steps(h, C.byref(a)))
+    return a.value
+
+
+def npsim_profile(h, enable=True):
+    _check(lib().npsim_profile(h, int(bool(enable))))
+
+
+KERNEL_GROUPS = ("allpairs", "cell_build", "cell_lj", "integrate")
+
+
+def npsim_kernel_times(h):
+    ms = np.zeros(4)
+    k = C.c_int32()
+    _check(lib().npsim_kernel_times(h, _p(ms, C.c_double), C.byref(k)))
+    return dict(zip(KERNEL_GROUPS, ms.tolist())), k.value
+
+
+class Sim:
+    """Owning wrapper around one simulation handle."""
+
+    def __init__(self, scenario, x0, v0, types, stream=None):
+        self.n = int(np.asarray(x0).reshape(-1, 3).shape[0])
+        self.scenario = scenario
+        self._types = types_from(scenario.types)
+        self._params = params_from(scenario)
+        self.h = npsim_create(self._types, self._params, x0, v0, types, stream)
+
+    @classmethod
+    def _wrap(cls, h, n, scenario=None):
+        s = cls.__new__(cls)
+        s.h, s.n, s.scenario = h, n, scenario
+        return s
+
+    def step(self, n_steps=1):
+        npsim_step(self.h, n_steps)
+
+    def state(self):
+        return npsim_get_state(self.h, self.n)
+
+    def set_state(self, x, v=None, step=0):
+        npsim_set_state(self.h, x, v, step)
+
+    def forces(self, what=0):
+        return npsim_forces(self.h, self.n, what)
+
+    def stats(self, **kw):
+        return npsim_stats(self.h, **kw)
+
+    def save(self, path):
+        npsim_save(self.h, path)
+
+    def allpairs_config(self):
+        return npsim_allpairs_config(self.h)
+
+    def launches_per_step(self):
+        return npsim_launches_per_step(self.h)
+
+    def chunk_steps(self):
+        return npsim_chunk_steps(self.h)
+
+    def profile(self, enable=True):
+        npsim_profile(self.h, enable)
+
+    def kernel_times(self):
+        return npsim_kernel_times(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            npsim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

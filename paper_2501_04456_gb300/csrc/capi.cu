@@ -1,0 +1,1209 @@
+// capi.cu -- runtime behind the C ABI of include/npsim.h: owns the device
+// buffers of one simulation, picks the all-pairs launch shape with a timing
+// autotuner, captures chunks of steps into CUDA graphs, and implements state
+// I/O, force queries, statistics, checkpoints and the test hooks.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "npsim_internal.cuh"
+
+using namespace npsim;
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define NP_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(e_ == cudaErrorMemoryAllocation ? NPSIM_ERR_OOM : NPSIM_ERR_CUDA, \
+                           "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                           __FILE__, __LINE__);                                         \
+    } while (0)
+
+#define NP_REQUIRE(cond, ...)                                                           \
+    do {                                                                                \
+        if (!(cond))                                                                    \
+            return set_err(NPSIM_ERR_INVALID_ARG, __VA_ARGS__);                         \
+    } while (0)
+
+constexpr int kChunk = 16;      // steps per captured graph
+constexpr double kKf = 1.593;   // fractal prefactor, Sec. 3.1
+
+template <class T> cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+}
+
+template <class T> void dfree(T *&p)
+{
+    if (p)
+        cudaFree((void *)p);
+    p = nullptr;
+}
+
+int check_device(int *sms)
+{
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1)
+        return set_err(NPSIM_ERR_NO_DEVICE, "no CUDA device visible");
+    int dev = 0;
+    NP_CUDA(cudaGetDevice(&dev));
+    int major = 0, minor = 0;
+    NP_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    NP_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    if (!(major == 10 && minor == 3))
+        return set_err(NPSIM_ERR_NO_DEVICE,
+                       "device %d is sm_%d%d; this library is built for sm_103a only", dev,
+                       major, minor);
+    if (sms)
+        NP_CUDA(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+    return NPSIM_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune_cache; // (n, lj) -> config index
+
+void fill_streamk(StreamK &sk, int n, const ApConfig &c, int grid_target)
+{
+    sk.itile = c.block * c.ki;
+    sk.jtile = c.jt;
+    sk.n_it = (n + sk.itile - 1) / sk.itile;
+    sk.n_jt = (n + c.jt - 1) / c.jt;
+    sk.W = (long long)sk.n_it * sk.n_jt;
+    sk.grid = (int)std::min<long long>(std::max(grid_target, 1), sk.W);
+    sk.pad_ = 0;
+}
+
+size_t slots_doubles(const StreamK &sk)
+{
+    return (size_t)(sk.n_it + sk.grid) * 3 * (size_t)sk.itile;
+}
+
+} // namespace
+
+struct npsim_sim {
+    int n = 0, T = 0, sms = 0;
+    npsim_params_t P{};
+    npsim_type_t types[NPSIM_MAX_TYPES]{};
+    double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES]{};
+    bool has_ov = false;
+    std::vector<int32_t> h_type;
+    double d_mean = 1.0;
+    float charge_f[NPSIM_MAX_TYPES]{};
+
+    cudaStream_t user = nullptr, cap = nullptr;
+
+    double *x = nullptr, *v = nullptr, *F = nullptr, *F_tmp = nullptr;
+    float4 *xq = nullptr;
+    int *typ = nullptr;
+    double *slots = nullptr;
+    double *F_lj = nullptr;
+    PairTab *tab_full = nullptr, *tab_lj = nullptr;
+    long long *d_step = nullptr;
+    int *d_flags = nullptr;
+    unsigned *d_done = nullptr;
+
+    CellGrid grid{};
+    CellBufs cb{};
+    bool cell = false;
+
+    bool ap = false, ap_lj = false;
+    int ap_idx = 0;
+    StreamK sk{};
+    StepParams sp{};
+
+    std::map<int, cudaGraphExec_t> graphs;
+    int64_t step = 0;
+    int last_chunk = 0;
+
+    // per-kernel timing: events around each kernel group of each step of a chunk
+    bool profiling = false;
+    cudaEvent_t ev[kChunk][4][2]{};
+
+    // statistics (allocated on first use)
+    CellGrid sgrid{};
+    CellBufs scb{};
+    int s_cells_cap = 0;
+    unsigned long long *s_hist = nullptr, *s_rhist = nullptr;
+    int s_hist_cap = 0, s_rhist_cap = 0;
+    double *s_part = nullptr, *s_vec = nullptr;
+    unsigned long long *s_table = nullptr;
+    unsigned long long s_table_size = 0;
+    int *s_count = nullptr;
+
+    ~npsim_sim()
+    {
+        for (auto &g : graphs)
+            cudaGraphExecDestroy(g.second);
+        graphs.clear();
+        for (int j = 0; j < kChunk; ++j)
+            for (int k = 0; k < 4; ++k)
+                for (int e = 0; e < 2; ++e)
+                    if (ev[j][k][e])
+                        cudaEventDestroy(ev[j][k][e]);
+        dfree(x);
+        dfree(v);
+        dfree(F);
+        dfree(F_tmp);
+        dfree(xq);
+        dfree(typ);
+        dfree(slots);
+        dfree(F_lj);
+        dfree(tab_full);
+        dfree(tab_lj);
+        dfree(d_step);
+        dfree(d_flags);
+        dfree(d_done);
+        CellBufs *bufs[2] = {&cb, &scb};
+        for (CellBufs *b : bufs) {
+            dfree(b->key);
+            dfree(b->rank);
+            dfree(b->count);
+            dfree(b->start);
+            dfree(b->sorted);
+            dfree(b->sxq);
+            dfree(b->styp);
+            dfree(b->tile_sum);
+        }
+        dfree(s_hist);
+        dfree(s_rhist);
+        dfree(s_part);
+        dfree(s_vec);
+        dfree(s_table);
+        dfree(s_count);
+        if (cap)
+            cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+int alloc_cells(CellGrid &g, CellBufs &b, int n)
+{
+    NP_CUDA(dalloc(&b.key, n));
+    NP_CUDA(dalloc(&b.rank, n));
+    NP_CUDA(dalloc(&b.count, g.n_cells));
+    NP_CUDA(dalloc(&b.start, (size_t)g.n_cells + 1));
+    NP_CUDA(dalloc(&b.sorted, n));
+    NP_CUDA(dalloc(&b.sxq, n));
+    NP_CUDA(dalloc(&b.styp, n));
+    NP_CUDA(dalloc(&b.tile_sum, cell_scan_tiles(g.n_cells)));
+    return NPSIM_OK;
+}
+
+// Cell grid over [-L, L)^3 with edge >= h_min, at most max_cells cells.
+CellGrid make_grid(double L, double h_min, long long max_cells)
+{
+    CellGrid g{};
+    double h = h_min * (1.0 + 1e-5);
+    long long dim = (long long)std::ceil(2.0 * L / h);
+    if (dim < 1)
+        dim = 1;
+    while (dim * dim * dim > max_cells && dim > 1) {
+        h *= 1.1;
+        dim = (long long)std::ceil(2.0 * L / h);
+    }
+    g.dim = (int)dim;
+    g.n_cells = (int)(dim * dim * dim);
+    g.inv_h = (float)(1.0 / h);
+    g.L = (float)L;
+    return g;
+}
+
+// Queue the pair forces of the current positions and one integrator pass.
+// Kernel groups timed by npsim_kernel_times.
+enum { KG_ALLPAIRS = 0, KG_CELL_BUILD = 1, KG_CELL_LJ = 2, KG_INTEGRATE = 3 };
+
+int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext, double *Fout,
+                 cudaStream_t st, int prof_slot = -1)
+{
+    const bool lj_cell = want_lj && s->cell;
+    const bool ap_lj = want_lj && s->P.lj_mode == 1;
+    const bool ap_coul = want_coul && s->P.coulomb;
+    const bool ap = ap_lj || ap_coul;
+    const bool prof = prof_slot >= 0 && s->profiling;
+    auto mark = [&](int group, int edge) -> cudaError_t {
+        // inside stream capture a plain cudaEventRecord only orders the capture;
+        // the External flag makes it a real event-record node of the graph
+        return prof ? cudaEventRecordWithFlags(s->ev[prof_slot][group][edge], st,
+                                               cudaEventRecordExternal)
+                    : cudaSuccess;
+    };
+    if (lj_cell) {
+        NP_CUDA(mark(KG_CELL_BUILD, 0));
+        NP_CUDA(launch_cell_build(s->grid, s->xq, s->typ, s->n, s->cb, s->d_flags, st));
+        NP_CUDA(mark(KG_CELL_BUILD, 1));
+        NP_CUDA(mark(KG_CELL_LJ, 0));
+        NP_CUDA(launch_cell_lj(s->grid, s->cb, s->n, s->tab_full, s->F_lj, st));
+        NP_CUDA(mark(KG_CELL_LJ, 1));
+    }
+    if (ap) {
+        const PairTab *tab = ap_lj ? (ap_coul ? s->tab_full : s->tab_lj) : nullptr;
+        NP_CUDA(mark(KG_ALLPAIRS, 0));
+        NP_CUDA(launch_allpairs(s->ap_idx, ap_lj, s->sk, s->xq, s->typ, s->n, tab, s->slots,
+                                st));
+        NP_CUDA(mark(KG_ALLPAIRS, 1));
+    }
+    IntArgs a{};
+    a.x = s->x;
+    a.v = s->v;
+    a.F = Fout;
+    a.typ = s->typ;
+    a.xq = s->xq;
+    a.slots = ap ? s->slots : nullptr;
+    a.sk = s->sk;
+    a.F_lj = lj_cell ? s->F_lj : nullptr;
+    a.ext_on = ext ? 1 : 0;
+    a.field_slots = (ap && !ap_lj) ? 1 : 0;
+    a.step = s->d_step;
+    a.flags = s->d_flags;
+    a.done = s->d_done;
+    NP_CUDA(mark(KG_INTEGRATE, 0));
+    NP_CUDA(launch_integrate(mode, a, s->sp, st));
+    NP_CUDA(mark(KG_INTEGRATE, 1));
+    return NPSIM_OK;
+}
+
+int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
+{
+    IntArgs a{};
+    a.x = s->x;
+    a.v = s->v;
+    a.F = s->F;
+    a.typ = s->typ;
+    a.xq = s->xq;
+    a.sk = s->sk;
+    a.step = s->d_step;
+    a.flags = s->d_flags;
+    a.done = s->d_done;
+    NP_CUDA(launch_integrate(MODE_A, a, s->sp, st));
+    for (int j = 0; j < k; ++j) {
+        int rc = enqueue_pass(s, j + 1 < k ? MODE_BA : MODE_B, true, true, true, s->F, st, j);
+        if (rc)
+            return rc;
+    }
+    return NPSIM_OK;
+}
+
+int get_graph(npsim_sim *s, int k, cudaGraphExec_t *out)
+{
+    auto it = s->graphs.find(k);
+    if (it != s->graphs.end()) {
+        *out = it->second;
+        return NPSIM_OK;
+    }
+    NP_CUDA(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_chunk(s, k, s->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+    if (rc) {
+        if (g)
+            cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    s->graphs[k] = ex;
+    *out = ex;
+    return NPSIM_OK;
+}
+
+int read_flags(npsim_sim *s)
+{
+    int h = 0;
+    NP_CUDA(cudaMemcpyAsync(&h, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->user));
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    if (h) {
+        NP_CUDA(cudaMemsetAsync(s->d_flags, 0, sizeof(int), s->user));
+        if (h & FLAG_NONFINITE)
+            return set_err(NPSIM_ERR_NONFINITE, "a position became non-finite");
+        if (h & FLAG_TIMEOUT)
+            return set_err(NPSIM_ERR_TIMEOUT, "a bounded device wait expired");
+        return set_err(NPSIM_ERR_CUDA, "device error word 0x%x", h);
+    }
+    return NPSIM_OK;
+}
+
+// Pick the all-pairs launch shape: time each candidate on the current positions.
+int autotune(npsim_sim *s)
+{
+    const bool lj = s->ap_lj;
+    const std::pair<int, int> key(s->n, lj ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            s->ap_idx = it->second;
+            return NPSIM_OK;
+        }
+    }
+    const char *env = getenv("NPSIM_AUTOTUNE");
+    const int nc = ap_num_configs();
+    int best = 0;
+    if (env && env[0] == '0') {
+        best = 0;
+    } else if (env && env[0] >= '1' && env[0] <= '9' && env[1] == ':') {
+        best = std::min(nc - 1, atoi(env + 2)); // "1:<index>" forces a configuration
+    } else {
+        // scratch big enough for every candidate
+        size_t need = 0;
+        for (int c = 0; c < nc; ++c) {
+            const int occ = ap_occupancy(c, lj);
+            if (occ <= 0)
+                continue;
+            StreamK sk;
+            fill_streamk(sk, s->n, ap_config(c), occ * s->sms);
+            need = std::max(need, slots_doubles(sk));
+        }
+        double *tmp = nullptr;
+        NP_CUDA(dalloc(&tmp, need));
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        const PairTab *tab = lj ? s->tab_full : nullptr;
+        for (int c = 0; c < nc; ++c) {
+            const int occ = ap_occupancy(c, lj);
+            if (occ <= 0)
+                continue;
+            StreamK sk;
+            fill_streamk(sk, s->n, ap_config(c), occ * s->sms);
+            if (launch_allpairs(c, lj, sk, s->xq, s->typ, s->n, tab, tmp, s->user) != cudaSuccess)
+                continue;
+            const int reps = s->n > 100000 ? 2 : 5;
+            cudaEventRecord(e0, s->user);
+            for (int r = 0; r < reps; ++r)
+                launch_allpairs(c, lj, sk, s->xq, s->typ, s->n, tab, tmp, s->user);
+            cudaEventRecord(e1, s->user);
+            if (cudaEventSynchronize(e1) != cudaSuccess)
+                continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(tmp);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return set_err(NPSIM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    }
+    s->ap_idx = best;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = best;
+    return NPSIM_OK;
+}
+
+void to_soa(const double *aos, int n, std::vector<double> &soa)
+{
+    soa.resize(3 * (size_t)n);
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d)
+            soa[(size_t)d * n + i] = aos[3 * (size_t)i + d];
+}
+
+void to_aos(const std::vector<double> &soa, int n, double *aos)
+{
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d)
+            aos[3 * (size_t)i + d] = soa[(size_t)d * n + i];
+}
+
+int upload_state(npsim_sim *s, const double *x, const double *v, int64_t step)
+{
+    std::vector<double> buf;
+    to_soa(x, s->n, buf);
+    NP_CUDA(cudaMemcpyAsync(s->x, buf.data(), sizeof(double) * buf.size(),
+                            cudaMemcpyHostToDevice, s->user));
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    if (v) {
+        to_soa(v, s->n, buf);
+        NP_CUDA(cudaMemcpyAsync(s->v, buf.data(), sizeof(double) * buf.size(),
+                                cudaMemcpyHostToDevice, s->user));
+        NP_CUDA(cudaStreamSynchronize(s->user));
+    } else {
+        NP_CUDA(cudaMemsetAsync(s->v, 0, sizeof(double) * 3 * (size_t)s->n, s->user));
+    }
+    long long st = step;
+    NP_CUDA(cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice,
+                            s->user));
+    NP_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->user));
+    int rc = enqueue_pass(s, MODE_FORCES, true, true, true, s->F, s->user);
+    if (rc)
+        return rc;
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    s->step = step;
+    return read_flags(s);
+}
+
+int validate(const npsim_type_t *types, const npsim_params_t *p, int64_t n)
+{
+    NP_REQUIRE(types && p, "types and params are required");
+    NP_REQUIRE(n >= 1 && n <= (1ll << 29), "n = %lld out of range [1, 2^29]", (long long)n);
+    NP_REQUIRE(p->n_types >= 1 && p->n_types <= NPSIM_MAX_TYPES, "n_types = %d",
+               p->n_types);
+    NP_REQUIRE(p->dt > 0 && std::isfinite(p->dt), "dt must be positive");
+    NP_REQUIRE(p->kT >= 0, "kT must be >= 0");
+    NP_REQUIRE(p->rot_mode >= 0 && p->rot_mode <= 2, "rot_mode must be 0, 1 or 2");
+    NP_REQUIRE(p->lj_mode >= 0 && p->lj_mode <= 2, "lj_mode must be 0, 1 or 2");
+    NP_REQUIRE(p->integrator == 0 || p->integrator == 1, "integrator must be 0 or 1");
+    NP_REQUIRE(p->R0 > 0 || !p->wall, "R0 must be positive when the wall is on");
+    NP_REQUIRE(p->lj_mode == 0 || p->lj_cut > 0, "lj_cut must be positive");
+    for (int t = 0; t < p->n_types; ++t) {
+        NP_REQUIRE(types[t].sigma > 0 && types[t].mass > 0, "type %d: sigma, mass > 0", t);
+        NP_REQUIRE(types[t].gamma >= 0 && types[t].eps >= 0 && types[t].k_wall >= 0,
+                   "type %d: gamma, eps, k_wall >= 0", t);
+        NP_REQUIRE(p->integrator == 0 || types[t].gamma > 0,
+                   "type %d: the overdamped integrator needs gamma > 0", t);
+    }
+    return NPSIM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *npsim_last_error(void) { return g_err.c_str(); }
+
+int npsim_device_info(int *sm_count, int *clock_khz, int *cc_major, int *cc_minor)
+{
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1)
+        return set_err(NPSIM_ERR_NO_DEVICE, "no CUDA device visible");
+    int dev = 0;
+    NP_CUDA(cudaGetDevice(&dev));
+    if (sm_count)
+        NP_CUDA(cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev));
+    if (clock_khz)
+        NP_CUDA(cudaDeviceGetAttribute(clock_khz, cudaDevAttrClockRate, dev));
+    if (cc_major)
+        NP_CUDA(cudaDeviceGetAttribute(cc_major, cudaDevAttrComputeCapabilityMajor, dev));
+    if (cc_minor)
+        NP_CUDA(cudaDeviceGetAttribute(cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
+    return NPSIM_OK;
+}
+
+int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_t n,
+                 const double *x0, const double *v0, const int32_t *type, void *stream,
+                 npsim_sim_t *out)
+{
+    if (!out)
+        return set_err(NPSIM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = validate(types, params, n);
+    if (rc)
+        return rc;
+    NP_REQUIRE(x0 && type, "x0 and type are required");
+    int sms = 0;
+    rc = check_device(&sms);
+    if (rc)
+        return rc;
+    for (int64_t i = 0; i < n; ++i) {
+        NP_REQUIRE(type[i] >= 0 && type[i] < params->n_types, "type[%lld] = %d out of range",
+                   (long long)i, type[i]);
+        NP_REQUIRE(std::isfinite(x0[3 * i]) && std::isfinite(x0[3 * i + 1]) &&
+                       std::isfinite(x0[3 * i + 2]),
+                   "x0[%lld] is not finite", (long long)i);
+    }
+
+    npsim_sim *s = new npsim_sim();
+    s->n = (int)n;
+    s->T = params->n_types;
+    s->sms = sms;
+    s->P = *params;
+    for (int t = 0; t < s->T; ++t)
+        s->types[t] = types[t];
+    if (params->eps_override) {
+        s->has_ov = true;
+        for (int k = 0; k < s->T * s->T; ++k)
+            s->eps_ov[k] = params->eps_override[k];
+    }
+    s->P.eps_override = nullptr;
+    s->h_type.assign(type, type + n);
+    s->user = (cudaStream_t)stream;
+
+    auto bail = [&](int code) {
+        delete s;
+        return code;
+    };
+    cudaError_t ce = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (ce != cudaSuccess)
+        return bail(set_err(NPSIM_ERR_CUDA, "stream create: %s", cudaGetErrorString(ce)));
+
+    // per-type coefficients and pair tables (float64 on the host)
+    std::vector<long long> tcount(s->T, 0);
+    for (int64_t i = 0; i < n; ++i)
+        tcount[type[i]]++;
+    double dsum = 0.0;
+    for (int t = 0; t < s->T; ++t)
+        dsum += (double)tcount[t] * types[t].sigma;
+    s->d_mean = dsum / (double)n;
+
+    StepParams &sp = s->sp;
+    sp.n = s->n;
+    sp.n_types = s->T;
+    sp.rot_mode = params->rot_mode;
+    sp.wall = params->wall;
+    sp.integrator = params->integrator;
+    sp.seed = params->seed;
+    sp.dt = params->dt;
+    sp.R0 = params->R0;
+    sp.k_evap = params->k_evap;
+    sp.g = params->g;
+    sp.omega2 = params->omega * params->omega;
+    const double C = params->bjerrum;
+    for (int t = 0; t < s->T; ++t) {
+        const npsim_type_t &ty = types[t];
+        TypeCoef &c = sp.tc[t];
+        c.mass = ty.mass;
+        c.inv_mass = 1.0 / ty.mass;
+        c.half_sigma = 0.5 * ty.sigma;
+        c.k_wall = ty.k_wall;
+        c.c1 = std::exp(-ty.gamma * params->dt);
+        c.sd_o = std::sqrt((1.0 - c.c1 * c.c1) * params->kT / ty.mass);
+        c.mob = ty.gamma > 0 ? 1.0 / (ty.mass * ty.gamma) : 0.0;
+        c.sd_bd = std::sqrt(2.0 * params->kT * params->dt * c.mob);
+        c.charge_c = C * ty.charge;
+        s->charge_f[t] = (float)ty.charge;
+    }
+    PairTab tf{}, tl{};
+    double rc_max = 0.0;
+    for (int a = 0; a < s->T; ++a)
+        for (int b = 0; b < s->T; ++b) {
+            const double sig = 0.5 * (types[a].sigma + types[b].sigma);
+            const double eps = s->has_ov ? s->eps_ov[a * s->T + b]
+                                         : std::sqrt(types[a].eps * types[b].eps);
+            const double rc = params->lj_cut * sig;
+            rc_max = std::max(rc_max, rc);
+            const float4 e = make_float4((float)(sig * sig), (float)(24.0 * eps),
+                                         (float)(rc * rc),
+                                         (float)(params->coulomb ? C * types[a].charge *
+                                                                       types[b].charge
+                                                                 : 0.0));
+            tf.e[a * NPSIM_MAX_TYPES + b] = e;
+            tl.e[a * NPSIM_MAX_TYPES + b] = make_float4(e.x, e.y, e.z, 0.0f);
+        }
+
+#define BAIL_CUDA(call)                                                                 \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return bail(set_err(e_ == cudaErrorMemoryAllocation ? NPSIM_ERR_OOM         \
+                                                                 : NPSIM_ERR_CUDA,      \
+                                "%s failed: %s", #call, cudaGetErrorString(e_)));       \
+    } while (0)
+
+    const size_t n3 = 3 * (size_t)n;
+    BAIL_CUDA(dalloc(&s->x, n3));
+    BAIL_CUDA(dalloc(&s->v, n3));
+    BAIL_CUDA(dalloc(&s->F, n3));
+    BAIL_CUDA(dalloc(&s->F_tmp, n3));
+    BAIL_CUDA(dalloc(&s->xq, (size_t)n));
+    BAIL_CUDA(dalloc(&s->typ, (size_t)n));
+    BAIL_CUDA(dalloc(&s->tab_full, 1));
+    BAIL_CUDA(dalloc(&s->tab_lj, 1));
+    BAIL_CUDA(dalloc(&s->d_step, 1));
+    BAIL_CUDA(dalloc(&s->d_flags, 1));
+    BAIL_CUDA(dalloc(&s->d_done, 1));
+    BAIL_CUDA(cudaMemsetAsync(s->d_flags, 0, sizeof(int), s->user));
+    BAIL_CUDA(cudaMemsetAsync(s->d_done, 0, sizeof(unsigned), s->user));
+    BAIL_CUDA(cudaMemcpyAsync(s->tab_full, &tf, sizeof(PairTab), cudaMemcpyHostToDevice,
+                              s->user));
+    BAIL_CUDA(cudaMemcpyAsync(s->tab_lj, &tl, sizeof(PairTab), cudaMemcpyHostToDevice,
+                              s->user));
+    BAIL_CUDA(cudaMemcpyAsync(s->typ, type, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
+                              s->user));
+    BAIL_CUDA(cudaStreamSynchronize(s->user));
+
+    s->cell = params->lj_mode == 2;
+    if (s->cell) {
+        double L = params->R0;
+        for (int64_t i = 0; i < 3 * n; ++i)
+            L = std::max(L, std::fabs(x0[i]));
+        L += rc_max;
+        s->grid = make_grid(L, rc_max, std::max<long long>(4 * n + 4096, 1 << 16));
+        rc = alloc_cells(s->grid, s->cb, s->n);
+        if (rc)
+            return bail(rc);
+        BAIL_CUDA(dalloc(&s->F_lj, n3));
+    }
+    s->ap_lj = params->lj_mode == 1;
+    s->ap = params->coulomb || s->ap_lj;
+
+    // positions for the mirror (needed before tuning)
+    {
+        std::vector<double> buf;
+        to_soa(x0, s->n, buf);
+        BAIL_CUDA(cudaMemcpy(s->x, buf.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+        BAIL_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->user));
+    }
+    if (s->ap) {
+        rc = autotune(s);
+        if (rc)
+            return bail(rc);
+        const int occ = std::max(1, ap_occupancy(s->ap_idx, s->ap_lj));
+        fill_streamk(s->sk, s->n, ap_config(s->ap_idx), occ * s->sms);
+        BAIL_CUDA(dalloc(&s->slots, slots_doubles(s->sk)));
+    } else {
+        s->sk = StreamK{};
+        s->sk.itile = 1;
+        s->sk.n_jt = 1;
+        s->sk.grid = 1;
+        s->sk.W = 1;
+    }
+#undef BAIL_CUDA
+    rc = upload_state(s, x0, v0, 0);
+    if (rc)
+        return bail(rc);
+    *out = s;
+    return NPSIM_OK;
+}
+
+void npsim_destroy(npsim_sim_t sim)
+{
+    if (!sim)
+        return;
+    cudaStreamSynchronize(sim->user);
+    delete sim;
+}
+
+int npsim_step(npsim_sim_t s, int64_t n_steps)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    NP_REQUIRE(n_steps >= 0, "n_steps must be >= 0");
+    int64_t rem = n_steps;
+    while (rem > 0) {
+        const int k = (int)std::min<int64_t>(rem, kChunk);
+        cudaGraphExec_t ex = nullptr;
+        int rc = get_graph(s, k, &ex);
+        if (rc)
+            return rc;
+        NP_CUDA(cudaGraphLaunch(ex, s->user));
+        s->last_chunk = k;
+        rem -= k;
+        s->step += k;
+    }
+    return read_flags(s);
+}
+
+int npsim_get_state(npsim_sim_t s, double *x, double *v, double *F, int64_t *step)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    std::vector<double> buf(3 * (size_t)s->n);
+    double *src[3] = {s->x, s->v, s->F};
+    double *dst[3] = {x, v, F};
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k])
+            continue;
+        NP_CUDA(cudaMemcpy(buf.data(), src[k], sizeof(double) * buf.size(),
+                           cudaMemcpyDeviceToHost));
+        to_aos(buf, s->n, dst[k]);
+    }
+    if (step)
+        *step = s->step;
+    return NPSIM_OK;
+}
+
+int npsim_set_state(npsim_sim_t s, const double *x, const double *v, int64_t step)
+{
+    NP_REQUIRE(s && x, "sim and x are required");
+    NP_REQUIRE(step >= 0, "step must be >= 0");
+    return upload_state(s, x, v, step);
+}
+
+int npsim_forces(npsim_sim_t s, int what, double *F)
+{
+    NP_REQUIRE(s && F, "sim and F are required");
+    NP_REQUIRE(what >= 0 && what <= 3, "what must be 0..3");
+    const bool lj = what == 0 || what == 1 || what == 2;
+    const bool coul = what == 0 || what == 1 || what == 3;
+    int rc = enqueue_pass(s, MODE_FORCES, lj, coul, what == 0, s->F_tmp, s->user);
+    if (rc)
+        return rc;
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    std::vector<double> buf(3 * (size_t)s->n);
+    NP_CUDA(cudaMemcpy(buf.data(), s->F_tmp, sizeof(double) * buf.size(),
+                       cudaMemcpyDeviceToHost));
+    to_aos(buf, s->n, F);
+    return NPSIM_OK;
+}
+
+int npsim_positions_device(npsim_sim_t s, float *dev_xyzq)
+{
+    NP_REQUIRE(s && dev_xyzq, "sim and buffer are required");
+    NP_CUDA(cudaMemcpyAsync(dev_xyzq, s->xq, sizeof(float4) * (size_t)s->n,
+                            cudaMemcpyDeviceToDevice, s->user));
+    return NPSIM_OK;
+}
+
+int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_tile,
+                          int *grid)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    const ApConfig c = ap_config(s->ap_idx);
+    if (block)
+        *block = s->ap ? c.block : 0;
+    if (i_per_thread)
+        *i_per_thread = s->ap ? c.ki : 0;
+    if (j_tile)
+        *j_tile = s->ap ? c.jt : 0;
+    if (grid)
+        *grid = s->ap ? s->sk.grid : 0;
+    return NPSIM_OK;
+}
+
+int npsim_launches_per_step(npsim_sim_t s, int *launches)
+{
+    NP_REQUIRE(s && launches, "sim and launches are required");
+    *launches = 1 + (s->ap ? 1 : 0) + (s->cell ? cell_build_launches() + 1 : 0);
+    return NPSIM_OK;
+}
+
+int npsim_chunk_steps(npsim_sim_t s, int *chunk)
+{
+    NP_REQUIRE(s && chunk, "sim and chunk are required");
+    *chunk = kChunk;
+    return NPSIM_OK;
+}
+
+int npsim_profile(npsim_sim_t s, int enable)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    if (enable && !s->ev[0][0][0]) {
+        for (int j = 0; j < kChunk; ++j)
+            for (int k = 0; k < 4; ++k)
+                for (int e = 0; e < 2; ++e)
+                    NP_CUDA(cudaEventCreate(&s->ev[j][k][e]));
+    }
+    if ((enable != 0) != s->profiling) {
+        for (auto &g : s->graphs)
+            cudaGraphExecDestroy(g.second);
+        s->graphs.clear();
+        s->profiling = enable != 0;
+        s->last_chunk = 0;
+    }
+    return NPSIM_OK;
+}
+
+int npsim_kernel_times(npsim_sim_t s, double *ms, int *samples)
+{
+    NP_REQUIRE(s && ms, "sim and ms are required");
+    NP_REQUIRE(s->profiling, "profiling is not enabled (npsim_profile)");
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    const bool used[4] = {s->ap, s->cell, s->cell, true};
+    const int k = s->last_chunk;
+    for (int g = 0; g < 4; ++g) {
+        double tot = 0.0;
+        if (used[g])
+            for (int j = 0; j < k; ++j) {
+                float t = 0.f;
+                NP_CUDA(cudaEventElapsedTime(&t, s->ev[j][g][0], s->ev[j][g][1]));
+                tot += t;
+            }
+        ms[g] = (k > 0 && used[g]) ? tot / k : 0.0;
+    }
+    if (samples)
+        *samples = k;
+    return NPSIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Statistics
+
+int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
+                double *rdf_g, int64_t *radial_counts, double *radial_c, npsim_stats_t *out)
+{
+    NP_REQUIRE(s && cfg && out, "sim, cfg and out are required");
+    NP_REQUIRE(cfg->n_bins >= 0 && cfg->radial_bins >= 0, "bins must be >= 0");
+    NP_REQUIRE(cfg->n_bins == 0 || cfg->r_max > 0, "r_max must be positive");
+    NP_REQUIRE(cfg->max_scales >= 0 && cfg->max_scales <= NPSIM_MAX_SCALES,
+               "max_scales must be in [0, %d]", NPSIM_MAX_SCALES);
+    const int n = s->n;
+    cudaStream_t st = s->user;
+    memset(out, 0, sizeof(*out));
+    const double t = (double)s->step * s->P.dt;
+    const double R2 = s->P.R0 * s->P.R0 - s->P.k_evap * t;
+    const double R = R2 > 0 ? std::sqrt(R2) : 0.0;
+    out->R = R;
+    out->d_mean = s->d_mean;
+    const double pi = 3.14159265358979323846;
+
+    const int nblk = (n + 255) / 256;
+    if (!s->s_part) {
+        NP_CUDA(dalloc(&s->s_part, 3 * (size_t)nblk));
+        NP_CUDA(dalloc(&s->s_vec, 8));
+        NP_CUDA(dalloc(&s->s_count, 1));
+    }
+    std::vector<double> part(3 * (size_t)nblk);
+    // extent of the cloud (minimum and maximum corner)
+    NP_CUDA(launch_block_reduce(2, s->x, n, nullptr, s->s_part, st));
+    NP_CUDA(cudaMemcpyAsync(part.data(), s->s_part, sizeof(double) * part.size(),
+                            cudaMemcpyDeviceToHost, st));
+    NP_CUDA(cudaStreamSynchronize(st));
+    double o[3] = {INFINITY, INFINITY, INFINITY};
+    for (int b = 0; b < nblk; ++b)
+        for (int d = 0; d < 3; ++d)
+            o[d] = std::min(o[d], part[3 * b + d]);
+
+    if (cfg->n_bins > 0 && rdf_counts) {
+        // cell grid with edge >= r_max over the cloud (positions are needed in
+        // float32 only to choose candidates)
+        double L = R;
+        std::vector<double> xs(3 * (size_t)n);
+        NP_CUDA(cudaMemcpy(xs.data(), s->x, sizeof(double) * xs.size(), cudaMemcpyDeviceToHost));
+        for (double vv : xs)
+            L = std::max(L, std::fabs(vv));
+        L += cfg->r_max + 1.0;
+        CellGrid g = make_grid(L, cfg->r_max * (1.0 + 1e-4) + 1e-3, std::max<long long>(4 * n + 4096, 1 << 16));
+        if (g.n_cells > s->s_cells_cap) {
+            CellBufs &b = s->scb;
+            dfree(b.key); dfree(b.rank); dfree(b.count); dfree(b.start);
+            dfree(b.sorted); dfree(b.sxq); dfree(b.styp); dfree(b.tile_sum);
+            int rc = alloc_cells(g, s->scb, n);
+            if (rc)
+                return rc;
+            s->s_cells_cap = g.n_cells;
+        }
+        s->sgrid = g;
+        if (cfg->n_bins > s->s_hist_cap) {
+            dfree(s->s_hist);
+            NP_CUDA(dalloc(&s->s_hist, cfg->n_bins));
+            s->s_hist_cap = cfg->n_bins;
+        }
+        NP_CUDA(launch_cell_build(g, s->xq, s->typ, n, s->scb, s->d_flags, st));
+        NP_CUDA(launch_pair_hist(s->x, n, cfg->r_max, cfg->n_bins, g, s->scb, s->s_hist, st));
+        std::vector<unsigned long long> h(cfg->n_bins);
+        NP_CUDA(cudaMemcpyAsync(h.data(), s->s_hist, sizeof(unsigned long long) * h.size(),
+                                cudaMemcpyDeviceToHost, st));
+        NP_CUDA(cudaStreamSynchronize(st));
+        const double dr = cfg->r_max / (double)cfg->n_bins;
+        const double V = 4.0 / 3.0 * pi * R * R * R;
+        for (int b = 0; b < cfg->n_bins; ++b) {
+            rdf_counts[b] = (int64_t)h[b];
+            if (rdf_g) {
+                const double r0 = b * dr, r1 = (b + 1) * dr;
+                const double dV = 4.0 / 3.0 * pi * (r1 * r1 * r1 - r0 * r0 * r0);
+                rdf_g[b] = ((double)h[b] / (double)n) / ((double)(n - 1) * dV / V);
+            }
+        }
+    }
+    if (cfg->radial_bins > 0 && radial_counts) {
+        if (cfg->radial_bins > s->s_rhist_cap) {
+            dfree(s->s_rhist);
+            NP_CUDA(dalloc(&s->s_rhist, cfg->radial_bins));
+            s->s_rhist_cap = cfg->radial_bins;
+        }
+        NP_CUDA(launch_radial_hist(s->x, n, R, cfg->radial_bins, s->s_rhist, st));
+        std::vector<unsigned long long> h(cfg->radial_bins);
+        NP_CUDA(cudaMemcpyAsync(h.data(), s->s_rhist, sizeof(unsigned long long) * h.size(),
+                                cudaMemcpyDeviceToHost, st));
+        NP_CUDA(cudaStreamSynchronize(st));
+        const double dr = R / (double)cfg->radial_bins;
+        const double V = 4.0 / 3.0 * pi * R * R * R;
+        for (int b = 0; b < cfg->radial_bins; ++b) {
+            radial_counts[b] = (int64_t)h[b];
+            if (radial_c) {
+                const double r0 = b * dr, r1 = (b + 1) * dr;
+                const double dV = 4.0 / 3.0 * pi * (r1 * r1 * r1 - r0 * r0 * r0);
+                radial_c[b] = ((double)h[b] / (double)n) / (dV / V);
+            }
+        }
+    }
+    // centre of mass and radius of gyration (Eqs. r0, Rg), fractal equation (Eq. N)
+    NP_CUDA(launch_block_reduce(0, s->x, n, nullptr, s->s_part, st));
+    NP_CUDA(cudaMemcpyAsync(part.data(), s->s_part, sizeof(double) * part.size(),
+                            cudaMemcpyDeviceToHost, st));
+    NP_CUDA(cudaStreamSynchronize(st));
+    double c[3] = {0, 0, 0};
+    for (int b = 0; b < nblk; ++b)
+        for (int d = 0; d < 3; ++d)
+            c[d] += part[3 * b + d];
+    for (int d = 0; d < 3; ++d)
+        c[d] /= (double)n;
+    NP_CUDA(cudaMemcpyAsync(s->s_vec, c, sizeof(c), cudaMemcpyHostToDevice, st));
+    NP_CUDA(launch_block_reduce(1, s->x, n, s->s_vec, s->s_part, st));
+    NP_CUDA(cudaMemcpyAsync(part.data(), s->s_part, sizeof(double) * part.size(),
+                            cudaMemcpyDeviceToHost, st));
+    NP_CUDA(cudaStreamSynchronize(st));
+    double ss = 0.0;
+    for (int b = 0; b < nblk; ++b)
+        ss += part[3 * b];
+    const double Rg = std::sqrt(ss / (double)n);
+    out->Rg = Rg;
+    out->Df_rg = std::log((double)n / kKf) / std::log(2.0 * Rg / s->d_mean);
+    for (int d = 0; d < 3; ++d)
+        out->center[d] = c[d];
+
+    out->Df_box = NAN;
+    if (cfg->boxcount) {
+        unsigned long long tsz = 1;
+        while (tsz < 2ull * (unsigned long long)n)
+            tsz <<= 1;
+        if (tsz > s->s_table_size) {
+            dfree(s->s_table);
+            NP_CUDA(dalloc(&s->s_table, tsz));
+            s->s_table_size = tsz;
+        }
+        NP_CUDA(cudaMemcpyAsync(s->s_vec + 3, o, sizeof(o), cudaMemcpyHostToDevice, st));
+        int ns = 0;
+        while (ns < cfg->max_scales && s->d_mean * std::ldexp(1.0, ns) <= 2.0 * Rg)
+            ++ns;
+        for (int k = 0; k < ns; ++k) {
+            const double eps = s->d_mean * std::ldexp(1.0, k);
+            NP_CUDA(launch_boxcount(s->x, n, s->s_vec + 3, eps, s->s_table, tsz, s->s_count,
+                                    s->d_flags, st));
+            int cnt = 0;
+            NP_CUDA(cudaMemcpyAsync(&cnt, s->s_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+            NP_CUDA(cudaStreamSynchronize(st));
+            out->nbox[k] = cnt;
+        }
+        out->n_scales = ns;
+        if (ns - 1 >= 2) {
+            // least squares of ln N_box on ln eps over scales k >= 1
+            const int m = ns - 1;
+            double mx = 0, my = 0;
+            for (int k = 1; k < ns; ++k) {
+                mx += std::log(s->d_mean * std::ldexp(1.0, k));
+                my += std::log((double)out->nbox[k]);
+            }
+            mx /= m;
+            my /= m;
+            double sxy = 0, sxx = 0;
+            for (int k = 1; k < ns; ++k) {
+                const double ex = std::log(s->d_mean * std::ldexp(1.0, k)) - mx;
+                sxy += ex * (std::log((double)out->nbox[k]) - my);
+                sxx += ex * ex;
+            }
+            out->Df_box = -sxy / sxx;
+        }
+    }
+    return read_flags(s);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints
+
+namespace {
+const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version, n_types;
+    int64_t n, step;
+    int32_t rot_mode, lj_mode, coulomb, wall, integrator, has_ov;
+    uint64_t seed;
+    double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut;
+    double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    npsim_type_t types[NPSIM_MAX_TYPES];
+};
+} // namespace
+
+int npsim_save(npsim_sim_t s, const char *path)
+{
+    NP_REQUIRE(s && path, "sim and path are required");
+    CkptHeader h{};
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.n_types = s->T;
+    h.n = s->n;
+    h.step = s->step;
+    h.rot_mode = s->P.rot_mode;
+    h.lj_mode = s->P.lj_mode;
+    h.coulomb = s->P.coulomb;
+    h.wall = s->P.wall;
+    h.integrator = s->P.integrator;
+    h.has_ov = s->has_ov ? 1 : 0;
+    h.seed = s->P.seed;
+    h.dt = s->P.dt;
+    h.kT = s->P.kT;
+    h.R0 = s->P.R0;
+    h.k_evap = s->P.k_evap;
+    h.g = s->P.g;
+    h.omega = s->P.omega;
+    h.bjerrum = s->P.bjerrum;
+    h.lj_cut = s->P.lj_cut;
+    memcpy(h.eps_ov, s->eps_ov, sizeof(h.eps_ov));
+    memcpy(h.types, s->types, sizeof(h.types));
+    std::vector<double> x(3 * (size_t)s->n), v(3 * (size_t)s->n);
+    int rc = npsim_get_state(s, x.data(), v.data(), nullptr, nullptr);
+    if (rc)
+        return rc;
+    FILE *f = fopen(path, "wb");
+    if (!f)
+        return set_err(NPSIM_ERR_IO, "cannot open %s for writing", path);
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
+              fwrite(x.data(), sizeof(double), x.size(), f) == x.size() &&
+              fwrite(v.data(), sizeof(double), v.size(), f) == v.size() &&
+              fwrite(s->h_type.data(), sizeof(int32_t), s->h_type.size(), f) ==
+                  s->h_type.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok)
+        return set_err(NPSIM_ERR_IO, "short write to %s", path);
+    return NPSIM_OK;
+}
+
+int npsim_load(const char *path, const npsim_type_t *types_override,
+               const npsim_params_t *params_override, void *stream, npsim_sim_t *out)
+{
+    NP_REQUIRE(path && out, "path and out are required");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f)
+        return set_err(NPSIM_ERR_IO, "cannot open %s", path);
+    CkptHeader h{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
+        h.n < 1 || h.n > (1ll << 29) || h.n_types < 1 || h.n_types > NPSIM_MAX_TYPES) {
+        fclose(f);
+        return set_err(NPSIM_ERR_IO, "%s is not an npsim checkpoint", path);
+    }
+    std::vector<double> x(3 * (size_t)h.n), v(3 * (size_t)h.n);
+    std::vector<int32_t> ty((size_t)h.n);
+    bool ok = fread(x.data(), sizeof(double), x.size(), f) == x.size() &&
+              fread(v.data(), sizeof(double), v.size(), f) == v.size() &&
+              fread(ty.data(), sizeof(int32_t), ty.size(), f) == ty.size();
+    fclose(f);
+    if (!ok)
+        return set_err(NPSIM_ERR_IO, "%s is truncated", path);
+    npsim_params_t p{};
+    p.n_types = h.n_types;
+    p.rot_mode = h.rot_mode;
+    p.lj_mode = h.lj_mode;
+    p.coulomb = h.coulomb;
+    p.wall = h.wall;
+    p.integrator = h.integrator;
+    p.seed = h.seed;
+    p.dt = h.dt;
+    p.kT = h.kT;
+    p.R0 = h.R0;
+    p.k_evap = h.k_evap;
+    p.g = h.g;
+    p.omega = h.omega;
+    p.bjerrum = h.bjerrum;
+    p.lj_cut = h.lj_cut;
+    p.eps_override = h.has_ov ? h.eps_ov : nullptr;
+    if (params_override) {
+        p = *params_override;
+        NP_REQUIRE(p.n_types == h.n_types, "params_override changes n_types");
+    }
+    const npsim_type_t *tys = types_override ? types_override : h.types;
+    npsim_sim_t s = nullptr;
+    int rc = npsim_create(tys, &p, h.n, x.data(), v.data(), ty.data(), stream, &s);
+    if (rc)
+        return rc;
+    rc = npsim_set_state(s, x.data(), v.data(), h.step);
+    if (rc) {
+        npsim_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return NPSIM_OK;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// Test hooks
+
+namespace {
+
+__global__ void k_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                         long long n_blocks, uint32_t *out)
+{
+    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= n_blocks)
+        return;
+    const unsigned long long lo = (unsigned long long)c0 + (unsigned long long)b;
+    const U4 r = philox10(U4{(uint32_t)lo, c1 + (uint32_t)(lo >> 32), c2, c3}, (uint32_t)seed,
+                          (uint32_t)(seed >> 32));
+    out[4 * b + 0] = r.x;
+    out[4 * b + 1] = r.y;
+    out[4 * b + 2] = r.z;
+    out[4 * b + 3] = r.w;
+}
+
+__global__ void k_normals(uint64_t seed, long long step, int n, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    double a, b, c;
+    normals3(seed, (uint32_t)i, step, 0u, a, b, c);
+    out[3 * i + 0] = a;
+    out[3 * i + 1] = b;
+    out[3 * i + 2] = c;
+}
+
+} // namespace
+
+extern "C" int npsim_philox(uint64_t seed, const uint32_t ctr[4], int64_t n_blocks,
+                            uint32_t *out)
+{
+    NP_REQUIRE(ctr && out, "ctr and out are required");
+    NP_REQUIRE(n_blocks >= 0 && n_blocks <= (1ll << 28), "n_blocks out of range");
+    int rc = check_device(nullptr);
+    if (rc)
+        return rc;
+    if (n_blocks == 0)
+        return NPSIM_OK;
+    uint32_t *d = nullptr;
+    NP_CUDA(dalloc(&d, 4 * (size_t)n_blocks));
+    k_philox<<<(unsigned)((n_blocks + 255) / 256), 256>>>(seed, ctr[0], ctr[1], ctr[2], ctr[3],
+                                                          n_blocks, d);
+    cudaError_t e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * (size_t)n_blocks,
+                               cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "philox: %s", cudaGetErrorString(e));
+    return NPSIM_OK;
+}
+
+extern "C" int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out)
+{
+    NP_REQUIRE(out, "out is required");
+    NP_REQUIRE(n >= 0 && n <= (1ll << 29), "n out of range");
+    int rc = check_device(nullptr);
+    if (rc)
+        return rc;
+    if (n == 0)
+        return NPSIM_OK;
+    double *d = nullptr;
+    NP_CUDA(dalloc(&d, 3 * (size_t)n));
+    k_normals<<<(unsigned)((n + 255) / 256), 256>>>(seed, step, (int)n, d);
+    cudaError_t e = cudaMemcpy(out, d, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "normals: %s", cudaGetErrorString(e));
+    return NPSIM_OK;
+}

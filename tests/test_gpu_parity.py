@@ -1,0 +1,344 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Forces are compared at float32-representable positions (the positions the
+float32 pair kernels see exactly), with the metric
+max_i |dF_i| / max(|F_i|, rms_j |F_j|) <= 1e-5.  Trajectories are compared after
+100 steps to 1e-4 sigma.  Philox words are compared bit for bit; integer
+histogram counts exactly.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from gpu_helpers import (FORCE_TOL, TRAJ_TOL, cutoff_ambiguous, force_error, library,
+                         small, with_)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    return library()
+
+
+# --------------------------------------------------------------------------
+# Philox and normals
+
+
+def test_philox_bit_exact(P):
+    for seed in (0, 1, 0x123456789, 0xFFFFFFFFFFFFFFFF):
+        for ctr in ([0, 0, 0, 0], [0xFFFFFF00, 7, 3, 1], [5, 0xFFFFFFFF, 0, 2]):
+            g = P.npsim_philox(seed, ctr, 4096)
+            o = oracle.philox_blocks(seed, ctr, 4096)
+            assert np.array_equal(g, o), (seed, ctr)
+
+
+def test_normals_match_oracle(P):
+    for seed, step in ((3, 0), (0xABCDEF, 123456789012)):
+        g = P.npsim_normals(seed, step, 50000)
+        o = oracle.normals(seed, step, 0, 50000)
+        d = np.abs(g - o)
+        # float32 Box-Muller: ~1e-7 relative; the worst case is at tiny radii
+        assert np.median(d) < 1e-6
+        assert d.max() < 2e-4
+
+
+# --------------------------------------------------------------------------
+# Forces
+
+
+def _scen(name):
+    if name == "lj1000_cell":
+        return wl.config1()
+    if name == "coul_lj_allpairs_3001":
+        return small(wl.config2(), 3001)
+    if name == "coul_allpairs_lj_cell_5003":
+        return small(wl.config3(), 5003)
+    if name == "lj_allpairs_only_1537":
+        return with_(small(wl.config2(), 1537), coulomb=False)
+    if name == "coul_only_2049":
+        return with_(small(wl.config3(), 2049), lj_mode=0)
+    if name == "eps_matrix_1200":
+        sc = small(wl.config2(), 1200)
+        return with_(sc, eps_override=np.array([[0.155, 1.26], [1.26, 0.155]]) * 4)
+    raise KeyError(name)
+
+
+SCENARIOS = ["lj1000_cell", "coul_lj_allpairs_3001", "coul_allpairs_lj_cell_5003",
+             "lj_allpairs_only_1537", "coul_only_2049", "eps_matrix_1200"]
+
+
+def _oracle_pair(sc, x, types, lj=True, coul=True, sel=None):
+    sig = [t.sigma for t in sc.types]
+    eps = [t.eps for t in sc.types]
+    q = [t.charge for t in sc.types]
+    return oracle.pair_forces(x, types, sig, eps, q, sc.bjerrum, lj_cut=sc.lj_cut,
+                              lj=lj and sc.lj_mode != 0, coulomb=coul and sc.coulomb,
+                              eps_override=sc.eps_override, sel=sel)
+
+
+@pytest.mark.parametrize("name", SCENARIOS)
+def test_forces_parity(P, name):
+    sc = _scen(name)
+    types, x, v = wl.initial_state(sc, fp32_positions=True)
+    amb = cutoff_ambiguous(x, types, sc)
+    assert amb.sum() <= max(2, len(x) // 500)
+    keep = ~amb
+    with P.Sim(sc, x, v, types) as sim:
+        F_pair = sim.forces(1)
+        F_lj = sim.forces(2)
+        F_coul = sim.forces(3)
+        F_tot = sim.forces(0)
+        _, _, F_state, _ = sim.state()
+    o_pair = _oracle_pair(sc, x, types)
+    o_lj = _oracle_pair(sc, x, types, coul=False)
+    o_coul = _oracle_pair(sc, x, types, lj=False)
+    o_tot = oracle.total_forces(sc, x, types, 0.0)
+    for got, ref, what in ((F_pair, o_pair, "pair"), (F_lj, o_lj, "lj"),
+                           (F_coul, o_coul, "coulomb"), (F_tot, o_tot, "total"),
+                           (F_state, o_tot, "state")):
+        if not np.any(ref):
+            assert np.all(got == 0), what
+            continue
+        err = force_error(got, ref)[keep]
+        assert err.max() <= FORCE_TOL, (what, float(err.max()), int(err.argmax()))
+    # Newton's third law on the GPU pair forces
+    assert np.abs(F_pair.sum(0)).max() <= 1e-6 * np.abs(F_pair).sum()
+
+
+def test_forces_full_size_sampled(P):
+    """The 250000-NP scenario at full size, in the launch configuration the benchmark
+    times: sampled rows against the oracle row by row."""
+    sc = wl.config3()
+    types, x, v = wl.initial_state(sc, fp32_positions=True)
+    with P.Sim(sc, x, v, types) as sim:
+        F = sim.forces(0)
+        cfg = sim.allpairs_config()
+    rng = np.random.default_rng(0)
+    it = cfg["block"] * cfg["i_per_thread"]
+    sel = np.unique(np.concatenate([[0, 1, sc.n - 1, sc.n - 2, it - 1, it, it + 1],
+                                    rng.choice(sc.n, 41, replace=False)]))
+    o = _oracle_pair(sc, x, types, sel=sel) + oracle.external_forces(sc, x[sel], types[sel], 0.0)
+    amb = cutoff_ambiguous(x, types, sc)[sel]
+    rms = np.sqrt((F ** 2).sum(1).mean())
+    err = np.linalg.norm(F[sel] - o, axis=1) / np.maximum(np.linalg.norm(o, axis=1), rms)
+    assert err[~amb].max() <= FORCE_TOL, float(err.max())
+    # zero net internal force over all rows
+    Fp = None
+    with P.Sim(sc, x, v, types) as sim:
+        Fp = sim.forces(1)
+    assert np.abs(Fp.sum(0)).max() <= 1e-6 * np.abs(Fp).sum()
+
+
+# --------------------------------------------------------------------------
+# Trajectories
+
+
+TRAJ = ["lj1000_cell", "coul_lj_allpairs_2048", "coul_allpairs_lj_cell_4096",
+        "overdamped_lj_1000"]
+
+
+def _traj_scen(name):
+    if name == "lj1000_cell":
+        return wl.config1()
+    if name == "coul_lj_allpairs_2048":
+        return small(wl.config2(), 2048)
+    if name == "coul_allpairs_lj_cell_4096":
+        return small(wl.config3(), 4096)
+    if name == "overdamped_lj_1000":
+        return with_(wl.config1(), integrator=1)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", TRAJ)
+def test_trajectory_parity_100_steps(P, name):
+    sc = _traj_scen(name)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as sim:
+        sim.step(100)
+        xg, vg, Fg, st = sim.state()
+    assert st == 100
+    xo, vo, Fo = oracle.run(sc, x, v, types, 0, 100)
+    dx = np.abs(xg - xo).max()
+    assert dx <= TRAJ_TOL, dx
+    if sc.integrator == 0:
+        assert np.abs(vg - vo).max() <= 1e-2
+    assert force_error(Fg, Fo).max() <= 1e-3
+
+
+# --------------------------------------------------------------------------
+# Determinism, chunking and checkpoints
+
+
+def test_chunking_and_runs_are_bit_identical(P):
+    sc = small(wl.config3(), 3000)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as a:
+        a.step(37)
+        xa, va, Fa, _ = a.state()
+    with P.Sim(sc, x, v, types) as b:
+        for k in (5, 16, 1, 15):
+            b.step(k)
+        xb, vb, Fb, st = b.state()
+    assert st == 37
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(Fa, Fb)
+
+
+def test_checkpoint_resume_is_bit_exact(P, tmp_path):
+    sc = small(wl.config2(), 1500)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as a:
+        a.step(40)
+        xa, va, _, _ = a.state()
+    path = str(tmp_path / "ck.bin")
+    with P.Sim(sc, x, v, types) as b:
+        b.step(20)
+        b.save(path)
+    h = P.npsim_load(path)
+    c = P.Sim._wrap(h, sc.n, sc)
+    try:
+        _, _, _, st = c.state()
+        assert st == 20
+        c.step(20)
+        xc, vc, _, st = c.state()
+        assert st == 40
+    finally:
+        c.close()
+    assert np.array_equal(xa, xc) and np.array_equal(va, vc)
+
+
+# --------------------------------------------------------------------------
+# Statistics
+
+
+def test_stats_parity(P):
+    sc = small(wl.config3(), 6000)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as sim:
+        sim.step(10)
+        xg, _, _, _ = sim.state()
+        st = sim.stats(r_max=10.0, n_bins=128, radial_bins=32, boxcount=True)
+    R = oracle.radius(sc.R0, sc.k_evap, 10 * sc.dt)
+    assert st["R"] == pytest.approx(R, rel=1e-14)
+    c_o = oracle.pair_hist(xg, 10.0, 128)
+    assert np.array_equal(st["rdf_counts"], c_o)
+    _, g_o = oracle.rdf(xg, 10.0, 128, R)
+    assert np.allclose(st["rdf_g"], g_o, rtol=1e-12, atol=0)
+    rc_o, C_o = oracle.radial_concentration(xg, R, 32, R)
+    assert np.array_equal(st["radial_counts"], rc_o)
+    assert np.allclose(st["radial_c"], C_o, rtol=1e-12)
+    Rg, Df, r0 = oracle.rg(xg, st["d_mean"])
+    assert st["Rg"] == pytest.approx(Rg, rel=1e-12)
+    assert st["Df_rg"] == pytest.approx(Df, rel=1e-10)
+    assert np.allclose(st["center"], r0, rtol=1e-10, atol=1e-12)
+    Dfb, nb = oracle.boxcount_df(xg, st["d_mean"], Rg)
+    assert np.array_equal(st["nbox"], nb)
+    assert st["Df_box"] == pytest.approx(Dfb, rel=1e-10)
+
+
+def test_stats_boxcount_lattice_on_gpu(P):
+    """A filled cubic lattice gives N_box = (L/2^k)^3 and D_f = 3 on the GPU path."""
+    L = 32
+    g = (np.arange(L) - L / 2 + 0.5) * 1.0
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    xl = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    t = wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=0.0)
+    sc = wl.Scenario(name="lattice", types=[t], n=len(xl), R0=100.0, wall=False,
+                     lj_mode=0, coulomb=False)
+    with P.Sim(sc, xl, None, np.zeros(len(xl), np.int32)) as sim:
+        st = sim.stats(r_max=3.0, n_bins=30, boxcount=True)
+    # 2 R_g = 2 sqrt(3 (L^2 - 1)/12) = 31.98: scales eps = 1 .. 16
+    assert len(st["nbox"]) == 5
+    for k in range(5):
+        assert st["nbox"][k] == (L // 2 ** k) ** 3
+    assert st["Df_box"] == pytest.approx(3.0, abs=0.02)
+
+
+# --------------------------------------------------------------------------
+# Edge cases
+
+
+def test_single_and_two_particles(P):
+    t = wl.TypeSpec(sigma=1.0, eps=1.0, mass=2.0, charge=1.0, gamma=3.0, k_wall=40.0)
+    sc = wl.Scenario(name="two", types=[t], n=2, seed=0, dt=0.01, kT=0.0, R0=2.0,
+                     k_evap=1.0, bjerrum=0.5, coulomb=True, lj_mode=1, lj_cut=2.5)
+    x0 = np.array([[0.0, 0.0, 0.9], [0.0, 0.0, -0.4]])
+    v0 = np.array([[0.1, 0.0, 0.0], [0.0, 0.0, 0.2]])
+    ty = np.zeros(2, np.int32)
+    with P.Sim(sc, x0, v0, ty) as sim:
+        assert force_error(sim.forces(0), oracle.total_forces(sc, x0, ty, 0.0)).max() < FORCE_TOL
+        sim.step(3)
+        xg, vg, _, _ = sim.state()
+    xo, vo, _ = oracle.run(sc, x0, v0, ty, 0, 3)
+    assert np.abs(xg - xo).max() < 1e-9
+    sc1 = with_(sc, n=1)
+    with P.Sim(sc1, x0[:1], v0[:1], ty[:1]) as sim:
+        F = sim.forces(0)
+        assert np.allclose(F, oracle.external_forces(sc1, x0[:1], ty[:1], 0.0), rtol=1e-14)
+        assert np.all(sim.forces(1) == 0)
+        sim.step(5)
+
+
+@pytest.mark.parametrize("n", [511, 512, 513, 2047])
+def test_ragged_sizes(P, n):
+    sc = small(wl.config2(), n)
+    types, x, v = wl.initial_state(sc, fp32_positions=True)
+    with P.Sim(sc, x, v, types) as sim:
+        F = sim.forces(1)
+    amb = cutoff_ambiguous(x, types, sc)
+    err = force_error(F, _oracle_pair(sc, x, types))[~amb]
+    assert err.max() <= FORCE_TOL
+
+
+def test_invalid_arguments_are_errors(P):
+    sc = wl.config1()
+    types, x, v = wl.initial_state(sc)
+    with pytest.raises(P.NpsimError) as e:
+        P.Sim(sc, x[:0], None, types[:0])
+    assert e.value.code == -1
+    bad = types.copy()
+    bad[3] = 7
+    with pytest.raises(P.NpsimError) as e:
+        P.Sim(sc, x, v, bad)
+    assert e.value.code == -1
+    with pytest.raises(P.NpsimError):
+        P.Sim(with_(sc, dt=0.0), x, v, types)
+
+
+def test_free_particles_msd_and_equipartition_gpu(P):
+    """Same closed forms as the oracle pins, on the GPU integrator."""
+    n, steps = 20000, 300
+    t = wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.5, charge=0.0, gamma=2.0, k_wall=0.0)
+    sc = wl.Scenario(name="free", types=[t], n=n, seed=21, dt=2e-3, kT=1.3, R0=1e9,
+                     wall=False, lj_mode=0, coulomb=False)
+    ty = np.zeros(n, np.int32)
+    x0 = np.zeros((n, 3))
+    v0 = wl.maxwell_velocities(sc, ty, seed=1)
+    with P.Sim(sc, x0, v0, ty) as sim:
+        sim.step(steps)
+        x, v, _, _ = sim.state()
+    T = steps * sc.dt
+    D = 1.3 / (1.5 * 2.0)
+    msd_th = 6 * D * (T - (1 - math.exp(-2.0 * T)) / 2.0)
+    d2 = (x ** 2).sum(1)
+    assert abs(d2.mean() - msd_th) < 4 * d2.std() / math.sqrt(n) + 0.01 * msd_th
+    ke = 1.5 * (v ** 2).sum(1) / 3
+    assert abs(ke.mean() - 1.3) < 4 * ke.std() / math.sqrt(n)
+    xo, vo, _ = oracle.run(sc, x0, v0, ty, 0, steps)
+    assert np.abs(x - xo).max() < 1e-6
+
+
+def test_nonfinite_position_is_reported(P):
+    sc = small(wl.config2(), 600)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as sim:
+        xb = x.copy()
+        xb[5] = [1e300, 0.0, 0.0]  # float32 mirror overflows -> non-finite forces
+        sim.set_state(xb, v, 0)
+        with pytest.raises(P.NpsimError) as e:
+            sim.step(2)
+        assert e.value.code == -3
