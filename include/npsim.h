@@ -182,10 +182,16 @@ int npsim_philox(uint64_t seed, const uint32_t ctr[4], int64_t n_blocks, uint32_
  * (Box-Muller on Philox counter (i, step, 0)), n x 3 into host out. */
 int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out);
 
-/* Kernel-launch configuration of the all-pairs kernel chosen by the autotuner
- * (block threads, i per thread, j-tile length, grid size). */
+/* Launch shape of the all-pairs kernel chosen by the autotuner: threads per
+ * CTA, particles i per thread, j-tile length, CTAs, the index of the shape in
+ * the autotuner's table, and 1 if it is the packed float32x2 Coulomb kernel.
+ * Any pointer may be NULL.  The environment variable NPSIM_AUTOTUNE=1:<index>
+ * forces a shape at npsim_create (NPSIM_AUTOTUNE=0: the first shape). */
 int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j_tile,
-                          int *grid);
+                          int *grid, int *index, int *packed);
+
+/* Number of launch shapes in the autotuner's table. */
+int npsim_allpairs_num_configs(int *count);
 
 /* Kernel launches per step in a long run (pair kernels + cell-list kernels + one
  * integrator pass); npsim_step adds one integrator launch per graph chunk. */

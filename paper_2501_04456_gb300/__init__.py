@@ -98,7 +98,8 @@ def lib():
                                      C.POINTER(npsim_params_t), C.c_void_p, C.POINTER(_h)]
             L.npsim_philox.argtypes = [C.c_uint64, _u32, C.c_int64, _u32]
             L.npsim_normals.argtypes = [C.c_uint64, C.c_int64, C.c_int64, _d]
-            L.npsim_allpairs_config.argtypes = [_h, _i32, _i32, _i32, _i32]
+            L.npsim_allpairs_config.argtypes = [_h, _i32, _i32, _i32, _i32, _i32, _i32]
+            L.npsim_allpairs_num_configs.argtypes = [_i32]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
             L.npsim_chunk_steps.argtypes = [_h, _i32]
             L.npsim_profile.argtypes = [_h, C.c_int]
@@ -277,9 +278,16 @@ def npsim_normals(seed, step, n):
 
 
 def npsim_allpairs_config(h):
-    a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-    _check(lib().npsim_allpairs_config(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
-    return {"block": a.value, "i_per_thread": b.value, "j_tile": c.value, "grid": d.value}
+    v = [C.c_int32() for _ in range(6)]
+    _check(lib().npsim_allpairs_config(h, *[C.byref(x) for x in v]))
+    keys = ("block", "i_per_thread", "j_tile", "grid", "index", "packed")
+    return {k: x.value for k, x in zip(keys, v)}
+
+
+def npsim_allpairs_num_configs():
+    a = C.c_int32()
+    _check(lib().npsim_allpairs_num_configs(C.byref(a)))
+    return a.value
 
 
 def npsim_launches_per_step(h):

@@ -355,6 +355,21 @@ int read_flags(npsim_sim *s)
 int autotune(npsim_sim *s)
 {
     const bool lj = s->ap_lj;
+    const int nc = ap_num_configs();
+    // NPSIM_AUTOTUNE=0 takes the first shape; NPSIM_AUTOTUNE=1:<index> forces one
+    // (ignored if that shape cannot run this sum); neither touches the cache.
+    const char *env = getenv("NPSIM_AUTOTUNE");
+    if (env && env[0] == '0') {
+        s->ap_idx = 0;
+        return NPSIM_OK;
+    }
+    if (env && env[0] == '1' && env[1] == ':') {
+        const int idx = atoi(env + 2);
+        if (idx >= 0 && idx < nc && ap_occupancy(idx, lj) > 0) {
+            s->ap_idx = idx;
+            return NPSIM_OK;
+        }
+    }
     const std::pair<int, int> key(s->n, lj ? 1 : 0);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -364,14 +379,8 @@ int autotune(npsim_sim *s)
             return NPSIM_OK;
         }
     }
-    const char *env = getenv("NPSIM_AUTOTUNE");
-    const int nc = ap_num_configs();
     int best = 0;
-    if (env && env[0] == '0') {
-        best = 0;
-    } else if (env && env[0] >= '1' && env[0] <= '9' && env[1] == ':') {
-        best = std::min(nc - 1, atoi(env + 2)); // "1:<index>" forces a configuration
-    } else {
+    {
         // scratch big enough for every candidate
         size_t need = 0;
         for (int c = 0; c < nc; ++c) {
@@ -768,7 +777,7 @@ int npsim_positions_device(npsim_sim_t s, float *dev_xyzq)
 }
 
 int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_tile,
-                          int *grid)
+                          int *grid, int *index, int *packed)
 {
     NP_REQUIRE(s, "sim is NULL");
     const ApConfig c = ap_config(s->ap_idx);
@@ -780,6 +789,17 @@ int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_t
         *j_tile = s->ap ? c.jt : 0;
     if (grid)
         *grid = s->ap ? s->sk.grid : 0;
+    if (index)
+        *index = s->ap ? s->ap_idx : -1;
+    if (packed)
+        *packed = (s->ap && ap_packed(s->ap_idx)) ? 1 : 0;
+    return NPSIM_OK;
+}
+
+int npsim_allpairs_num_configs(int *count)
+{
+    NP_REQUIRE(count, "count is NULL");
+    *count = ap_num_configs();
     return NPSIM_OK;
 }
 

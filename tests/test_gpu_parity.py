@@ -110,6 +110,33 @@ def test_forces_parity(P, name):
     assert np.abs(F_pair.sum(0)).max() <= 1e-6 * np.abs(F_pair).sum()
 
 
+def test_every_launch_shape(P, monkeypatch):
+    """Each all-pairs launch shape of the autotuner's table (scalar and packed
+    float32x2), forced in turn, gives the oracle's forces on a ragged size."""
+    sc_c = with_(small(wl.config3(), 1531), lj_mode=0)          # Coulomb only
+    sc_l = with_(small(wl.config2(), 1531), coulomb=True)        # Coulomb + LJ
+    st_c = wl.initial_state(sc_c, fp32_positions=True)
+    st_l = wl.initial_state(sc_l, fp32_positions=True)
+    ref_c = _oracle_pair(sc_c, st_c[1], st_c[0])
+    ref_l = _oracle_pair(sc_l, st_l[1], st_l[0])
+    amb_l = cutoff_ambiguous(st_l[1], st_l[0], sc_l)
+    seen_packed = False
+    for idx in range(P.npsim_allpairs_num_configs()):
+        monkeypatch.setenv("NPSIM_AUTOTUNE", f"1:{idx}")
+        with P.Sim(sc_c, st_c[1], st_c[2], st_c[0]) as sim:
+            cfg = sim.allpairs_config()
+            assert cfg["index"] == idx
+            seen_packed |= bool(cfg["packed"])
+            err = force_error(sim.forces(1), ref_c)
+            assert err.max() <= FORCE_TOL, (idx, float(err.max()))
+        with P.Sim(sc_l, st_l[1], st_l[2], st_l[0]) as sim:
+            cfg = sim.allpairs_config()
+            assert not cfg["packed"]  # the LJ sum runs on the scalar kernel
+            err = force_error(sim.forces(1), ref_l)[~amb_l]
+            assert err.max() <= FORCE_TOL, (idx, float(err.max()))
+    assert seen_packed
+
+
 def test_forces_full_size_sampled(P):
     """The 250000-NP scenario at full size, in the launch configuration the benchmark
     times: sampled rows against the oracle row by row."""
