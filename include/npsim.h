@@ -193,6 +193,32 @@ int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j
 /* Number of launch shapes in the autotuner's table. */
 int npsim_allpairs_num_configs(int *count);
 
+/*
+ * All-pairs Coulomb forces without any device allocation.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc when
+ * they need forces -- code inside an open CUDA stream capture (where allocation
+ * is not allowed), frameworks whose own pool owns all device memory, or
+ * real-time loops that cannot risk an allocation's latency or failure.
+ *
+ * Computes F_i = C q_i sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3, the same sum
+ * as npsim_forces(sim, 3, ...), from dev_xyzq (device, n float4 records
+ * (x, y, z, q) in float32, e.g. filled by npsim_positions_device) into dev_F
+ * (device, n x 3 float64, row-major).  Both buffers are the caller's.  C is
+ * `bjerrum`.  Work is queued on `stream`; the call does not synchronise.
+ *
+ * Scratch: the partial sums live in one fixed __device__ array of 3.75 MiB that
+ * every GPU loading the library holds until the process exits.  n must be in
+ * [1, 32768]; larger n is rejected with NPSIM_ERR_INVALID_ARG.  The first call
+ * on a device looks up the array's device address for that device (set-up,
+ * once per device, with that device current); make that first call before any
+ * stream capture.  Every call on a device shares the array: calls that overlap
+ * on the GPU (different streams without ordering) race and give wrong forces.
+ * Each call writes every partial it reads, so nothing carries over from the
+ * previous call.  Allocates nothing (no cudaMalloc/cudaFree).
+ */
+int npsim_coulomb_forces_noalloc(const float *dev_xyzq, int64_t n, double bjerrum,
+                                 double *dev_F, void *stream);
+
 /* Kernel launches per step in a long run (pair kernels + cell-list kernels + one
  * integrator pass); npsim_step adds one integrator launch per graph chunk. */
 int npsim_launches_per_step(npsim_sim_t sim, int *launches);

@@ -100,6 +100,8 @@ def lib():
             L.npsim_normals.argtypes = [C.c_uint64, C.c_int64, C.c_int64, _d]
             L.npsim_allpairs_config.argtypes = [_h, _i32, _i32, _i32, _i32, _i32, _i32]
             L.npsim_allpairs_num_configs.argtypes = [_i32]
+            L.npsim_coulomb_forces_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_double,
+                                                       C.c_void_p, C.c_void_p]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
             L.npsim_chunk_steps.argtypes = [_h, _i32]
             L.npsim_profile.argtypes = [_h, C.c_int]
@@ -288,6 +290,14 @@ def npsim_allpairs_num_configs():
     a = C.c_int32()
     _check(lib().npsim_allpairs_num_configs(C.byref(a)))
     return a.value
+
+
+def npsim_coulomb_forces_noalloc(dev_xyzq, n, bjerrum, dev_F, stream=None):
+    """Coulomb forces from a device float4 (x, y, z, q) buffer into a device n x 3
+    float64 buffer, with no device allocation (pointers as integers)."""
+    _check(lib().npsim_coulomb_forces_noalloc(C.c_void_p(int(dev_xyzq)), int(n),
+                                              float(bjerrum), C.c_void_p(int(dev_F)),
+                                              _stream_handle(stream)))
 
 
 def npsim_launches_per_step(h):

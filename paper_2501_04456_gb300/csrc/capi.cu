@@ -103,6 +103,19 @@ size_t slots_doubles(const StreamK &sk)
 
 } // namespace
 
+namespace npsim {
+int report_error(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+} // namespace npsim
+
 struct npsim_sim {
     int n = 0, T = 0, sms = 0;
     npsim_params_t P{};

@@ -142,6 +142,10 @@ struct CellGrid {
     float L;        // grid covers [-L, L)^3; coordinates outside are clamped
 };
 
+// Record a message for npsim_last_error() on this thread and return `code`
+// (defined in capi.cu).
+int report_error(int code, const char *fmt, ...);
+
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the .cu files).
 
