@@ -65,6 +65,9 @@ typedef struct {
     int32_t coulomb;    /* 1: all-pairs Coulomb (not truncated), 0: off */
     int32_t wall;       /* 1: interface spring on, 0: off (bulk liquid) */
     int32_t integrator; /* 0: BAOAB Langevin, 1: overdamped (Brownian dynamics) */
+    int32_t skip_neutral; /* 1: leave NPs of charge 0 out of the all-pairs Coulomb sum
+                             (their terms are exactly zero); 0: sum over all pairs */
+    int32_t reserved_;    /* set to 0 */
     uint64_t seed;      /* Philox key of the noise */
     double dt;          /* time step */
     double kT;          /* temperature of the noise */
@@ -184,7 +187,8 @@ int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out);
 
 /* Launch shape of the all-pairs kernel chosen by the autotuner: threads per
  * CTA, particles i per thread, j-tile length, CTAs, the index of the shape in
- * the autotuner's table, and 1 if it is the packed float32x2 Coulomb kernel.
+ * the autotuner's table, and 1 if it is the packed float32x2 Coulomb kernel, 2
+ * if it is the packed Coulomb kernel over partners grouped by charge value.
  * Any pointer may be NULL.  The environment variable NPSIM_AUTOTUNE=1:<index>
  * forces a shape at npsim_create (NPSIM_AUTOTUNE=0: the first shape). */
 int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j_tile,

@@ -42,6 +42,7 @@ class npsim_type_t(C.Structure):
 class npsim_params_t(C.Structure):
     _fields_ = [("n_types", C.c_int32), ("rot_mode", C.c_int32), ("lj_mode", C.c_int32),
                 ("coulomb", C.c_int32), ("wall", C.c_int32), ("integrator", C.c_int32),
+                ("skip_neutral", C.c_int32), ("reserved_", C.c_int32),
                 ("seed", C.c_uint64), ("dt", C.c_double), ("kT", C.c_double),
                 ("R0", C.c_double), ("k_evap", C.c_double), ("g", C.c_double),
                 ("omega", C.c_double), ("bjerrum", C.c_double), ("lj_cut", C.c_double),
@@ -164,6 +165,7 @@ def params_from(sc):
     p.coulomb = int(bool(sc.coulomb))
     p.wall = int(bool(sc.wall))
     p.integrator = sc.integrator
+    p.skip_neutral = int(bool(getattr(sc, "skip_neutral", False)))
     p.seed = sc.seed
     p.dt, p.kT, p.R0, p.k_evap = sc.dt, sc.kT, sc.R0, sc.k_evap
     p.g, p.omega, p.bjerrum, p.lj_cut = sc.g, sc.omega, sc.bjerrum, sc.lj_cut

@@ -1,0 +1,180 @@
+// allpairs_grouped.cu -- all-pairs Coulomb forces (step (ii) of the loop in
+// arXiv 2501.04456 Sec. 2.2) with the partners ordered by charge value.
+//
+// Charge is a property of the NP type (Sec. 2.1: NPs of several types with
+// their own radius, mass and charge), so the particles can be listed once, at
+// creation, grouped by charge value, each group padded to a whole number of
+// 512-particle blocks.  Every j-tile then holds partners of one charge q_t,
+// and the sum over a tile factors as
+//   sum_{j in tile} q_j r_ij / r^3 = q_t sum_{j in tile} r_ij / r^3,
+// which removes the per-pair multiply by q_j: 11 FP32 operations per pair on
+// the packed float32x2 instructions (FADD2 / FMUL2 / FFMA2), two partners per
+// register pair, plus one MUFU.RSQ per pair.  The tile sum is multiplied by q_t
+// once and added into a compensated (TwoSum) float32 accumulator.
+//
+// Rows (particles i) and columns (partners j) both follow the grouped order:
+// perm[k] is the particle at position k (-1 for padding, placed far away).
+// Neutral particles form the last group; with `skip neutral` the caller limits
+// rows and columns to the charged groups, since every Coulomb term with a
+// neutral particle is exactly zero.  The (row tile x column tile) units are
+// split over the CTAs as in the other all-pairs kernels (stream-K), one
+// float64 partial per (row, CTA) written to slot row + CTA.
+#include "npsim_internal.cuh"
+
+namespace npsim {
+
+namespace {
+
+constexpr float kSelfEps = 1e-20f; // added to r^2; the self pair has r_ij = 0 exactly
+constexpr float kPad = 1.0e18f;    // padding: far enough that 1/r^3 underflows to 0
+
+template <int BLOCK, int KI, int JT>
+__global__ void __launch_bounds__(BLOCK)
+k_coulomb_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_perm,
+              const float *__restrict__ qblk, StreamK sk, double *__restrict__ slots)
+{
+    constexpr int ITILE = BLOCK * KI;
+    constexpr int JP = JT / 2;
+    __shared__ float4 s_a[JP]; // (-x0, -x1, -y0, -y1)
+    __shared__ float2 s_b[JP]; // (-z0, -z1)
+
+    const int c = blockIdx.x;
+    const long long p_end = sk_begin(sk, c + 1);
+    long long p = sk_begin(sk, c);
+    const float2 eps2 = make_float2(kSelfEps, kSelfEps);
+
+    while (p < p_end) {
+        const int r = (int)(p / sk.n_jt);
+        const int jt0 = (int)(p - (long long)r * sk.n_jt);
+        const int jt1 = (int)min((long long)sk.n_jt, (long long)jt0 + (p_end - p));
+
+        float2 xi[KI], yi[KI], zi[KI];
+        float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const int pos = r * ITILE + k * BLOCK + threadIdx.x;
+            const int i = pos < n_perm ? perm[pos] : -1;
+            float4 q = make_float4(kPad, kPad, kPad, 0.0f);
+            if (i >= 0)
+                q = xq[i];
+            xi[k] = make_float2(q.x, q.x);
+            yi[k] = make_float2(q.y, q.y);
+            zi[k] = make_float2(q.z, q.z);
+            hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
+        }
+
+        for (int jt = jt0; jt < jt1; ++jt) {
+            __syncthreads(); // the previous tile has been consumed
+            for (int m = threadIdx.x; m < JP; m += BLOCK) {
+                const int k0 = jt * JT + 2 * m;
+                const int j0 = perm[k0], j1 = perm[k0 + 1]; // n_perm is a multiple of JT
+                const float4 pad = make_float4(-kPad, -kPad, -kPad, 0.0f);
+                const float4 a = j0 >= 0 ? xq[j0] : pad;
+                const float4 b = j1 >= 0 ? xq[j1] : pad;
+                s_a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
+                s_b[m] = make_float2(-a.z, -b.z);
+            }
+            __syncthreads();
+
+            float2 ax[KI], ay[KI], az[KI];
+#pragma unroll
+            for (int k = 0; k < KI; ++k)
+                ax[k] = ay[k] = az[k] = make_float2(0.0f, 0.0f);
+
+#pragma unroll 2
+            for (int m = 0; m < JP; ++m) {
+                const float4 a = s_a[m];
+                const float2 nz = s_b[m];
+                const float2 nx = make_float2(a.x, a.y), ny = make_float2(a.z, a.w);
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    const float2 dx = __fadd2_rn(xi[k], nx);
+                    const float2 dy = __fadd2_rn(yi[k], ny);
+                    const float2 dz = __fadd2_rn(zi[k], nz);
+                    float2 r2 = __ffma2_rn(dz, dz, eps2);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dx, dx, r2);
+                    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                    const float2 f = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+                    ax[k] = __ffma2_rn(f, dx, ax[k]);
+                    ay[k] = __ffma2_rn(f, dy, ay[k]);
+                    az[k] = __ffma2_rn(f, dz, az[k]);
+                }
+            }
+            const float qt = qblk[jt * (JT / 256)];
+#pragma unroll
+            for (int k = 0; k < KI; ++k) {
+                two_sum_acc(hx[k], lx[k], qt * ax[k].x);
+                two_sum_acc(hx[k], lx[k], qt * ax[k].y);
+                two_sum_acc(hy[k], ly[k], qt * ay[k].x);
+                two_sum_acc(hy[k], ly[k], qt * ay[k].y);
+                two_sum_acc(hz[k], lz[k], qt * az[k].x);
+                two_sum_acc(hz[k], lz[k], qt * az[k].y);
+            }
+        }
+
+        double *slot = slots + (size_t)(r + c) * 3 * ITILE;
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const int idx = k * BLOCK + threadIdx.x;
+            slot[idx] = (double)hx[k] + (double)lx[k];
+            slot[ITILE + idx] = (double)hy[k] + (double)ly[k];
+            slot[2 * ITILE + idx] = (double)hz[k] + (double)lz[k];
+        }
+        p += jt1 - jt0;
+    }
+}
+
+struct GEntry {
+    ApConfig cfg;
+    const void *fn;
+};
+
+#define NPSIM_GRP(B, K, J) GEntry{ApConfig{B, K, J, 0}, (const void *)k_coulomb_grp<B, K, J>}
+
+const GEntry kGrp[] = {
+    NPSIM_GRP(512, 2, 512), NPSIM_GRP(256, 2, 512), NPSIM_GRP(256, 4, 256),
+    NPSIM_GRP(256, 2, 256), NPSIM_GRP(128, 4, 256), NPSIM_GRP(512, 1, 512),
+    NPSIM_GRP(1024, 1, 512),
+};
+
+template <int B, int K, int J>
+cudaError_t launch_g(const StreamK &sk, const float4 *xq, const int *perm, int n_perm,
+                     const float *qblk, double *slots, cudaStream_t st)
+{
+    k_coulomb_grp<B, K, J><<<sk.grid, B, 0, st>>>(xq, perm, n_perm, qblk, sk, slots);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+int grp_num_configs() { return (int)(sizeof(kGrp) / sizeof(kGrp[0])); }
+
+ApConfig grp_config(int idx) { return kGrp[idx].cfg; }
+
+int grp_occupancy(int idx)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kGrp[idx].fn, kGrp[idx].cfg.block,
+                                                      0) != cudaSuccess)
+        return 0;
+    return occ;
+}
+
+cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq,
+                                    const int *perm, int n_perm, const float *qblk,
+                                    double *slots, cudaStream_t st)
+{
+    switch (idx) {
+    case 0: return launch_g<512, 2, 512>(sk, xq, perm, n_perm, qblk, slots, st);
+    case 1: return launch_g<256, 2, 512>(sk, xq, perm, n_perm, qblk, slots, st);
+    case 2: return launch_g<256, 4, 256>(sk, xq, perm, n_perm, qblk, slots, st);
+    case 3: return launch_g<256, 2, 256>(sk, xq, perm, n_perm, qblk, slots, st);
+    case 4: return launch_g<128, 4, 256>(sk, xq, perm, n_perm, qblk, slots, st);
+    case 5: return launch_g<512, 1, 512>(sk, xq, perm, n_perm, qblk, slots, st);
+    case 6: return launch_g<1024, 1, 512>(sk, xq, perm, n_perm, qblk, slots, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace npsim

@@ -3,6 +3,7 @@
 // autotuner, captures chunks of steps into CUDA graphs, and implements state
 // I/O, force queries, statistics, checkpoints and the test hooks.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -83,7 +84,8 @@ int check_device(int *sms)
 }
 
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tune_cache; // (n, lj) -> config index
+// (n, lj, grouped length, skip_neutral) -> launch shape
+std::map<std::array<long long, 4>, int> g_tune_cache;
 
 void fill_streamk(StreamK &sk, int n, const ApConfig &c, int grid_target)
 {
@@ -144,6 +146,13 @@ struct npsim_sim {
 
     bool ap = false, ap_lj = false;
     int ap_idx = 0;
+
+    // charge-grouped order for the grouped Coulomb kernel (built when Coulomb is on)
+    int *perm = nullptr;    // [n_perm] particle at each grouped position, -1 = padding
+    float *qblk = nullptr;  // [n_perm / 256] charge of each 256-position block
+    int *row_pos = nullptr; // [n] grouped position of particle i (-1: no Coulomb row)
+    int n_perm = 0;         // grouped length (multiple of 512)
+    int grp_len = 0;        // rows and columns the grouped kernel covers
     StreamK sk{};
     StepParams sp{};
 
@@ -183,6 +192,9 @@ struct npsim_sim {
         dfree(xq);
         dfree(typ);
         dfree(slots);
+        dfree(perm);
+        dfree(qblk);
+        dfree(row_pos);
         dfree(F_lj);
         dfree(tab_full);
         dfree(tab_lj);
@@ -245,6 +257,51 @@ CellGrid make_grid(double L, double h_min, long long max_cells)
     return g;
 }
 
+// Launch shapes of the all-pairs sum in one index space: [0, nc) the
+// identity-order kernels of allpairs.cu (scalar and packed), then the
+// charge-grouped kernels of allpairs_grouped.cu (Coulomb only).
+int shape_count() { return ap_num_configs() + grp_num_configs(); }
+
+bool shape_grouped(int k) { return k >= ap_num_configs(); }
+
+ApConfig shape_config(int k)
+{
+    return shape_grouped(k) ? grp_config(k - ap_num_configs()) : ap_config(k);
+}
+
+int shape_occupancy(const npsim_sim *s, int k, bool lj)
+{
+    if (shape_grouped(k))
+        return (lj || !s->perm || s->grp_len == 0) ? 0 : grp_occupancy(k - ap_num_configs());
+    return ap_occupancy(k, lj);
+}
+
+void shape_streamk(const npsim_sim *s, int k, int grid_target, StreamK &sk)
+{
+    const ApConfig c = shape_config(k);
+    if (!shape_grouped(k)) {
+        fill_streamk(sk, s->n, c, grid_target);
+        return;
+    }
+    // rows and columns over the grouped order (grp_len is a multiple of 512)
+    sk.itile = c.block * c.ki;
+    sk.jtile = c.jt;
+    sk.n_it = (s->grp_len + sk.itile - 1) / sk.itile;
+    sk.n_jt = s->grp_len / c.jt;
+    sk.W = (long long)sk.n_it * sk.n_jt;
+    sk.grid = (int)std::min<long long>(std::max(grid_target, 1), sk.W);
+    sk.pad_ = 0;
+}
+
+cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, const StreamK &sk,
+                         const PairTab *tab, double *slots, cudaStream_t st)
+{
+    if (shape_grouped(k))
+        return launch_allpairs_grouped(k - ap_num_configs(), sk, s->xq, s->perm, s->n_perm,
+                                       s->qblk, slots, st);
+    return launch_allpairs(k, lj, sk, s->xq, s->typ, s->n, tab, slots, st);
+}
+
 // Queue the pair forces of the current positions and one integrator pass.
 // Kernel groups timed by npsim_kernel_times.
 enum { KG_ALLPAIRS = 0, KG_CELL_BUILD = 1, KG_CELL_LJ = 2, KG_INTEGRATE = 3 };
@@ -254,8 +311,12 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
 {
     const bool lj_cell = want_lj && s->cell;
     const bool ap_lj = want_lj && s->P.lj_mode == 1;
-    const bool ap_coul = want_coul && s->P.coulomb;
+    // with every charged NP left out (skip_neutral and no charges) the grouped
+    // Coulomb sum is empty
+    const bool ap_coul = want_coul && s->P.coulomb &&
+                         !(shape_grouped(s->ap_idx) && s->grp_len == 0);
     const bool ap = ap_lj || ap_coul;
+    const bool grouped = ap && !ap_lj && shape_grouped(s->ap_idx);
     const bool prof = prof_slot >= 0 && s->profiling;
     auto mark = [&](int group, int edge) -> cudaError_t {
         // inside stream capture a plain cudaEventRecord only orders the capture;
@@ -275,8 +336,7 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     if (ap) {
         const PairTab *tab = ap_lj ? (ap_coul ? s->tab_full : s->tab_lj) : nullptr;
         NP_CUDA(mark(KG_ALLPAIRS, 0));
-        NP_CUDA(launch_allpairs(s->ap_idx, ap_lj, s->sk, s->xq, s->typ, s->n, tab, s->slots,
-                                st));
+        NP_CUDA(shape_launch(s, s->ap_idx, ap_lj, s->sk, tab, s->slots, st));
         NP_CUDA(mark(KG_ALLPAIRS, 1));
     }
     IntArgs a{};
@@ -290,6 +350,7 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     a.F_lj = lj_cell ? s->F_lj : nullptr;
     a.ext_on = ext ? 1 : 0;
     a.field_slots = (ap && !ap_lj) ? 1 : 0;
+    a.row_pos = grouped ? s->row_pos : nullptr;
     a.step = s->d_step;
     a.flags = s->d_flags;
     a.done = s->d_done;
@@ -368,7 +429,7 @@ int read_flags(npsim_sim *s)
 int autotune(npsim_sim *s)
 {
     const bool lj = s->ap_lj;
-    const int nc = ap_num_configs();
+    const int nc = shape_count();
     // NPSIM_AUTOTUNE=0 takes the first shape; NPSIM_AUTOTUNE=1:<index> forces one
     // (ignored if that shape cannot run this sum); neither touches the cache.
     const char *env = getenv("NPSIM_AUTOTUNE");
@@ -378,12 +439,13 @@ int autotune(npsim_sim *s)
     }
     if (env && env[0] == '1' && env[1] == ':') {
         const int idx = atoi(env + 2);
-        if (idx >= 0 && idx < nc && ap_occupancy(idx, lj) > 0) {
+        if (idx >= 0 && idx < nc && shape_occupancy(s, idx, lj) > 0) {
             s->ap_idx = idx;
             return NPSIM_OK;
         }
     }
-    const std::pair<int, int> key(s->n, lj ? 1 : 0);
+    const std::array<long long, 4> key{s->n, lj ? 1 : 0, s->grp_len,
+                                       s->P.skip_neutral ? 1 : 0};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -397,11 +459,11 @@ int autotune(npsim_sim *s)
         // scratch big enough for every candidate
         size_t need = 0;
         for (int c = 0; c < nc; ++c) {
-            const int occ = ap_occupancy(c, lj);
+            const int occ = shape_occupancy(s, c, lj);
             if (occ <= 0)
                 continue;
             StreamK sk;
-            fill_streamk(sk, s->n, ap_config(c), occ * s->sms);
+            shape_streamk(s, c, occ * s->sms, sk);
             need = std::max(need, slots_doubles(sk));
         }
         double *tmp = nullptr;
@@ -412,17 +474,17 @@ int autotune(npsim_sim *s)
         float best_ms = 1e30f;
         const PairTab *tab = lj ? s->tab_full : nullptr;
         for (int c = 0; c < nc; ++c) {
-            const int occ = ap_occupancy(c, lj);
+            const int occ = shape_occupancy(s, c, lj);
             if (occ <= 0)
                 continue;
             StreamK sk;
-            fill_streamk(sk, s->n, ap_config(c), occ * s->sms);
-            if (launch_allpairs(c, lj, sk, s->xq, s->typ, s->n, tab, tmp, s->user) != cudaSuccess)
+            shape_streamk(s, c, occ * s->sms, sk);
+            if (shape_launch(s, c, lj, sk, tab, tmp, s->user) != cudaSuccess)
                 continue;
             const int reps = s->n > 100000 ? 2 : 5;
             cudaEventRecord(e0, s->user);
             for (int r = 0; r < reps; ++r)
-                launch_allpairs(c, lj, sk, s->xq, s->typ, s->n, tab, tmp, s->user);
+                shape_launch(s, c, lj, sk, tab, tmp, s->user);
             cudaEventRecord(e1, s->user);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 continue;
@@ -443,6 +505,72 @@ int autotune(npsim_sim *s)
     s->ap_idx = best;
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune_cache[key] = best;
+    return NPSIM_OK;
+}
+
+// Charge-grouped order (types carry the charge): the distinct non-zero
+// charges in order of first type, then the neutral NPs; inside a group NPs keep
+// their index order; every group is padded with -1 to a multiple of 512.
+int build_grouping(npsim_sim *s, const int32_t *type)
+{
+    std::vector<double> gq;
+    std::vector<int> tg(s->T);
+    for (int t = 0; t < s->T; ++t) {
+        const double q = s->types[t].charge;
+        if (q == 0.0)
+            continue;
+        int g = -1;
+        for (size_t k = 0; k < gq.size(); ++k)
+            if (gq[k] == q)
+                g = (int)k;
+        if (g < 0) {
+            g = (int)gq.size();
+            gq.push_back(q);
+        }
+        tg[t] = g;
+    }
+    const int neutral = (int)gq.size();
+    for (int t = 0; t < s->T; ++t)
+        if (s->types[t].charge == 0.0)
+            tg[t] = neutral;
+    std::vector<int> perm;
+    std::vector<float> qb;
+    std::vector<int> pos(s->n, -1);
+    int charged_len = 0;
+    for (int g = 0; g <= neutral; ++g) {
+        for (int i = 0; i < s->n; ++i)
+            if (tg[type[i]] == g) {
+                pos[i] = (int)perm.size();
+                perm.push_back(i);
+            }
+        while (perm.size() % 512)
+            perm.push_back(-1);
+        const float q = g < neutral ? (float)gq[g] : 0.0f;
+        while (qb.size() < perm.size() / 256)
+            qb.push_back(q);
+        if (g == neutral - 1 || (neutral == 0 && g == 0))
+            charged_len = neutral > 0 ? (int)perm.size() : 0;
+    }
+    if (perm.empty()) { // cannot happen for n >= 1; keep the buffers non-empty
+        perm.assign(512, -1);
+        qb.assign(2, 0.0f);
+    }
+    s->n_perm = (int)perm.size();
+    if (s->P.skip_neutral) {
+        s->grp_len = charged_len;
+        for (int i = 0; i < s->n; ++i)
+            if (tg[type[i]] == neutral)
+                pos[i] = -1;
+    } else {
+        s->grp_len = s->n_perm;
+    }
+    NP_CUDA(dalloc(&s->perm, perm.size()));
+    NP_CUDA(dalloc(&s->qblk, qb.size()));
+    NP_CUDA(dalloc(&s->row_pos, (size_t)s->n));
+    NP_CUDA(cudaMemcpy(s->perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
+    NP_CUDA(cudaMemcpy(s->qblk, qb.data(), sizeof(float) * qb.size(), cudaMemcpyHostToDevice));
+    NP_CUDA(cudaMemcpy(s->row_pos, pos.data(), sizeof(int) * pos.size(),
+                       cudaMemcpyHostToDevice));
     return NPSIM_OK;
 }
 
@@ -690,11 +818,16 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
         BAIL_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->user));
     }
     if (s->ap) {
+        if (params->coulomb) {
+            rc = build_grouping(s, type);
+            if (rc)
+                return bail(rc);
+        }
         rc = autotune(s);
         if (rc)
             return bail(rc);
-        const int occ = std::max(1, ap_occupancy(s->ap_idx, s->ap_lj));
-        fill_streamk(s->sk, s->n, ap_config(s->ap_idx), occ * s->sms);
+        const int occ = std::max(1, shape_occupancy(s, s->ap_idx, s->ap_lj));
+        shape_streamk(s, s->ap_idx, occ * s->sms, s->sk);
         BAIL_CUDA(dalloc(&s->slots, slots_doubles(s->sk)));
     } else {
         s->sk = StreamK{};
@@ -793,7 +926,7 @@ int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_t
                           int *grid, int *index, int *packed)
 {
     NP_REQUIRE(s, "sim is NULL");
-    const ApConfig c = ap_config(s->ap_idx);
+    const ApConfig c = shape_config(s->ap_idx);
     if (block)
         *block = s->ap ? c.block : 0;
     if (i_per_thread)
@@ -805,14 +938,14 @@ int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_t
     if (index)
         *index = s->ap ? s->ap_idx : -1;
     if (packed)
-        *packed = (s->ap && ap_packed(s->ap_idx)) ? 1 : 0;
+        *packed = !s->ap ? 0 : shape_grouped(s->ap_idx) ? 2 : ap_packed(s->ap_idx) ? 1 : 0;
     return NPSIM_OK;
 }
 
 int npsim_allpairs_num_configs(int *count)
 {
     NP_REQUIRE(count, "count is NULL");
-    *count = ap_num_configs();
+    *count = shape_count();
     return NPSIM_OK;
 }
 

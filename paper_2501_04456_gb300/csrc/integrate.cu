@@ -48,10 +48,11 @@ k_integrate(IntArgs a, StepParams p)
         double fx, fy, fz;
         if (ASSEMBLE) {
             fx = fy = fz = 0.0;
-            if (a.slots) {
+            const int pos = a.row_pos ? a.row_pos[i] : i;
+            if (a.slots && pos >= 0) {
                 const StreamK &sk = a.sk;
-                const int r = i / sk.itile;
-                const int idx = i - r * sk.itile;
+                const int r = pos / sk.itile;
+                const int idx = pos - r * sk.itile;
                 const long long u0 = (long long)r * sk.n_jt;
                 const int c0 = sk_cta_of(sk, u0);
                 const int c1 = sk_cta_of(sk, u0 + sk.n_jt - 1);

@@ -158,6 +158,15 @@ int ap_num_configs();
 ApConfig ap_config(int idx);
 int ap_occupancy(int idx, bool lj);
 bool ap_packed(int idx); // float32x2 Coulomb-only kernel
+// Charge-grouped packed Coulomb kernel (allpairs_grouped.cu): rows and columns
+// follow perm (grouped by charge, groups padded to 512), qblk = charge of each
+// 256-position block.
+int grp_num_configs();
+ApConfig grp_config(int idx);
+int grp_occupancy(int idx);
+cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq,
+                                    const int *perm, int n_perm, const float *qblk,
+                                    double *slots, cudaStream_t st);
 cudaError_t launch_allpairs(int cfg_idx, bool lj, const StreamK &sk, const float4 *xq,
                             const int *typ, int n, const PairTab *tab, double *slots,
                             cudaStream_t st);
@@ -177,6 +186,8 @@ struct IntArgs {
     const double *slots;     // stream-K partials (or NULL)
     StreamK sk;
     const double *F_lj;      // cell-list LJ forces SoA [3][n] (or NULL)
+    const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
+                             // no Coulomb partial); NULL: row position = i
     int ext_on;              // add external forces
     int field_slots;         // slots hold sum_j q_j r_ij/r^3 (Coulomb-only kernel): scale by C q_i
     long long *step;         // device step counter

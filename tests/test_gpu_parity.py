@@ -137,6 +137,28 @@ def test_every_launch_shape(P, monkeypatch):
     assert seen_packed
 
 
+def test_skip_neutral_forces_and_steps(P):
+    """Leaving the neutral NPs out of the Coulomb sum (their terms are exactly zero)
+    gives the oracle's forces, and the same trajectory to rounding."""
+    sc = small(wl.config3(), 3001)  # 60 % neutral NPs
+    types, x, v = wl.initial_state(sc, fp32_positions=True)
+    sc_s = with_(sc, skip_neutral=True)
+    amb = cutoff_ambiguous(x, types, sc)
+    with P.Sim(sc_s, x, v, types) as sim:
+        F = sim.forces(0)
+        Fc = sim.forces(3)
+        sim.step(20)
+        xs, _, _, _ = sim.state()
+    assert force_error(F, oracle.total_forces(sc, x, types, 0.0))[~amb].max() <= FORCE_TOL
+    assert force_error(Fc, _oracle_pair(sc, x, types, lj=False)).max() <= FORCE_TOL
+    neutral = np.array([sc.types[t].charge == 0 for t in types])
+    assert np.all(Fc[neutral] == 0)
+    with P.Sim(sc, x, v, types) as sim:
+        sim.step(20)
+        xa, _, _, _ = sim.state()
+    assert np.abs(xs - xa).max() < 1e-9
+
+
 def test_forces_full_size_sampled(P):
     """The 250000-NP scenario at full size, in the launch configuration the benchmark
     times: sampled rows against the oracle row by row."""
