@@ -44,6 +44,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-skip", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -220,6 +221,59 @@ def _traffic_from_profile(kernel_src):
     return None
 
 
+def _ensemble_measure(P, torch, stream, steps, warmup, n_plain=16, steps_per_droplet=10000):
+    """Droplets/s of the 256-droplet ensemble (N log-uniform in [512, 32768]) run as
+    one batched ensemble, and of the same droplets run one after another with the
+    single-droplet path.  Each droplet is a 10000-step run; both rates come from
+    measured per-step times.  The plain rate times a stratified sample of
+    n_plain droplets (every 256/n_plain-th by N) and scales its summed step time
+    to all 256.  The ensemble's working set (~250 MB) exceeds L2, so no flush."""
+    import numpy as np
+    import workloads as wl
+    scs = wl.ensemble_config()
+    drops = [(sc, *wl.initial_state(sc)) for sc in scs]
+    drops = [(sc, x, v, t) for sc, t, x, v in drops]
+    ens = P.Ensemble(drops, stream=stream)
+    n_tot, pairs = ens.info()
+    ens.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    cfg = ens.config()
+    ens.close()
+    order = np.argsort([sc.n for sc in scs])
+    stride = max(1, len(scs) // n_plain)
+    sample = order[stride // 2::stride][:n_plain]
+    plain_ms = 0.0
+    for d in sample:
+        sc, x, v, t = drops[d]
+        with P.Sim(sc, x, v, t, stream=stream) as sim:
+            sim.step(2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(16)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plain_ms += e0.elapsed_time(e1) / 16
+    plain_ms_all = plain_ms * len(scs) / len(sample)
+    ens_dps = len(scs) / (ms * 1e-3 * steps_per_droplet)
+    plain_dps = len(scs) / (plain_ms_all * 1e-3 * steps_per_droplet)
+    return {"droplets": len(scs), "steps_per_droplet": steps_per_droplet,
+            "n_particles": n_tot, "pairs_per_step": pairs,
+            "ms_per_step": ms, "droplets_per_s": ens_dps,
+            "pair_interactions_per_s": pairs / (ms * 1e-3),
+            "allpairs_launch": cfg,
+            "plain": {"ms_per_step_all_droplets": plain_ms_all, "droplets_per_s": plain_dps,
+                      "sample": f"{len(sample)} of {len(scs)} droplets, every {stride}-th by N; "
+                                f"summed step time x {len(scs) / len(sample):.0f}"},
+            "speedup_vs_plain": ens_dps / plain_dps}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -327,6 +381,10 @@ def run_ours(a):
                 "allpairs_launch": s3.allpairs_config()}
         s3.close()
 
+    ens = None
+    if not a.no_ensemble and rank == 0:
+        ens = _ensemble_measure(P, torch, stream, max(3, a.steps // 2), a.warmup)
+
     # end to end through the C ABI with host buffers: create from host arrays,
     # then per step one step and a device->host read of the positions
     e2e = None
@@ -381,6 +439,7 @@ def run_ours(a):
                          "frac_at_sampled_clock": (achieved / (peak_tflops * clk["sm_mhz"] /
                                                                max_mhz)) if clk else None},
             "skip_neutral": skip,
+            "ensemble": ens,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

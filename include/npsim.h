@@ -197,6 +197,54 @@ int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j
 /* Number of launch shapes in the autotuner's table. */
 int npsim_allpairs_num_configs(int *count);
 
+/* ------------------------------------------------------------------------
+ * Ensemble: many independent droplets (each the system of Sec. 2 with its own
+ * types, charges, radius law and seed) advanced together.  One all-pairs launch
+ * and one integrator launch per step cover every droplet: the (i-tile x
+ * j-tile) work rectangles of all droplets are laid end to end and split evenly
+ * over the CTAs, so droplets of very different N share the GPU in one launch.
+ * Steps replay from captured CUDA graphs; the launch shape is chosen by timing
+ * every candidate at npsim_ens_create (NPSIM_ENS_SHAPE=<index> forces one).
+ */
+typedef struct npsim_ens *npsim_ens_t;
+
+/* One droplet: same meaning as the arguments of npsim_create.  params.lj_mode
+ * must be 0 or 1 (the ensemble sums LJ inside the all-pairs kernel);
+ * params.skip_neutral is ignored. */
+typedef struct {
+    int64_t n;
+    const npsim_type_t *types; /* params.n_types entries */
+    npsim_params_t params;
+    const double *x0;          /* n x 3 */
+    const double *v0;          /* n x 3 or NULL (zero) */
+    const int32_t *type;       /* n */
+} npsim_droplet_t;
+
+/* Create an ensemble of n_drops droplets (the library copies all inputs) and
+ * compute the initial forces.  Errors as npsim_create, per droplet. */
+int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream,
+                     npsim_ens_t *out);
+
+/* Advance every droplet by n_steps steps (all droplets share the step counter);
+ * one device-to-host read of the error word at the end. */
+int npsim_ens_step(npsim_ens_t ens, int64_t n_steps);
+
+/* State of droplet d (host arrays, any may be NULL; n_d x 3). */
+int npsim_ens_get_state(npsim_ens_t ens, int32_t d, double *x, double *v, double *F,
+                        int64_t *step);
+
+/* Total forces of droplet d at the current state (recomputed), n_d x 3. */
+int npsim_ens_forces(npsim_ens_t ens, int32_t d, double *F);
+
+/* Launch shape of the ensemble all-pairs kernel (any pointer may be NULL). */
+int npsim_ens_config(npsim_ens_t ens, int *block, int *i_per_thread, int *j_tile, int *grid,
+                     int *index);
+
+/* Total NPs and ordered pairs sum_d n_d (n_d - 1) per step. */
+int npsim_ens_info(npsim_ens_t ens, int64_t *n_total, double *pairs_per_step);
+
+void npsim_ens_destroy(npsim_ens_t ens);
+
 /*
  * All-pairs Coulomb forces without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc when

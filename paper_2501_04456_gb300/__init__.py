@@ -49,6 +49,12 @@ class npsim_params_t(C.Structure):
                 ("eps_override", C.POINTER(C.c_double))]
 
 
+class npsim_droplet_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("types", C.POINTER(npsim_type_t)),
+                ("params", npsim_params_t), ("x0", C.POINTER(C.c_double)),
+                ("v0", C.POINTER(C.c_double)), ("type", C.POINTER(C.c_int32))]
+
+
 class npsim_stats_cfg_t(C.Structure):
     _fields_ = [("r_max", C.c_double), ("n_bins", C.c_int32), ("radial_bins", C.c_int32),
                 ("boxcount", C.c_int32), ("max_scales", C.c_int32)]
@@ -104,6 +110,15 @@ def lib():
             L.npsim_coulomb_forces_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_double,
                                                        C.c_void_p, C.c_void_p]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
+            L.npsim_ens_create.argtypes = [C.POINTER(npsim_droplet_t), C.c_int32, C.c_void_p,
+                                           C.POINTER(_h)]
+            L.npsim_ens_step.argtypes = [_h, C.c_int64]
+            L.npsim_ens_get_state.argtypes = [_h, C.c_int32, _d, _d, _d, _i64]
+            L.npsim_ens_forces.argtypes = [_h, C.c_int32, _d]
+            L.npsim_ens_config.argtypes = [_h, _i32, _i32, _i32, _i32, _i32]
+            L.npsim_ens_info.argtypes = [_h, _i64, _d]
+            L.npsim_ens_destroy.argtypes = [_h]
+            L.npsim_ens_destroy.restype = None
             L.npsim_chunk_steps.argtypes = [_h, _i32]
             L.npsim_profile.argtypes = [_h, C.c_int]
             L.npsim_kernel_times.argtypes = [_h, _d, _i32]
@@ -380,6 +395,110 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             npsim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# --------------------------------------------------------------------------
+# Ensemble of droplets
+
+
+def npsim_ens_create(droplets, stream=None):
+    """droplets: sequence of (scenario, x0, v0, type).  Returns (handle, keepalive)."""
+    arr = (npsim_droplet_t * len(droplets))()
+    keep = []
+    for k, (sc, x0, v0, ty) in enumerate(droplets):
+        x0 = _aos(x0)
+        n = x0.shape[0]
+        v0 = None if v0 is None else _aos(v0, n)
+        ty = np.ascontiguousarray(ty, dtype=np.int32)
+        tys = types_from(sc.types)
+        par = params_from(sc)
+        keep += [x0, v0, ty, tys, par]
+        arr[k].n = n
+        arr[k].types = C.cast(tys, C.POINTER(npsim_type_t))
+        arr[k].params = par
+        arr[k].x0 = _p(x0, C.c_double)
+        arr[k].v0 = None if v0 is None else _p(v0, C.c_double)
+        arr[k].type = _p(ty, C.c_int32)
+    h = _h()
+    _check(lib().npsim_ens_create(arr, len(droplets), _stream_handle(stream), C.byref(h)))
+    return h
+
+
+def npsim_ens_step(h, n_steps):
+    _check(lib().npsim_ens_step(h, int(n_steps)))
+
+
+def npsim_ens_get_state(h, d, n):
+    x = np.empty((n, 3))
+    v = np.empty((n, 3))
+    F = np.empty((n, 3))
+    st = C.c_int64()
+    _check(lib().npsim_ens_get_state(h, int(d), _p(x, C.c_double), _p(v, C.c_double),
+                                     _p(F, C.c_double), C.byref(st)))
+    return x, v, F, st.value
+
+
+def npsim_ens_forces(h, d, n):
+    F = np.empty((n, 3))
+    _check(lib().npsim_ens_forces(h, int(d), _p(F, C.c_double)))
+    return F
+
+
+def npsim_ens_config(h):
+    v = [C.c_int32() for _ in range(5)]
+    _check(lib().npsim_ens_config(h, *[C.byref(x) for x in v]))
+    return dict(zip(("block", "i_per_thread", "j_tile", "grid", "index"), [x.value for x in v]))
+
+
+def npsim_ens_info(h):
+    n = C.c_int64()
+    p = C.c_double()
+    _check(lib().npsim_ens_info(h, C.byref(n), C.byref(p)))
+    return n.value, p.value
+
+
+def npsim_ens_destroy(h):
+    lib().npsim_ens_destroy(h)
+
+
+class Ensemble:
+    """Owning wrapper around an ensemble handle; droplets = [(scenario, x0, v0, type)]."""
+
+    def __init__(self, droplets, stream=None):
+        self.sizes = [int(np.asarray(d[1]).reshape(-1, 3).shape[0]) for d in droplets]
+        self.h = npsim_ens_create(droplets, stream)
+
+    def step(self, n_steps=1):
+        npsim_ens_step(self.h, n_steps)
+
+    def state(self, d):
+        return npsim_ens_get_state(self.h, d, self.sizes[d])
+
+    def forces(self, d):
+        return npsim_ens_forces(self.h, d, self.sizes[d])
+
+    def config(self):
+        return npsim_ens_config(self.h)
+
+    def info(self):
+        return npsim_ens_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            npsim_ens_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -616,6 +616,55 @@ int upload_state(npsim_sim *s, const double *x, const double *v, int64_t step)
     return read_flags(s);
 }
 
+// Per-type integrator coefficients (float64 on the host): BAOAB O-step factors
+// c1 = exp(-gamma dt), sqrt((1 - c1^2) kT / m); overdamped mobility 1/(m gamma)
+// and noise sqrt(2 kT dt / (m gamma)); C q for the Coulomb field.
+void fill_coefs(const npsim_type_t *types, const npsim_params_t *params, TypeCoef *tc,
+                float *charge_f)
+{
+    const double C = params->bjerrum;
+    for (int t = 0; t < params->n_types; ++t) {
+        const npsim_type_t &ty = types[t];
+        TypeCoef &c = tc[t];
+        c.mass = ty.mass;
+        c.inv_mass = 1.0 / ty.mass;
+        c.half_sigma = 0.5 * ty.sigma;
+        c.k_wall = ty.k_wall;
+        c.c1 = std::exp(-ty.gamma * params->dt);
+        c.sd_o = std::sqrt((1.0 - c.c1 * c.c1) * params->kT / ty.mass);
+        c.mob = ty.gamma > 0 ? 1.0 / (ty.mass * ty.gamma) : 0.0;
+        c.sd_bd = std::sqrt(2.0 * params->kT * params->dt * c.mob);
+        c.charge_c = C * ty.charge;
+        if (charge_f)
+            charge_f[t] = (float)ty.charge;
+    }
+}
+
+// Type-pair tables (sigma_ab^2, 24 eps_ab, rc_ab^2, C q_a q_b) with Lorentz-Berthelot
+// mixing unless eps_ov (T x T) is given; tl is the same with the Coulomb column 0.
+// Returns the largest cutoff.
+double fill_tabs(const npsim_type_t *types, const npsim_params_t *params, const double *eps_ov,
+                 PairTab *tf, PairTab *tl)
+{
+    const int T = params->n_types;
+    const double C = params->bjerrum;
+    double rc_max = 0.0;
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const double sig = 0.5 * (types[a].sigma + types[b].sigma);
+            const double eps = eps_ov ? eps_ov[a * T + b] : std::sqrt(types[a].eps * types[b].eps);
+            const double rc = params->lj_cut * sig;
+            rc_max = std::max(rc_max, rc);
+            const float4 e = make_float4(
+                (float)(sig * sig), (float)(24.0 * eps), (float)(rc * rc),
+                (float)(params->coulomb ? C * types[a].charge * types[b].charge : 0.0));
+            tf->e[a * NPSIM_MAX_TYPES + b] = e;
+            if (tl)
+                tl->e[a * NPSIM_MAX_TYPES + b] = make_float4(e.x, e.y, e.z, 0.0f);
+        }
+    return rc_max;
+}
+
 int validate(const npsim_type_t *types, const npsim_params_t *p, int64_t n)
 {
     NP_REQUIRE(types && p, "types and params are required");
@@ -731,38 +780,9 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
     sp.k_evap = params->k_evap;
     sp.g = params->g;
     sp.omega2 = params->omega * params->omega;
-    const double C = params->bjerrum;
-    for (int t = 0; t < s->T; ++t) {
-        const npsim_type_t &ty = types[t];
-        TypeCoef &c = sp.tc[t];
-        c.mass = ty.mass;
-        c.inv_mass = 1.0 / ty.mass;
-        c.half_sigma = 0.5 * ty.sigma;
-        c.k_wall = ty.k_wall;
-        c.c1 = std::exp(-ty.gamma * params->dt);
-        c.sd_o = std::sqrt((1.0 - c.c1 * c.c1) * params->kT / ty.mass);
-        c.mob = ty.gamma > 0 ? 1.0 / (ty.mass * ty.gamma) : 0.0;
-        c.sd_bd = std::sqrt(2.0 * params->kT * params->dt * c.mob);
-        c.charge_c = C * ty.charge;
-        s->charge_f[t] = (float)ty.charge;
-    }
+    fill_coefs(types, params, sp.tc, s->charge_f);
     PairTab tf{}, tl{};
-    double rc_max = 0.0;
-    for (int a = 0; a < s->T; ++a)
-        for (int b = 0; b < s->T; ++b) {
-            const double sig = 0.5 * (types[a].sigma + types[b].sigma);
-            const double eps = s->has_ov ? s->eps_ov[a * s->T + b]
-                                         : std::sqrt(types[a].eps * types[b].eps);
-            const double rc = params->lj_cut * sig;
-            rc_max = std::max(rc_max, rc);
-            const float4 e = make_float4((float)(sig * sig), (float)(24.0 * eps),
-                                         (float)(rc * rc),
-                                         (float)(params->coulomb ? C * types[a].charge *
-                                                                       types[b].charge
-                                                                 : 0.0));
-            tf.e[a * NPSIM_MAX_TYPES + b] = e;
-            tl.e[a * NPSIM_MAX_TYPES + b] = make_float4(e.x, e.y, e.z, 0.0f);
-        }
+    const double rc_max = fill_tabs(types, params, s->has_ov ? s->eps_ov : nullptr, &tf, &tl);
 
 #define BAIL_CUDA(call)                                                                 \
     do {                                                                                \
@@ -1294,6 +1314,527 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
         return rc;
     }
     *out = s;
+    return NPSIM_OK;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ensemble of independent droplets
+
+struct npsim_ens {
+    int D = 0, n_total = 0, sms = 0;
+    std::vector<int> off, cnt;
+    std::vector<EnsDrop> h_drops;
+    std::vector<PairTab> h_tabs;
+    std::vector<npsim_params_t> P;
+    std::vector<std::vector<npsim_type_t>> types;
+    std::vector<std::vector<double>> eps_ov;
+    std::vector<int32_t> h_type;
+
+    cudaStream_t user = nullptr, cap = nullptr;
+    double *x = nullptr, *v = nullptr, *F = nullptr, *F_tmp = nullptr;
+    float4 *xq = nullptr;
+    int *typ = nullptr, *drop_of = nullptr;
+    EnsDrop *drops = nullptr;
+    PairTab *tabs = nullptr;
+    long long *unit0 = nullptr;
+    double *slots = nullptr;
+    long long *d_step = nullptr;
+    int *d_flags = nullptr;
+    unsigned *d_done = nullptr;
+
+    int shape = 0;
+    StreamK sk{};
+    std::map<int, cudaGraphExec_t> graphs;
+    int64_t step = 0;
+
+    ~npsim_ens()
+    {
+        for (auto &g : graphs)
+            cudaGraphExecDestroy(g.second);
+        dfree(x);
+        dfree(v);
+        dfree(F);
+        dfree(F_tmp);
+        dfree(xq);
+        dfree(typ);
+        dfree(drop_of);
+        dfree(drops);
+        dfree(tabs);
+        dfree(unit0);
+        dfree(slots);
+        dfree(d_step);
+        dfree(d_flags);
+        dfree(d_done);
+        if (cap)
+            cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+// Droplet geometry for launch shape `shape`: rows and (i-tile x j-tile) units of
+// every droplet laid end to end.  Returns the total number of units.
+long long ens_geometry(npsim_ens *e, int shape, std::vector<long long> &unit0, long long *rows)
+{
+    const ApConfig c = ens_config(shape);
+    const int itile = c.block * c.ki;
+    long long u = 0, r = 0;
+    unit0.assign(e->D + 1, 0);
+    for (int d = 0; d < e->D; ++d) {
+        EnsDrop &g = e->h_drops[d];
+        g.n_it = (e->cnt[d] + itile - 1) / itile;
+        g.n_jt = (e->cnt[d] + c.jt - 1) / c.jt;
+        g.row0 = (int)r;
+        g.unit0 = u;
+        unit0[d] = u;
+        u += (long long)g.n_it * g.n_jt;
+        r += g.n_it;
+    }
+    unit0[e->D] = u;
+    if (rows)
+        *rows = r;
+    return u;
+}
+
+void ens_streamk(long long W, const ApConfig &c, int grid_target, StreamK &sk)
+{
+    sk.itile = c.block * c.ki;
+    sk.jtile = c.jt;
+    sk.n_it = 0;
+    sk.n_jt = 0;
+    sk.W = W;
+    sk.grid = (int)std::min<long long>(std::max(grid_target, 1), W);
+    sk.pad_ = 0;
+}
+
+int ens_upload_geometry(npsim_ens *e, const std::vector<long long> &unit0)
+{
+    NP_CUDA(cudaMemcpyAsync(e->drops, e->h_drops.data(), sizeof(EnsDrop) * e->D,
+                            cudaMemcpyHostToDevice, e->user));
+    NP_CUDA(cudaMemcpyAsync(e->unit0, unit0.data(), sizeof(long long) * unit0.size(),
+                            cudaMemcpyHostToDevice, e->user));
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    return NPSIM_OK;
+}
+
+EnsAllpairsArgs ens_ap_args(npsim_ens *e, double *slots)
+{
+    EnsAllpairsArgs a{};
+    a.xq = e->xq;
+    a.typ = e->typ;
+    a.drops = e->drops;
+    a.unit0 = e->unit0;
+    a.tabs = e->tabs;
+    a.n_drops = e->D;
+    a.slots = slots;
+    return a;
+}
+
+int ens_pass(npsim_ens *e, int mode, bool ext, double *Fout, cudaStream_t st)
+{
+    NP_CUDA(launch_ens_allpairs(e->shape, e->sk, ens_ap_args(e, e->slots), st));
+    EnsIntArgs a{};
+    a.x = e->x;
+    a.v = e->v;
+    a.F = Fout;
+    a.typ = e->typ;
+    a.xq = e->xq;
+    a.drop_of = e->drop_of;
+    a.drops = e->drops;
+    a.slots = e->slots;
+    a.ext_on = ext ? 1 : 0;
+    a.step = e->d_step;
+    a.flags = e->d_flags;
+    a.done = e->d_done;
+    NP_CUDA(launch_ens_integrate(mode, a, e->n_total, e->D, e->sk, st));
+    return NPSIM_OK;
+}
+
+int ens_chunk(npsim_ens *e, int k, cudaStream_t st)
+{
+    EnsIntArgs a{};
+    a.x = e->x;
+    a.v = e->v;
+    a.F = e->F;
+    a.typ = e->typ;
+    a.xq = e->xq;
+    a.drop_of = e->drop_of;
+    a.drops = e->drops;
+    a.step = e->d_step;
+    a.flags = e->d_flags;
+    a.done = e->d_done;
+    NP_CUDA(launch_ens_integrate(MODE_A, a, e->n_total, e->D, e->sk, st));
+    for (int j = 0; j < k; ++j) {
+        int rc = ens_pass(e, j + 1 < k ? MODE_BA : MODE_B, true, e->F, st);
+        if (rc)
+            return rc;
+    }
+    return NPSIM_OK;
+}
+
+int ens_graph(npsim_ens *e, int k, cudaGraphExec_t *out)
+{
+    auto it = e->graphs.find(k);
+    if (it != e->graphs.end()) {
+        *out = it->second;
+        return NPSIM_OK;
+    }
+    NP_CUDA(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = ens_chunk(e, k, e->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->cap, &g);
+    if (rc) {
+        if (g)
+            cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+    e->graphs[k] = ex;
+    *out = ex;
+    return NPSIM_OK;
+}
+
+// Time every ensemble launch shape on the current positions; keep the fastest.
+int ens_autotune(npsim_ens *e)
+{
+    const int nc = ens_num_configs();
+    const char *env = getenv("NPSIM_ENS_SHAPE");
+    std::vector<long long> unit0;
+    int best = -1;
+    if (env) {
+        const int idx = atoi(env);
+        if (idx >= 0 && idx < nc && ens_occupancy(idx) > 0)
+            best = idx;
+    }
+    if (best < 0) {
+        size_t need = 0;
+        for (int c = 0; c < nc; ++c) {
+            const int occ = ens_occupancy(c);
+            if (occ <= 0)
+                continue;
+            long long rows = 0;
+            const long long W = ens_geometry(e, c, unit0, &rows);
+            StreamK sk;
+            ens_streamk(W, ens_config(c), occ * e->sms, sk);
+            need = std::max(need, (size_t)(rows + sk.grid) * 3 * (size_t)sk.itile);
+        }
+        double *tmp = nullptr;
+        NP_CUDA(dalloc(&tmp, need));
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        for (int c = 0; c < nc; ++c) {
+            const int occ = ens_occupancy(c);
+            if (occ <= 0)
+                continue;
+            const long long W = ens_geometry(e, c, unit0, nullptr);
+            int rc = ens_upload_geometry(e, unit0);
+            if (rc) {
+                cudaFree(tmp);
+                return rc;
+            }
+            StreamK sk;
+            ens_streamk(W, ens_config(c), occ * e->sms, sk);
+            e->shape = c;
+            if (launch_ens_allpairs(c, sk, ens_ap_args(e, tmp), e->user) != cudaSuccess)
+                continue;
+            cudaEventRecord(e0, e->user);
+            for (int r = 0; r < 2; ++r)
+                launch_ens_allpairs(c, sk, ens_ap_args(e, tmp), e->user);
+            cudaEventRecord(e1, e->user);
+            if (cudaEventSynchronize(e1) != cudaSuccess)
+                continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(tmp);
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess)
+            return set_err(NPSIM_ERR_CUDA, "ensemble autotune: %s", cudaGetErrorString(ce));
+        if (best < 0)
+            best = 0;
+    }
+    e->shape = best;
+    long long rows = 0;
+    const long long W = ens_geometry(e, best, unit0, &rows);
+    ens_streamk(W, ens_config(best), std::max(1, ens_occupancy(best)) * e->sms, e->sk);
+    int rc = ens_upload_geometry(e, unit0);
+    if (rc)
+        return rc;
+    NP_CUDA(dalloc(&e->slots, (size_t)(rows + e->sk.grid) * 3 * (size_t)e->sk.itile));
+    return NPSIM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream,
+                     npsim_ens_t *out)
+{
+    NP_REQUIRE(out, "out is NULL");
+    *out = nullptr;
+    NP_REQUIRE(drops && n_drops >= 1, "need at least one droplet");
+    long long total = 0;
+    for (int d = 0; d < n_drops; ++d) {
+        const npsim_droplet_t &dr = drops[d];
+        int rc = validate(dr.types, &dr.params, dr.n);
+        if (rc)
+            return set_err(rc, "droplet %d: %s", d, g_err.c_str());
+        NP_REQUIRE(dr.params.lj_mode != 2, "droplet %d: the ensemble sums LJ inside the all-pairs "
+                                           "kernel (lj_mode 0 or 1)", d);
+        NP_REQUIRE(dr.x0 && dr.type, "droplet %d: x0 and type are required", d);
+        for (int64_t i = 0; i < dr.n; ++i)
+            NP_REQUIRE(dr.type[i] >= 0 && dr.type[i] < dr.params.n_types,
+                       "droplet %d: type[%lld] out of range", d, (long long)i);
+        total += dr.n;
+    }
+    NP_REQUIRE(total <= (1ll << 29), "too many particles in the ensemble");
+    int sms = 0;
+    int rc = check_device(&sms);
+    if (rc)
+        return rc;
+
+    npsim_ens *e = new npsim_ens();
+    auto bail = [&](int code) {
+        delete e;
+        return code;
+    };
+    e->D = n_drops;
+    e->n_total = (int)total;
+    e->sms = sms;
+    e->user = (cudaStream_t)stream;
+    e->off.resize(n_drops);
+    e->cnt.resize(n_drops);
+    e->h_drops.assign(n_drops, EnsDrop{});
+    e->h_tabs.assign(n_drops, PairTab{});
+    e->P.resize(n_drops);
+    e->types.resize(n_drops);
+    e->eps_ov.resize(n_drops);
+    std::vector<double> xs(3 * (size_t)total), vs(3 * (size_t)total, 0.0);
+    std::vector<int> dof((size_t)total);
+    std::vector<float4> xq0((size_t)total);
+    e->h_type.resize((size_t)total);
+    int off = 0;
+    for (int d = 0; d < n_drops; ++d) {
+        const npsim_droplet_t &dr = drops[d];
+        const int n = (int)dr.n;
+        e->off[d] = off;
+        e->cnt[d] = n;
+        e->P[d] = dr.params;
+        e->types[d].assign(dr.types, dr.types + dr.params.n_types);
+        if (dr.params.eps_override)
+            e->eps_ov[d].assign(dr.params.eps_override,
+                                dr.params.eps_override + dr.params.n_types * dr.params.n_types);
+        e->P[d].eps_override = nullptr;
+        EnsDrop &g = e->h_drops[d];
+        g.offset = off;
+        g.n = n;
+        g.rot_mode = dr.params.rot_mode;
+        g.wall = dr.params.wall;
+        g.integrator = dr.params.integrator;
+        g.seed = dr.params.seed;
+        g.dt = dr.params.dt;
+        g.R0 = dr.params.R0;
+        g.k_evap = dr.params.k_evap;
+        g.g = dr.params.g;
+        g.omega2 = dr.params.omega * dr.params.omega;
+        float qf[NPSIM_MAX_TYPES] = {};
+        fill_coefs(dr.types, &dr.params, g.tc, qf);
+        npsim_params_t pc = dr.params;
+        if (pc.lj_mode == 0) { // no LJ: zero the LJ columns of the table
+            pc.lj_cut = 0.0;
+        }
+        fill_tabs(dr.types, &pc, e->eps_ov[d].empty() ? nullptr : e->eps_ov[d].data(),
+                  &e->h_tabs[d], nullptr);
+        if (pc.lj_mode == 0)
+            for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) {
+                e->h_tabs[d].e[k].y = 0.0f;
+                e->h_tabs[d].e[k].z = 0.0f;
+            }
+        for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < 3; ++k) {
+                xs[(size_t)k * total + off + i] = dr.x0[3 * (size_t)i + k];
+                if (dr.v0)
+                    vs[(size_t)k * total + off + i] = dr.v0[3 * (size_t)i + k];
+            }
+            dof[off + i] = d;
+            e->h_type[off + i] = dr.type[i];
+        }
+        off += n;
+    }
+#define EBAIL(call)                                                                     \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return bail(set_err(e_ == cudaErrorMemoryAllocation ? NPSIM_ERR_OOM         \
+                                                                 : NPSIM_ERR_CUDA,      \
+                                "%s failed: %s", #call, cudaGetErrorString(e_)));       \
+    } while (0)
+    EBAIL(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
+    const size_t n3 = 3 * (size_t)total;
+    EBAIL(dalloc(&e->x, n3));
+    EBAIL(dalloc(&e->v, n3));
+    EBAIL(dalloc(&e->F, n3));
+    EBAIL(dalloc(&e->F_tmp, n3));
+    EBAIL(dalloc(&e->xq, (size_t)total));
+    EBAIL(dalloc(&e->typ, (size_t)total));
+    EBAIL(dalloc(&e->drop_of, (size_t)total));
+    EBAIL(dalloc(&e->drops, (size_t)n_drops));
+    EBAIL(dalloc(&e->tabs, (size_t)n_drops));
+    EBAIL(dalloc(&e->unit0, (size_t)n_drops + 1));
+    EBAIL(dalloc(&e->d_step, 1));
+    EBAIL(dalloc(&e->d_flags, 1));
+    EBAIL(dalloc(&e->d_done, 1));
+    EBAIL(cudaMemcpy(e->x, xs.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+    EBAIL(cudaMemcpy(e->v, vs.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+    EBAIL(cudaMemcpy(e->typ, e->h_type.data(), sizeof(int) * (size_t)total,
+                     cudaMemcpyHostToDevice));
+    EBAIL(cudaMemcpy(e->drop_of, dof.data(), sizeof(int) * (size_t)total,
+                     cudaMemcpyHostToDevice));
+    EBAIL(cudaMemcpy(e->tabs, e->h_tabs.data(), sizeof(PairTab) * (size_t)n_drops,
+                     cudaMemcpyHostToDevice));
+    for (int i = 0; i < (int)total; ++i) {
+        const int d = dof[i];
+        const float q = (float)e->types[d][e->h_type[i]].charge;
+        xq0[i] = make_float4((float)xs[i], (float)xs[total + i], (float)xs[2 * total + i], q);
+    }
+    EBAIL(cudaMemcpy(e->xq, xq0.data(), sizeof(float4) * (size_t)total, cudaMemcpyHostToDevice));
+    EBAIL(cudaMemset(e->d_step, 0, sizeof(long long)));
+    EBAIL(cudaMemset(e->d_flags, 0, sizeof(int)));
+    EBAIL(cudaMemset(e->d_done, 0, sizeof(unsigned)));
+#undef EBAIL
+    rc = ens_autotune(e);
+    if (rc)
+        return bail(rc);
+    rc = ens_pass(e, MODE_FORCES, true, e->F, e->user);
+    if (rc)
+        return bail(rc);
+    if (cudaStreamSynchronize(e->user) != cudaSuccess)
+        return bail(set_err(NPSIM_ERR_CUDA, "initial forces failed"));
+    *out = e;
+    return NPSIM_OK;
+}
+
+void npsim_ens_destroy(npsim_ens_t e)
+{
+    if (!e)
+        return;
+    cudaStreamSynchronize(e->user);
+    delete e;
+}
+
+int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
+{
+    NP_REQUIRE(e, "ensemble is NULL");
+    NP_REQUIRE(n_steps >= 0, "n_steps must be >= 0");
+    int64_t rem = n_steps;
+    while (rem > 0) {
+        const int k = (int)std::min<int64_t>(rem, kChunk);
+        cudaGraphExec_t ex = nullptr;
+        int rc = ens_graph(e, k, &ex);
+        if (rc)
+            return rc;
+        NP_CUDA(cudaGraphLaunch(ex, e->user));
+        rem -= k;
+        e->step += k;
+    }
+    int h = 0;
+    NP_CUDA(cudaMemcpyAsync(&h, e->d_flags, sizeof(int), cudaMemcpyDeviceToHost, e->user));
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    if (h) {
+        NP_CUDA(cudaMemsetAsync(e->d_flags, 0, sizeof(int), e->user));
+        return set_err(NPSIM_ERR_NONFINITE, "a position became non-finite");
+    }
+    return NPSIM_OK;
+}
+
+int npsim_ens_get_state(npsim_ens_t e, int32_t d, double *x, double *v, double *F,
+                        int64_t *step)
+{
+    NP_REQUIRE(e && d >= 0 && d < e->D, "bad ensemble or droplet index");
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    const int n = e->cnt[d], off = e->off[d];
+    std::vector<double> buf((size_t)n);
+    double *src[3] = {e->x, e->v, e->F};
+    double *dst[3] = {x, v, F};
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k])
+            continue;
+        for (int c = 0; c < 3; ++c) {
+            NP_CUDA(cudaMemcpy(buf.data(), src[k] + (size_t)c * e->n_total + off,
+                               sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n; ++i)
+                dst[k][3 * (size_t)i + c] = buf[i];
+        }
+    }
+    if (step)
+        *step = e->step;
+    return NPSIM_OK;
+}
+
+int npsim_ens_forces(npsim_ens_t e, int32_t d, double *F)
+{
+    NP_REQUIRE(e && F && d >= 0 && d < e->D, "bad ensemble, droplet index or F");
+    int rc = ens_pass(e, MODE_FORCES, true, e->F_tmp, e->user);
+    if (rc)
+        return rc;
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    const int n = e->cnt[d], off = e->off[d];
+    std::vector<double> buf((size_t)n);
+    for (int c = 0; c < 3; ++c) {
+        NP_CUDA(cudaMemcpy(buf.data(), e->F_tmp + (size_t)c * e->n_total + off,
+                           sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i)
+            F[3 * (size_t)i + c] = buf[i];
+    }
+    return NPSIM_OK;
+}
+
+int npsim_ens_config(npsim_ens_t e, int *block, int *i_per_thread, int *j_tile, int *grid,
+                     int *index)
+{
+    NP_REQUIRE(e, "ensemble is NULL");
+    const ApConfig c = ens_config(e->shape);
+    if (block)
+        *block = c.block;
+    if (i_per_thread)
+        *i_per_thread = c.ki;
+    if (j_tile)
+        *j_tile = c.jt;
+    if (grid)
+        *grid = e->sk.grid;
+    if (index)
+        *index = e->shape;
+    return NPSIM_OK;
+}
+
+int npsim_ens_info(npsim_ens_t e, int64_t *n_total, double *pairs_per_step)
+{
+    NP_REQUIRE(e, "ensemble is NULL");
+    if (n_total)
+        *n_total = e->n_total;
+    if (pairs_per_step) {
+        double p = 0.0;
+        for (int d = 0; d < e->D; ++d)
+            p += (double)e->cnt[d] * (double)(e->cnt[d] - 1);
+        *pairs_per_step = p;
+    }
     return NPSIM_OK;
 }
 

@@ -198,6 +198,50 @@ struct IntArgs {
 cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
                              cudaStream_t st);
 
+// Ensemble of droplets (ensemble.cu).  Geometry depends on the launch shape:
+// n_it = ceil(n / itile), n_jt = ceil(n / jtile); row0 and unit0 are prefix sums
+// of n_it and n_it * n_jt over the droplets.
+struct EnsDrop {
+    int offset, n, n_it, n_jt, row0, rot_mode, wall, integrator;
+    long long unit0;
+    uint64_t seed;
+    double dt, R0, k_evap, g, omega2;
+    TypeCoef tc[NPSIM_MAX_TYPES];
+};
+
+struct EnsAllpairsArgs {
+    const float4 *xq;
+    const int *typ;
+    const EnsDrop *drops;
+    const long long *unit0; // n_drops + 1 entries
+    const PairTab *tabs;    // one table per droplet
+    int n_drops;
+    int pad_;
+    double *slots;
+};
+
+struct EnsIntArgs {
+    double *x, *v, *F;
+    const int *typ;
+    float4 *xq;
+    const int *drop_of;
+    const EnsDrop *drops;
+    const double *slots;
+    int ext_on;
+    int pad_;
+    long long *step;
+    int *flags;
+    unsigned *done;
+};
+
+int ens_num_configs();
+ApConfig ens_config(int idx);
+int ens_occupancy(int idx);
+cudaError_t launch_ens_allpairs(int idx, const StreamK &sk, const EnsAllpairsArgs &a,
+                                cudaStream_t st);
+cudaError_t launch_ens_integrate(int mode, const EnsIntArgs &a, int n_total, int n_drops,
+                                 const StreamK &sk, cudaStream_t st);
+
 // Cell list (celllist.cu)
 struct CellBufs {
     int *key, *rank, *count, *start, *sorted, *tile_sum;

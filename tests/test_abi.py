@@ -67,6 +67,7 @@ def test_struct_layouts_match_c(libpath, tmp_path):
         "npsim_params_t": [f[0] for f in P.npsim_params_t._fields_],
         "npsim_stats_cfg_t": [f[0] for f in P.npsim_stats_cfg_t._fields_],
         "npsim_stats_t": [f[0] for f in P.npsim_stats_t._fields_],
+        "npsim_droplet_t": [f[0] for f in P.npsim_droplet_t._fields_],
     }
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "npsim.h"',
              "int main(void){"]

@@ -1,0 +1,68 @@
+"""Batched ensemble of droplets of uneven N (one launch per force pass for all
+droplets) against the FP64 oracle and against single-droplet runs."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from gpu_helpers import FORCE_TOL, TRAJ_TOL, cutoff_ambiguous, force_error, library
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    return library()
+
+
+@pytest.fixture(scope="module")
+def drops():
+    scs = wl.ensemble_config(n_droplets=6, master_seed=7, n_min=300, n_max=3000)
+    out = []
+    for sc in scs:
+        types, x, v = wl.initial_state(sc, fp32_positions=True)
+        out.append((sc, x, v, types))
+    return out
+
+
+def test_ensemble_forces_match_oracle(P, drops):
+    with P.Ensemble(drops) as ens:
+        for d, (sc, x, v, types) in enumerate(drops):
+            F = ens.forces(d)
+            ref = oracle.total_forces(sc, x, types, 0.0)
+            amb = cutoff_ambiguous(x, types, sc)
+            err = force_error(F, ref)[~amb]
+            assert err.max() <= FORCE_TOL, (d, sc.n, float(err.max()))
+
+
+def test_ensemble_every_shape(P, drops, monkeypatch):
+    sc, x, v, types = drops[2]
+    ref = [oracle.total_forces(s, xx, tt, 0.0) for s, xx, _, tt in drops]
+    for idx in range(6):
+        monkeypatch.setenv("NPSIM_ENS_SHAPE", str(idx))
+        with P.Ensemble(drops) as ens:
+            assert ens.config()["index"] == idx
+            for d, (s, xx, vv, tt) in enumerate(drops):
+                amb = cutoff_ambiguous(xx, tt, s)
+                err = force_error(ens.forces(d), ref[d])[~amb]
+                assert err.max() <= FORCE_TOL, (idx, d, float(err.max()))
+
+
+def test_ensemble_trajectories_match_oracle_and_single_runs(P, drops):
+    steps = 60
+    with P.Ensemble(drops) as ens:
+        n_tot, pairs = ens.info()
+        assert n_tot == sum(len(d[1]) for d in drops)
+        assert pairs == sum(len(d[1]) * (len(d[1]) - 1) for d in drops)
+        ens.step(steps)
+        states = [ens.state(d) for d in range(len(drops))]
+    for d, (sc, x, v, types) in enumerate(drops):
+        xe, ve, Fe, st = states[d]
+        assert st == steps
+        xo, vo, Fo = oracle.run(sc, x, v, types, 0, steps)
+        assert np.abs(xe - xo).max() <= TRAJ_TOL, d
+        with P.Sim(sc, x, v, types) as sim:
+            sim.step(steps)
+            xs, vs, _, _ = sim.state()
+        # same physics, same Philox keys; only the float summation order differs
+        assert np.abs(xe - xs).max() <= 1e-8, d
