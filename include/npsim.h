@@ -245,6 +245,66 @@ int npsim_ens_info(npsim_ens_t ens, int64_t *n_total, double *pairs_per_step);
 
 void npsim_ens_destroy(npsim_ens_t ens);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate (no counterpart in the paper): a deep ensemble of n_nets
+ * multilayer perceptrons, n_in inputs -> n_layers hidden layers of n_hidden
+ * units with SiLU -> n_out outputs, mapping scenario parameters to statistics
+ * of the final aggregate (fractal dimension, RDF bins).  BF16 weights and
+ * activations, FP32 accumulation on the tcgen05 tensor cores, FP32 master
+ * weights trained with AdamW by the library's own forward and backward
+ * kernels.  Inputs and targets are standardised with npsim_surr_set_norm.
+ * Host arrays are row-major float32 (samples x features).  The library owns the
+ * object and its device memory; calls use the object's own stream and return
+ * after synchronising it.
+ */
+typedef struct npsim_surr *npsim_surr_t;
+
+/* Shape limits: n_in <= 64, n_hidden in [16, 256] step 16, 1..8 hidden layers,
+ * n_out <= 256, 1..64 networks.  Weights: He-uniform from `seed`, biases 0. */
+int npsim_surr_create(int32_t n_in, int32_t n_hidden, int32_t n_layers, int32_t n_out,
+                      int32_t n_nets, uint64_t seed, npsim_surr_t *out);
+void npsim_surr_destroy(npsim_surr_t s);
+
+/* Standardisation x' = (x - x_mean) / x_std, y' = (y - y_mean) / y_std (NULL =
+ * 0 mean / unit std).  Standard deviations must be positive. */
+int npsim_surr_set_norm(npsim_surr_t s, const float *x_mean, const float *x_std,
+                        const float *y_mean, const float *y_std);
+
+/* Parameters of one network as a flat float32 vector: for each layer in order
+ * W (out_pad x in_pad, row-major; in_pad = n_in or n_hidden rounded up to 16,
+ * out_pad = n_hidden or n_out rounded up to 16) then b (out_pad).  Padded
+ * entries are zero.  get also returns the last computed gradients (either
+ * pointer may be NULL). */
+int npsim_surr_param_count(npsim_surr_t s, int64_t *count);
+int npsim_surr_get_params(npsim_surr_t s, int32_t net, float *flat, float *grads);
+int npsim_surr_set_params(npsim_surr_t s, int32_t net, const float *flat);
+
+/* Test hook: forward and backward pass of network `net` on B samples (X: B x n_in,
+ * Y: B x n_out, raw units), no update.  Mean-squared error over the
+ * standardised outputs; gradients in the flat layout (param_count floats);
+ * loss and the standardised prediction Yhat (B x n_out) optional. */
+int npsim_surr_grads(npsim_surr_t s, int32_t net, const float *X, const float *Y, int32_t B,
+                     float *grads, float *loss, float *Yhat);
+
+/* Train every network of the ensemble for `epochs` passes over n_samples samples
+ * with AdamW (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay wd on weights),
+ * minibatches of `batch`, each network with its own shuffled order.  final_loss
+ * (optional): loss of the last minibatch. */
+int npsim_surr_train(npsim_surr_t s, const float *X, const float *Y, int32_t n_samples,
+                     int32_t epochs, int32_t batch, float lr, float wd, uint64_t shuffle_seed,
+                     float *final_loss);
+
+/* Predict B samples: mean over the networks (B x n_out, raw units) and the
+ * spread, the standard deviation across networks (B x n_out, may be NULL). */
+int npsim_surr_predict(npsim_surr_t s, const float *X, int32_t B, float *Y_mean,
+                       float *Y_spread);
+
+/* Test hook: C = A B^T on the tcgen05 GEMM kernel for host BF16 matrices (bit
+ * patterns; A: M x K, B: N x K, row-major), C: M x N float32.  N, K and n_tile
+ * must be multiples of 16, n_tile <= 256. */
+int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
+                    int32_t n_tile, float *C);
+
 /*
  * All-pairs Coulomb forces without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc when

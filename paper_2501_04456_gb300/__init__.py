@@ -119,6 +119,21 @@ def lib():
             L.npsim_ens_info.argtypes = [_h, _i64, _d]
             L.npsim_ens_destroy.argtypes = [_h]
             L.npsim_ens_destroy.restype = None
+            _f = C.POINTER(C.c_float)
+            L.npsim_surr_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                            C.c_int32, C.c_uint64, C.POINTER(_h)]
+            L.npsim_surr_destroy.argtypes = [_h]
+            L.npsim_surr_destroy.restype = None
+            L.npsim_surr_set_norm.argtypes = [_h, _f, _f, _f, _f]
+            L.npsim_surr_param_count.argtypes = [_h, _i64]
+            L.npsim_surr_get_params.argtypes = [_h, C.c_int32, _f, _f]
+            L.npsim_surr_set_params.argtypes = [_h, C.c_int32, _f]
+            L.npsim_surr_grads.argtypes = [_h, C.c_int32, _f, _f, C.c_int32, _f, _f, _f]
+            L.npsim_surr_train.argtypes = [_h, _f, _f, C.c_int32, C.c_int32, C.c_int32,
+                                           C.c_float, C.c_float, C.c_uint64, _f]
+            L.npsim_surr_predict.argtypes = [_h, _f, C.c_int32, _f, _f]
+            L.npsim_gemm_bf16.argtypes = [C.POINTER(C.c_uint16), C.POINTER(C.c_uint16),
+                                          C.c_int32, C.c_int32, C.c_int32, C.c_int32, _f]
             L.npsim_chunk_steps.argtypes = [_h, _i32]
             L.npsim_profile.argtypes = [_h, C.c_int]
             L.npsim_kernel_times.argtypes = [_h, _d, _i32]
@@ -499,6 +514,108 @@ class Ensemble:
     def close(self):
         if getattr(self, "h", None):
             npsim_ens_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# --------------------------------------------------------------------------
+# Learned surrogate (deep ensemble of MLPs on the tcgen05 tensor cores)
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a if shape is None else a.reshape(shape)
+
+
+def npsim_gemm_bf16(A_bits, B_bits, n_tile=64):
+    """C = A B^T on the tensor-core GEMM; A (M x K), B (N x K) uint16 BF16 bit patterns."""
+    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    M, K = A.shape
+    N = B.shape[0]
+    Cm = np.zeros((M, N), np.float32)
+    _check(lib().npsim_gemm_bf16(_p(A, C.c_uint16), _p(B, C.c_uint16), M, N, K, n_tile,
+                                 _p(Cm, C.c_float)))
+    return Cm
+
+
+class Surrogate:
+    """Deep ensemble of MLPs: n_in -> n_layers x n_hidden (SiLU) -> n_out."""
+
+    def __init__(self, n_in=8, n_hidden=256, n_layers=4, n_out=65, n_nets=4, seed=0):
+        self.n_in, self.n_out, self.n_nets = n_in, n_out, n_nets
+        self.h = _h()
+        _check(lib().npsim_surr_create(n_in, n_hidden, n_layers, n_out, n_nets,
+                                       C.c_uint64(seed), C.byref(self.h)))
+        c = C.c_int64()
+        _check(lib().npsim_surr_param_count(self.h, C.byref(c)))
+        self.n_params = c.value
+
+    def set_norm(self, x_mean=None, x_std=None, y_mean=None, y_std=None):
+        args = []
+        keep = []
+        for v, n in ((x_mean, self.n_in), (x_std, self.n_in), (y_mean, self.n_out),
+                     (y_std, self.n_out)):
+            if v is None:
+                args.append(None)
+            else:
+                a = _f32(v).reshape(n)
+                keep.append(a)
+                args.append(_p(a, C.c_float))
+        _check(lib().npsim_surr_set_norm(self.h, *args))
+
+    def get_params(self, net=0):
+        p = np.zeros(self.n_params, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        _check(lib().npsim_surr_get_params(self.h, net, _p(p, C.c_float), _p(g, C.c_float)))
+        return p, g
+
+    def set_params(self, net, flat):
+        f = _f32(flat).reshape(self.n_params)
+        _check(lib().npsim_surr_set_params(self.h, net, _p(f, C.c_float)))
+
+    def grads(self, net, X, Y):
+        X = _f32(X, (-1, self.n_in))
+        Y = _f32(Y, (-1, self.n_out))
+        B = X.shape[0]
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        yh = np.zeros((B, self.n_out), np.float32)
+        _check(lib().npsim_surr_grads(self.h, net, _p(X, C.c_float), _p(Y, C.c_float), B,
+                                      _p(g, C.c_float), C.byref(loss), _p(yh, C.c_float)))
+        return g, loss.value, yh
+
+    def train(self, X, Y, epochs=10, batch=512, lr=1e-3, wd=1e-4, seed=0):
+        X = _f32(X, (-1, self.n_in))
+        Y = _f32(Y, (-1, self.n_out))
+        loss = C.c_float()
+        _check(lib().npsim_surr_train(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0],
+                                      epochs, batch, lr, wd, C.c_uint64(seed), C.byref(loss)))
+        return loss.value
+
+    def predict(self, X):
+        X = _f32(X, (-1, self.n_in))
+        B = X.shape[0]
+        m = np.zeros((B, self.n_out), np.float32)
+        sp = np.zeros((B, self.n_out), np.float32)
+        _check(lib().npsim_surr_predict(self.h, _p(X, C.c_float), B, _p(m, C.c_float),
+                                        _p(sp, C.c_float)))
+        return m, sp
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().npsim_surr_destroy(self.h)
             self.h = None
 
     def __del__(self):

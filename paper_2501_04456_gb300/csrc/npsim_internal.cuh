@@ -2,6 +2,7 @@
 // CUDA translation units (never by the CPU oracle).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -241,6 +242,46 @@ cudaError_t launch_ens_allpairs(int idx, const StreamK &sk, const EnsAllpairsArg
                                 cudaStream_t st);
 cudaError_t launch_ens_integrate(int mode, const EnsIntArgs &a, int n_total, int n_drops,
                                  const StreamK &sk, cudaStream_t st);
+
+// BF16 tensor-core MLP kernels (mlp.cu).
+enum : int {
+    GEMM_F32 = 0,  // C (FP32) = A B^T (+ bias)
+    GEMM_ACT = 1,  // z = A B^T + bias -> Z (FP32, optional); C (BF16) = SiLU(z) or z
+    GEMM_DACT = 2, // C (BF16, and FP32 if Cf) = (A B^T) * SiLU'(Z)
+};
+
+struct GemmArgs {
+    const __nv_bfloat16 *A; // M x K, row-major, lda
+    const __nv_bfloat16 *B; // N x K, row-major, ldb
+    int M, N, K, lda, ldb, ldc;
+    int n_tile;    // columns per CTA (multiple of 16, <= 256)
+    int tmem_cols; // power of two >= max(32, n_tile)
+    int mode, act;
+    const float *bias;      // N or NULL
+    float *Cf;              // FP32 output (M x N, ldc) or NULL
+    __nv_bfloat16 *Cb;      // BF16 output or NULL
+    float *Z;               // pre-activation (GEMM_ACT writes, GEMM_DACT reads), ldc
+    int *flags;             // FLAG_TIMEOUT on a bounded wait that expired
+};
+
+struct AdamArgs {
+    float lr, b1, b2, eps, wd, bc1, bc2; // bc = 1 - beta^t
+};
+
+int gemm_smem_bytes(int n_tile);
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t st);
+cudaError_t launch_transpose_bf16(const void *in, int R, int C, int ldi, void *out, int ldo,
+                                  cudaStream_t st);
+cudaError_t launch_mse_grad(const float *y, const float *t, const float *w, int M, int m_valid,
+                            int n_valid, int ldy, float *gf, void *gb, float *loss,
+                            cudaStream_t st);
+cudaError_t launch_colsum(const float *G, int M, int N, int ld, float *out, cudaStream_t st);
+cudaError_t launch_adamw(float *w, const float *g, float *m, float *v, int rows, int cols,
+                         const AdamArgs &a, void *wb, void *wt, const unsigned char *mask,
+                         cudaStream_t st);
+cudaError_t launch_f32_to_bf16(const float *x, int n, void *y, cudaStream_t st);
+cudaError_t launch_weights_bf16(const float *w, int rows, int cols, void *wb, void *wt,
+                                cudaStream_t st);
 
 // Cell list (celllist.cu)
 struct CellBufs {
