@@ -45,6 +45,7 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-skip", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-surrogate", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -274,6 +275,27 @@ def _ensemble_measure(P, torch, stream, steps, warmup, n_plain=16, steps_per_dro
             "speedup_vs_plain": ens_dps / plain_dps}
 
 
+def _surrogate_measure(P, batch=4096, n_nets=4, reps=7):
+    """Inference of the surrogate (deep ensemble of 4 MLPs 8 -> 4 x 256 -> 65, BF16
+    tcgen05 kernels) at batch 4096 through npsim_surr_predict: host inputs in,
+    mean and spread out (host copies included)."""
+    import numpy as np
+    X = np.random.default_rng(0).standard_normal((batch, 8)).astype(np.float32)
+    with P.Surrogate(8, 256, 4, 65, n_nets=n_nets, seed=0) as s:
+        s.predict(X)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            s.predict(X)
+            ts.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.median(ts)
+    flops = 2.0 * batch * (16 * 256 + 3 * 256 * 256 + 256 * 80) * n_nets
+    return {"batch": batch, "nets": n_nets, "ms_per_batch": ms,
+            "predictions_per_s": batch / (ms * 1e-3),
+            "tflops_with_host_copies": flops / (ms * 1e-3) / 1e12,
+            "note": "weights untrained: inference cost does not depend on them"}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -385,6 +407,10 @@ def run_ours(a):
     if not a.no_ensemble and rank == 0:
         ens = _ensemble_measure(P, torch, stream, max(3, a.steps // 2), a.warmup)
 
+    surr = None
+    if not a.no_surrogate and rank == 0:
+        surr = _surrogate_measure(P)
+
     # end to end through the C ABI with host buffers: create from host arrays,
     # then per step one step and a device->host read of the positions
     e2e = None
@@ -440,6 +466,7 @@ def run_ours(a):
                                                                max_mhz)) if clk else None},
             "skip_neutral": skip,
             "ensemble": ens,
+            "surrogate": surr,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
