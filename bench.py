@@ -46,6 +46,8 @@ def _args():
     ap.add_argument("--no-skip", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-surrogate", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--case", default="step", choices=["step", "integrator", "surrogate"],
+                    help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -477,8 +479,48 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+def run_integrator_case(a):
+    """Profiling case: the integrator alone (no pair forces) on a.n free NPs of the
+    paper-scale composition in a droplet with its interface spring, so that the
+    state is larger than L2 for a.n >= 1e6.  Prints the mean step time."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_2501_04456_gb300 import build as _b
+    _b.build()
+    import paper_2501_04456_gb300 as P
+    sc = dataclasses.replace(_scenario(a.n, 0), coulomb=False, lj_mode=0)
+    types = wl.assign_types(sc)
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal((sc.n, 3))
+    x = v / np.linalg.norm(v, axis=1, keepdims=True) * (sc.R0 * rng.random(sc.n) ** (1 / 3))[:, None]
+    stream = torch.cuda.current_stream()
+    with P.Sim(sc, x, None, types, stream=stream) as sim:
+        sim.profile(True)
+        sim.step(a.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(a.steps)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / a.steps
+        kt, k = sim.kernel_times()
+    print(json.dumps({"case": "integrator", "n": sc.n, "ms_per_step": 1e3 * dt,
+                      "integrate_ms": kt["integrate"], "samples": k}), flush=True)
+
+
 def main():
     a = _args()
+    if a.case == "integrator":
+        run_integrator_case(a)
+        return
+    if a.case == "surrogate":
+        from paper_2501_04456_gb300 import build as _b
+        _b.build()
+        import paper_2501_04456_gb300 as P
+        print(json.dumps({"case": "surrogate", **_surrogate_measure(P, reps=a.steps)}),
+              flush=True)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:
