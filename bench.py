@@ -206,17 +206,26 @@ def _peaks():
         return {}
 
 
-def _traffic_from_profile(kernel_src):
-    """dram bytes per launch recorded by the committed ncu summary, if it was taken
-    on the current all-pairs source (else null)."""
+def kernel_source_hash(packed):
+    """sha256[:16] of the all-pairs kernel source a launch shape runs (its .cu file
+    followed by the shared device header)."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2501_04456_gb300", "csrc")
+    name = "allpairs_grouped.cu" if packed == 2 else "allpairs.cu"
+    src = b"".join(open(os.path.join(csrc, f), "rb").read()
+                   for f in (name, "npsim_internal.cuh"))
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def _traffic_from_profile(packed):
+    """dram bytes per launch recorded by the committed ncu summary, if it was taken
+    on the current source of the all-pairs kernel in use (else null)."""
     path = os.path.join(ROOT, "profiles", "allpairs_paper_scale250000.md")
     try:
         txt = open(path).read()
-        src = open(kernel_src, "rb").read()
+        h = kernel_source_hash(packed)
     except OSError:
         return None
-    h = hashlib.sha256(src).hexdigest()[:16]
     m_h = re.search(r"source sha256\[:16\]:\s*([0-9a-f]{16})", txt)
     m_t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
     if m_h and m_t and m_h.group(1) == h:
@@ -376,8 +385,7 @@ def run_ours(a):
     peak_tflops = info["sm_count"] * 128 * 2 * max_mhz * 1e6 / 1e12
     ap_avg = sum(ap_ms) / len(ap_ms)
     achieved = FLOPS_PER_PAIR * pairs_per_step / (ap_avg * 1e-3) / 1e12
-    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2501_04456_gb300", "csrc",
-                                                 "allpairs.cu"))
+    traffic = _traffic_from_profile(cfg.get("packed", 0))
 
     # the same workload with the neutral NPs left out of the Coulomb sum (their
     # Coulomb terms are exactly zero): reported beside the headline, which sums
@@ -448,7 +456,9 @@ def run_ours(a):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 pair math, f64 accumulation and integration",
+            "dtype": "f32",
+            "precision": "f32 pair math; compensated f32 (hi + lo) force accumulation and "
+                         "positions; f32 velocities",
             "data": "synthetic (seeded placement in the droplet, Maxwell velocities)",
             "config": {"workload": sc.name, "n_particles": n, "types": 3,
                        "forces": "all-pairs Coulomb + cell-list LJ 2.5 sigma_ab",

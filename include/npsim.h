@@ -46,8 +46,8 @@ enum {
     NPSIM_ERR_NO_DEVICE = -7    /* no CUDA device, or not an sm_103 device */
 };
 
-/* Per-type NP properties (Sec. 2.1: "radius, mass, charge"; a spring constant of
- * the interface per NP type; friction from Stokes' law). */
+/* Per-type NP properties (Sec. 2.1: each NP type has its own size, mass and
+ * charge, and its own interface spring constant; friction from Stokes' law). */
 typedef struct {
     double sigma;  /* diameter; LJ length of the like pair; radius = sigma/2 */
     double eps;    /* LJ well depth of the like pair */
@@ -90,9 +90,9 @@ const char *npsim_last_error(void);
 int npsim_device_info(int *sm_count, int *clock_khz, int *cc_major, int *cc_minor);
 
 /*
- * Create a simulation of n NPs (Sec. 2.1: NPs "initially randomly distributed in
- * a sphere"; the caller supplies the initial state so that runs are
- * reproducible).  x0: n x 3 positions; v0: n x 3 velocities or NULL (zero);
+ * Create a simulation of n NPs (Sec. 2.1 starts from NPs placed at random
+ * inside the droplet sphere; the caller supplies the initial state so that
+ * runs are reproducible).  x0: n x 3 positions; v0: n x 3 velocities or NULL (zero);
  * type: n type indices.  Pair parameters follow Lorentz-Berthelot mixing,
  * sigma_ab = (sigma_a + sigma_b)/2, unless params->eps_override is set
  * (Table 1 prints such a matrix).  The initial total force F(x0, t=0) is
@@ -119,7 +119,10 @@ void npsim_destroy(npsim_sim_t sim);
 int npsim_step(npsim_sim_t sim, int64_t n_steps);
 
 /* Copy the state to host arrays (any may be NULL): x, v (n x 3), F (n x 3 total
- * force at x and the current time), *step (steps taken since t = 0). */
+ * force at x and the current time), *step (steps taken since t = 0).  On the
+ * device a position is kept as a pair of float32 words (hi + lo, about 48
+ * significant bits), a velocity as float32 and a force as a float32 (hi, lo)
+ * pair; x and F are returned as the float64 sums of their pairs. */
 int npsim_get_state(npsim_sim_t sim, double *x, double *v, double *F, int64_t *step);
 
 /* Replace the state (x required, v may be NULL = zero) and set the step counter;
@@ -168,10 +171,13 @@ int npsim_stats(npsim_sim_t sim, const npsim_stats_cfg_t *cfg, int64_t *rdf_coun
                 double *rdf_g, int64_t *radial_counts, double *radial_c,
                 npsim_stats_t *out);
 
-/* Checkpoint (Sec. 2.2: "stopped and restarted with different parameters from
- * the saved NPs configuration"): positions, velocities, types, step counter and
- * parameters.  npsim_load creates a new object; params_override (or NULL)
- * replaces the saved scenario parameters, types_override likewise. */
+/* Checkpoint (Sec. 2.2: a run can be halted and resumed from its saved NP
+ * configuration, possibly with other parameters): the raw state words
+ * (position hi and lo float32 words, float32 velocities), types, step counter
+ * and parameters, so that a resumed run is bit-identical to an uninterrupted
+ * one.  npsim_load creates a new object; params_override (or NULL) replaces
+ * the saved scenario parameters, types_override likewise.  Errors: IO (file
+ * cannot be opened, is truncated or is not a checkpoint of this format). */
 int npsim_save(npsim_sim_t sim, const char *path);
 int npsim_load(const char *path, const npsim_type_t *types_override,
                const npsim_params_t *params_override, void *stream, npsim_sim_t *out);

@@ -1,7 +1,7 @@
 /*
  * oracle.c -- FP64 CPU oracle of the Langevin nanoparticle-aggregation step
- * (Derkachov et al., arXiv 2501.04456, "A numerical toy model of Langevin
- * dynamics ...").
+ * (arXiv 2501.04456, a Langevin-dynamics model of nanoparticle aggregation in
+ * an evaporating droplet).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
  * GPU library is checked against.  Only the test suite, the smoke check and
@@ -127,8 +127,8 @@ void or_normals(uint64_t seed, int64_t step, uint32_t purpose, int64_t n,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Per type-pair interaction table (Sec. 2.1: interactions "within each NP
- * type and between types can be freely set"; Table 1 prints an epsilon
+/* Per type-pair interaction table (Sec. 2.1: the like and unlike type pairs
+ * each have their own interaction parameters; Table 1 prints an epsilon
  * matrix).  Default mixing is Lorentz-Berthelot: sigma_ab = (sigma_a +
  * sigma_b)/2, eps_ab = sqrt(eps_a eps_b); an explicit T x T epsilon matrix
  * replaces the eps rule.  The LJ cutoff is lj_cut * sigma_ab.              */

@@ -16,7 +16,7 @@
 //  * each j-tile's float32 partial is added into a (hi, lo) TwoSum pair, so the
 //    per-particle accumulation is compensated (FP32 pair math, ~FP64 sum);
 //  * the (i-tile x j-tile) work is split evenly over exactly `grid` CTAs
-//    (stream-K); each CTA writes one float64 partial per i-tile row it
+//    (stream-K); each CTA writes one compensated (hi, lo) float32 partial per i-tile row it
 //    touches, and the integrator sums the (at most a few) partials of a row in
 //    CTA order -- deterministic, and balanced to one tile for any N.
 #include "npsim_internal.cuh"
@@ -32,7 +32,7 @@ constexpr float kFar = 1.0e15f;      // padding position for ragged tiles
 template <int BLOCK, int KI, int JT, bool LJ>
 __global__ void __launch_bounds__(BLOCK)
 k_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
-           StreamK sk, const PairTab *__restrict__ tab, double *__restrict__ slots)
+           StreamK sk, const PairTab *__restrict__ tab, float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
     __shared__ float4 s_x[JT];
@@ -130,13 +130,16 @@ k_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
             }
         }
 
-        double *slot = slots + (size_t)(r + c) * 3 * ITILE;
+        float *slot = slots + (size_t)(r + c) * 6 * ITILE; // (hi x, y, z, lo x, y, z)
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
             const int idx = k * BLOCK + threadIdx.x;
-            slot[idx] = (double)hx[k] + (double)lx[k];
-            slot[ITILE + idx] = (double)hy[k] + (double)ly[k];
-            slot[2 * ITILE + idx] = (double)hz[k] + (double)lz[k];
+            slot[idx] = hx[k];
+            slot[ITILE + idx] = hy[k];
+            slot[2 * ITILE + idx] = hz[k];
+            slot[3 * ITILE + idx] = lx[k];
+            slot[4 * ITILE + idx] = ly[k];
+            slot[5 * ITILE + idx] = lz[k];
         }
         p += jt1 - jt0;
     }
@@ -151,7 +154,7 @@ k_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
 // one FADD2 with the i coordinate duplicated in both lanes.
 template <int BLOCK, int KI, int JT>
 __global__ void __launch_bounds__(BLOCK)
-k_coulomb_x2(const float4 *__restrict__ xq, int n, StreamK sk, double *__restrict__ slots)
+k_coulomb_x2(const float4 *__restrict__ xq, int n, StreamK sk, float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
     constexpr int JP = JT / 2;
@@ -232,13 +235,16 @@ k_coulomb_x2(const float4 *__restrict__ xq, int n, StreamK sk, double *__restric
             }
         }
 
-        double *slot = slots + (size_t)(r + c) * 3 * ITILE;
+        float *slot = slots + (size_t)(r + c) * 6 * ITILE; // (hi x, y, z, lo x, y, z)
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
             const int idx = k * BLOCK + threadIdx.x;
-            slot[idx] = (double)hx[k] + (double)lx[k];
-            slot[ITILE + idx] = (double)hy[k] + (double)ly[k];
-            slot[2 * ITILE + idx] = (double)hz[k] + (double)lz[k];
+            slot[idx] = hx[k];
+            slot[ITILE + idx] = hy[k];
+            slot[2 * ITILE + idx] = hz[k];
+            slot[3 * ITILE + idx] = lx[k];
+            slot[4 * ITILE + idx] = ly[k];
+            slot[5 * ITILE + idx] = lz[k];
         }
         p += jt1 - jt0;
     }
@@ -269,7 +275,7 @@ const Entry kEntries[] = {
 
 template <int B, int K, int J>
 cudaError_t launch_one(bool lj, const StreamK &sk, const float4 *xq, const int *typ, int n,
-                       const PairTab *tab, double *slots, cudaStream_t st)
+                       const PairTab *tab, float *slots, cudaStream_t st)
 {
     if (lj)
         k_allpairs<B, K, J, true><<<sk.grid, B, 0, st>>>(xq, typ, n, sk, tab, slots);
@@ -279,7 +285,7 @@ cudaError_t launch_one(bool lj, const StreamK &sk, const float4 *xq, const int *
 }
 
 template <int B, int K, int J>
-cudaError_t launch_x2(bool lj, const StreamK &sk, const float4 *xq, int n, double *slots,
+cudaError_t launch_x2(bool lj, const StreamK &sk, const float4 *xq, int n, float *slots,
                       cudaStream_t st)
 {
     if (lj)
@@ -309,7 +315,7 @@ int ap_occupancy(int idx, bool lj)
 }
 
 cudaError_t launch_allpairs(int idx, bool lj, const StreamK &sk, const float4 *xq,
-                            const int *typ, int n, const PairTab *tab, double *slots,
+                            const int *typ, int n, const PairTab *tab, float *slots,
                             cudaStream_t st)
 {
     switch (idx) {

@@ -18,7 +18,7 @@
 // rows and columns to the charged groups, since every Coulomb term with a
 // neutral particle is exactly zero.  The (row tile x column tile) units are
 // split over the CTAs as in the other all-pairs kernels (stream-K), one
-// float64 partial per (row, CTA) written to slot row + CTA.
+// compensated (hi, lo) float32 partial per (row, CTA) written to slot row + CTA.
 #include "npsim_internal.cuh"
 
 namespace npsim {
@@ -31,7 +31,7 @@ constexpr float kPad = 1.0e18f;    // padding: far enough that 1/r^3 underflows 
 template <int BLOCK, int KI, int JT>
 __global__ void __launch_bounds__(BLOCK)
 k_coulomb_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_perm,
-              const float *__restrict__ qblk, StreamK sk, double *__restrict__ slots)
+              const float *__restrict__ qblk, StreamK sk, float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
     constexpr int JP = JT / 2;
@@ -113,13 +113,16 @@ k_coulomb_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n
             }
         }
 
-        double *slot = slots + (size_t)(r + c) * 3 * ITILE;
+        float *slot = slots + (size_t)(r + c) * 6 * ITILE; // (hi x, y, z, lo x, y, z)
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
             const int idx = k * BLOCK + threadIdx.x;
-            slot[idx] = (double)hx[k] + (double)lx[k];
-            slot[ITILE + idx] = (double)hy[k] + (double)ly[k];
-            slot[2 * ITILE + idx] = (double)hz[k] + (double)lz[k];
+            slot[idx] = hx[k];
+            slot[ITILE + idx] = hy[k];
+            slot[2 * ITILE + idx] = hz[k];
+            slot[3 * ITILE + idx] = lx[k];
+            slot[4 * ITILE + idx] = ly[k];
+            slot[5 * ITILE + idx] = lz[k];
         }
         p += jt1 - jt0;
     }
@@ -140,7 +143,7 @@ const GEntry kGrp[] = {
 
 template <int B, int K, int J>
 cudaError_t launch_g(const StreamK &sk, const float4 *xq, const int *perm, int n_perm,
-                     const float *qblk, double *slots, cudaStream_t st)
+                     const float *qblk, float *slots, cudaStream_t st)
 {
     k_coulomb_grp<B, K, J><<<sk.grid, B, 0, st>>>(xq, perm, n_perm, qblk, sk, slots);
     return cudaGetLastError();
@@ -163,7 +166,7 @@ int grp_occupancy(int idx)
 
 cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq,
                                     const int *perm, int n_perm, const float *qblk,
-                                    double *slots, cudaStream_t st)
+                                    float *slots, cudaStream_t st)
 {
     switch (idx) {
     case 0: return launch_g<512, 2, 512>(sk, xq, perm, n_perm, qblk, slots, st);

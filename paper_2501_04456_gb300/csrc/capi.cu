@@ -98,9 +98,11 @@ void fill_streamk(StreamK &sk, int n, const ApConfig &c, int grid_target)
     sk.pad_ = 0;
 }
 
-size_t slots_doubles(const StreamK &sk)
+// Floats of stream-K partial slots: one slot per (i-tile row, CTA) pair a row
+// can meet, each (hi x, y, z, lo x, y, z) x itile.
+size_t slots_floats(const StreamK &sk)
 {
-    return (size_t)(sk.n_it + sk.grid) * 3 * (size_t)sk.itile;
+    return (size_t)(sk.n_it + sk.grid) * 6 * (size_t)sk.itile;
 }
 
 } // namespace
@@ -130,11 +132,15 @@ struct npsim_sim {
 
     cudaStream_t user = nullptr, cap = nullptr;
 
-    double *x = nullptr, *v = nullptr, *F = nullptr, *F_tmp = nullptr;
+    // State: position = xq.xyz (hi words) + x_lo; velocity and force in float32,
+    // forces as (hi, lo) pairs.  x is float64 scratch for uploads and statistics.
+    double *x = nullptr;                  // [3][n]
+    float *x_lo = nullptr, *v = nullptr;  // [3][n]
+    float *F = nullptr, *F_tmp = nullptr; // [6][n]
     float4 *xq = nullptr;
     int *typ = nullptr;
-    double *slots = nullptr;
-    double *F_lj = nullptr;
+    float *slots = nullptr;
+    float *F_lj = nullptr;                // [6][n]
     PairTab *tab_full = nullptr, *tab_lj = nullptr;
     long long *d_step = nullptr;
     int *d_flags = nullptr;
@@ -186,6 +192,7 @@ struct npsim_sim {
                     if (ev[j][k][e])
                         cudaEventDestroy(ev[j][k][e]);
         dfree(x);
+        dfree(x_lo);
         dfree(v);
         dfree(F);
         dfree(F_tmp);
@@ -294,7 +301,7 @@ void shape_streamk(const npsim_sim *s, int k, int grid_target, StreamK &sk)
 }
 
 cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, const StreamK &sk,
-                         const PairTab *tab, double *slots, cudaStream_t st)
+                         const PairTab *tab, float *slots, cudaStream_t st)
 {
     if (shape_grouped(k))
         return launch_allpairs_grouped(k - ap_num_configs(), sk, s->xq, s->perm, s->n_perm,
@@ -306,7 +313,7 @@ cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, const StreamK &sk,
 // Kernel groups timed by npsim_kernel_times.
 enum { KG_ALLPAIRS = 0, KG_CELL_BUILD = 1, KG_CELL_LJ = 2, KG_INTEGRATE = 3 };
 
-int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext, double *Fout,
+int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext, float *Fout,
                  cudaStream_t st, int prof_slot = -1)
 {
     const bool lj_cell = want_lj && s->cell;
@@ -340,7 +347,7 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
         NP_CUDA(mark(KG_ALLPAIRS, 1));
     }
     IntArgs a{};
-    a.x = s->x;
+    a.x_lo = s->x_lo;
     a.v = s->v;
     a.F = Fout;
     a.typ = s->typ;
@@ -363,7 +370,7 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
 int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
 {
     IntArgs a{};
-    a.x = s->x;
+    a.x_lo = s->x_lo;
     a.v = s->v;
     a.F = s->F;
     a.typ = s->typ;
@@ -464,9 +471,9 @@ int autotune(npsim_sim *s)
                 continue;
             StreamK sk;
             shape_streamk(s, c, occ * s->sms, sk);
-            need = std::max(need, slots_doubles(sk));
+            need = std::max(need, slots_floats(sk));
         }
-        double *tmp = nullptr;
+        float *tmp = nullptr;
         NP_CUDA(dalloc(&tmp, need));
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -589,6 +596,58 @@ void to_aos(const std::vector<double> &soa, int n, double *aos)
             aos[3 * (size_t)i + d] = soa[(size_t)d * n + i];
 }
 
+// Device float32 array -> host float64 vector (count values).
+int fetch_f32(const float *d, size_t count, std::vector<double> &out)
+{
+    std::vector<float> h(count);
+    NP_CUDA(cudaMemcpy(h.data(), d, sizeof(float) * count, cudaMemcpyDeviceToHost));
+    out.assign(h.begin(), h.end());
+    return NPSIM_OK;
+}
+
+// Forces [6][n] as (hi, lo) float pairs -> float64 SoA [3][n].
+int fetch_hilo(const float *d, int n, std::vector<double> &soa)
+{
+    std::vector<double> h;
+    int rc = fetch_f32(d, 6 * (size_t)n, h);
+    if (rc)
+        return rc;
+    soa.resize(3 * (size_t)n);
+    for (size_t k = 0; k < 3 * (size_t)n; ++k)
+        soa[k] = h[k] + h[3 * (size_t)n + k];
+    return NPSIM_OK;
+}
+
+// Host float64 SoA -> device float32 (rounded to nearest).
+int put_f32(const std::vector<double> &src, float *d, cudaStream_t st)
+{
+    std::vector<float> h(src.begin(), src.end());
+    NP_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+    NP_CUDA(cudaStreamSynchronize(st));
+    return NPSIM_OK;
+}
+
+// Positions in float64 (hi + lo of every coordinate) into s->x.
+int positions_f64(npsim_sim *s)
+{
+    NP_CUDA(launch_positions_f64(s->xq, s->x_lo, s->n, s->x, s->user));
+    return NPSIM_OK;
+}
+
+// Set the step counter and recompute the forces of the current state.
+int finish_upload(npsim_sim *s, int64_t step)
+{
+    long long st = step;
+    NP_CUDA(cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice,
+                            s->user));
+    int rc = enqueue_pass(s, MODE_FORCES, true, true, true, s->F, s->user);
+    if (rc)
+        return rc;
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    s->step = step;
+    return read_flags(s);
+}
+
 int upload_state(npsim_sim *s, const double *x, const double *v, int64_t step)
 {
     std::vector<double> buf;
@@ -598,22 +657,29 @@ int upload_state(npsim_sim *s, const double *x, const double *v, int64_t step)
     NP_CUDA(cudaStreamSynchronize(s->user));
     if (v) {
         to_soa(v, s->n, buf);
-        NP_CUDA(cudaMemcpyAsync(s->v, buf.data(), sizeof(double) * buf.size(),
-                                cudaMemcpyHostToDevice, s->user));
-        NP_CUDA(cudaStreamSynchronize(s->user));
+        int rc = put_f32(buf, s->v, s->user);
+        if (rc)
+            return rc;
     } else {
-        NP_CUDA(cudaMemsetAsync(s->v, 0, sizeof(double) * 3 * (size_t)s->n, s->user));
+        NP_CUDA(cudaMemsetAsync(s->v, 0, sizeof(float) * 3 * (size_t)s->n, s->user));
     }
-    long long st = step;
-    NP_CUDA(cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice,
-                            s->user));
-    NP_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->user));
-    int rc = enqueue_pass(s, MODE_FORCES, true, true, true, s->F, s->user);
-    if (rc)
-        return rc;
+    NP_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->x_lo, s->user));
+    return finish_upload(s, step);
+}
+
+// Replace the state by raw words (hi [3][n], lo [3][n], v [3][n], float32 SoA).
+int upload_words(npsim_sim *s, const float *words, int64_t step)
+{
+    const size_t n = (size_t)s->n;
+    std::vector<float4> xq(n);
+    for (size_t i = 0; i < n; ++i)
+        xq[i] = make_float4(words[i], words[n + i], words[2 * n + i],
+                            s->charge_f[s->h_type[i]]);
     NP_CUDA(cudaStreamSynchronize(s->user));
-    s->step = step;
-    return read_flags(s);
+    NP_CUDA(cudaMemcpy(s->xq, xq.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
+    NP_CUDA(cudaMemcpy(s->x_lo, words + 3 * n, sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+    NP_CUDA(cudaMemcpy(s->v, words + 6 * n, sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+    return finish_upload(s, step);
 }
 
 // Per-type integrator coefficients (float64 on the host): BAOAB O-step factors
@@ -635,6 +701,17 @@ void fill_coefs(const npsim_type_t *types, const npsim_params_t *params, TypeCoe
         c.mob = ty.gamma > 0 ? 1.0 / (ty.mass * ty.gamma) : 0.0;
         c.sd_bd = std::sqrt(2.0 * params->kT * params->dt * c.mob);
         c.charge_c = C * ty.charge;
+        c.hdt_m = (float)(0.5 * params->dt / ty.mass);
+        c.c1f = (float)c.c1;
+        c.c1lo = (float)(c.c1 - (double)c.c1f);
+        c.sd_of = (float)c.sd_o;
+        c.dt_mob = (float)(params->dt * c.mob);
+        c.sd_bdf = (float)c.sd_bd;
+        c.qc = (float)c.charge_c;
+        c.mg = (float)(ty.mass * params->g);
+        c.mw2 = (float)(ty.mass * params->omega * params->omega);
+        c.kw = (float)ty.k_wall;
+        c.hs = (float)c.half_sigma;
         if (charge_f)
             charge_f[t] = (float)ty.charge;
     }
@@ -795,9 +872,10 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
 
     const size_t n3 = 3 * (size_t)n;
     BAIL_CUDA(dalloc(&s->x, n3));
+    BAIL_CUDA(dalloc(&s->x_lo, n3));
     BAIL_CUDA(dalloc(&s->v, n3));
-    BAIL_CUDA(dalloc(&s->F, n3));
-    BAIL_CUDA(dalloc(&s->F_tmp, n3));
+    BAIL_CUDA(dalloc(&s->F, 2 * n3));
+    BAIL_CUDA(dalloc(&s->F_tmp, 2 * n3));
     BAIL_CUDA(dalloc(&s->xq, (size_t)n));
     BAIL_CUDA(dalloc(&s->typ, (size_t)n));
     BAIL_CUDA(dalloc(&s->tab_full, 1));
@@ -825,7 +903,7 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
         rc = alloc_cells(s->grid, s->cb, s->n);
         if (rc)
             return bail(rc);
-        BAIL_CUDA(dalloc(&s->F_lj, n3));
+        BAIL_CUDA(dalloc(&s->F_lj, 2 * n3));
     }
     s->ap_lj = params->lj_mode == 1;
     s->ap = params->coulomb || s->ap_lj;
@@ -835,7 +913,7 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
         std::vector<double> buf;
         to_soa(x0, s->n, buf);
         BAIL_CUDA(cudaMemcpy(s->x, buf.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
-        BAIL_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->user));
+        BAIL_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->x_lo, s->user));
     }
     if (s->ap) {
         if (params->coulomb) {
@@ -848,7 +926,7 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
             return bail(rc);
         const int occ = std::max(1, shape_occupancy(s, s->ap_idx, s->ap_lj));
         shape_streamk(s, s->ap_idx, occ * s->sms, s->sk);
-        BAIL_CUDA(dalloc(&s->slots, slots_doubles(s->sk)));
+        BAIL_CUDA(dalloc(&s->slots, slots_floats(s->sk)));
     } else {
         s->sk = StreamK{};
         s->sk.itile = 1;
@@ -896,14 +974,23 @@ int npsim_get_state(npsim_sim_t s, double *x, double *v, double *F, int64_t *ste
     NP_REQUIRE(s, "sim is NULL");
     NP_CUDA(cudaStreamSynchronize(s->user));
     std::vector<double> buf(3 * (size_t)s->n);
-    double *src[3] = {s->x, s->v, s->F};
-    double *dst[3] = {x, v, F};
-    for (int k = 0; k < 3; ++k) {
-        if (!dst[k])
-            continue;
-        NP_CUDA(cudaMemcpy(buf.data(), src[k], sizeof(double) * buf.size(),
+    int rc = NPSIM_OK;
+    if (x) {
+        if ((rc = positions_f64(s)))
+            return rc;
+        NP_CUDA(cudaMemcpy(buf.data(), s->x, sizeof(double) * buf.size(),
                            cudaMemcpyDeviceToHost));
-        to_aos(buf, s->n, dst[k]);
+        to_aos(buf, s->n, x);
+    }
+    if (v) {
+        if ((rc = fetch_f32(s->v, buf.size(), buf)))
+            return rc;
+        to_aos(buf, s->n, v);
+    }
+    if (F) {
+        if ((rc = fetch_hilo(s->F, s->n, buf)))
+            return rc;
+        to_aos(buf, s->n, F);
     }
     if (step)
         *step = s->step;
@@ -927,9 +1014,9 @@ int npsim_forces(npsim_sim_t s, int what, double *F)
     if (rc)
         return rc;
     NP_CUDA(cudaStreamSynchronize(s->user));
-    std::vector<double> buf(3 * (size_t)s->n);
-    NP_CUDA(cudaMemcpy(buf.data(), s->F_tmp, sizeof(double) * buf.size(),
-                       cudaMemcpyDeviceToHost));
+    std::vector<double> buf;
+    if ((rc = fetch_hilo(s->F_tmp, s->n, buf)))
+        return rc;
     to_aos(buf, s->n, F);
     return NPSIM_OK;
 }
@@ -1052,6 +1139,9 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
         NP_CUDA(dalloc(&s->s_vec, 8));
         NP_CUDA(dalloc(&s->s_count, 1));
     }
+    int rc0 = positions_f64(s);
+    if (rc0)
+        return rc0;
     std::vector<double> part(3 * (size_t)nblk);
     // extent of the cloud (minimum and maximum corner)
     NP_CUDA(launch_block_reduce(2, s->x, n, nullptr, s->s_part, st));
@@ -1202,13 +1292,16 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
 // Checkpoints
 
 namespace {
-const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '1'};
+// Layout: header, then the raw state words so that a resumed run is
+// bit-identical: position hi words [3][n], lo words [3][n], velocities [3][n]
+// (float32 SoA), then the types (int32[n]).
+const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '2'};
 
 struct CkptHeader {
     char magic[8];
     int32_t version, n_types;
     int64_t n, step;
-    int32_t rot_mode, lj_mode, coulomb, wall, integrator, has_ov;
+    int32_t rot_mode, lj_mode, coulomb, wall, integrator, has_ov, skip_neutral, pad_;
     uint64_t seed;
     double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut;
     double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
@@ -1221,7 +1314,7 @@ int npsim_save(npsim_sim_t s, const char *path)
     NP_REQUIRE(s && path, "sim and path are required");
     CkptHeader h{};
     memcpy(h.magic, kMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.n_types = s->T;
     h.n = s->n;
     h.step = s->step;
@@ -1231,6 +1324,7 @@ int npsim_save(npsim_sim_t s, const char *path)
     h.wall = s->P.wall;
     h.integrator = s->P.integrator;
     h.has_ov = s->has_ov ? 1 : 0;
+    h.skip_neutral = s->P.skip_neutral;
     h.seed = s->P.seed;
     h.dt = s->P.dt;
     h.kT = s->P.kT;
@@ -1242,16 +1336,25 @@ int npsim_save(npsim_sim_t s, const char *path)
     h.lj_cut = s->P.lj_cut;
     memcpy(h.eps_ov, s->eps_ov, sizeof(h.eps_ov));
     memcpy(h.types, s->types, sizeof(h.types));
-    std::vector<double> x(3 * (size_t)s->n), v(3 * (size_t)s->n);
-    int rc = npsim_get_state(s, x.data(), v.data(), nullptr, nullptr);
-    if (rc)
-        return rc;
+    const size_t n = (size_t)s->n;
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    std::vector<float4> xq(n);
+    std::vector<float> words(9 * n);
+    NP_CUDA(cudaMemcpy(xq.data(), s->xq, sizeof(float4) * n, cudaMemcpyDeviceToHost));
+    NP_CUDA(cudaMemcpy(words.data() + 3 * n, s->x_lo, sizeof(float) * 3 * n,
+                       cudaMemcpyDeviceToHost));
+    NP_CUDA(cudaMemcpy(words.data() + 6 * n, s->v, sizeof(float) * 3 * n,
+                       cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) {
+        words[i] = xq[i].x;
+        words[n + i] = xq[i].y;
+        words[2 * n + i] = xq[i].z;
+    }
     FILE *f = fopen(path, "wb");
     if (!f)
         return set_err(NPSIM_ERR_IO, "cannot open %s for writing", path);
     bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
-              fwrite(x.data(), sizeof(double), x.size(), f) == x.size() &&
-              fwrite(v.data(), sizeof(double), v.size(), f) == v.size() &&
+              fwrite(words.data(), sizeof(float), words.size(), f) == words.size() &&
               fwrite(s->h_type.data(), sizeof(int32_t), s->h_type.size(), f) ==
                   s->h_type.size();
     ok = (fclose(f) == 0) && ok;
@@ -1269,19 +1372,26 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     if (!f)
         return set_err(NPSIM_ERR_IO, "cannot open %s", path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 ||
         h.n < 1 || h.n > (1ll << 29) || h.n_types < 1 || h.n_types > NPSIM_MAX_TYPES) {
         fclose(f);
         return set_err(NPSIM_ERR_IO, "%s is not an npsim checkpoint", path);
     }
-    std::vector<double> x(3 * (size_t)h.n), v(3 * (size_t)h.n);
-    std::vector<int32_t> ty((size_t)h.n);
-    bool ok = fread(x.data(), sizeof(double), x.size(), f) == x.size() &&
-              fread(v.data(), sizeof(double), v.size(), f) == v.size() &&
+    const size_t n = (size_t)h.n;
+    std::vector<float> words(9 * n);
+    std::vector<int32_t> ty(n);
+    bool ok = fread(words.data(), sizeof(float), words.size(), f) == words.size() &&
               fread(ty.data(), sizeof(int32_t), ty.size(), f) == ty.size();
     fclose(f);
     if (!ok)
         return set_err(NPSIM_ERR_IO, "%s is truncated", path);
+    // float64 values (AoS) for creation: x = hi + lo, v
+    std::vector<double> x(3 * n), v(3 * n);
+    for (size_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            x[3 * i + d] = (double)words[d * n + i] + (double)words[(3 + d) * n + i];
+            v[3 * i + d] = (double)words[(6 + d) * n + i];
+        }
     npsim_params_t p{};
     p.n_types = h.n_types;
     p.rot_mode = h.rot_mode;
@@ -1289,6 +1399,7 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     p.coulomb = h.coulomb;
     p.wall = h.wall;
     p.integrator = h.integrator;
+    p.skip_neutral = h.skip_neutral;
     p.seed = h.seed;
     p.dt = h.dt;
     p.kT = h.kT;
@@ -1308,7 +1419,7 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     int rc = npsim_create(tys, &p, h.n, x.data(), v.data(), ty.data(), stream, &s);
     if (rc)
         return rc;
-    rc = npsim_set_state(s, x.data(), v.data(), h.step);
+    rc = upload_words(s, words.data(), h.step);
     if (rc) {
         npsim_destroy(s);
         return rc;
@@ -1333,13 +1444,15 @@ struct npsim_ens {
     std::vector<int32_t> h_type;
 
     cudaStream_t user = nullptr, cap = nullptr;
-    double *x = nullptr, *v = nullptr, *F = nullptr, *F_tmp = nullptr;
+    // state layouts as in npsim_sim, over the concatenation of the droplets
+    float *x_lo = nullptr, *v = nullptr;  // [3][n_total]
+    float *F = nullptr, *F_tmp = nullptr; // [6][n_total]
     float4 *xq = nullptr;
     int *typ = nullptr, *drop_of = nullptr;
     EnsDrop *drops = nullptr;
     PairTab *tabs = nullptr;
     long long *unit0 = nullptr;
-    double *slots = nullptr;
+    float *slots = nullptr;
     long long *d_step = nullptr;
     int *d_flags = nullptr;
     unsigned *d_done = nullptr;
@@ -1353,7 +1466,7 @@ struct npsim_ens {
     {
         for (auto &g : graphs)
             cudaGraphExecDestroy(g.second);
-        dfree(x);
+        dfree(x_lo);
         dfree(v);
         dfree(F);
         dfree(F_tmp);
@@ -1419,7 +1532,7 @@ int ens_upload_geometry(npsim_ens *e, const std::vector<long long> &unit0)
     return NPSIM_OK;
 }
 
-EnsAllpairsArgs ens_ap_args(npsim_ens *e, double *slots)
+EnsAllpairsArgs ens_ap_args(npsim_ens *e, float *slots)
 {
     EnsAllpairsArgs a{};
     a.xq = e->xq;
@@ -1432,11 +1545,11 @@ EnsAllpairsArgs ens_ap_args(npsim_ens *e, double *slots)
     return a;
 }
 
-int ens_pass(npsim_ens *e, int mode, bool ext, double *Fout, cudaStream_t st)
+int ens_pass(npsim_ens *e, int mode, bool ext, float *Fout, cudaStream_t st)
 {
     NP_CUDA(launch_ens_allpairs(e->shape, e->sk, ens_ap_args(e, e->slots), st));
     EnsIntArgs a{};
-    a.x = e->x;
+    a.x_lo = e->x_lo;
     a.v = e->v;
     a.F = Fout;
     a.typ = e->typ;
@@ -1455,7 +1568,7 @@ int ens_pass(npsim_ens *e, int mode, bool ext, double *Fout, cudaStream_t st)
 int ens_chunk(npsim_ens *e, int k, cudaStream_t st)
 {
     EnsIntArgs a{};
-    a.x = e->x;
+    a.x_lo = e->x_lo;
     a.v = e->v;
     a.F = e->F;
     a.typ = e->typ;
@@ -1524,9 +1637,9 @@ int ens_autotune(npsim_ens *e)
             const long long W = ens_geometry(e, c, unit0, &rows);
             StreamK sk;
             ens_streamk(W, ens_config(c), occ * e->sms, sk);
-            need = std::max(need, (size_t)(rows + sk.grid) * 3 * (size_t)sk.itile);
+            need = std::max(need, (size_t)(rows + sk.grid) * 6 * (size_t)sk.itile);
         }
-        double *tmp = nullptr;
+        float *tmp = nullptr;
         NP_CUDA(dalloc(&tmp, need));
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -1576,7 +1689,7 @@ int ens_autotune(npsim_ens *e)
     int rc = ens_upload_geometry(e, unit0);
     if (rc)
         return rc;
-    NP_CUDA(dalloc(&e->slots, (size_t)(rows + e->sk.grid) * 3 * (size_t)e->sk.itile));
+    NP_CUDA(dalloc(&e->slots, (size_t)(rows + e->sk.grid) * 6 * (size_t)e->sk.itile));
     return NPSIM_OK;
 }
 
@@ -1688,10 +1801,10 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
     } while (0)
     EBAIL(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
     const size_t n3 = 3 * (size_t)total;
-    EBAIL(dalloc(&e->x, n3));
+    EBAIL(dalloc(&e->x_lo, n3));
     EBAIL(dalloc(&e->v, n3));
-    EBAIL(dalloc(&e->F, n3));
-    EBAIL(dalloc(&e->F_tmp, n3));
+    EBAIL(dalloc(&e->F, 2 * n3));
+    EBAIL(dalloc(&e->F_tmp, 2 * n3));
     EBAIL(dalloc(&e->xq, (size_t)total));
     EBAIL(dalloc(&e->typ, (size_t)total));
     EBAIL(dalloc(&e->drop_of, (size_t)total));
@@ -1701,8 +1814,14 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
     EBAIL(dalloc(&e->d_step, 1));
     EBAIL(dalloc(&e->d_flags, 1));
     EBAIL(dalloc(&e->d_done, 1));
-    EBAIL(cudaMemcpy(e->x, xs.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
-    EBAIL(cudaMemcpy(e->v, vs.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+    {
+        // position = hi (nearest float, in xq) + lo (the float nearest the rest)
+        std::vector<float> lo(n3), vf(vs.begin(), vs.end());
+        for (size_t k = 0; k < n3; ++k)
+            lo[k] = (float)(xs[k] - (double)(float)xs[k]);
+        EBAIL(cudaMemcpy(e->x_lo, lo.data(), sizeof(float) * n3, cudaMemcpyHostToDevice));
+        EBAIL(cudaMemcpy(e->v, vf.data(), sizeof(float) * n3, cudaMemcpyHostToDevice));
+    }
     EBAIL(cudaMemcpy(e->typ, e->h_type.data(), sizeof(int) * (size_t)total,
                      cudaMemcpyHostToDevice));
     EBAIL(cudaMemcpy(e->drop_of, dof.data(), sizeof(int) * (size_t)total,
@@ -1770,18 +1889,35 @@ int npsim_ens_get_state(npsim_ens_t e, int32_t d, double *x, double *v, double *
     NP_REQUIRE(e && d >= 0 && d < e->D, "bad ensemble or droplet index");
     NP_CUDA(cudaStreamSynchronize(e->user));
     const int n = e->cnt[d], off = e->off[d];
-    std::vector<double> buf((size_t)n);
-    double *src[3] = {e->x, e->v, e->F};
-    double *dst[3] = {x, v, F};
-    for (int k = 0; k < 3; ++k) {
-        if (!dst[k])
-            continue;
+    const size_t N = (size_t)e->n_total;
+    std::vector<float> a((size_t)n), b((size_t)n);
+    // component c of droplet d's rows of a [k][N] float array
+    auto rows = [&](const float *src, int c, std::vector<float> &dst) -> cudaError_t {
+        return cudaMemcpy(dst.data(), src + c * N + off, sizeof(float) * (size_t)n,
+                          cudaMemcpyDeviceToHost);
+    };
+    if (x) {
+        std::vector<float4> h((size_t)n);
+        NP_CUDA(cudaMemcpy(h.data(), e->xq + off, sizeof(float4) * (size_t)n,
+                           cudaMemcpyDeviceToHost));
         for (int c = 0; c < 3; ++c) {
-            NP_CUDA(cudaMemcpy(buf.data(), src[k] + (size_t)c * e->n_total + off,
-                               sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
-            for (int i = 0; i < n; ++i)
-                dst[k][3 * (size_t)i + c] = buf[i];
+            NP_CUDA(rows(e->x_lo, c, a));
+            for (int i = 0; i < n; ++i) {
+                const float hi = c == 0 ? h[i].x : c == 1 ? h[i].y : h[i].z;
+                x[3 * (size_t)i + c] = (double)hi + (double)a[i];
+            }
         }
+    }
+    for (int c = 0; v && c < 3; ++c) {
+        NP_CUDA(rows(e->v, c, a));
+        for (int i = 0; i < n; ++i)
+            v[3 * (size_t)i + c] = (double)a[i];
+    }
+    for (int c = 0; F && c < 3; ++c) {
+        NP_CUDA(rows(e->F, c, a));
+        NP_CUDA(rows(e->F, 3 + c, b));
+        for (int i = 0; i < n; ++i)
+            F[3 * (size_t)i + c] = (double)a[i] + (double)b[i];
     }
     if (step)
         *step = e->step;
@@ -1796,12 +1932,15 @@ int npsim_ens_forces(npsim_ens_t e, int32_t d, double *F)
         return rc;
     NP_CUDA(cudaStreamSynchronize(e->user));
     const int n = e->cnt[d], off = e->off[d];
-    std::vector<double> buf((size_t)n);
+    const size_t N = (size_t)e->n_total;
+    std::vector<float> a((size_t)n), b((size_t)n);
     for (int c = 0; c < 3; ++c) {
-        NP_CUDA(cudaMemcpy(buf.data(), e->F_tmp + (size_t)c * e->n_total + off,
-                           sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+        NP_CUDA(cudaMemcpy(a.data(), e->F_tmp + c * N + off, sizeof(float) * (size_t)n,
+                           cudaMemcpyDeviceToHost));
+        NP_CUDA(cudaMemcpy(b.data(), e->F_tmp + (3 + c) * N + off, sizeof(float) * (size_t)n,
+                           cudaMemcpyDeviceToHost));
         for (int i = 0; i < n; ++i)
-            F[3 * (size_t)i + c] = buf[i];
+            F[3 * (size_t)i + c] = (double)a[i] + (double)b[i];
     }
     return NPSIM_OK;
 }

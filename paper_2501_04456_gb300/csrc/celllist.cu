@@ -1,5 +1,5 @@
-// celllist.cu -- cell binning (step (i) of the loop in arXiv 2501.04456 Sec. 2.2,
-// "arrange NPs into the cells ... to identify which are close to each other")
+// celllist.cu -- cell binning (step (i) of the loop in arXiv 2501.04456 Sec. 2.2:
+// NPs are sorted into spatial cells so that near neighbours are found quickly)
 // and the truncated, unshifted Lennard-Jones force over the 27 neighbouring
 // cells (step (ii)):
 //   F_i = sum_{j != i, r < rc_ij} 24 eps_ij (2 (s_ij/r)^12 - (s_ij/r)^6) r_ij / r^2.
@@ -194,7 +194,7 @@ __global__ void k_cell_gather(const int *__restrict__ sorted, const float4 *__re
 __global__ void __launch_bounds__(128)
 k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
           const float4 *__restrict__ sxq, const int *__restrict__ styp, int n,
-          const PairTab *__restrict__ tab, double *__restrict__ F_lj)
+          const PairTab *__restrict__ tab, float *__restrict__ F_lj)
 {
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += blockDim.x)
@@ -239,9 +239,12 @@ k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sor
         }
     }
     const int i = sorted[p];
-    F_lj[i] = (double)hx + (double)lx;
-    F_lj[n + i] = (double)hy + (double)ly;
-    F_lj[2 * n + i] = (double)hz + (double)lz;
+    F_lj[i] = hx; // hi x, y, z then lo x, y, z ([6][n])
+    F_lj[n + i] = hy;
+    F_lj[2 * n + i] = hz;
+    F_lj[3 * n + i] = lx;
+    F_lj[4 * n + i] = ly;
+    F_lj[5 * n + i] = lz;
 }
 
 } // namespace
@@ -270,7 +273,7 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
 }
 
 cudaError_t launch_cell_lj(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
-                           double *F_lj, cudaStream_t st)
+                           float *F_lj, cudaStream_t st)
 {
     const int B = 128;
     k_cell_lj<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.sxq, b.styp, n, tab,

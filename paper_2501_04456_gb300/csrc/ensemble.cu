@@ -8,8 +8,8 @@
 // units; the rectangles are laid end to end and the resulting unit sequence is
 // split evenly over the CTAs (stream-K), so a 512-NP droplet and a 32768-NP
 // droplet share the GPU in proportion to their N^2 work within one launch.
-// A CTA writes one float64 partial per (global row, CTA) segment into slot
-// row + CTA; the integrator sums a row's partials in CTA order.
+// A CTA writes one compensated (hi, lo) float32 partial per (global row, CTA)
+// segment into slot row + CTA; the integrator sums a row's partials in CTA order.
 //
 // The pair body is the scalar Coulomb + truncated-LJ body of allpairs.cu with
 // the droplet's own type-pair table (sigma_ab^2, 24 eps_ab, rc_ab^2, C q_a q_b);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(BLOCK)
 k_ens_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ,
                const EnsDrop *__restrict__ drops, const long long *__restrict__ unit0,
                const PairTab *__restrict__ tabs, int n_drops, StreamK sk,
-               double *__restrict__ slots)
+               float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
     __shared__ float4 s_x[JT];
@@ -142,13 +142,16 @@ k_ens_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ,
             }
         }
 
-        double *slot = slots + (size_t)(D.row0 + r + c) * 3 * ITILE;
+        float *slot = slots + (size_t)(D.row0 + r + c) * 6 * ITILE; // hi x,y,z, lo x,y,z
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
             const int idx = k * BLOCK + threadIdx.x;
-            slot[idx] = (double)hx[k] + (double)lx[k];
-            slot[ITILE + idx] = (double)hy[k] + (double)ly[k];
-            slot[2 * ITILE + idx] = (double)hz[k] + (double)lz[k];
+            slot[idx] = hx[k];
+            slot[ITILE + idx] = hy[k];
+            slot[2 * ITILE + idx] = hz[k];
+            slot[3 * ITILE + idx] = lx[k];
+            slot[4 * ITILE + idx] = ly[k];
+            slot[5 * ITILE + idx] = lz[k];
         }
         p += jt1 - jt0;
     }
@@ -158,23 +161,39 @@ template <int MODE>
 __global__ void __launch_bounds__(256)
 k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
 {
+    // A CTA of 256 consecutive particles spans at most 256 droplets; the
+    // spring radius of every (droplet, type) it touches is evaluated once.
+    constexpr int kSpan = 256;
+    __shared__ float2 s_reff2[kSpan * NPSIM_MAX_TYPES];
+    __shared__ float s_reff[kSpan * NPSIM_MAX_TYPES];
     constexpr bool ASSEMBLE = (MODE != MODE_A);
-    constexpr bool DO_B = (MODE == MODE_BA || MODE == MODE_B);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long long step = *a.step;
+    const int i0 = blockIdx.x * blockDim.x;
+    const int d0 = a.drop_of[i0]; // i0 < n_total: the grid is ceil(n_total / 256)
+    if (ASSEMBLE && a.ext_on) {
+        const int i_last = min(i0 + (int)blockDim.x, n_total) - 1;
+        const int span = a.drop_of[i_last] - d0 + 1;
+        for (int k = threadIdx.x; k < span * NPSIM_MAX_TYPES; k += blockDim.x) {
+            const EnsDrop &D = a.drops[d0 + k / NPSIM_MAX_TYPES];
+            spring_radius(D.R0, D.k_evap, D.dt, step, D.tc[k % NPSIM_MAX_TYPES].half_sigma,
+                          s_reff2[k], s_reff[k]);
+        }
+        __syncthreads();
+    }
 
+    const int i = i0 + threadIdx.x;
     if (i < n_total) {
+        const int n = n_total;
         const int d = a.drop_of[i];
         const EnsDrop &D = a.drops[d];
         const int li = i - D.offset;
         const int ti = a.typ[i];
         const TypeCoef tc = D.tc[ti];
-        const int n = n_total;
-        double xx = a.x[i], xy = a.x[n + i], xz = a.x[2 * n + i];
-        double fx, fy, fz;
+        const float4 xh = a.xq[i];
+        const float lx = a.x_lo[i], ly = a.x_lo[n + i], lz = a.x_lo[2 * n + i];
+        float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
         if (ASSEMBLE) {
-            fx = fy = fz = 0.0;
             if (a.slots) {
                 const int r = li / sk.itile;
                 const int idx = li - r * sk.itile;
@@ -182,91 +201,30 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 const int c0 = sk_cta_of(sk, u0);
                 const int c1 = sk_cta_of(sk, u0 + D.n_jt - 1);
                 for (int c = c0; c <= c1; ++c) {
-                    const double *slot = a.slots + (size_t)(D.row0 + r + c) * 3 * sk.itile;
-                    fx += slot[idx];
-                    fy += slot[sk.itile + idx];
-                    fz += slot[2 * sk.itile + idx];
+                    const float *slot = a.slots + (size_t)(D.row0 + r + c) * 6 * sk.itile + idx;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        df_add_df(Fh[k], Fl[k], slot[k * sk.itile], slot[(3 + k) * sk.itile]);
                 }
             }
             if (a.ext_on) {
-                const double t = (double)step * D.dt;
-                const double R2 = D.R0 * D.R0 - D.k_evap * t;
-                const double R = R2 > 0.0 ? sqrt(R2) : 0.0;
-                if (D.wall) {
-                    const double rr = sqrt(xx * xx + xy * xy + xz * xz);
-                    const double s = rr - (R - tc.half_sigma);
-                    if (s > 0.0 && rr > 0.0) {
-                        const double f = -tc.k_wall * s / rr;
-                        fx += f * xx;
-                        fy += f * xy;
-                        fz += f * xz;
-                    }
-                }
-                fz += -tc.mass * D.g;
-                if (D.rot_mode == 1) {
-                    fx += tc.mass * D.omega2 * xx;
-                    fy += tc.mass * D.omega2 * xy;
-                } else if (D.rot_mode == 2) {
-                    fx += tc.mass * D.omega2 * xx;
-                    fy += tc.mass * D.omega2 * xy;
-                    fz += tc.mass * D.omega2 * xz;
-                }
+                const int e = (d - d0) * NPSIM_MAX_TYPES + ti;
+                float ex, ey, ez;
+                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, s_reff2[e], s_reff[e],
+                               D.wall, D.rot_mode, ex, ey, ez);
+                df_add(Fh[0], Fl[0], ex);
+                df_add(Fh[1], Fl[1], ey);
+                df_add(Fh[2], Fl[2], ez);
             }
         } else {
-            fx = a.F[i];
-            fy = a.F[n + i];
-            fz = a.F[2 * n + i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Fh[k] = a.F[k * n + i];
+                Fl[k] = a.F[(3 + k) * n + i];
+            }
         }
-        if (MODE == MODE_FORCES) {
-            a.F[i] = fx;
-            a.F[n + i] = fy;
-            a.F[2 * n + i] = fz;
-        } else {
-            double vx = a.v[i], vy = a.v[n + i], vz = a.v[2 * n + i];
-            const double hdt = 0.5 * D.dt;
-            if (DO_B && D.integrator == 0) {
-                vx += hdt * fx * tc.inv_mass;
-                vy += hdt * fy * tc.inv_mass;
-                vz += hdt * fz * tc.inv_mass;
-            }
-            if (MODE == MODE_B) {
-                a.F[i] = fx;
-                a.F[n + i] = fy;
-                a.F[2 * n + i] = fz;
-            }
-            if (DO_A) {
-                double n0, n1, n2;
-                normals3(D.seed, (uint32_t)li, step, 0u, n0, n1, n2);
-                if (D.integrator == 0) {
-                    vx += hdt * fx * tc.inv_mass;
-                    vy += hdt * fy * tc.inv_mass;
-                    vz += hdt * fz * tc.inv_mass;
-                    xx += hdt * vx;
-                    xy += hdt * vy;
-                    xz += hdt * vz;
-                    vx = tc.c1 * vx + tc.sd_o * n0;
-                    vy = tc.c1 * vy + tc.sd_o * n1;
-                    vz = tc.c1 * vz + tc.sd_o * n2;
-                    xx += hdt * vx;
-                    xy += hdt * vy;
-                    xz += hdt * vz;
-                } else {
-                    xx += fx * D.dt * tc.mob + tc.sd_bd * n0;
-                    xy += fy * D.dt * tc.mob + tc.sd_bd * n1;
-                    xz += fz * D.dt * tc.mob + tc.sd_bd * n2;
-                }
-                a.x[i] = xx;
-                a.x[n + i] = xy;
-                a.x[2 * n + i] = xz;
-                const float4 old = a.xq[i];
-                a.xq[i] = make_float4((float)xx, (float)xy, (float)xz, old.w);
-                if (!(isfinite(xx) && isfinite(xy) && isfinite(xz)))
-                    atomicOr(a.flags, FLAG_NONFINITE);
-            }
-            a.v[i] = vx;
-            a.v[n + i] = vy;
-            a.v[2 * n + i] = vz;
-        }
+        advance_particle<MODE>(i, n, (uint32_t)li, tc, D.integrator, 0.5f * (float)D.dt, D.seed,
+                               step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags);
     }
     if (DO_A) {
         __syncthreads();

@@ -11,14 +11,21 @@
 // The paper adds a fixed-magnitude random vector and has no temperature; the
 // thermostat here is the fluctuation-dissipation-consistent reading of it.
 //
-// One kernel serves four modes (see IntMode): it sums the stream-K partials
-// of the all-pairs kernel (and the cell-list LJ forces) into the total force,
-// adds the external forces at t = step*dt, and applies the B half kick and/or
-// the BAOA part of the next step.  Positions and velocities are float64
-// (structure of arrays, coalesced); the float32 mirror (x, y, z, q) the pair
-// kernels read is written whenever positions move.  The step counter lives in
-// device memory and is advanced by the last CTA to finish, so a captured CUDA
-// graph replays without parameter updates.
+// Precision without float64 arithmetic (GB300's FP64 rate is ~1/64 of FP32):
+// the position is the unevaluated sum of two floats, hi (the float32 word the
+// pair kernels read) + lo, updated with TwoSum (about 48 significant bits, so
+// increments far below one float ulp of |x| accumulate); forces are summed as
+// hi/lo pairs; velocities and the per-step increments are float32.  The
+// interface distance |x| - (R - sigma/2), a difference of two nearly equal
+// numbers, is formed from |x|^2 - R_eff^2 (see external_force); R(t) and
+// R_eff^2 come from one float64 evaluation per CTA.
+//
+// One kernel serves four modes (see IntMode): it sums the stream-K partials of
+// the all-pairs kernel (and the cell-list LJ forces) into the total force, adds
+// the external forces at t = step*dt, and applies the B half kick and/or the
+// BAOA part of the next step.  The step counter lives in device memory and is
+// advanced by the last CTA to finish, so a captured CUDA graph replays without
+// parameter updates.
 #include "npsim_internal.cuh"
 
 namespace npsim {
@@ -30,24 +37,30 @@ __global__ void __launch_bounds__(256)
 k_integrate(IntArgs a, StepParams p)
 {
     __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
-    if (threadIdx.x < NPSIM_MAX_TYPES)
-        s_tc[threadIdx.x] = p.tc[threadIdx.x];
+    __shared__ float2 s_reff2[NPSIM_MAX_TYPES];
+    __shared__ float s_reff[NPSIM_MAX_TYPES];
+    const long long step = *a.step; // positions are x_step at t = step * dt
+    if (threadIdx.x < NPSIM_MAX_TYPES) {
+        const TypeCoef tc = p.tc[threadIdx.x];
+        s_tc[threadIdx.x] = tc;
+        // the spring's equilibrium radius at t, once per CTA
+        spring_radius(p.R0, p.k_evap, p.dt, step, tc.half_sigma, s_reff2[threadIdx.x],
+                      s_reff[threadIdx.x]);
+    }
     __syncthreads();
 
     const int n = p.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const long long step = *a.step; // positions are x_step at t = step * dt
     constexpr bool ASSEMBLE = (MODE != MODE_A);
-    constexpr bool DO_B = (MODE == MODE_BA || MODE == MODE_B);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
 
     if (i < n) {
         const int ti = a.typ[i];
-        const TypeCoef tc = s_tc[ti];
-        double xx = a.x[i], xy = a.x[n + i], xz = a.x[2 * n + i];
-        double fx, fy, fz;
+        const TypeCoef &tc = s_tc[ti];
+        float4 xh = a.xq[i];
+        float lx = a.x_lo[i], ly = a.x_lo[n + i], lz = a.x_lo[2 * n + i];
+        float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
         if (ASSEMBLE) {
-            fx = fy = fz = 0.0;
             const int pos = a.row_pos ? a.row_pos[i] : i;
             if (a.slots && pos >= 0) {
                 const StreamK &sk = a.sk;
@@ -57,102 +70,40 @@ k_integrate(IntArgs a, StepParams p)
                 const int c0 = sk_cta_of(sk, u0);
                 const int c1 = sk_cta_of(sk, u0 + sk.n_jt - 1);
                 for (int c = c0; c <= c1; ++c) {
-                    const double *slot = a.slots + (size_t)(r + c) * 3 * sk.itile;
-                    fx += slot[idx];
-                    fy += slot[sk.itile + idx];
-                    fz += slot[2 * sk.itile + idx];
+                    const float *slot = a.slots + (size_t)(r + c) * 6 * sk.itile + idx;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        df_add_df(Fh[d], Fl[d], slot[d * sk.itile], slot[(3 + d) * sk.itile]);
                 }
-                if (a.field_slots) { // the Coulomb-only kernel returns sum_j q_j r_ij / r^3
-                    fx *= tc.charge_c;
-                    fy *= tc.charge_c;
-                    fz *= tc.charge_c;
+                if (a.field_slots) { // the Coulomb-only kernels return sum_j q_j r_ij / r^3
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        df_mul(Fh[d], Fl[d], tc.qc);
                 }
             }
             if (a.F_lj) {
-                fx += a.F_lj[i];
-                fy += a.F_lj[n + i];
-                fz += a.F_lj[2 * n + i];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    df_add_df(Fh[d], Fl[d], a.F_lj[d * n + i], a.F_lj[(3 + d) * n + i]);
             }
             if (a.ext_on) {
-                const double t = (double)step * p.dt;
-                const double R2 = p.R0 * p.R0 - p.k_evap * t;
-                const double R = R2 > 0.0 ? sqrt(R2) : 0.0;
-                if (p.wall) {
-                    const double rr = sqrt(xx * xx + xy * xy + xz * xz);
-                    const double s = rr - (R - tc.half_sigma);
-                    if (s > 0.0 && rr > 0.0) {
-                        const double f = -tc.k_wall * s / rr;
-                        fx += f * xx;
-                        fy += f * xy;
-                        fz += f * xz;
-                    }
-                }
-                fz += -tc.mass * p.g;
-                if (p.rot_mode == 1) {
-                    fx += tc.mass * p.omega2 * xx;
-                    fy += tc.mass * p.omega2 * xy;
-                } else if (p.rot_mode == 2) {
-                    fx += tc.mass * p.omega2 * xx;
-                    fy += tc.mass * p.omega2 * xy;
-                    fz += tc.mass * p.omega2 * xz;
-                }
+                float ex, ey, ez;
+                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, s_reff2[ti], s_reff[ti],
+                               p.wall, p.rot_mode, ex, ey, ez);
+                df_add(Fh[0], Fl[0], ex);
+                df_add(Fh[1], Fl[1], ey);
+                df_add(Fh[2], Fl[2], ez);
             }
         } else {
-            fx = a.F[i];
-            fy = a.F[n + i];
-            fz = a.F[2 * n + i];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Fh[d] = a.F[d * n + i];
+                Fl[d] = a.F[(3 + d) * n + i];
+            }
         }
 
-        if (MODE == MODE_FORCES) {
-            a.F[i] = fx;
-            a.F[n + i] = fy;
-            a.F[2 * n + i] = fz;
-        } else {
-            double vx = a.v[i], vy = a.v[n + i], vz = a.v[2 * n + i];
-            const double hdt = 0.5 * p.dt;
-            if (DO_B && p.integrator == 0) {
-                vx += hdt * fx * tc.inv_mass;
-                vy += hdt * fy * tc.inv_mass;
-                vz += hdt * fz * tc.inv_mass;
-            }
-            if (MODE == MODE_B) {
-                a.F[i] = fx;
-                a.F[n + i] = fy;
-                a.F[2 * n + i] = fz;
-            }
-            if (DO_A) {
-                double n0, n1, n2;
-                normals3(p.seed, (uint32_t)i, step, 0u, n0, n1, n2);
-                if (p.integrator == 0) {
-                    vx += hdt * fx * tc.inv_mass;
-                    vy += hdt * fy * tc.inv_mass;
-                    vz += hdt * fz * tc.inv_mass;
-                    xx += hdt * vx;
-                    xy += hdt * vy;
-                    xz += hdt * vz;
-                    vx = tc.c1 * vx + tc.sd_o * n0;
-                    vy = tc.c1 * vy + tc.sd_o * n1;
-                    vz = tc.c1 * vz + tc.sd_o * n2;
-                    xx += hdt * vx;
-                    xy += hdt * vy;
-                    xz += hdt * vz;
-                } else {
-                    xx += fx * p.dt * tc.mob + tc.sd_bd * n0;
-                    xy += fy * p.dt * tc.mob + tc.sd_bd * n1;
-                    xz += fz * p.dt * tc.mob + tc.sd_bd * n2;
-                }
-                a.x[i] = xx;
-                a.x[n + i] = xy;
-                a.x[2 * n + i] = xz;
-                const float4 old = a.xq[i];
-                a.xq[i] = make_float4((float)xx, (float)xy, (float)xz, old.w);
-                if (!(isfinite(xx) && isfinite(xy) && isfinite(xz)))
-                    atomicOr(a.flags, FLAG_NONFINITE);
-            }
-            a.v[i] = vx;
-            a.v[n + i] = vy;
-            a.v[2 * n + i] = vz;
-        }
+        advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
+                               step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags);
     }
 
     if (DO_A) {
@@ -171,26 +122,51 @@ k_integrate(IntArgs a, StepParams p)
     }
 }
 
+// hi = float(x), lo = float(x - hi): the nearest float and the remainder.
 __global__ void k_mirror(const double *__restrict__ x, const int *__restrict__ typ,
-                         PairTab charges, int n, float4 *__restrict__ xq)
+                         PairTab charges, int n, float4 *__restrict__ xq,
+                         float *__restrict__ x_lo)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    xq[i] = make_float4((float)x[i], (float)x[n + i], (float)x[2 * n + i],
-                        charges.e[typ[i]].x);
+    float h[3];
+    for (int d = 0; d < 3; ++d) {
+        const double v = x[d * n + i];
+        h[d] = (float)v;
+        x_lo[d * n + i] = (float)(v - (double)h[d]);
+    }
+    xq[i] = make_float4(h[0], h[1], h[2], charges.e[typ[i]].x);
+}
+
+__global__ void k_positions_f64(const float4 *__restrict__ xq, const float *__restrict__ x_lo,
+                                int n, double *__restrict__ x)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float4 h = xq[i];
+    x[i] = (double)h.x + (double)x_lo[i];
+    x[n + i] = (double)h.y + (double)x_lo[n + i];
+    x[2 * n + i] = (double)h.z + (double)x_lo[2 * n + i];
 }
 
 } // namespace
 
-// Float32 mirror (x, y, z, q) of the float64 positions.
 cudaError_t launch_mirror(const double *x, const int *typ, const float *charge_by_type,
-                          int n, float4 *xq, cudaStream_t st)
+                          int n, float4 *xq, float *x_lo, cudaStream_t st)
 {
     PairTab q{};
     for (int t = 0; t < NPSIM_MAX_TYPES; ++t)
         q.e[t].x = charge_by_type[t];
-    k_mirror<<<(n + 255) / 256, 256, 0, st>>>(x, typ, q, n, xq);
+    k_mirror<<<(n + 255) / 256, 256, 0, st>>>(x, typ, q, n, xq, x_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_positions_f64(const float4 *xq, const float *x_lo, int n, double *x,
+                                 cudaStream_t st)
+{
+    k_positions_f64<<<(n + 255) / 256, 256, 0, st>>>(xq, x_lo, n, x);
     return cudaGetLastError();
 }
 

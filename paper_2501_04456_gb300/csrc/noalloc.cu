@@ -1,8 +1,8 @@
 // noalloc.cu -- all-pairs Coulomb forces for callers that must not allocate
 // device memory.
 //
-// The regular path keeps the all-pairs partial sums (one float64 slot per
-// i-tile row and CTA of the stream-K split) in memory that npsim_create
+// The regular path keeps the all-pairs partial sums (one slot of compensated
+// float32 (hi, lo) pairs per i-tile row and CTA of the stream-K split) in memory that npsim_create
 // allocates.  Some callers cannot allocate at the moment they need forces:
 // code running inside a CUDA stream capture (cudaMalloc is not a legal
 // operation while a capture is open), code running under a framework that
@@ -28,20 +28,20 @@ namespace {
 
 // Largest number of NPs one call accepts, and the fixed scratch it needs: with a
 // launch shape of i-tile 512 and at most kMaxGrid CTAs, a call writes at most
-// (ceil(n / 512) + kMaxGrid) slots of 3 x 512 doubles.
+// (ceil(n / 512) + kMaxGrid) slots of 6 x 512 floats.
 constexpr int kMaxN = 32768;
 constexpr int kMaxGrid = 256;
 constexpr int kMaxItile = 512;
-constexpr size_t kScratchDoubles =
-    (size_t)((kMaxN + kMaxItile - 1) / kMaxItile + kMaxGrid) * 3 * kMaxItile; // 3.75 MiB
+constexpr size_t kScratchFloats =
+    (size_t)((kMaxN + kMaxItile - 1) / kMaxItile + kMaxGrid) * 6 * kMaxItile; // 3.75 MiB
 
-__device__ __align__(256) double g_scratch[kScratchDoubles];
+__device__ __align__(256) float g_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
 
 struct DeviceSetup {
     bool done = false;
-    double *scratch = nullptr; // device address of g_scratch on this device
+    float *scratch = nullptr;  // device address of g_scratch on this device
     int shape = -1;            // all-pairs launch shape (index in the autotuner table)
     int grid_cap = 0;          // CTAs: min(kMaxGrid, resident CTAs of the shape)
 };
@@ -79,7 +79,7 @@ int setup_device(int dev, DeviceSetup &out)
         if (shape < 0)
             return report_error(NPSIM_ERR_CUDA, "no packed all-pairs shape with i-tile %d",
                                 kMaxItile);
-        s.scratch = (double *)ptr;
+        s.scratch = (float *)ptr;
         s.shape = shape;
         s.grid_cap = cap;
         s.done = true;
@@ -101,10 +101,11 @@ __global__ void k_noalloc_reduce(const float4 *__restrict__ xq, int n, StreamK s
     const int c1 = sk_cta_of(sk, u0 + sk.n_jt - 1);
     double fx = 0.0, fy = 0.0, fz = 0.0;
     for (int c = c0; c <= c1; ++c) {
-        const double *slot = g_scratch + (size_t)(r + c) * 3 * sk.itile;
-        fx += slot[idx];
-        fy += slot[sk.itile + idx];
-        fz += slot[2 * sk.itile + idx];
+        // slots hold (hi x, y, z, lo x, y, z) float words
+        const float *slot = g_scratch + (size_t)(r + c) * 6 * sk.itile;
+        fx += (double)slot[idx] + (double)slot[3 * sk.itile + idx];
+        fy += (double)slot[sk.itile + idx] + (double)slot[4 * sk.itile + idx];
+        fz += (double)slot[2 * sk.itile + idx] + (double)slot[5 * sk.itile + idx];
     }
     const double qc = C * (double)xq[i].w;
     F[3 * (size_t)i + 0] = qc * fx;
@@ -153,9 +154,9 @@ extern "C" int npsim_coulomb_forces_noalloc(const float *dev_xyzq, int64_t n, do
     sk.n_jt = (int)((n + c.jt - 1) / c.jt);
     sk.W = (long long)sk.n_it * sk.n_jt;
     sk.grid = (int)(sk.W < su.grid_cap ? sk.W : su.grid_cap);
-    if ((size_t)(sk.n_it + sk.grid) * 3 * (size_t)sk.itile > kScratchDoubles)
-        return report_error(NPSIM_ERR_INVALID_ARG, "n = %lld needs more scratch than %zu doubles",
-                            (long long)n, kScratchDoubles);
+    if ((size_t)(sk.n_it + sk.grid) * 6 * (size_t)sk.itile > kScratchFloats)
+        return report_error(NPSIM_ERR_INVALID_ARG, "n = %lld needs more scratch than %zu floats",
+                            (long long)n, kScratchFloats);
 
     cudaStream_t st = (cudaStream_t)stream;
     const float4 *xq = (const float4 *)dev_xyzq;

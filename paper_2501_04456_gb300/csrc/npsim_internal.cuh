@@ -84,7 +84,126 @@ struct TypeCoef {
     double c1, sd_o;    // BAOAB O step: v <- c1 v + sd_o xi
     double mob, sd_bd;  // overdamped: x += F dt mob + sd_bd xi
     double charge_c;    // C * q (Coulomb-only all-pairs kernel returns the field)
+    // float32 copies used by the integrator (all of its arithmetic is float32 or
+    // compensated float32): dt/(2m), c1 as hi + lo (its rounding error would
+    // otherwise compound over the 1/(gamma dt) steps a velocity remembers),
+    // sd_o, dt*mob, sd_bd, C q, m g, m w^2, k_wall, sigma/2
+    float hdt_m, c1f, c1lo, sd_of, dt_mob, sd_bdf, qc, mg, mw2, kw, hs;
 };
+
+// ---------------------------------------------------------------------------
+// Compensated float32 ("double-float") arithmetic: a value is an unevaluated
+// sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48 significant bits.
+// Every operation is rounded separately (no fused multiply-add contraction).
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ float2 df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    return make_float2(s, e);
+}
+
+// Dekker's Fast2Sum (|a| >= |b| or a == 0): s + e == a + b exactly.
+__device__ __forceinline__ float2 df_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// (h, l) += b, renormalised.
+__device__ __forceinline__ void df_add(float &h, float &l, float b)
+{
+    const float2 t = df_two_sum(h, b);
+    const float2 u = df_fast_two_sum(t.x, __fadd_rn(t.y, l));
+    h = u.x;
+    l = u.y;
+}
+
+// (h, l) += (bh, bl), renormalised.
+__device__ __forceinline__ void df_add_df(float &h, float &l, float bh, float bl)
+{
+    const float2 t = df_two_sum(h, bh);
+    const float2 u = df_fast_two_sum(t.x, __fadd_rn(__fadd_rn(t.y, l), bl));
+    h = u.x;
+    l = u.y;
+}
+
+// (h, l) *= b (float), renormalised; the product of h and b is exact via FMA.
+__device__ __forceinline__ void df_mul(float &h, float &l, float b)
+{
+    const float p = __fmul_rn(h, b);
+    const float e = __fmaf_rn(h, b, -p);
+    const float2 u = df_fast_two_sum(p, __fmaf_rn(l, b, e));
+    h = u.x;
+    l = u.y;
+}
+
+// Equilibrium radius of the interface spring for a particle of half-diameter
+// hs at t = step dt: R_eff = R(t) - hs with R(t)^2 = R0^2 - k t (radius-square
+// law, 0 once the droplet has gone).  Returned as R_eff (float) and R_eff^2 as a
+// (hi, lo) float pair, from one float64 evaluation.
+__device__ __forceinline__ void spring_radius(double R0, double k_evap, double dt, long long step,
+                                              double hs, float2 &reff2, float &reff)
+{
+    const double t = (double)step * dt;
+    const double R2 = R0 * R0 - k_evap * t;
+    const double R = R2 > 0.0 ? sqrt(R2) : 0.0;
+    const double re = R - hs;
+    const double re2 = re * re;
+    const float h = (float)re2;
+    reff2 = make_float2(h, (float)(re2 - (double)h));
+    reff = (float)re;
+}
+
+// External forces (interface spring, gravity, centrifugal) on a particle at
+// x = xh + xl (float hi / lo words).  The spring needs s = |x| - R_eff, the
+// difference of two nearly equal numbers; it is formed as
+// (|x|^2 - R_eff^2) / (|x| + R_eff) with |x|^2 from exact products and sums
+// (the lo^2 terms lie below the precision kept), so s keeps float32 relative
+// precision however large |x| is.
+__device__ __forceinline__ void external_force(const float4 &xh, float lx, float ly, float lz,
+                                               float kw, float mg, float mw2, float2 reff2,
+                                               float reff, int wall, int rot_mode, float &fx,
+                                               float &fy, float &fz)
+{
+    fx = fy = fz = 0.0f;
+    if (wall) {
+        float r2h = 0.0f, r2l = 0.0f;
+        const float hh[3] = {xh.x, xh.y, xh.z}, ll[3] = {lx, ly, lz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float p = __fmul_rn(hh[d], hh[d]);
+            const float e = __fmaf_rn(hh[d], hh[d], -p);
+            df_add_df(r2h, r2l, p, __fmaf_rn(2.0f * hh[d], ll[d], e));
+        }
+        const float rr = sqrtf(r2h);
+        float s;
+        if (reff > 0.0f) {
+            float dh = r2h, dl = r2l;
+            df_add_df(dh, dl, -reff2.x, -reff2.y);
+            s = dh / (rr + reff);
+        } else {
+            s = rr - reff;
+        }
+        if (s > 0.0f && rr > 0.0f) {
+            const float f = -kw * s / rr;
+            fx = f * xh.x;
+            fy = f * xh.y;
+            fz = f * xh.z;
+        }
+    }
+    fz -= mg;
+    if (rot_mode == 1) {
+        fx += mw2 * xh.x;
+        fy += mw2 * xh.y;
+    } else if (rot_mode == 2) {
+        fx += mw2 * xh.x;
+        fy += mw2 * xh.y;
+        fz += mw2 * xh.z;
+    }
+}
 
 struct StepParams {
     int n;
@@ -167,9 +286,9 @@ ApConfig grp_config(int idx);
 int grp_occupancy(int idx);
 cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq,
                                     const int *perm, int n_perm, const float *qblk,
-                                    double *slots, cudaStream_t st);
+                                    float *slots, cudaStream_t st);
 cudaError_t launch_allpairs(int cfg_idx, bool lj, const StreamK &sk, const float4 *xq,
-                            const int *typ, int n, const PairTab *tab, double *slots,
+                            const int *typ, int n, const PairTab *tab, float *slots,
                             cudaStream_t st);
 
 // Integrator (integrate.cu)
@@ -180,13 +299,17 @@ enum IntMode : int {
     MODE_B = 3,      // assemble F, finish the step (B), write F and v
 };
 
+// State of the integrator: position = xq.xyz (float32, the word the pair kernels
+// read) + x_lo (float32 SoA [3][n]); velocity float32 SoA [3][n]; force as
+// float32 hi/lo SoA [6][n] (hi x, y, z, then lo x, y, z).  Stream-K partial
+// slots and cell-list LJ forces use the same hi/lo layout.
 struct IntArgs {
-    double *x, *v, *F;       // SoA [3][n]
+    float *x_lo, *v, *F;     // see above
     const int *typ;
-    float4 *xq;              // float32 mirror (x, y, z, q), written when positions move
-    const double *slots;     // stream-K partials (or NULL)
+    float4 *xq;              // (x hi, y hi, z hi, q)
+    const float *slots;      // stream-K partials [slot][6][itile] (or NULL)
     StreamK sk;
-    const double *F_lj;      // cell-list LJ forces SoA [3][n] (or NULL)
+    const float *F_lj;       // cell-list LJ forces [6][n] (or NULL)
     const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
                              // no Coulomb partial); NULL: row position = i
     int ext_on;              // add external forces
@@ -195,6 +318,70 @@ struct IntArgs {
     int *flags;
     unsigned *done;          // last-block counter
 };
+
+// One particle's update after its force (Fh + Fl) has been assembled: store F
+// (MODE_FORCES, MODE_B), the closing half kick B (MODE_BA, MODE_B) and the
+// B-A-O-A part of the next step, or the overdamped update (MODE_A, MODE_BA).
+// Arrays are SoA over n particles: x_lo [3][n], v_ [3][n], F [6][n]; xq holds
+// the hi words of the position.  Noise is drawn for particle noise_idx.
+template <int MODE>
+__device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_idx,
+                                                 const TypeCoef &tc, int integrator, float hdt,
+                                                 uint64_t seed, long long step, const float4 &xh,
+                                                 float lx, float ly, float lz, const float Fh[3],
+                                                 const float Fl[3], float *x_lo, float *v_,
+                                                 float *F, float4 *xq, int *flags)
+{
+    constexpr bool DO_B = (MODE == MODE_BA || MODE == MODE_B);
+    constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    if (MODE == MODE_FORCES || MODE == MODE_B) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            F[d * n + i] = Fh[d];
+            F[(3 + d) * n + i] = Fl[d];
+        }
+    }
+    if (MODE == MODE_FORCES)
+        return;
+    const float f[3] = {__fadd_rn(Fh[0], Fl[0]), __fadd_rn(Fh[1], Fl[1]),
+                        __fadd_rn(Fh[2], Fl[2])};
+    float v[3] = {v_[i], v_[n + i], v_[2 * n + i]};
+    const bool baoab = integrator == 0;
+    if (DO_B && baoab) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            v[d] = __fmaf_rn(tc.hdt_m, f[d], v[d]);
+    }
+    if (DO_A) {
+        double n0, n1, n2;
+        normals3(seed, noise_idx, step, 0u, n0, n1, n2);
+        const float nz[3] = {(float)n0, (float)n1, (float)n2};
+        float xhi[3] = {xh.x, xh.y, xh.z}, xlo[3] = {lx, ly, lz};
+        if (baoab) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                v[d] = __fmaf_rn(tc.hdt_m, f[d], v[d]);               // B
+                df_add(xhi[d], xlo[d], __fmul_rn(hdt, v[d]));         // A
+                v[d] = __fmaf_rn(tc.c1f, v[d],
+                                 __fmaf_rn(tc.c1lo, v[d], __fmul_rn(tc.sd_of, nz[d]))); // O
+                df_add(xhi[d], xlo[d], __fmul_rn(hdt, v[d]));         // A
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                df_add(xhi[d], xlo[d], __fmaf_rn(f[d], tc.dt_mob, __fmul_rn(tc.sd_bdf, nz[d])));
+        }
+        xq[i] = make_float4(xhi[0], xhi[1], xhi[2], xh.w);
+        x_lo[i] = xlo[0];
+        x_lo[n + i] = xlo[1];
+        x_lo[2 * n + i] = xlo[2];
+        if (!(isfinite(xhi[0]) && isfinite(xhi[1]) && isfinite(xhi[2])))
+            atomicOr(flags, FLAG_NONFINITE);
+    }
+    v_[i] = v[0];
+    v_[n + i] = v[1];
+    v_[2 * n + i] = v[2];
+}
 
 cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
                              cudaStream_t st);
@@ -218,16 +405,16 @@ struct EnsAllpairsArgs {
     const PairTab *tabs;    // one table per droplet
     int n_drops;
     int pad_;
-    double *slots;
+    float *slots;
 };
 
 struct EnsIntArgs {
-    double *x, *v, *F;
+    float *x_lo, *v, *F;     // layouts as in IntArgs, over the concatenation
     const int *typ;
     float4 *xq;
     const int *drop_of;
     const EnsDrop *drops;
-    const double *slots;
+    const float *slots;
     int ext_on;
     int pad_;
     long long *step;
@@ -292,7 +479,7 @@ struct CellBufs {
 cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
                               CellBufs &b, int *flags, cudaStream_t st);
 cudaError_t launch_cell_lj(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
-                           double *F_lj, cudaStream_t st);
+                           float *F_lj, cudaStream_t st);
 int cell_build_launches();
 int cell_scan_tiles(int n_cells);
 
@@ -309,8 +496,12 @@ cudaError_t launch_block_reduce(int mode, const double *x, int n, const double *
 cudaError_t launch_boxcount(const double *x, int n, const double *origin, double eps,
                             unsigned long long *table, unsigned long long table_size,
                             int *count, int *flags, cudaStream_t st);
+// Split float64 positions (SoA) into the integrator's hi (mirror) / lo words,
+// and back (x = hi + lo in float64, for statistics).
 cudaError_t launch_mirror(const double *x, const int *typ, const float *charge_by_type,
-                          int n, float4 *xq, cudaStream_t st);
+                          int n, float4 *xq, float *x_lo, cudaStream_t st);
+cudaError_t launch_positions_f64(const float4 *xq, const float *x_lo, int n, double *x,
+                                 cudaStream_t st);
 
 // Test hooks (capi.cu)
 cudaError_t launch_philox(uint64_t seed, const uint32_t ctr[4], long long n_blocks,

@@ -378,7 +378,40 @@ def test_free_particles_msd_and_equipartition_gpu(P):
     ke = 1.5 * (v ** 2).sum(1) / 3
     assert abs(ke.mean() - 1.3) < 4 * ke.std() / math.sqrt(n)
     xo, vo, _ = oracle.run(sc, x0, v0, ty, 0, steps)
-    assert np.abs(x - xo).max() < 1e-6
+    # Velocities are float32 on the device: each step rounds v by <= 2^-24 |v|
+    # (|v| <= ~5 here), and the Langevin damping remembers a velocity error for
+    # ~1/(gamma dt) = 250 steps, so v differs from the float64 oracle by ~1e-6 and
+    # x = sum of v dt by a few 1e-6 at most over 300 steps (the 100-step
+    # position bound of the method is 1e-4 sigma).
+    assert np.abs(v - vo).max() < 1e-5
+    assert np.abs(x - xo).max() < 1e-5
+
+
+def test_position_keeps_increments_below_float32_resolution(P):
+    """Positions are hi + lo float pairs: a drift of 1e-7 sigma per step along z
+    at z in [150, 250] sigma, 76x below half a float32 ulp there (7.6e-6), must
+    accumulate as in float64; a plain float32 position would not move."""
+    n, steps = 1024, 2000
+    t = wl.TypeSpec(sigma=1.0, eps=0.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=0.0)
+    sc = wl.Scenario(name="drift", types=[t], n=n, seed=5, dt=1e-3, kT=0.0, g=1e-4,
+                     R0=1e9, wall=False, lj_mode=0, coulomb=False, integrator=1)
+    rng = np.random.default_rng(3)
+    x0 = np.column_stack([rng.uniform(-250, 250, n), rng.uniform(-250, 250, n),
+                          rng.uniform(150, 250, n)])
+    x0 = x0.astype(np.float32).astype(np.float64)
+    ty = np.zeros(n, np.int32)
+    with P.Sim(sc, x0, None, ty) as sim:
+        sim.step(steps)
+        x, _, _, st = sim.state()
+    assert st == steps
+    xo, _, _ = oracle.run(sc, x0, np.zeros_like(x0), ty, 0, steps)
+    dz, dzo = x[:, 2] - x0[:, 2], xo[:, 2] - x0[:, 2]
+    # float64 oracle: 2000 adds at |z| <= 250 round by <= 2000 * 1.5e-14
+    assert np.allclose(dzo, -steps * sc.dt * sc.g / t.gamma, rtol=1e-6, atol=0)
+    # the per-step increment is rounded to float32 (~6e-8 relative) and each
+    # compensated add is exact to ~2^-48 |x|: 2000 adds at |x| <= 250 give < 2e-9
+    assert np.abs(dz - dzo).max() <= 1e-8
+    assert np.array_equal(x[:, :2], x0[:, :2])
 
 
 def test_nonfinite_position_is_reported(P):
