@@ -46,7 +46,8 @@ def _args():
     ap.add_argument("--no-skip", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-surrogate", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--case", default="step", choices=["step", "integrator", "surrogate"],
+    ap.add_argument("--no-hbm", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--case", default="step", choices=["step", "integrator", "surrogate", "hbm"],
                     help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -211,7 +212,7 @@ def kernel_source_hash(packed):
     followed by the shared device header)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2501_04456_gb300", "csrc")
-    name = "allpairs_grouped.cu" if packed == 2 else "allpairs.cu"
+    name = "allpairs_grouped.cu" if packed in (2, 3) else "allpairs.cu"
     src = b"".join(open(os.path.join(csrc, f), "rb").read()
                    for f in (name, "npsim_internal.cuh"))
     return hashlib.sha256(src).hexdigest()[:16]
@@ -284,6 +285,95 @@ def _ensemble_measure(P, torch, stream, steps, warmup, n_plain=16, steps_per_dro
                       "sample": f"{len(sample)} of {len(scs)} droplets, every {stride}-th by N; "
                                 f"summed step time x {len(scs) / len(sample):.0f}"},
             "speedup_vs_plain": ens_dps / plain_dps}
+
+
+# Algorithmic bytes per NP of the integrator launches (float32 words): mode BA
+# reads the position hi words with the charge (16), lo words (12), velocity (12)
+# and type (4) and writes the position (28) and velocity (12); mode B reads the
+# same and writes the force as (hi, lo) pairs (24) and the velocity (12).
+INT_BYTES_BA = 16 + 12 + 12 + 4 + 16 + 12 + 12
+INT_BYTES_B = 16 + 12 + 12 + 4 + 24 + 12
+# Cell list per NP: hash (read 16, write key + rank 8), scatter (key, rank,
+# start, sorted: 16), per-cell sort (sorted read + write: 8), gather (sorted 4,
+# hi words 16, type 4, written 20), LJ (own record 20, sorted index 4, force as
+# (hi, lo) pairs 24); per cell: count reset, three scan passes and the sort's
+# range reads (28).
+CELL_BYTES_NP = 24 + 16 + 8 + 44 + 48
+CELL_BYTES_CELL = 28
+
+
+def _hbm_peak():
+    return float(_peaks().get("hbm_gbs") or 6780.0)
+
+
+def _kernel_chunks(sim, groups, chunks):
+    """Mean per-step duration (ms) of the named kernel groups over `chunks` full
+    graph chunks (events inside the step graph)."""
+    k = sim.chunk_steps()
+    ts = []
+    for _ in range(chunks):
+        sim.step(k)
+        kt, _ = sim.kernel_times()
+        ts.append(sum(kt[g] for g in groups))
+    return sum(ts) / len(ts), k
+
+
+def _integrator_roofline(P, stream, n=1 << 23, chunks=4):
+    """The fused integrator alone on n free NPs of the paper-scale composition in a
+    droplet (interface spring, gravity and noise on, no pair forces): a state of
+    ~0.7 GB, well beyond L2, so the launches stream from HBM.  Per graph chunk of
+    K steps: K-1 launches of mode BA and one of mode B."""
+    import dataclasses
+    import numpy as np
+    import workloads as wl
+    sc = dataclasses.replace(_scenario(n, 0), coulomb=False, lj_mode=0)
+    types = wl.assign_types(sc)
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal((n, 3))
+    x = d / np.linalg.norm(d, axis=1, keepdims=True) * \
+        ((sc.R0 - 2.0) * rng.random(n) ** (1 / 3))[:, None]
+    with P.Sim(sc, x, None, types, stream=stream) as sim:
+        sim.profile(True)
+        sim.step(2 * sim.chunk_steps())  # warm-up
+        ms, k = _kernel_chunks(sim, ("integrate",), chunks)
+    per_np = ((k - 1) * INT_BYTES_BA + INT_BYTES_B) / k
+    gbs = per_np * n / (ms * 1e-3) / 1e9
+    peak = _hbm_peak()
+    return {"n": n, "bytes_per_np": per_np, "ms_per_launch": ms, "bound": "hbm",
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "state": "free NPs, paper-scale composition, spring + gravity + noise"}
+
+
+def _cell_list_roofline(P, stream, n=1 << 22, chunks=4):
+    """Cell build + LJ over 27 cells on an LJ-only droplet of n NPs of the
+    paper-scale composition at the paper-scale initial number density (jittered
+    cubic lattice inside R0 - 2, types shuffled), so that the list (~0.5 GB with
+    the cell arrays) exceeds L2."""
+    import dataclasses
+    import numpy as np
+    import workloads as wl
+    sc = dataclasses.replace(_scenario(n, 0), coulomb=False, lj_mode=2)
+    rng = np.random.default_rng(1)
+    R = sc.R0 - 2.0
+    a = (4.0 / 3.0 * np.pi * R ** 3 / n) ** (1.0 / 3.0)
+    m = int(np.ceil(R / a)) + 1
+    g = np.arange(-m, m + 1) * a
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pts = pts[np.argsort(np.linalg.norm(pts, axis=1), kind="stable")[:n]]
+    x = pts + rng.uniform(-0.1 * a, 0.1 * a, pts.shape)
+    types = rng.permutation(wl.assign_types(sc)).astype(np.int32)
+    with P.Sim(sc, x, None, types, stream=stream) as sim:
+        sim.profile(True)
+        dim, cells = sim.cell_grid()
+        sim.step(2 * sim.chunk_steps())
+        ms, _ = _kernel_chunks(sim, ("cell_build", "cell_lj"), chunks)
+        kt, _ = sim.kernel_times()
+    byts = CELL_BYTES_NP * n + CELL_BYTES_CELL * cells
+    gbs = byts / (ms * 1e-3) / 1e9
+    peak = _hbm_peak()
+    return {"n": n, "cells": cells, "lattice_spacing": a, "bytes_per_step": byts,
+            "ms_per_step": ms, "ms_build": kt["cell_build"], "ms_lj": kt["cell_lj"],
+            "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak}
 
 
 def _surrogate_measure(P, batch=4096, n_nets=4, reps=7):
@@ -418,6 +508,11 @@ def run_ours(a):
         ens = _ensemble_measure(P, torch, stream, max(3, a.steps // 2), a.warmup)
 
     surr = None
+    hbm = {}
+    if not a.no_hbm and rank == 0:
+        hbm["integrator"] = _integrator_roofline(P, stream)
+        hbm["cell_list"] = _cell_list_roofline(P, stream)
+
     if not a.no_surrogate and rank == 0:
         surr = _surrogate_measure(P)
 
@@ -479,6 +574,7 @@ def run_ours(a):
             "skip_neutral": skip,
             "ensemble": ens,
             "surrogate": surr,
+            **hbm,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -523,6 +619,16 @@ def main():
     a = _args()
     if a.case == "integrator":
         run_integrator_case(a)
+        return
+    if a.case == "hbm":
+        import torch
+        from paper_2501_04456_gb300 import build as _b
+        _b.build()
+        import paper_2501_04456_gb300 as P
+        stream = torch.cuda.current_stream()
+        n = a.n if a.n != 250000 else 1 << 23  # --n sets the integrator's size (cell list: n/2)
+        print(json.dumps({"case": "hbm", "integrator": _integrator_roofline(P, stream, n),
+                          "cell_list": _cell_list_roofline(P, stream, n // 2)}), flush=True)
         return
     if a.case == "surrogate":
         from paper_2501_04456_gb300 import build as _b

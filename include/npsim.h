@@ -194,8 +194,9 @@ int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out);
 /* Launch shape of the all-pairs kernel chosen by the autotuner: threads per
  * CTA, particles i per thread, j-tile length, CTAs, the index of the shape in
  * the autotuner's table, and 1 if it is the packed float32x2 Coulomb kernel, 2
- * if it is the packed Coulomb kernel over partners grouped by charge value.
- * Any pointer may be NULL.  The environment variable NPSIM_AUTOTUNE=1:<index>
+ * if it is the packed Coulomb kernel over partners grouped by charge value, 3
+ * if it is the packed LJ + Coulomb kernel over partners grouped by type (0: the
+ * scalar kernel).  Any pointer may be NULL.  The environment variable NPSIM_AUTOTUNE=1:<index>
  * forces a shape at npsim_create (NPSIM_AUTOTUNE=0: the first shape). */
 int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j_tile,
                           int *grid, int *index, int *packed);
@@ -340,6 +341,12 @@ int npsim_coulomb_forces_noalloc(const float *dev_xyzq, int64_t n, double bjerru
 /* Kernel launches per step in a long run (pair kernels + cell-list kernels + one
  * integrator pass); npsim_step adds one integrator launch per graph chunk. */
 int npsim_launches_per_step(npsim_sim_t sim, int *launches);
+
+/* Cell grid of the LJ cell list (lj_mode 2): cells per axis and in total; both
+ * 0 when the scenario has no cell list.  The grid covers [-L, L)^3 with L the
+ * largest |coordinate| at creation (or R0) plus the largest cutoff, cell edge
+ * >= the largest cutoff. */
+int npsim_cell_grid(npsim_sim_t sim, int *dim, int64_t *n_cells);
 
 /* Steps per captured CUDA graph (npsim_step replays ceil(n / chunk) graphs). */
 int npsim_chunk_steps(npsim_sim_t sim, int *chunk);

@@ -110,6 +110,7 @@ def lib():
             L.npsim_coulomb_forces_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_double,
                                                        C.c_void_p, C.c_void_p]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
+            L.npsim_cell_grid.argtypes = [_h, _i32, _i64]
             L.npsim_ens_create.argtypes = [C.POINTER(npsim_droplet_t), C.c_int32, C.c_void_p,
                                            C.POINTER(_h)]
             L.npsim_ens_step.argtypes = [_h, C.c_int64]
@@ -338,6 +339,13 @@ def npsim_launches_per_step(h):
     return a.value
 
 
+def npsim_cell_grid(h):
+    """(cells per axis, cells) of the LJ cell list; (0, 0) without one."""
+    d, c = C.c_int32(), C.c_int64()
+    _check(lib().npsim_cell_grid(h, C.byref(d), C.byref(c)))
+    return d.value, c.value
+
+
 def npsim_chunk_steps(h):
     a = C.c_int32()
     _check(lib().npsim_chunk_steps(h, C.byref(a)))
@@ -400,6 +408,9 @@ class Sim:
 
     def chunk_steps(self):
         return npsim_chunk_steps(self.h)
+
+    def cell_grid(self):
+        return npsim_cell_grid(self.h)
 
     def profile(self, enable=True):
         npsim_profile(self.h, enable)

@@ -1,32 +1,38 @@
-// allpairs_grouped.cu -- all-pairs Coulomb forces (step (ii) of the loop in
-// arXiv 2501.04456 Sec. 2.2) with the partners ordered by charge value.
+// allpairs_grouped.cu -- all-pairs forces (step (ii) of the loop in arXiv
+// 2501.04456 Sec. 2.2) with the particles listed in a grouped order.
 //
-// Charge is a property of the NP type (Sec. 2.1: NPs of several types with
-// their own radius, mass and charge), so the particles can be listed once, at
-// creation, grouped by charge value, each group padded to a whole number of
-// 512-particle blocks.  Every j-tile then holds partners of one charge q_t,
-// and the sum over a tile factors as
-//   sum_{j in tile} q_j r_ij / r^3 = q_t sum_{j in tile} r_ij / r^3,
-// which removes the per-pair multiply by q_j: 11 FP32 operations per pair on
-// the packed float32x2 instructions (FADD2 / FMUL2 / FFMA2), two partners per
-// register pair, plus one MUFU.RSQ per pair.  The tile sum is multiplied by q_t
-// once and added into a compensated (TwoSum) float32 accumulator.
+// Charge, size and LJ depth are properties of the NP type (Sec. 2.1: NPs of
+// several types with their own radius, mass and charge), so the particles can
+// be listed once, at creation, grouped by type (charged types first), each
+// group padded to a whole number of 512-position blocks.  Every j-tile then
+// holds partners of one type, and the per-pair parameters become per-tile
+// constants:
+//  * k_coulomb_grp (Coulomb only): the tile sum factors as
+//      sum_{j in tile} q_j r_ij / r^3 = q_t sum_{j in tile} r_ij / r^3,
+//    which removes the per-pair multiply by q_j: 11 FP32 operations per pair
+//    on the packed float32x2 instructions (FADD2 / FMUL2 / FFMA2), two
+//    partners per register pair, plus one MUFU.RSQ per pair; the tile sum is
+//    multiplied by q_t once and added into a compensated (TwoSum) accumulator.
+//    The result is the field sum_j q_j r_ij / r^3 (the integrator multiplies
+//    by C q_i).  Neutral types form the last groups; with `skip neutral` the
+//    caller limits rows and columns to the charged groups, since every
+//    Coulomb term with a neutral particle is exactly zero.
+//  * k_ljc_grp (LJ + Coulomb): the type-pair constants of a row and a tile are
+//    loaded once per tile (ljc_tile_sweep); the result is the force.
 //
 // Rows (particles i) and columns (partners j) both follow the grouped order:
 // perm[k] is the particle at position k (-1 for padding, placed far away).
-// Neutral particles form the last group; with `skip neutral` the caller limits
-// rows and columns to the charged groups, since every Coulomb term with a
-// neutral particle is exactly zero.  The (row tile x column tile) units are
-// split over the CTAs as in the other all-pairs kernels (stream-K), one
-// compensated (hi, lo) float32 partial per (row, CTA) written to slot row + CTA.
+// The (row tile x column tile) units are split over the CTAs as in the other
+// all-pairs kernels (stream-K), one compensated (hi, lo) float32 partial per
+// (row, CTA) written to slot row + CTA.
 #include "npsim_internal.cuh"
 
 namespace npsim {
 
 namespace {
 
-constexpr float kSelfEps = 1e-20f; // added to r^2; the self pair has r_ij = 0 exactly
-constexpr float kPad = 1.0e18f;    // padding: far enough that 1/r^3 underflows to 0
+constexpr float kSelfEps = kPairSelfEps;
+constexpr float kPad = kPairPad;
 
 template <int BLOCK, int KI, int JT>
 __global__ void __launch_bounds__(BLOCK)
@@ -128,6 +134,100 @@ k_coulomb_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n
     }
 }
 
+// LJ + Coulomb over the type-grouped order: the constants of row k and tile
+// jt come from the table passed in (full, LJ only or Coulomb only).
+template <int BLOCK, int KI, int JT>
+__global__ void __launch_bounds__(BLOCK)
+k_ljc_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_perm,
+          const int *__restrict__ tblk, const PairTab *__restrict__ tab, StreamK sk,
+          float *__restrict__ slots)
+{
+    constexpr int ITILE = BLOCK * KI;
+    constexpr int JP = JT / 2;
+    __shared__ float4 s_a[JP]; // (-x0, -x1, -y0, -y1)
+    __shared__ float2 s_b[JP]; // (-z0, -z1)
+    __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += BLOCK)
+        s_tab[k] = tab->e[k];
+
+    const int c = blockIdx.x;
+    const long long p_end = sk_begin(sk, c + 1);
+    long long p = sk_begin(sk, c);
+
+    while (p < p_end) {
+        const int r = (int)(p / sk.n_jt);
+        const int jt0 = (int)(p - (long long)r * sk.n_jt);
+        const int jt1 = (int)min((long long)sk.n_jt, (long long)jt0 + (p_end - p));
+
+        float2 xi[KI], yi[KI], zi[KI];
+        int trow[KI];
+        float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const int pos = r * ITILE + k * BLOCK + threadIdx.x;
+            const int i = pos < n_perm ? perm[pos] : -1;
+            float4 q = make_float4(kPad, kPad, kPad, 0.0f);
+            if (i >= 0)
+                q = xq[i];
+            xi[k] = make_float2(q.x, q.x);
+            yi[k] = make_float2(q.y, q.y);
+            zi[k] = make_float2(q.z, q.z);
+            trow[k] = (pos < n_perm ? tblk[pos >> 8] : 0) * NPSIM_MAX_TYPES;
+            hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
+        }
+
+        for (int jt = jt0; jt < jt1; ++jt) {
+            __syncthreads(); // the previous tile has been consumed (and s_tab is loaded)
+            for (int m = threadIdx.x; m < JP; m += BLOCK) {
+                const int k0 = jt * JT + 2 * m;
+                const int j0 = perm[k0], j1 = perm[k0 + 1]; // n_perm is a multiple of JT
+                const float4 pad = make_float4(-kPad, -kPad, -kPad, 0.0f);
+                const float4 a = j0 >= 0 ? xq[j0] : pad;
+                const float4 b = j1 >= 0 ? xq[j1] : pad;
+                s_a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
+                s_b[m] = make_float2(-a.z, -b.z);
+            }
+            __syncthreads();
+
+            const int tt = tblk[(jt * JT) >> 8]; // one type per tile
+            float4 cst[KI];
+            float2 ax[KI], ay[KI], az[KI];
+#pragma unroll
+            for (int k = 0; k < KI; ++k) {
+                cst[k] = s_tab[trow[k] + tt];
+                ax[k] = ay[k] = az[k] = make_float2(0.0f, 0.0f);
+            }
+            const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
+            if (diag)
+                ljc_tile_sweep<KI, true>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
+            else
+                ljc_tile_sweep<KI, false>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
+#pragma unroll
+            for (int k = 0; k < KI; ++k) {
+                two_sum_acc(hx[k], lx[k], ax[k].x);
+                two_sum_acc(hx[k], lx[k], ax[k].y);
+                two_sum_acc(hy[k], ly[k], ay[k].x);
+                two_sum_acc(hy[k], ly[k], ay[k].y);
+                two_sum_acc(hz[k], lz[k], az[k].x);
+                two_sum_acc(hz[k], lz[k], az[k].y);
+            }
+        }
+
+        float *slot = slots + (size_t)(r + c) * 6 * ITILE; // (hi x, y, z, lo x, y, z)
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const int idx = k * BLOCK + threadIdx.x;
+            slot[idx] = hx[k];
+            slot[ITILE + idx] = hy[k];
+            slot[2 * ITILE + idx] = hz[k];
+            slot[3 * ITILE + idx] = lx[k];
+            slot[4 * ITILE + idx] = ly[k];
+            slot[5 * ITILE + idx] = lz[k];
+        }
+        p += jt1 - jt0;
+    }
+}
+
 struct GEntry {
     ApConfig cfg;
     const void *fn;
@@ -146,6 +246,21 @@ cudaError_t launch_g(const StreamK &sk, const float4 *xq, const int *perm, int n
                      const float *qblk, float *slots, cudaStream_t st)
 {
     k_coulomb_grp<B, K, J><<<sk.grid, B, 0, st>>>(xq, perm, n_perm, qblk, sk, slots);
+    return cudaGetLastError();
+}
+
+#define NPSIM_LJG(B, K, J) GEntry{ApConfig{B, K, J, 0}, (const void *)k_ljc_grp<B, K, J>}
+
+const GEntry kLjg[] = {
+    NPSIM_LJG(256, 1, 512), NPSIM_LJG(256, 2, 512), NPSIM_LJG(512, 1, 512),
+    NPSIM_LJG(128, 2, 256), NPSIM_LJG(256, 2, 256), NPSIM_LJG(128, 4, 256),
+};
+
+template <int B, int K, int J>
+cudaError_t launch_l(const StreamK &sk, const float4 *xq, const int *perm, int n_perm,
+                     const int *tblk, const PairTab *tab, float *slots, cudaStream_t st)
+{
+    k_ljc_grp<B, K, J><<<sk.grid, B, 0, st>>>(xq, perm, n_perm, tblk, tab, sk, slots);
     return cudaGetLastError();
 }
 
@@ -176,6 +291,34 @@ cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq
     case 4: return launch_g<128, 4, 256>(sk, xq, perm, n_perm, qblk, slots, st);
     case 5: return launch_g<512, 1, 512>(sk, xq, perm, n_perm, qblk, slots, st);
     case 6: return launch_g<1024, 1, 512>(sk, xq, perm, n_perm, qblk, slots, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int ljg_num_configs() { return (int)(sizeof(kLjg) / sizeof(kLjg[0])); }
+
+ApConfig ljg_config(int idx) { return kLjg[idx].cfg; }
+
+int ljg_occupancy(int idx)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kLjg[idx].fn, kLjg[idx].cfg.block,
+                                                      0) != cudaSuccess)
+        return 0;
+    return occ;
+}
+
+cudaError_t launch_allpairs_ljgrp(int idx, const StreamK &sk, const float4 *xq,
+                                  const int *perm, int n_perm, const int *tblk,
+                                  const PairTab *tab, float *slots, cudaStream_t st)
+{
+    switch (idx) {
+    case 0: return launch_l<256, 1, 512>(sk, xq, perm, n_perm, tblk, tab, slots, st);
+    case 1: return launch_l<256, 2, 512>(sk, xq, perm, n_perm, tblk, tab, slots, st);
+    case 2: return launch_l<512, 1, 512>(sk, xq, perm, n_perm, tblk, tab, slots, st);
+    case 3: return launch_l<128, 2, 256>(sk, xq, perm, n_perm, tblk, tab, slots, st);
+    case 4: return launch_l<256, 2, 256>(sk, xq, perm, n_perm, tblk, tab, slots, st);
+    case 5: return launch_l<128, 4, 256>(sk, xq, perm, n_perm, tblk, tab, slots, st);
     default: return cudaErrorInvalidValue;
     }
 }

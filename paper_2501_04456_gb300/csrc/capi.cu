@@ -141,8 +141,9 @@ struct npsim_sim {
     int *typ = nullptr;
     float *slots = nullptr;
     float *F_lj = nullptr;                // [6][n]
-    PairTab *tab_full = nullptr, *tab_lj = nullptr;
+    PairTab *tab_full = nullptr, *tab_lj = nullptr, *tab_coul = nullptr;
     long long *d_step = nullptr;
+    float4 *d_spring = nullptr; // [2][NPSIM_MAX_TYPES] spring radius table (spring_entry)
     int *d_flags = nullptr;
     unsigned *d_done = nullptr;
 
@@ -153,12 +154,13 @@ struct npsim_sim {
     bool ap = false, ap_lj = false;
     int ap_idx = 0;
 
-    // charge-grouped order for the grouped Coulomb kernel (built when Coulomb is on)
+    // type-grouped order for the grouped kernels (built when pair sums are on)
     int *perm = nullptr;    // [n_perm] particle at each grouped position, -1 = padding
     float *qblk = nullptr;  // [n_perm / 256] charge of each 256-position block
-    int *row_pos = nullptr; // [n] grouped position of particle i (-1: no Coulomb row)
+    int *tblk = nullptr;    // [n_perm / 256] type of each 256-position block
+    int *row_pos = nullptr; // [n] grouped position of particle i (-1: no pair row)
     int n_perm = 0;         // grouped length (multiple of 512)
-    int grp_len = 0;        // rows and columns the grouped kernel covers
+    int grp_len = 0;        // rows and columns the grouped kernels cover
     StreamK sk{};
     StepParams sp{};
 
@@ -201,11 +203,14 @@ struct npsim_sim {
         dfree(slots);
         dfree(perm);
         dfree(qblk);
+        dfree(tblk);
         dfree(row_pos);
         dfree(F_lj);
         dfree(tab_full);
         dfree(tab_lj);
+        dfree(tab_coul);
         dfree(d_step);
+        dfree(d_spring);
         dfree(d_flags);
         dfree(d_done);
         CellBufs *bufs[2] = {&cb, &scb};
@@ -264,22 +269,31 @@ CellGrid make_grid(double L, double h_min, long long max_cells)
     return g;
 }
 
-// Launch shapes of the all-pairs sum in one index space: [0, nc) the
-// identity-order kernels of allpairs.cu (scalar and packed), then the
-// charge-grouped kernels of allpairs_grouped.cu (Coulomb only).
-int shape_count() { return ap_num_configs() + grp_num_configs(); }
+// Launch shapes of the all-pairs sum in one index space: [0, A) the
+// identity-order kernels of allpairs.cu (scalar and packed), then [A, A + G) the
+// charge-grouped Coulomb kernels and [A + G, A + G + L) the type-grouped LJ +
+// Coulomb kernels of allpairs_grouped.cu.
+int shape_count() { return ap_num_configs() + grp_num_configs() + ljg_num_configs(); }
 
 bool shape_grouped(int k) { return k >= ap_num_configs(); }
 
+bool shape_ljg(int k) { return k >= ap_num_configs() + grp_num_configs(); }
+
 ApConfig shape_config(int k)
 {
+    if (shape_ljg(k))
+        return ljg_config(k - ap_num_configs() - grp_num_configs());
     return shape_grouped(k) ? grp_config(k - ap_num_configs()) : ap_config(k);
 }
 
 int shape_occupancy(const npsim_sim *s, int k, bool lj)
 {
+    if (shape_grouped(k) && (!s->perm || s->grp_len == 0))
+        return 0;
+    if (shape_ljg(k))
+        return ljg_occupancy(k - ap_num_configs() - grp_num_configs());
     if (shape_grouped(k))
-        return (lj || !s->perm || s->grp_len == 0) ? 0 : grp_occupancy(k - ap_num_configs());
+        return lj ? 0 : grp_occupancy(k - ap_num_configs());
     return ap_occupancy(k, lj);
 }
 
@@ -300,13 +314,24 @@ void shape_streamk(const npsim_sim *s, int k, int grid_target, StreamK &sk)
     sk.pad_ = 0;
 }
 
-cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, const StreamK &sk,
-                         const PairTab *tab, float *slots, cudaStream_t st)
+// Type-pair table of a pair sum: LJ + Coulomb, LJ only or Coulomb only.
+const PairTab *pair_table(const npsim_sim *s, bool lj, bool coul)
 {
+    return lj ? (coul ? s->tab_full : s->tab_lj) : s->tab_coul;
+}
+
+cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, bool coul, const StreamK &sk,
+                         float *slots, cudaStream_t st)
+{
+    if (shape_ljg(k))
+        return launch_allpairs_ljgrp(k - ap_num_configs() - grp_num_configs(), sk, s->xq,
+                                     s->perm, s->n_perm, s->tblk, pair_table(s, lj, coul),
+                                     slots, st);
     if (shape_grouped(k))
         return launch_allpairs_grouped(k - ap_num_configs(), sk, s->xq, s->perm, s->n_perm,
                                        s->qblk, slots, st);
-    return launch_allpairs(k, lj, sk, s->xq, s->typ, s->n, tab, slots, st);
+    return launch_allpairs(k, lj, sk, s->xq, s->typ, s->n, lj ? pair_table(s, lj, coul) : nullptr,
+                           slots, st);
 }
 
 // Queue the pair forces of the current positions and one integrator pass.
@@ -323,7 +348,10 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     const bool ap_coul = want_coul && s->P.coulomb &&
                          !(shape_grouped(s->ap_idx) && s->grp_len == 0);
     const bool ap = ap_lj || ap_coul;
-    const bool grouped = ap && !ap_lj && shape_grouped(s->ap_idx);
+    const bool ljg = shape_ljg(s->ap_idx);
+    // the ungrouped kernels also serve a Coulomb-only pass of an LJ simulation
+    // whose tuned shape is charge-grouped (never: LJ excludes it) or type-grouped
+    const bool grouped = ap && shape_grouped(s->ap_idx) && (ljg || !ap_lj);
     const bool prof = prof_slot >= 0 && s->profiling;
     auto mark = [&](int group, int edge) -> cudaError_t {
         // inside stream capture a plain cudaEventRecord only orders the capture;
@@ -341,9 +369,8 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
         NP_CUDA(mark(KG_CELL_LJ, 1));
     }
     if (ap) {
-        const PairTab *tab = ap_lj ? (ap_coul ? s->tab_full : s->tab_lj) : nullptr;
         NP_CUDA(mark(KG_ALLPAIRS, 0));
-        NP_CUDA(shape_launch(s, s->ap_idx, ap_lj, s->sk, tab, s->slots, st));
+        NP_CUDA(shape_launch(s, s->ap_idx, ap_lj, ap_coul, s->sk, s->slots, st));
         NP_CUDA(mark(KG_ALLPAIRS, 1));
     }
     IntArgs a{};
@@ -356,8 +383,9 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     a.sk = s->sk;
     a.F_lj = lj_cell ? s->F_lj : nullptr;
     a.ext_on = ext ? 1 : 0;
-    a.field_slots = (ap && !ap_lj) ? 1 : 0;
+    a.field_slots = (ap && !ap_lj && !ljg) ? 1 : 0; // ljg sums C q_a q_b from its table
     a.row_pos = grouped ? s->row_pos : nullptr;
+    a.spring = s->d_spring;
     a.step = s->d_step;
     a.flags = s->d_flags;
     a.done = s->d_done;
@@ -376,6 +404,7 @@ int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
     a.typ = s->typ;
     a.xq = s->xq;
     a.sk = s->sk;
+    a.spring = s->d_spring;
     a.step = s->d_step;
     a.flags = s->d_flags;
     a.done = s->d_done;
@@ -479,19 +508,19 @@ int autotune(npsim_sim *s)
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
-        const PairTab *tab = lj ? s->tab_full : nullptr;
+        const bool coul = s->P.coulomb != 0;
         for (int c = 0; c < nc; ++c) {
             const int occ = shape_occupancy(s, c, lj);
             if (occ <= 0)
                 continue;
             StreamK sk;
             shape_streamk(s, c, occ * s->sms, sk);
-            if (shape_launch(s, c, lj, sk, tab, tmp, s->user) != cudaSuccess)
+            if (shape_launch(s, c, lj, coul, sk, tmp, s->user) != cudaSuccess)
                 continue;
             const int reps = s->n > 100000 ? 2 : 5;
             cudaEventRecord(e0, s->user);
             for (int r = 0; r < reps; ++r)
-                shape_launch(s, c, lj, sk, tab, tmp, s->user);
+                shape_launch(s, c, lj, coul, sk, tmp, s->user);
             cudaEventRecord(e1, s->user);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 continue;
@@ -515,67 +544,62 @@ int autotune(npsim_sim *s)
     return NPSIM_OK;
 }
 
-// Charge-grouped order (types carry the charge): the distinct non-zero
-// charges in order of first type, then the neutral NPs; inside a group NPs keep
-// their index order; every group is padded with -1 to a multiple of 512.
+// Type-grouped order: the charged types first (in type order), then the
+// neutral ones; inside a group NPs keep their index order; every group is
+// padded with -1 to a multiple of 512, so each 256-position block has one type
+// (and one charge).  With skip_neutral and no LJ in the pair sum, the grouped
+// kernels cover only the charged groups and neutral NPs have no pair row.
 int build_grouping(npsim_sim *s, const int32_t *type)
 {
-    std::vector<double> gq;
-    std::vector<int> tg(s->T);
-    for (int t = 0; t < s->T; ++t) {
-        const double q = s->types[t].charge;
-        if (q == 0.0)
-            continue;
-        int g = -1;
-        for (size_t k = 0; k < gq.size(); ++k)
-            if (gq[k] == q)
-                g = (int)k;
-        if (g < 0) {
-            g = (int)gq.size();
-            gq.push_back(q);
-        }
-        tg[t] = g;
-    }
-    const int neutral = (int)gq.size();
+    std::vector<int> order;
+    for (int t = 0; t < s->T; ++t)
+        if (s->types[t].charge != 0.0)
+            order.push_back(t);
+    const int n_charged_types = (int)order.size();
     for (int t = 0; t < s->T; ++t)
         if (s->types[t].charge == 0.0)
-            tg[t] = neutral;
-    std::vector<int> perm;
+            order.push_back(t);
+    std::vector<std::vector<int>> members(s->T);
+    for (int i = 0; i < s->n; ++i)
+        members[type[i]].push_back(i);
+    std::vector<int> perm, tb;
     std::vector<float> qb;
     std::vector<int> pos(s->n, -1);
     int charged_len = 0;
-    for (int g = 0; g <= neutral; ++g) {
-        for (int i = 0; i < s->n; ++i)
-            if (tg[type[i]] == g) {
-                pos[i] = (int)perm.size();
-                perm.push_back(i);
-            }
+    for (int g = 0; g < (int)order.size(); ++g) {
+        const int t = order[g];
+        if (members[t].empty())
+            continue;
+        for (int i : members[t]) {
+            pos[i] = (int)perm.size();
+            perm.push_back(i);
+        }
         while (perm.size() % 512)
             perm.push_back(-1);
-        const float q = g < neutral ? (float)gq[g] : 0.0f;
-        while (qb.size() < perm.size() / 256)
-            qb.push_back(q);
-        if (g == neutral - 1 || (neutral == 0 && g == 0))
-            charged_len = neutral > 0 ? (int)perm.size() : 0;
-    }
-    if (perm.empty()) { // cannot happen for n >= 1; keep the buffers non-empty
-        perm.assign(512, -1);
-        qb.assign(2, 0.0f);
+        while (qb.size() < perm.size() / 256) {
+            qb.push_back((float)s->types[t].charge);
+            tb.push_back(t);
+        }
+        if (g < n_charged_types)
+            charged_len = (int)perm.size();
     }
     s->n_perm = (int)perm.size();
-    if (s->P.skip_neutral) {
+    const bool skip = s->P.skip_neutral && s->P.lj_mode != 1;
+    if (skip) {
         s->grp_len = charged_len;
         for (int i = 0; i < s->n; ++i)
-            if (tg[type[i]] == neutral)
+            if (s->types[type[i]].charge == 0.0)
                 pos[i] = -1;
     } else {
         s->grp_len = s->n_perm;
     }
     NP_CUDA(dalloc(&s->perm, perm.size()));
     NP_CUDA(dalloc(&s->qblk, qb.size()));
+    NP_CUDA(dalloc(&s->tblk, tb.size()));
     NP_CUDA(dalloc(&s->row_pos, (size_t)s->n));
     NP_CUDA(cudaMemcpy(s->perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
     NP_CUDA(cudaMemcpy(s->qblk, qb.data(), sizeof(float) * qb.size(), cudaMemcpyHostToDevice));
+    NP_CUDA(cudaMemcpy(s->tblk, tb.data(), sizeof(int) * tb.size(), cudaMemcpyHostToDevice));
     NP_CUDA(cudaMemcpy(s->row_pos, pos.data(), sizeof(int) * pos.size(),
                        cudaMemcpyHostToDevice));
     return NPSIM_OK;
@@ -640,6 +664,12 @@ int finish_upload(npsim_sim *s, int64_t step)
     long long st = step;
     NP_CUDA(cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice,
                             s->user));
+    float4 tab[NPSIM_MAX_TYPES] = {};
+    for (int t = 0; t < s->T; ++t)
+        tab[t] = spring_entry(s->P.R0, s->P.k_evap, s->P.dt, st, 0.5 * s->types[t].sigma);
+    NP_CUDA(cudaMemcpyAsync(s->d_spring + (st & 1) * NPSIM_MAX_TYPES, tab, sizeof(tab),
+                            cudaMemcpyHostToDevice, s->user));
+    NP_CUDA(cudaStreamSynchronize(s->user)); // tab lives on this stack frame
     int rc = enqueue_pass(s, MODE_FORCES, true, true, true, s->F, s->user);
     if (rc)
         return rc;
@@ -858,8 +888,10 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
     sp.g = params->g;
     sp.omega2 = params->omega * params->omega;
     fill_coefs(types, params, sp.tc, s->charge_f);
-    PairTab tf{}, tl{};
+    PairTab tf{}, tl{}, tc{};
     const double rc_max = fill_tabs(types, params, s->has_ov ? s->eps_ov : nullptr, &tf, &tl);
+    for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) // Coulomb only: no LJ pair in range
+        tc.e[k] = make_float4(0.0f, 0.0f, 0.0f, tf.e[k].w);
 
 #define BAIL_CUDA(call)                                                                 \
     do {                                                                                \
@@ -880,7 +912,10 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
     BAIL_CUDA(dalloc(&s->typ, (size_t)n));
     BAIL_CUDA(dalloc(&s->tab_full, 1));
     BAIL_CUDA(dalloc(&s->tab_lj, 1));
+    BAIL_CUDA(dalloc(&s->tab_coul, 1));
     BAIL_CUDA(dalloc(&s->d_step, 1));
+    BAIL_CUDA(dalloc(&s->d_spring, 2 * NPSIM_MAX_TYPES));
+    BAIL_CUDA(cudaMemsetAsync(s->d_spring, 0, sizeof(float4) * 2 * NPSIM_MAX_TYPES, s->user));
     BAIL_CUDA(dalloc(&s->d_flags, 1));
     BAIL_CUDA(dalloc(&s->d_done, 1));
     BAIL_CUDA(cudaMemsetAsync(s->d_flags, 0, sizeof(int), s->user));
@@ -888,6 +923,8 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
     BAIL_CUDA(cudaMemcpyAsync(s->tab_full, &tf, sizeof(PairTab), cudaMemcpyHostToDevice,
                               s->user));
     BAIL_CUDA(cudaMemcpyAsync(s->tab_lj, &tl, sizeof(PairTab), cudaMemcpyHostToDevice,
+                              s->user));
+    BAIL_CUDA(cudaMemcpyAsync(s->tab_coul, &tc, sizeof(PairTab), cudaMemcpyHostToDevice,
                               s->user));
     BAIL_CUDA(cudaMemcpyAsync(s->typ, type, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
                               s->user));
@@ -916,11 +953,9 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
         BAIL_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->x_lo, s->user));
     }
     if (s->ap) {
-        if (params->coulomb) {
-            rc = build_grouping(s, type);
-            if (rc)
-                return bail(rc);
-        }
+        rc = build_grouping(s, type);
+        if (rc)
+            return bail(rc);
         rc = autotune(s);
         if (rc)
             return bail(rc);
@@ -1045,7 +1080,11 @@ int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_t
     if (index)
         *index = s->ap ? s->ap_idx : -1;
     if (packed)
-        *packed = !s->ap ? 0 : shape_grouped(s->ap_idx) ? 2 : ap_packed(s->ap_idx) ? 1 : 0;
+        *packed = !s->ap                  ? 0
+                  : shape_ljg(s->ap_idx)     ? 3
+                  : shape_grouped(s->ap_idx) ? 2
+                  : ap_packed(s->ap_idx)     ? 1
+                                             : 0;
     return NPSIM_OK;
 }
 
@@ -1060,6 +1099,16 @@ int npsim_launches_per_step(npsim_sim_t s, int *launches)
 {
     NP_REQUIRE(s && launches, "sim and launches are required");
     *launches = 1 + (s->ap ? 1 : 0) + (s->cell ? cell_build_launches() + 1 : 0);
+    return NPSIM_OK;
+}
+
+int npsim_cell_grid(npsim_sim_t s, int *dim, int64_t *n_cells)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    if (dim)
+        *dim = s->cell ? s->grid.dim : 0;
+    if (n_cells)
+        *n_cells = s->cell ? s->grid.n_cells : 0;
     return NPSIM_OK;
 }
 
@@ -1449,11 +1498,13 @@ struct npsim_ens {
     float *F = nullptr, *F_tmp = nullptr; // [6][n_total]
     float4 *xq = nullptr;
     int *typ = nullptr, *drop_of = nullptr;
+    int *perm = nullptr, *tblk = nullptr, *row_pos = nullptr; // type-grouped order
     EnsDrop *drops = nullptr;
     PairTab *tabs = nullptr;
     long long *unit0 = nullptr;
     float *slots = nullptr;
     long long *d_step = nullptr;
+    float4 *d_spring = nullptr; // [2][D][NPSIM_MAX_TYPES]
     int *d_flags = nullptr;
     unsigned *d_done = nullptr;
 
@@ -1473,11 +1524,15 @@ struct npsim_ens {
         dfree(xq);
         dfree(typ);
         dfree(drop_of);
+        dfree(perm);
+        dfree(tblk);
+        dfree(row_pos);
         dfree(drops);
         dfree(tabs);
         dfree(unit0);
         dfree(slots);
         dfree(d_step);
+        dfree(d_spring);
         dfree(d_flags);
         dfree(d_done);
         if (cap)
@@ -1497,8 +1552,8 @@ long long ens_geometry(npsim_ens *e, int shape, std::vector<long long> &unit0, l
     unit0.assign(e->D + 1, 0);
     for (int d = 0; d < e->D; ++d) {
         EnsDrop &g = e->h_drops[d];
-        g.n_it = (e->cnt[d] + itile - 1) / itile;
-        g.n_jt = (e->cnt[d] + c.jt - 1) / c.jt;
+        g.n_it = (g.npad + itile - 1) / itile;
+        g.n_jt = g.npad / c.jt; // npad is a multiple of 256, jt divides 256
         g.row0 = (int)r;
         g.unit0 = u;
         unit0[d] = u;
@@ -1536,7 +1591,8 @@ EnsAllpairsArgs ens_ap_args(npsim_ens *e, float *slots)
 {
     EnsAllpairsArgs a{};
     a.xq = e->xq;
-    a.typ = e->typ;
+    a.perm = e->perm;
+    a.tblk = e->tblk;
     a.drops = e->drops;
     a.unit0 = e->unit0;
     a.tabs = e->tabs;
@@ -1555,8 +1611,10 @@ int ens_pass(npsim_ens *e, int mode, bool ext, float *Fout, cudaStream_t st)
     a.typ = e->typ;
     a.xq = e->xq;
     a.drop_of = e->drop_of;
+    a.row_pos = e->row_pos;
     a.drops = e->drops;
     a.slots = e->slots;
+    a.spring = e->d_spring;
     a.ext_on = ext ? 1 : 0;
     a.step = e->d_step;
     a.flags = e->d_flags;
@@ -1574,7 +1632,9 @@ int ens_chunk(npsim_ens *e, int k, cudaStream_t st)
     a.typ = e->typ;
     a.xq = e->xq;
     a.drop_of = e->drop_of;
+    a.row_pos = e->row_pos;
     a.drops = e->drops;
+    a.spring = e->d_spring;
     a.step = e->d_step;
     a.flags = e->d_flags;
     a.done = e->d_done;
@@ -1791,6 +1851,28 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
         }
         off += n;
     }
+    // type-grouped order of every droplet: its types in order, each group padded
+    // with -1 to a multiple of 256 positions
+    std::vector<int> gperm, gtblk, gpos((size_t)total, -1);
+    for (int d = 0; d < n_drops; ++d) {
+        EnsDrop &g = e->h_drops[d];
+        g.gpos0 = (int)gperm.size();
+        for (int t = 0; t < drops[d].params.n_types; ++t) {
+            const size_t start = gperm.size();
+            for (int i = 0; i < e->cnt[d]; ++i)
+                if (drops[d].type[i] == t) {
+                    gpos[(size_t)e->off[d] + i] = (int)gperm.size();
+                    gperm.push_back(e->off[d] + i);
+                }
+            if (gperm.size() == start)
+                continue;
+            while (gperm.size() % 256)
+                gperm.push_back(-1);
+            while (gtblk.size() < gperm.size() / 256)
+                gtblk.push_back(t);
+        }
+        g.npad = (int)gperm.size() - g.gpos0;
+    }
 #define EBAIL(call)                                                                     \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
@@ -1812,6 +1894,7 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
     EBAIL(dalloc(&e->tabs, (size_t)n_drops));
     EBAIL(dalloc(&e->unit0, (size_t)n_drops + 1));
     EBAIL(dalloc(&e->d_step, 1));
+    EBAIL(dalloc(&e->d_spring, (size_t)2 * n_drops * NPSIM_MAX_TYPES));
     EBAIL(dalloc(&e->d_flags, 1));
     EBAIL(dalloc(&e->d_done, 1));
     {
@@ -1826,6 +1909,13 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
                      cudaMemcpyHostToDevice));
     EBAIL(cudaMemcpy(e->drop_of, dof.data(), sizeof(int) * (size_t)total,
                      cudaMemcpyHostToDevice));
+    EBAIL(dalloc(&e->perm, gperm.size()));
+    EBAIL(dalloc(&e->tblk, gtblk.size()));
+    EBAIL(dalloc(&e->row_pos, (size_t)total));
+    EBAIL(cudaMemcpy(e->perm, gperm.data(), sizeof(int) * gperm.size(), cudaMemcpyHostToDevice));
+    EBAIL(cudaMemcpy(e->tblk, gtblk.data(), sizeof(int) * gtblk.size(), cudaMemcpyHostToDevice));
+    EBAIL(cudaMemcpy(e->row_pos, gpos.data(), sizeof(int) * (size_t)total,
+                     cudaMemcpyHostToDevice));
     EBAIL(cudaMemcpy(e->tabs, e->h_tabs.data(), sizeof(PairTab) * (size_t)n_drops,
                      cudaMemcpyHostToDevice));
     for (int i = 0; i < (int)total; ++i) {
@@ -1835,6 +1925,17 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
     }
     EBAIL(cudaMemcpy(e->xq, xq0.data(), sizeof(float4) * (size_t)total, cudaMemcpyHostToDevice));
     EBAIL(cudaMemset(e->d_step, 0, sizeof(long long)));
+    {
+        // spring radii of step 0 (buffer 0)
+        std::vector<float4> sp((size_t)2 * n_drops * NPSIM_MAX_TYPES, make_float4(0, 0, 0, 0));
+        for (int d = 0; d < n_drops; ++d)
+            for (int t = 0; t < drops[d].params.n_types; ++t)
+                sp[(size_t)d * NPSIM_MAX_TYPES + t] =
+                    spring_entry(drops[d].params.R0, drops[d].params.k_evap, drops[d].params.dt,
+                                 0, 0.5 * drops[d].types[t].sigma);
+        EBAIL(cudaMemcpy(e->d_spring, sp.data(), sizeof(float4) * sp.size(),
+                         cudaMemcpyHostToDevice));
+    }
     EBAIL(cudaMemset(e->d_flags, 0, sizeof(int)));
     EBAIL(cudaMemset(e->d_done, 0, sizeof(unsigned)));
 #undef EBAIL
@@ -2004,7 +2105,7 @@ __global__ void k_normals(uint64_t seed, long long step, int n, double *out)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    double a, b, c;
+    float a, b, c;
     normals3(seed, (uint32_t)i, step, 0u, a, b, c);
     out[3 * i + 0] = a;
     out[3 * i + 1] = b;

@@ -11,8 +11,11 @@
 // A CTA writes one compensated (hi, lo) float32 partial per (global row, CTA)
 // segment into slot row + CTA; the integrator sums a row's partials in CTA order.
 //
-// The pair body is the scalar Coulomb + truncated-LJ body of allpairs.cu with
-// the droplet's own type-pair table (sigma_ab^2, 24 eps_ab, rc_ab^2, C q_a q_b);
+// Inside the ensemble each droplet's particles are listed in a type-grouped
+// order (each type's group padded to 256 positions), so every j-tile holds
+// partners of one type and the pair body is the packed LJ + Coulomb sweep
+// (ljc_tile_sweep) with the droplet's own type-pair table (sigma_ab^2,
+// 24 eps_ab, rc_ab^2, C q_a q_b) read once per tile;
 // the integrator is the fused BAOAB / overdamped pass of integrate.cu with the
 // droplet's own coefficients.  Noise is keyed by the droplet's seed and counted
 // by the particle's index inside its droplet, so a droplet draws the same
@@ -22,10 +25,6 @@
 namespace npsim {
 
 namespace {
-
-constexpr float kSelfEps = 1e-20f;
-constexpr float kSelfMin = 1e-12f;
-constexpr float kFar = 1.0e15f;
 
 // Droplet whose unit range contains global unit u (unit0 has n_drops + 1 entries).
 __device__ __forceinline__ int drop_of_unit(const long long *__restrict__ unit0, int n_drops,
@@ -44,14 +43,15 @@ __device__ __forceinline__ int drop_of_unit(const long long *__restrict__ unit0,
 
 template <int BLOCK, int KI, int JT>
 __global__ void __launch_bounds__(BLOCK)
-k_ens_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ,
-               const EnsDrop *__restrict__ drops, const long long *__restrict__ unit0,
-               const PairTab *__restrict__ tabs, int n_drops, StreamK sk,
-               float *__restrict__ slots)
+k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
+          const int *__restrict__ tblk, const EnsDrop *__restrict__ drops,
+          const long long *__restrict__ unit0, const PairTab *__restrict__ tabs, int n_drops,
+          StreamK sk, float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
-    __shared__ float4 s_x[JT];
-    __shared__ int s_t[JT];
+    constexpr int JP = JT / 2;
+    __shared__ float4 s_a[JP]; // (-x0, -x1, -y0, -y1)
+    __shared__ float2 s_b[JP]; // (-z0, -z1)
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
 
     const int c = blockIdx.x;
@@ -74,71 +74,58 @@ k_ens_allpairs(const float4 *__restrict__ xq, const int *__restrict__ typ,
         const long long left = min(p_end, D.unit0 + (long long)D.n_it * D.n_jt) - p;
         const int jt1 = (int)min((long long)D.n_jt, (long long)jt0 + left);
 
-        float xi[KI], yi[KI], zi[KI];
+        float2 xi[KI], yi[KI], zi[KI];
         int trow[KI];
         float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
-            const int li = r * ITILE + k * BLOCK + threadIdx.x;
-            if (li < D.n) {
-                const float4 q = xq[D.offset + li];
-                xi[k] = q.x;
-                yi[k] = q.y;
-                zi[k] = q.z;
-                trow[k] = typ[D.offset + li] * NPSIM_MAX_TYPES;
-            } else {
-                xi[k] = yi[k] = zi[k] = kFar;
-                trow[k] = 0;
-            }
+            const int lpos = r * ITILE + k * BLOCK + threadIdx.x;
+            const bool in = lpos < D.npad;
+            const int i = in ? perm[D.gpos0 + lpos] : -1;
+            float4 q = make_float4(kPairPad, kPairPad, kPairPad, 0.0f);
+            if (i >= 0)
+                q = xq[i];
+            xi[k] = make_float2(q.x, q.x);
+            yi[k] = make_float2(q.y, q.y);
+            zi[k] = make_float2(q.z, q.z);
+            trow[k] = (in ? tblk[(D.gpos0 + lpos) >> 8] : 0) * NPSIM_MAX_TYPES;
             hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
         }
 
         for (int jt = jt0; jt < jt1; ++jt) {
-            __syncthreads();
-            for (int m = threadIdx.x; m < JT; m += BLOCK) {
-                const int lj = jt * JT + m;
-                if (lj < D.n) {
-                    s_x[m] = xq[D.offset + lj];
-                    s_t[m] = typ[D.offset + lj];
-                } else {
-                    s_x[m] = make_float4(-kFar, -kFar, -kFar, 0.0f);
-                    s_t[m] = 0;
-                }
+            __syncthreads(); // the previous tile has been consumed (and s_tab is loaded)
+            for (int m = threadIdx.x; m < JP; m += BLOCK) {
+                const int k0 = D.gpos0 + jt * JT + 2 * m; // npad is a multiple of JT
+                const int j0 = perm[k0], j1 = perm[k0 + 1];
+                const float4 pad = make_float4(-kPairPad, -kPairPad, -kPairPad, 0.0f);
+                const float4 a = j0 >= 0 ? xq[j0] : pad;
+                const float4 b = j1 >= 0 ? xq[j1] : pad;
+                s_a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
+                s_b[m] = make_float2(-a.z, -b.z);
             }
             __syncthreads();
 
-            float ax[KI], ay[KI], az[KI];
-#pragma unroll
-            for (int k = 0; k < KI; ++k)
-                ax[k] = ay[k] = az[k] = 0.0f;
-#pragma unroll 4
-            for (int m = 0; m < JT; ++m) {
-                const float4 pj = s_x[m];
-                const int tj = s_t[m];
-#pragma unroll
-                for (int k = 0; k < KI; ++k) {
-                    const float dx = xi[k] - pj.x;
-                    const float dy = yi[k] - pj.y;
-                    const float dz = zi[k] - pj.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kSelfEps)));
-                    const float rinv = rsqrtf(r2);
-                    const float rinv2 = rinv * rinv;
-                    const float4 t = s_tab[trow[k] + tj];
-                    const float s2 = t.x * rinv2;
-                    const float s6 = s2 * s2 * s2;
-                    float flj = t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f);
-                    flj = (r2 < t.z && r2 > kSelfMin) ? flj : 0.0f;
-                    const float f = fmaf(t.w * rinv, rinv2, flj);
-                    ax[k] = fmaf(f, dx, ax[k]);
-                    ay[k] = fmaf(f, dy, ay[k]);
-                    az[k] = fmaf(f, dz, az[k]);
-                }
-            }
+            const int tt = tblk[(D.gpos0 + jt * JT) >> 8]; // one type per tile
+            float4 cst[KI];
+            float2 ax[KI], ay[KI], az[KI];
 #pragma unroll
             for (int k = 0; k < KI; ++k) {
-                two_sum_acc(hx[k], lx[k], ax[k]);
-                two_sum_acc(hy[k], ly[k], ay[k]);
-                two_sum_acc(hz[k], lz[k], az[k]);
+                cst[k] = s_tab[trow[k] + tt];
+                ax[k] = ay[k] = az[k] = make_float2(0.0f, 0.0f);
+            }
+            const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
+            if (diag)
+                ljc_tile_sweep<KI, true>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
+            else
+                ljc_tile_sweep<KI, false>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
+#pragma unroll
+            for (int k = 0; k < KI; ++k) {
+                two_sum_acc(hx[k], lx[k], ax[k].x);
+                two_sum_acc(hx[k], lx[k], ax[k].y);
+                two_sum_acc(hy[k], ly[k], ay[k].x);
+                two_sum_acc(hy[k], ly[k], ay[k].y);
+                two_sum_acc(hz[k], lz[k], az[k].x);
+                two_sum_acc(hz[k], lz[k], az[k].y);
             }
         }
 
@@ -161,26 +148,22 @@ template <int MODE>
 __global__ void __launch_bounds__(256)
 k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
 {
-    // A CTA of 256 consecutive particles spans at most 256 droplets; the
-    // spring radius of every (droplet, type) it touches is evaluated once.
-    constexpr int kSpan = 256;
-    __shared__ float2 s_reff2[kSpan * NPSIM_MAX_TYPES];
-    __shared__ float s_reff[kSpan * NPSIM_MAX_TYPES];
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
     const long long step = *a.step;
     const int i0 = blockIdx.x * blockDim.x;
-    const int d0 = a.drop_of[i0]; // i0 < n_total: the grid is ceil(n_total / 256)
-    if (ASSEMBLE && a.ext_on) {
-        const int i_last = min(i0 + (int)blockDim.x, n_total) - 1;
-        const int span = a.drop_of[i_last] - d0 + 1;
-        for (int k = threadIdx.x; k < span * NPSIM_MAX_TYPES; k += blockDim.x) {
-            const EnsDrop &D = a.drops[d0 + k / NPSIM_MAX_TYPES];
-            spring_radius(D.R0, D.k_evap, D.dt, step, D.tc[k % NPSIM_MAX_TYPES].half_sigma,
-                          s_reff2[k], s_reff[k]);
+    if (DO_A) {
+        // spring radii of step + 1 for every (droplet, type), spread over the
+        // first CTAs of the launch (one entry per thread)
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_drops * NPSIM_MAX_TYPES;
+             e += gridDim.x * blockDim.x) {
+            const EnsDrop &D = a.drops[e / NPSIM_MAX_TYPES];
+            a.spring[(size_t)((step + 1) & 1) * n_drops * NPSIM_MAX_TYPES + e] =
+                spring_entry(D.R0, D.k_evap, D.dt, step + 1,
+                             D.tc[e % NPSIM_MAX_TYPES].half_sigma);
         }
-        __syncthreads();
     }
+    const float4 *spring = a.spring + (size_t)(step & 1) * n_drops * NPSIM_MAX_TYPES;
 
     const int i = i0 + threadIdx.x;
     if (i < n_total) {
@@ -195,8 +178,9 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
         float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
         if (ASSEMBLE) {
             if (a.slots) {
-                const int r = li / sk.itile;
-                const int idx = li - r * sk.itile;
+                const int lpos = a.row_pos[i] - D.gpos0; // row in the droplet's grouped order
+                const int r = lpos / sk.itile;
+                const int idx = lpos - r * sk.itile;
                 const long long u0 = D.unit0 + (long long)r * D.n_jt;
                 const int c0 = sk_cta_of(sk, u0);
                 const int c1 = sk_cta_of(sk, u0 + D.n_jt - 1);
@@ -208,10 +192,10 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 }
             }
             if (a.ext_on) {
-                const int e = (d - d0) * NPSIM_MAX_TYPES + ti;
                 float ex, ey, ez;
-                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, s_reff2[e], s_reff[e],
-                               D.wall, D.rot_mode, ex, ey, ez);
+                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2,
+                               spring[d * NPSIM_MAX_TYPES + ti], D.wall, D.rot_mode, ex, ey,
+                               ez);
                 df_add(Fh[0], Fl[0], ex);
                 df_add(Fh[1], Fl[1], ey);
                 df_add(Fh[2], Fl[2], ez);
@@ -245,18 +229,19 @@ struct EEntry {
     const void *fn;
 };
 
-#define NPSIM_ENS(B, K, J) EEntry{ApConfig{B, K, J, 0}, (const void *)k_ens_allpairs<B, K, J>}
+#define NPSIM_ENS(B, K, J) EEntry{ApConfig{B, K, J, 0}, (const void *)k_ens_ljc<B, K, J>}
 
+// j-tiles of at most 256 partners: the droplets' type groups are padded to 256
 const EEntry kEns[] = {
-    NPSIM_ENS(128, 2, 256), NPSIM_ENS(128, 4, 256), NPSIM_ENS(256, 2, 256),
-    NPSIM_ENS(256, 4, 256), NPSIM_ENS(64, 4, 128),  NPSIM_ENS(256, 1, 256),
+    NPSIM_ENS(128, 2, 256), NPSIM_ENS(256, 1, 256), NPSIM_ENS(256, 2, 256),
+    NPSIM_ENS(128, 4, 256), NPSIM_ENS(128, 2, 128), NPSIM_ENS(512, 1, 256),
 };
 
 template <int B, int K, int J>
 cudaError_t launch_e(const StreamK &sk, const EnsAllpairsArgs &a, cudaStream_t st)
 {
-    k_ens_allpairs<B, K, J><<<sk.grid, B, 0, st>>>(a.xq, a.typ, a.drops, a.unit0, a.tabs,
-                                                    a.n_drops, sk, a.slots);
+    k_ens_ljc<B, K, J><<<sk.grid, B, 0, st>>>(a.xq, a.perm, a.tblk, a.drops, a.unit0, a.tabs,
+                                               a.n_drops, sk, a.slots);
     return cudaGetLastError();
 }
 
@@ -280,11 +265,11 @@ cudaError_t launch_ens_allpairs(int idx, const StreamK &sk, const EnsAllpairsArg
 {
     switch (idx) {
     case 0: return launch_e<128, 2, 256>(sk, a, st);
-    case 1: return launch_e<128, 4, 256>(sk, a, st);
+    case 1: return launch_e<256, 1, 256>(sk, a, st);
     case 2: return launch_e<256, 2, 256>(sk, a, st);
-    case 3: return launch_e<256, 4, 256>(sk, a, st);
-    case 4: return launch_e<64, 4, 128>(sk, a, st);
-    case 5: return launch_e<256, 1, 256>(sk, a, st);
+    case 3: return launch_e<128, 4, 256>(sk, a, st);
+    case 4: return launch_e<128, 2, 128>(sk, a, st);
+    case 5: return launch_e<512, 1, 256>(sk, a, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -18,7 +18,8 @@
 // hi/lo pairs; velocities and the per-step increments are float32.  The
 // interface distance |x| - (R - sigma/2), a difference of two nearly equal
 // numbers, is formed from |x|^2 - R_eff^2 (see external_force); R(t) and
-// R_eff^2 come from one float64 evaluation per CTA.
+// R_eff^2 come from a per-type table evaluated once per step in float64 (by
+// the first CTA of the launch that advances the step, for the next step).
 //
 // One kernel serves four modes (see IntMode): it sums the stream-K partials of
 // the all-pairs kernel (and the cell-list LJ forces) into the total force, adds
@@ -33,26 +34,23 @@ namespace npsim {
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)
 k_integrate(IntArgs a, StepParams p)
 {
     __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
-    __shared__ float2 s_reff2[NPSIM_MAX_TYPES];
-    __shared__ float s_reff[NPSIM_MAX_TYPES];
     const long long step = *a.step; // positions are x_step at t = step * dt
-    if (threadIdx.x < NPSIM_MAX_TYPES) {
-        const TypeCoef tc = p.tc[threadIdx.x];
-        s_tc[threadIdx.x] = tc;
-        // the spring's equilibrium radius at t, once per CTA
-        spring_radius(p.R0, p.k_evap, p.dt, step, tc.half_sigma, s_reff2[threadIdx.x],
-                      s_reff[threadIdx.x]);
-    }
+    constexpr bool ASSEMBLE = (MODE != MODE_A);
+    constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    if (threadIdx.x < NPSIM_MAX_TYPES)
+        s_tc[threadIdx.x] = p.tc[threadIdx.x];
+    if (DO_A && blockIdx.x == 0 && threadIdx.x < p.n_types) // spring radius of step + 1
+        a.spring[((step + 1) & 1) * NPSIM_MAX_TYPES + threadIdx.x] =
+            spring_entry(p.R0, p.k_evap, p.dt, step + 1, p.tc[threadIdx.x].half_sigma);
     __syncthreads();
 
     const int n = p.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    constexpr bool ASSEMBLE = (MODE != MODE_A);
-    constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    const float4 *spring = a.spring + (step & 1) * NPSIM_MAX_TYPES;
 
     if (i < n) {
         const int ti = a.typ[i];
@@ -88,8 +86,8 @@ k_integrate(IntArgs a, StepParams p)
             }
             if (a.ext_on) {
                 float ex, ey, ez;
-                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, s_reff2[ti], s_reff[ti],
-                               p.wall, p.rot_mode, ex, ey, ez);
+                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, spring[ti], p.wall,
+                               p.rot_mode, ex, ey, ez);
                 df_add(Fh[0], Fl[0], ex);
                 df_add(Fh[1], Fl[1], ey);
                 df_add(Fh[2], Fl[2], ez);

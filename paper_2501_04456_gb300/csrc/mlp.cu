@@ -6,18 +6,26 @@
 // GEMM: C[M x N] = A[M x K] * B[N x K]^T, A and B row-major BF16 (both
 // "K-major"), FP32 accumulation in tensor memory, on the 5th-generation
 // tensor cores of sm_100+ (tcgen05):
-//  * one CTA of 128 threads computes a 128 x n_tile block (n_tile <= 256,
+//  * one CTA of 256 threads computes a 128 x n_tile block (n_tile <= 256,
 //    multiple of 16); the FP32 accumulator lives in TMEM (allocated per CTA);
-//  * operands are staged in shared memory in the canonical no-swizzle K-major
-//    layout of the tcgen05 matrix descriptors: 8-row x 16-byte core matrices,
-//    adjacent along K at 128 B (leading-dimension byte offset) and along M/N at
-//    1024 B (stride-dimension byte offset) for 64-column chunks;
-//  * one elected thread issues tcgen05.mma (M = 128, N = n_tile, K = 16 per
-//    instruction) and commits to an mbarrier; every wait on it is bounded
-//    (clock64 budget) and reports FLAG_TIMEOUT instead of hanging;
-//  * the epilogue reads the accumulator with tcgen05.ld (32 lanes x 32 bit,
-//    16 columns per load; warp w owns rows 32w..32w+31) and applies bias,
-//    SiLU, the SiLU derivative for back-propagation, or a plain FP32 store.
+//  * operands arrive by TMA (cp.async.bulk.tensor, 2-D tensor maps, boxes of
+//    8 K-columns x rows) into a ring of up to four stages of 64 K-columns each,
+//    in the canonical no-swizzle K-major layout of the tcgen05 matrix
+//    descriptors: 8-row x 16-byte core matrices, adjacent along M/N at 128 B
+//    (stride-dimension byte offset) and along K at rows x 16 B (leading-
+//    dimension byte offset).  Rows beyond M or N are zero-filled by the TMA;
+//  * one thread issues the loads (mbarrier expect_tx per stage), one thread
+//    issues tcgen05.mma (M = 128, N = n_tile, K = 16 per instruction) and
+//    releases each stage with tcgen05.commit; every wait is bounded (clock64
+//    budget) and reports FLAG_TIMEOUT instead of hanging;
+//  * the epilogue (8 warps) reads the accumulator with tcgen05.ld (32 lanes x
+//    32 bit, 16 columns per load; warps w and w + 4 share TMEM lanes
+//    32(w mod 4) .. +31 and split the 16-column groups), stages the tile in
+//    shared memory and writes it row by row (one warp per row, lanes along the
+//    columns), applying bias, SiLU, the SiLU derivative for back-propagation,
+//    or a plain FP32 store.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "npsim_internal.cuh"
@@ -76,33 +84,86 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return true;
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+// SiLU and its derivative with the fast exponential and division intrinsics:
+// their ~1e-6 relative error lies far below the BF16 rounding (2^-9) applied to
+// every activation and gradient.  A huge exp(-z) gives a quotient of exactly 0.
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ float dsilu(float z)
 {
-    const float s = 1.0f / (1.0f + expf(-z));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
 }
 
-constexpr int kChunkK = 64;   // K columns staged per round
-constexpr int kTileM = 128;   // rows per CTA
+constexpr int kChunkK = 64;    // K columns per pipeline stage
+constexpr int kTileM = 128;    // rows per CTA
 constexpr int kMaxTileN = 256;
+constexpr int kMaxStages = 4;
+constexpr int kStageBudget = 200 * 1024; // shared memory for the operand ring
 
-__global__ void __launch_bounds__(128, 1)
-k_gemm_bf16(GemmArgs g)
+__host__ __device__ __forceinline__ int stage_bytes(int n_tile)
+{
+    return (kTileM + n_tile) * kChunkK * 2;
+}
+
+// Shared memory of one CTA: the operand ring, reused by the epilogue for the
+// FP32 output tile (row pitch n_tile + 1 floats: conflict-free both ways).
+__host__ __device__ __forceinline__ int dyn_smem_bytes(int n_tile, int stages)
+{
+    const int ring = stages * stage_bytes(n_tile);
+    const int tile = kTileM * (n_tile + 1) * 4;
+    return ring > tile ? ring : tile;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// 2-D TMA load of the box at (x = K column, y = row) into shared memory,
+// completing `bytes` of the barrier's transaction count.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+
+constexpr int kGemmThreads = 256;
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            GemmArgs g, int stages)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *sA = smem;                          // 128 x 64 bf16 = 16 KB
-    uint8_t *sB = smem + kTileM * kChunkK * 2;   // n_tile x 64 bf16 <= 32 KB
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], done;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_issued;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kTileM;
     const int n0 = blockIdx.y * g.n_tile;
     const int nt = min(g.n_tile, g.N - n0); // multiple of 16 (N and n_tile are)
-    const uint32_t bar_a = smem_addr(&bar);
+    const int nchunks = (g.K + kChunkK - 1) / kChunkK;
+    const uint32_t base = smem_addr(smem);
+    const uint32_t sbytes = (uint32_t)stage_bytes(g.n_tile);
+    const uint32_t a_bytes = kTileM * kChunkK * 2;
+    const uint32_t done_bar = smem_addr(&done);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -111,74 +172,98 @@ k_gemm_bf16(GemmArgs g)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            mbar_init(smem_addr(&empty[s]), 1);
+        }
+        mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
+        s_issued = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
 
-    const int nchunks = (g.K + kChunkK - 1) / kChunkK;
-    const uint32_t idesc = idesc_bf16(kTileM, nt);
-    const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
-    for (int c = 0; c < nchunks; ++c) {
-        const int k0 = c * kChunkK;
-        const int kc = min(kChunkK, g.K - k0); // multiple of 16
-        if (c > 0) {
-            // the MMAs of the previous round must be done reading shared memory
-            if (tid == 0 && !mbar_wait_bounded(bar_a, (uint32_t)((c - 1) & 1)))
-                s_abort = 1;
-            __syncthreads();
-            if (s_abort)
-                break;
-        }
-        // stage A (128 x kc) and B (nt x kc): 16-byte pieces = core-matrix rows
-        const int kg_n = kc / 8;
-        for (int p = tid; p < kTileM * kg_n; p += 128) {
-            const int r = p / kg_n, kg = p - r * kg_n;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m0 + r < g.M)
-                v = *reinterpret_cast<const uint4 *>(g.A + (size_t)(m0 + r) * g.lda + k0 + kg * 8);
-            *reinterpret_cast<uint4 *>(sA + ((r >> 3) * 8 + kg) * 128 + (r & 7) * 16) = v;
-        }
-        for (int p = tid; p < nt * kg_n; p += 128) {
-            const int r = p / kg_n, kg = p - r * kg_n;
-            const uint4 v =
-                *reinterpret_cast<const uint4 *>(g.B + (size_t)(n0 + r) * g.ldb + k0 + kg * 8);
-            *reinterpret_cast<uint4 *>(sB + ((r >> 3) * 8 + kg) * 128 + (r & 7) * 16) = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            for (int ks = 0; ks < kc; ks += 16) {
-                const uint64_t ad = smem_desc(a_base + (ks / 8) * 128, 128, 1024);
-                const uint64_t bd = smem_desc(b_base + (ks / 8) * 128, 128, 1024);
-                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    if (warp == 0) {
+        if (lane == 0) { // TMA producer
+            int c = 0;
+            for (; c < nchunks; ++c) {
+                const int s = c % stages, u = c / stages;
+                if (u > 0 && !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((u - 1) & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                const int k0 = c * kChunkK, kc = min(kChunkK, g.K - k0);
+                const uint32_t sa = base + (uint32_t)s * sbytes, sb = sa + a_bytes;
+                const uint32_t fb = smem_addr(&full[s]);
+                mbar_expect_tx(fb, (uint32_t)((kTileM + g.n_tile) * kc * 2));
+                for (int kg = 0; kg < kc / 8; ++kg) {
+                    tma_load_2d(sa + (uint32_t)(kg * kTileM * 16), &tmA, k0 + kg * 8, m0, fb);
+                    tma_load_2d(sb + (uint32_t)(kg * g.n_tile * 16), &tmB, k0 + kg * 8, n0, fb);
+                }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                bar_a));
+            s_issued = c;
         }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) { // MMA issuer
+            const uint32_t idesc = idesc_bf16(kTileM, nt);
+            for (int c = 0; c < nchunks; ++c) {
+                const int s = c % stages, u = c / stages;
+                if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)(u & 1))) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int kc = min(kChunkK, g.K - c * kChunkK);
+                const uint32_t sa = base + (uint32_t)s * sbytes, sb = sa + a_bytes;
+                for (int ks = 0; ks < kc; ks += 16) {
+                    const uint64_t ad = smem_desc(sa + (uint32_t)((ks / 8) * kTileM * 16),
+                                                  kTileM * 16, 128);
+                    const uint64_t bd = smem_desc(sb + (uint32_t)((ks / 8) * g.n_tile * 16),
+                                                  (uint32_t)(g.n_tile * 16), 128);
+                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                     tmem),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+                mma_commit(smem_addr(&empty[s])); // stage s may be refilled
+            }
+            // fires once every MMA issued so far has completed (also after an abort)
+            mma_commit(done_bar);
+        }
+        __syncwarp();
     }
-    if (!s_abort) {
-        if (tid == 0 && !mbar_wait_bounded(bar_a, (uint32_t)((nchunks - 1) & 1)))
-            s_abort = 1;
-        __syncthreads();
-    }
-    if (s_abort) {
-        if (tid == 0)
+
+    // wait for the accumulator (bounded), then the epilogue
+    if (!mbar_wait_bounded(done_bar, 0))
+        atomicExch(&s_abort, 1);
+    __syncthreads();
+    const bool abort = s_abort != 0;
+    if (abort) {
+        if (tid == 0) {
             atomicOr(g.flags, FLAG_TIMEOUT);
+            // let the copies still in flight land before the CTA leaves: at most
+            // one outstanding load per stage (the last one issued)
+            const int issued = s_issued;
+            for (int s = 0; s < stages && s < issued; ++s) {
+                const int u_last = (issued - 1 - s) / stages;
+                mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)(u_last & 1));
+            }
+            mbar_wait_bounded(done_bar, 0);
+        }
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int row = m0 + warp * 32 + lane;
-        for (int j = 0; j < nt; j += 16) {
+        float *S = reinterpret_cast<float *>(smem);
+        const int pitch = g.n_tile + 1;
+        const int quad = warp & 3, half = warp >> 2;
+        const int rl = quad * 32 + lane;
+        for (int j = half * 16; j < nt; j += 32) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j;
+            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)j;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
@@ -186,29 +271,38 @@ k_gemm_bf16(GemmArgs g)
                            "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < g.M) {
-                for (int q = 0; q < 16; ++q) {
-                    const int col = n0 + j + q;
-                    float v = __uint_as_float(r[q]);
-                    if (g.mode == GEMM_F32) {
-                        if (g.bias)
-                            v += g.bias[col];
-                        g.Cf[(size_t)row * g.ldc + col] = v;
-                    } else if (g.mode == GEMM_ACT) {
-                        if (g.bias)
-                            v += g.bias[col];
-                        if (g.Z)
-                            g.Z[(size_t)row * g.ldc + col] = v;
-                        const float a = g.act ? silu(v) : v;
-                        g.Cb[(size_t)row * g.ldc + col] = __float2bfloat16_rn(a);
-                        if (g.Cf)
-                            g.Cf[(size_t)row * g.ldc + col] = a;
-                    } else { // GEMM_DACT: gradient through the SiLU of the previous layer
-                        const float d = v * dsilu(g.Z[(size_t)row * g.ldc + col]);
-                        g.Cb[(size_t)row * g.ldc + col] = __float2bfloat16_rn(d);
-                        if (g.Cf)
-                            g.Cf[(size_t)row * g.ldc + col] = d;
-                    }
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                S[rl * pitch + j + q] = __uint_as_float(r[q]);
+        }
+        __syncthreads();
+        // one warp per output row, lanes along the columns (coalesced)
+        const int rows = min(kTileM, g.M - m0);
+        constexpr int kWarps = kGemmThreads / 32;
+        for (int rr = warp; rr < rows; rr += kWarps) {
+            const size_t ro = (size_t)(m0 + rr) * g.ldc + n0;
+            const float *Sr = S + rr * pitch;
+            for (int cc = lane; cc < nt; cc += 32) {
+                const size_t o = ro + cc;
+                float v = Sr[cc];
+                if (g.mode == GEMM_F32) {
+                    if (g.bias)
+                        v += g.bias[n0 + cc];
+                    g.Cf[o] = v;
+                } else if (g.mode == GEMM_ACT) {
+                    if (g.bias)
+                        v += g.bias[n0 + cc];
+                    if (g.Z)
+                        g.Z[o] = v;
+                    const float act = g.act ? silu(v) : v;
+                    g.Cb[o] = __float2bfloat16_rn(act);
+                    if (g.Cf)
+                        g.Cf[o] = act;
+                } else { // GEMM_DACT: gradient through the SiLU of the previous layer
+                    const float d = v * dsilu(g.Z[o]);
+                    g.Cb[o] = __float2bfloat16_rn(d);
+                    if (g.Cf)
+                        g.Cf[o] = d;
                 }
             }
         }
@@ -336,24 +430,72 @@ __global__ void k_f32_to_bf16(const float *__restrict__ x, int n, __nv_bfloat16 
 
 } // namespace
 
-int gemm_smem_bytes(int n_tile) { return (kTileM + n_tile) * kChunkK * 2; }
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a row-major BF16 matrix (rows x K, leading dimension ld
+// elements) read in boxes of 8 K-columns x box_rows rows; out-of-range rows
+// read as zero.
+bool encode_operand(CUtensorMap *m, const __nv_bfloat16 *ptr, int rows, int K, int ld,
+                    int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+} // namespace
+
+int gemm_smem_bytes(int n_tile) { return dyn_smem_bytes(n_tile, kMaxStages); }
 
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || (g.N % 16) || (g.K % 16) || (g.n_tile % 16) ||
-        g.n_tile > kMaxTileN || (g.lda % 8) || (g.ldb % 8))
+        g.n_tile < 16 || g.n_tile > kMaxTileN || (g.lda % 8) || (g.ldb % 8) || g.lda < g.K ||
+        g.ldb < g.K || ((uintptr_t)g.A % 16) || ((uintptr_t)g.B % 16))
         return cudaErrorInvalidValue;
-    const int smem = gemm_smem_bytes(g.n_tile);
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             gemm_smem_bytes(kMaxTileN));
+                                             dyn_smem_bytes(kMaxTileN, kMaxStages));
         if (e != cudaSuccess)
             return e;
         attr_done = true;
     }
+    CUtensorMap ta, tb;
+    if (!encode_operand(&ta, g.A, g.M, g.K, g.lda, kTileM) ||
+        !encode_operand(&tb, g.B, g.N, g.K, g.ldb, g.n_tile))
+        return cudaErrorInvalidValue;
+    const int nchunks = (g.K + kChunkK - 1) / kChunkK;
+    int stages = kStageBudget / stage_bytes(g.n_tile);
+    stages = stages < kMaxStages ? stages : kMaxStages;
+    stages = stages < nchunks ? stages : nchunks;
     dim3 grid((g.M + kTileM - 1) / kTileM, (g.N + g.n_tile - 1) / g.n_tile);
-    k_gemm_bf16<<<grid, 128, smem, st>>>(g);
+    k_gemm_bf16<<<grid, kGemmThreads, dyn_smem_bytes(g.n_tile, stages), st>>>(ta, tb, g, stages);
     return cudaGetLastError();
 }
 

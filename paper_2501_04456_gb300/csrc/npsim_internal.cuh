@@ -44,8 +44,7 @@ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
 // step_hi, purpose), key = seed).  Uniforms u = (k + 1/2) 2^-32, rounded to
 // float; Box-Muller in float32 with the accurate logf / sincospif.
 __device__ __forceinline__ void normals3(uint64_t seed, uint32_t i, int64_t step,
-                                         uint32_t purpose, double &n0, double &n1,
-                                         double &n2)
+                                         uint32_t purpose, float &n0, float &n1, float &n2)
 {
     const uint64_t s = (uint64_t)step;
     U4 r = philox10(U4{i, (uint32_t)s, (uint32_t)(s >> 32), purpose}, (uint32_t)seed,
@@ -60,9 +59,9 @@ __device__ __forceinline__ void normals3(uint64_t seed, uint32_t i, int64_t step
     float s1, c1, s3, c3;
     sincospif(2.0f * u1, &s1, &c1);
     sincospif(2.0f * u3, &s3, &c3);
-    n0 = (double)(rho1 * c1);
-    n1 = (double)(rho1 * s1);
-    n2 = (double)(rho2 * c3);
+    n0 = rho1 * c1;
+    n1 = rho1 * s1;
+    n2 = rho2 * c3;
 }
 
 // Knuth's TwoSum: hi + lo accumulates a with the rounding error of hi + a
@@ -74,6 +73,67 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float a)
     float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(a, bp));
     hi = s;
     lo = __fadd_rn(lo, err);
+}
+
+// ---------------------------------------------------------------------------
+// Pair sums over grouped (padded) orders.
+constexpr float kPairSelfEps = 1e-20f; // added to r^2; the self pair has r_ij = 0 exactly
+constexpr float kPairSelfMin = 1e-12f; // LJ: r^2 below this is the self pair
+constexpr float kPairPad = 1.0e18f;    // padding position: every term with it underflows to 0
+
+// One j-tile of the packed LJ + Coulomb pair sum: KI rows per thread, JP
+// partner pairs staged in shared memory as negated coordinates, s_a = (-x0,
+// -x1, -y0, -y1), s_b = (-z0, -z1); cst[k] = (sigma_ab^2, 24 eps_ab, rc_ab^2,
+// C q_a q_b) of row k and the tile's type.  Per pair:
+//   d = x_i - x_j; r^2 = d.d (+ kPairSelfEps); 1/r = rsqrt(r^2);
+//   f = C q_a q_b / r^3 + [r^2 < rc_ab^2] 24 eps_ab / r^2 s^6 (2 s^6 - 1),
+//   s^2 = sigma_ab^2 / r^2;  a += f d,
+// on the packed float32x2 instructions, two partners per register pair.  DIAG
+// (a tile that holds a row's own column) also masks the self pair out of the
+// LJ term, whose r^-14 would overflow there.
+template <int KI, bool DIAG>
+__device__ __forceinline__ void ljc_tile_sweep(const float4 *__restrict__ s_a,
+                                          const float2 *__restrict__ s_b, int JP,
+                                          const float2 (&xi)[KI], const float2 (&yi)[KI],
+                                          const float2 (&zi)[KI], const float4 (&cst)[KI],
+                                          float2 (&ax)[KI], float2 (&ay)[KI], float2 (&az)[KI])
+{
+    const float2 eps2 = make_float2(kPairSelfEps, kPairSelfEps);
+    const float2 two = make_float2(2.0f, 2.0f), mone = make_float2(-1.0f, -1.0f);
+#pragma unroll 2
+    for (int m = 0; m < JP; ++m) {
+        const float4 a = s_a[m];
+        const float2 nz = s_b[m];
+        const float2 nx = make_float2(a.x, a.y), ny = make_float2(a.z, a.w);
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const float2 dx = __fadd2_rn(xi[k], nx);
+            const float2 dy = __fadd2_rn(yi[k], ny);
+            const float2 dz = __fadd2_rn(zi[k], nz);
+            float2 r2 = __ffma2_rn(dz, dz, eps2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dx, dx, r2);
+            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 s2 = __fmul2_rn(make_float2(cst[k].x, cst[k].x), ri2);
+            const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+            const float2 u = __ffma2_rn(two, s6, mone);
+            const float2 w = __fmul2_rn(make_float2(cst[k].y, cst[k].y), ri2);
+            float2 flj = __fmul2_rn(__fmul2_rn(w, s6), u);
+            if (DIAG) {
+                flj.x = (r2.x < cst[k].z && r2.x > kPairSelfMin) ? flj.x : 0.0f;
+                flj.y = (r2.y < cst[k].z && r2.y > kPairSelfMin) ? flj.y : 0.0f;
+            } else {
+                flj.x = r2.x < cst[k].z ? flj.x : 0.0f;
+                flj.y = r2.y < cst[k].z ? flj.y : 0.0f;
+            }
+            const float2 f =
+                __ffma2_rn(__fmul2_rn(make_float2(cst[k].w, cst[k].w), ri), ri2, flj);
+            ax[k] = __ffma2_rn(f, dx, ax[k]);
+            ay[k] = __ffma2_rn(f, dy, ay[k]);
+            az[k] = __ffma2_rn(f, dz, az[k]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -142,19 +202,20 @@ __device__ __forceinline__ void df_mul(float &h, float &l, float b)
 
 // Equilibrium radius of the interface spring for a particle of half-diameter
 // hs at t = step dt: R_eff = R(t) - hs with R(t)^2 = R0^2 - k t (radius-square
-// law, 0 once the droplet has gone).  Returned as R_eff (float) and R_eff^2 as a
-// (hi, lo) float pair, from one float64 evaluation.
-__device__ __forceinline__ void spring_radius(double R0, double k_evap, double dt, long long step,
-                                              double hs, float2 &reff2, float &reff)
+// law, 0 once the droplet has gone).  Returned as (R_eff^2 hi, R_eff^2 lo,
+// R_eff, 0) from one float64 evaluation.  Host and device both call this (the
+// explicit fma fixes the rounding), so a table set by the host equals the one
+// the integrator writes for the same step bit for bit.
+__host__ __device__ inline float4 spring_entry(double R0, double k_evap, double dt,
+                                               long long step, double hs)
 {
     const double t = (double)step * dt;
-    const double R2 = R0 * R0 - k_evap * t;
+    const double R2 = fma(-k_evap, t, R0 * R0);
     const double R = R2 > 0.0 ? sqrt(R2) : 0.0;
     const double re = R - hs;
     const double re2 = re * re;
     const float h = (float)re2;
-    reff2 = make_float2(h, (float)(re2 - (double)h));
-    reff = (float)re;
+    return make_float4(h, (float)(re2 - (double)h), (float)re, 0.0f);
 }
 
 // External forces (interface spring, gravity, centrifugal) on a particle at
@@ -164,8 +225,8 @@ __device__ __forceinline__ void spring_radius(double R0, double k_evap, double d
 // (the lo^2 terms lie below the precision kept), so s keeps float32 relative
 // precision however large |x| is.
 __device__ __forceinline__ void external_force(const float4 &xh, float lx, float ly, float lz,
-                                               float kw, float mg, float mw2, float2 reff2,
-                                               float reff, int wall, int rot_mode, float &fx,
+                                               float kw, float mg, float mw2, float4 spring,
+                                               int wall, int rot_mode, float &fx,
                                                float &fy, float &fz)
 {
     fx = fy = fz = 0.0f;
@@ -178,17 +239,20 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
             const float e = __fmaf_rn(hh[d], hh[d], -p);
             df_add_df(r2h, r2l, p, __fmaf_rn(2.0f * hh[d], ll[d], e));
         }
-        const float rr = sqrtf(r2h);
+        // |x| and 1/|x| from one rsqrt (a few ulp: far below the force tolerance)
+        const float rinv = rsqrtf(r2h);
+        const float rr = r2h * rinv;
+        const float reff = spring.z;
         float s;
         if (reff > 0.0f) {
             float dh = r2h, dl = r2l;
-            df_add_df(dh, dl, -reff2.x, -reff2.y);
-            s = dh / (rr + reff);
+            df_add_df(dh, dl, -spring.x, -spring.y);
+            s = __fdividef(dh, rr + reff);
         } else {
             s = rr - reff;
         }
-        if (s > 0.0f && rr > 0.0f) {
-            const float f = -kw * s / rr;
+        if (s > 0.0f && r2h > 0.0f) {
+            const float f = -kw * s * rinv;
             fx = f * xh.x;
             fy = f * xh.y;
             fz = f * xh.z;
@@ -287,6 +351,15 @@ int grp_occupancy(int idx);
 cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq,
                                     const int *perm, int n_perm, const float *qblk,
                                     float *slots, cudaStream_t st);
+// Type-grouped packed LJ + Coulomb kernel (allpairs_grouped.cu): rows and
+// columns follow perm (grouped by type, groups padded to 512), tblk = type of
+// each 256-position block; the table selects LJ + Coulomb, LJ or Coulomb.
+int ljg_num_configs();
+ApConfig ljg_config(int idx);
+int ljg_occupancy(int idx);
+cudaError_t launch_allpairs_ljgrp(int idx, const StreamK &sk, const float4 *xq,
+                                  const int *perm, int n_perm, const int *tblk,
+                                  const PairTab *tab, float *slots, cudaStream_t st);
 cudaError_t launch_allpairs(int cfg_idx, bool lj, const StreamK &sk, const float4 *xq,
                             const int *typ, int n, const PairTab *tab, float *slots,
                             cudaStream_t st);
@@ -312,6 +385,10 @@ struct IntArgs {
     const float *F_lj;       // cell-list LJ forces [6][n] (or NULL)
     const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
                              // no Coulomb partial); NULL: row position = i
+    float4 *spring;          // spring radius per type (spring_entry), two buffers
+                             // [2][NPSIM_MAX_TYPES]: buffer (step & 1) holds the
+                             // current step's; modes that advance the step write
+                             // the other one for step + 1
     int ext_on;              // add external forces
     int field_slots;         // slots hold sum_j q_j r_ij/r^3 (Coulomb-only kernel): scale by C q_i
     long long *step;         // device step counter
@@ -353,9 +430,8 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
             v[d] = __fmaf_rn(tc.hdt_m, f[d], v[d]);
     }
     if (DO_A) {
-        double n0, n1, n2;
-        normals3(seed, noise_idx, step, 0u, n0, n1, n2);
-        const float nz[3] = {(float)n0, (float)n1, (float)n2};
+        float nz[3];
+        normals3(seed, noise_idx, step, 0u, nz[0], nz[1], nz[2]);
         float xhi[3] = {xh.x, xh.y, xh.z}, xlo[3] = {lx, ly, lz};
         if (baoab) {
 #pragma unroll
@@ -386,11 +462,14 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
 cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
                              cudaStream_t st);
 
-// Ensemble of droplets (ensemble.cu).  Geometry depends on the launch shape:
-// n_it = ceil(n / itile), n_jt = ceil(n / jtile); row0 and unit0 are prefix sums
-// of n_it and n_it * n_jt over the droplets.
+// Ensemble of droplets (ensemble.cu).  Each droplet's particles are listed in a
+// type-grouped order (groups padded to 256 positions) at positions [gpos0,
+// gpos0 + npad) of the ensemble's grouped order.  Geometry depends on the
+// launch shape: n_it = ceil(npad / itile), n_jt = npad / jtile; row0 and unit0
+// are prefix sums of n_it and n_it * n_jt over the droplets.
 struct EnsDrop {
     int offset, n, n_it, n_jt, row0, rot_mode, wall, integrator;
+    int gpos0, npad;
     long long unit0;
     uint64_t seed;
     double dt, R0, k_evap, g, omega2;
@@ -399,7 +478,8 @@ struct EnsDrop {
 
 struct EnsAllpairsArgs {
     const float4 *xq;
-    const int *typ;
+    const int *perm;        // grouped position -> particle (-1: padding)
+    const int *tblk;        // type of each 256-position block
     const EnsDrop *drops;
     const long long *unit0; // n_drops + 1 entries
     const PairTab *tabs;    // one table per droplet
@@ -413,8 +493,10 @@ struct EnsIntArgs {
     const int *typ;
     float4 *xq;
     const int *drop_of;
+    const int *row_pos;      // grouped position of particle i
     const EnsDrop *drops;
     const float *slots;
+    float4 *spring;          // [2][n_drops][NPSIM_MAX_TYPES], as in IntArgs
     int ext_on;
     int pad_;
     long long *step;

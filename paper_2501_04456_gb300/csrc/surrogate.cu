@@ -75,6 +75,10 @@ struct npsim_surr {
     float *dzf[2] = {nullptr, nullptr};
     __nv_bfloat16 *tA = nullptr, *tB = nullptr; // transposes
     float *loss = nullptr, *outw = nullptr;
+    float *xin = nullptr;          // normalised FP32 inputs of a batch (staging)
+    float *y_all = nullptr;        // outputs of every network [n_nets][bcap][n_out_p]
+    float *ystat = nullptr;        // ensemble mean and spread [2][bcap][n_out]
+    float *d_ym = nullptr, *d_ys = nullptr; // output de-normalisation (n_out)
     int *flags = nullptr;
     long long adam_t = 0;
     // dataset on the device
@@ -115,6 +119,11 @@ struct npsim_surr {
         dfree2(tB);
         dfree2(loss);
         dfree2(outw);
+        dfree2(xin);
+        dfree2(y_all);
+        dfree2(ystat);
+        dfree2(d_ym);
+        dfree2(d_ys);
         dfree2(flags);
         dfree2(dsx);
         dfree2(dsy);
@@ -180,6 +189,9 @@ int alloc_batch(npsim_surr *s, int bcap)
     }
     dfree2(s->tA);
     dfree2(s->tB);
+    dfree2(s->xin);
+    dfree2(s->y_all);
+    dfree2(s->ystat);
     s->a.assign(s->NL + 1, nullptr);
     s->z.assign(s->NL, nullptr);
     SR_CUDA(dmalloc(&s->a[0], (size_t)bcap * s->n_in_p));
@@ -198,13 +210,17 @@ int alloc_batch(npsim_surr *s, int bcap)
     const int wmax = std::max(s->H, s->n_out_p);
     SR_CUDA(dmalloc(&s->tA, (size_t)bcap * wmax));
     SR_CUDA(dmalloc(&s->tB, (size_t)bcap * wmax));
+    SR_CUDA(dmalloc(&s->xin, (size_t)bcap * s->n_in_p));
+    SR_CUDA(dmalloc(&s->y_all, (size_t)s->n_nets * bcap * s->n_out_p));
+    SR_CUDA(dmalloc(&s->ystat, (size_t)2 * bcap * s->n_out));
     s->bcap = bcap;
     return NPSIM_OK;
 }
 
 // Forward pass of network k on the batch in a[0] (bp rows, a multiple of 128):
-// hidden layers write z (FP32) and a (BF16); the output layer writes y (FP32).
-int forward(npsim_surr *s, int k, int bp)
+// hidden layers write z (FP32) and a (BF16); the output layer writes y_out
+// (FP32; s->y when NULL).
+int forward(npsim_surr *s, int k, int bp, float *y_out = nullptr)
 {
     auto &net = s->nets[k];
     for (int l = 0; l < s->NL; ++l) {
@@ -214,7 +230,7 @@ int forward(npsim_surr *s, int k, int bp)
     }
     Layer &O = net[s->NL];
     SR_CUDA(gemm(s, GEMM_F32, s->a[s->NL], O.in_p, O.Wb, O.in_p, bp, O.out_p, O.in_p, O.b,
-                 s->y, nullptr, O.out_p, nullptr, 0));
+                 y_out ? y_out : s->y, nullptr, O.out_p, nullptr, 0));
     return NPSIM_OK;
 }
 
@@ -282,13 +298,9 @@ int upload_batch(npsim_surr *s, const float *X, const float *Y, int rows, int bp
     for (int r = 0; r < rows; ++r)
         for (int c = 0; c < s->n_in; ++c)
             xf[(size_t)r * s->n_in_p + c] = (X[(size_t)r * s->n_in + c] - s->xm[c]) / s->xs[c];
-    float *tmp = nullptr;
-    SR_CUDA(dmalloc(&tmp, xf.size()));
-    SR_CUDA(cudaMemcpyAsync(tmp, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice,
+    SR_CUDA(cudaMemcpyAsync(s->xin, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice,
                             s->st));
-    SR_CUDA(launch_f32_to_bf16(tmp, (int)xf.size(), s->a[0], s->st));
-    SR_CUDA(cudaStreamSynchronize(s->st));
-    cudaFree(tmp);
+    SR_CUDA(launch_f32_to_bf16(s->xin, (int)xf.size(), s->a[0], s->st));
     if (Y) {
         std::vector<float> yf((size_t)bp * s->n_out_p, 0.f);
         for (int r = 0; r < rows; ++r)
@@ -325,6 +337,27 @@ __global__ void k_gather_rows(const __nv_bfloat16 *__restrict__ sx, const float 
         x[(size_t)r * nx + c] = ok ? sx[(size_t)src * nx + c] : __float2bfloat16_rn(0.f);
     for (int c = threadIdx.x; c < ny; c += blockDim.x)
         y[(size_t)r * ny + c] = ok ? sy[(size_t)src * ny + c] : 0.f;
+}
+
+// Mean and spread (population standard deviation) over the networks of the
+// de-normalised outputs y * ys + ym, for rows < B and the n_out valid columns.
+__global__ void k_ens_stats(const float *__restrict__ y_all, int n_nets, int bp, int ldy, int B,
+                            int n_out, const float *__restrict__ ym, const float *__restrict__ ys,
+                            float *__restrict__ mean, float *__restrict__ spread)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * n_out)
+        return;
+    const int r = idx / n_out, c = idx - r * n_out;
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < n_nets; ++k) {
+        const double v = (double)y_all[((size_t)k * bp + r) * ldy + c] * ys[c] + ym[c];
+        s1 += v;
+        s2 += v * v;
+    }
+    const double m = s1 / n_nets;
+    mean[idx] = (float)m;
+    spread[idx] = (float)sqrt(fmax(0.0, s2 / n_nets - m * m));
 }
 
 } // namespace
@@ -426,8 +459,12 @@ int npsim_surr_create(int32_t n_in, int32_t n_hidden, int32_t n_layers, int32_t 
         }
     }
     if (dmalloc(&s->loss, 1) != cudaSuccess || dmalloc(&s->flags, 1) != cudaSuccess ||
-        dmalloc(&s->outw, (size_t)s->n_out_p) != cudaSuccess)
+        dmalloc(&s->outw, (size_t)s->n_out_p) != cudaSuccess ||
+        dmalloc(&s->d_ym, (size_t)n_out) != cudaSuccess ||
+        dmalloc(&s->d_ys, (size_t)n_out) != cudaSuccess)
         return bail(report_error(NPSIM_ERR_OOM, "surrogate scratch"));
+    cudaMemcpy(s->d_ym, s->ym.data(), sizeof(float) * n_out, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_ys, s->ys.data(), sizeof(float) * n_out, cudaMemcpyHostToDevice);
     std::vector<float> ow(s->n_out_p, 0.f);
     for (int c = 0; c < n_out; ++c)
         ow[c] = 1.f;
@@ -467,6 +504,11 @@ int npsim_surr_set_norm(npsim_surr_t s, const float *x_mean, const float *x_std,
         if (!(s->ys[c] > 0.f))
             return report_error(NPSIM_ERR_INVALID_ARG, "y_std[%d] must be positive", c);
     }
+    SR_CUDA(cudaMemcpyAsync(s->d_ym, s->ym.data(), sizeof(float) * s->n_out,
+                            cudaMemcpyHostToDevice, s->st));
+    SR_CUDA(cudaMemcpyAsync(s->d_ys, s->ys.data(), sizeof(float) * s->n_out,
+                            cudaMemcpyHostToDevice, s->st));
+    SR_CUDA(cudaStreamSynchronize(s->st));
     return NPSIM_OK;
 }
 
@@ -649,33 +691,23 @@ int npsim_surr_predict(npsim_surr_t s, const float *X, int32_t B, float *Y_mean,
     rc = upload_batch(s, X, nullptr, B, bp);
     if (rc)
         return rc;
-    std::vector<double> sum((size_t)B * s->n_out, 0.0), sum2((size_t)B * s->n_out, 0.0);
-    std::vector<float> yy((size_t)bp * s->n_out_p);
     for (int k = 0; k < s->n_nets; ++k) {
-        rc = forward(s, k, bp);
+        rc = forward(s, k, bp, s->y_all + (size_t)k * bp * s->n_out_p);
         if (rc)
             return rc;
-        SR_CUDA(cudaMemcpyAsync(yy.data(), s->y, sizeof(float) * yy.size(), cudaMemcpyDeviceToHost,
+    }
+    float *d_mean = s->ystat, *d_spread = s->ystat + (size_t)B * s->n_out;
+    const int ne = B * s->n_out;
+    k_ens_stats<<<(ne + 255) / 256, 256, 0, s->st>>>(s->y_all, s->n_nets, bp, s->n_out_p, B,
+                                                     s->n_out, s->d_ym, s->d_ys, d_mean,
+                                                     d_spread);
+    SR_CUDA(cudaGetLastError());
+    SR_CUDA(cudaMemcpyAsync(Y_mean, d_mean, sizeof(float) * ne, cudaMemcpyDeviceToHost, s->st));
+    if (Y_spread)
+        SR_CUDA(cudaMemcpyAsync(Y_spread, d_spread, sizeof(float) * ne, cudaMemcpyDeviceToHost,
                                 s->st));
-        SR_CUDA(cudaStreamSynchronize(s->st));
-        for (int r = 0; r < B; ++r)
-            for (int c = 0; c < s->n_out; ++c) {
-                const double v = (double)yy[(size_t)r * s->n_out_p + c] * s->ys[c] + s->ym[c];
-                sum[(size_t)r * s->n_out + c] += v;
-                sum2[(size_t)r * s->n_out + c] += v * v;
-            }
-    }
-    rc = check_flags(s);
-    if (rc)
-        return rc;
-    const double K = (double)s->n_nets;
-    for (size_t i = 0; i < sum.size(); ++i) {
-        const double m = sum[i] / K;
-        Y_mean[i] = (float)m;
-        if (Y_spread)
-            Y_spread[i] = (float)std::sqrt(std::max(0.0, sum2[i] / K - m * m));
-    }
-    return NPSIM_OK;
+    SR_CUDA(cudaStreamSynchronize(s->st));
+    return check_flags(s);
 }
 
 // Test hook: C = A B^T for host BF16 matrices (bit patterns), C in FP32.

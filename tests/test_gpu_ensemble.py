@@ -64,5 +64,8 @@ def test_ensemble_trajectories_match_oracle_and_single_runs(P, drops):
         with P.Sim(sc, x, v, types) as sim:
             sim.step(steps)
             xs, vs, _, _ = sim.state()
-        # same physics, same Philox keys; only the float summation order differs
-        assert np.abs(xe - xs).max() <= 1e-8, d
+        # same physics, same Philox keys; the pair sums differ only in float
+        # summation order (type groups padded to 256 here, to 512 in a single
+        # run), which 60 steps amplify to a few 1e-8; a wrong key or counter
+        # would differ by the noise amplitude itself (~1e-2)
+        assert np.abs(xe - xs).max() <= 1e-6, d

@@ -111,8 +111,10 @@ def test_forces_parity(P, name):
 
 
 def test_every_launch_shape(P, monkeypatch):
-    """Each all-pairs launch shape of the autotuner's table (scalar and packed
-    float32x2), forced in turn, gives the oracle's forces on a ragged size."""
+    """Each all-pairs launch shape of the autotuner's table (scalar, packed
+    float32x2, charge-grouped Coulomb, type-grouped LJ + Coulomb), forced in
+    turn, gives the oracle's forces on a ragged size, for a Coulomb-only and an
+    LJ + Coulomb sum."""
     sc_c = with_(small(wl.config3(), 1531), lj_mode=0)          # Coulomb only
     sc_l = with_(small(wl.config2(), 1531), coulomb=True)        # Coulomb + LJ
     st_c = wl.initial_state(sc_c, fp32_positions=True)
@@ -120,21 +122,27 @@ def test_every_launch_shape(P, monkeypatch):
     ref_c = _oracle_pair(sc_c, st_c[1], st_c[0])
     ref_l = _oracle_pair(sc_l, st_l[1], st_l[0])
     amb_l = cutoff_ambiguous(st_l[1], st_l[0], sc_l)
-    seen_packed = False
+    ref_lo = _oracle_pair(sc_l, st_l[1], st_l[0], coul=False)
+    ref_co = _oracle_pair(sc_l, st_l[1], st_l[0], lj=False)
+    seen = set()
     for idx in range(P.npsim_allpairs_num_configs()):
         monkeypatch.setenv("NPSIM_AUTOTUNE", f"1:{idx}")
         with P.Sim(sc_c, st_c[1], st_c[2], st_c[0]) as sim:
             cfg = sim.allpairs_config()
-            assert cfg["index"] == idx
-            seen_packed |= bool(cfg["packed"])
+            assert cfg["index"] == idx  # every shape can sum Coulomb alone
+            seen.add(cfg["packed"])
             err = force_error(sim.forces(1), ref_c)
             assert err.max() <= FORCE_TOL, (idx, float(err.max()))
         with P.Sim(sc_l, st_l[1], st_l[2], st_l[0]) as sim:
             cfg = sim.allpairs_config()
-            assert not cfg["packed"]  # the LJ sum runs on the scalar kernel
-            err = force_error(sim.forces(1), ref_l)[~amb_l]
-            assert err.max() <= FORCE_TOL, (idx, float(err.max()))
-    assert seen_packed
+            # the LJ sum runs on the scalar or on the type-grouped kernels
+            assert cfg["packed"] in (0, 3)
+            if cfg["index"] == idx:
+                seen.add(10 + cfg["packed"])
+            for what, ref in ((1, ref_l), (2, ref_lo), (3, ref_co)):
+                err = force_error(sim.forces(what), ref)[~amb_l]
+                assert err.max() <= FORCE_TOL, (idx, what, float(err.max()))
+    assert seen == {0, 1, 2, 3, 10, 13}
 
 
 def test_skip_neutral_forces_and_steps(P):
