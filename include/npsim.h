@@ -173,9 +173,9 @@ int npsim_stats(npsim_sim_t sim, const npsim_stats_cfg_t *cfg, int64_t *rdf_coun
 
 /* Checkpoint (Sec. 2.2: a run can be halted and resumed from its saved NP
  * configuration, possibly with other parameters): the raw state words
- * (position hi and lo float32 words, float32 velocities), types, step counter
- * and parameters, so that a resumed run is bit-identical to an uninterrupted
- * one.  npsim_load creates a new object; params_override (or NULL) replaces
+ * (position hi and lo float32 words, float32 velocities), types, step counter,
+ * parameters and the order in which the pair kernels sum over the NPs, so that
+ * a resumed run is bit-identical to an uninterrupted one.  npsim_load creates a new object; params_override (or NULL) replaces
  * the saved scenario parameters, types_override likewise.  Errors: IO (file
  * cannot be opened, is truncated or is not a checkpoint of this format). */
 int npsim_save(npsim_sim_t sim, const char *path);

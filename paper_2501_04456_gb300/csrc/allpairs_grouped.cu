@@ -139,14 +139,15 @@ k_coulomb_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n
 template <int BLOCK, int KI, int JT>
 __global__ void __launch_bounds__(BLOCK)
 k_ljc_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_perm,
-          const int *__restrict__ tblk, const PairTab *__restrict__ tab, StreamK sk,
-          float *__restrict__ slots)
+          const int *__restrict__ tblk, const PairTab *__restrict__ tab, float rc2_lim,
+          int has_coul, StreamK sk, float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
     constexpr int JP = JT / 2;
     __shared__ float4 s_a[JP]; // (-x0, -x1, -y0, -y1)
     __shared__ float2 s_b[JP]; // (-z0, -z1)
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rbox[6 * (BLOCK / 32)], s_jbox[6 * (BLOCK / 32)];
     for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += BLOCK)
         s_tab[k] = tab->e[k];
 
@@ -161,6 +162,7 @@ k_ljc_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_per
 
         float2 xi[KI], yi[KI], zi[KI];
         int trow[KI];
+        Box3 rb = box_empty();
         float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
@@ -174,10 +176,17 @@ k_ljc_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_per
             zi[k] = make_float2(q.z, q.z);
             trow[k] = (pos < n_perm ? tblk[pos >> 8] : 0) * NPSIM_MAX_TYPES;
             hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
+            if (i >= 0)
+                box_add(rb, q.x, q.y, q.z);
         }
+        // the row tile's bounding box (the tile loop's barriers order the reuse of s_rbox)
+        box_warp_store(rb, s_rbox);
+        __syncthreads();
+        rb = box_gather(s_rbox, BLOCK / 32);
 
         for (int jt = jt0; jt < jt1; ++jt) {
             __syncthreads(); // the previous tile has been consumed (and s_tab is loaded)
+            Box3 jb = box_empty();
             for (int m = threadIdx.x; m < JP; m += BLOCK) {
                 const int k0 = jt * JT + 2 * m;
                 const int j0 = perm[k0], j1 = perm[k0 + 1]; // n_perm is a multiple of JT
@@ -186,8 +195,14 @@ k_ljc_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_per
                 const float4 b = j1 >= 0 ? xq[j1] : pad;
                 s_a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
                 s_b[m] = make_float2(-a.z, -b.z);
+                if (j0 >= 0)
+                    box_add(jb, a.x, a.y, a.z);
+                if (j1 >= 0)
+                    box_add(jb, b.x, b.y, b.z);
             }
+            box_warp_store(jb, s_jbox);
             __syncthreads();
+            jb = box_gather(s_jbox, BLOCK / 32);
 
             const int tt = tblk[(jt * JT) >> 8]; // one type per tile
             float4 cst[KI];
@@ -197,19 +212,26 @@ k_ljc_grp(const float4 *__restrict__ xq, const int *__restrict__ perm, int n_per
                 cst[k] = s_tab[trow[k] + tt];
                 ax[k] = ay[k] = az[k] = make_float2(0.0f, 0.0f);
             }
+            // LJ only where the two tiles' boxes come within the largest cutoff
+            const bool lj_tile = rc2_lim > 0.0f && box_gap2(rb, jb) <= rc2_lim;
+            if (!lj_tile && !has_coul)
+                continue; // out of LJ range and no charges: the tile adds exactly 0
             const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
-            if (diag)
+            if (lj_tile && diag)
                 ljc_tile_sweep<KI, true>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
-            else
+            else if (lj_tile)
                 ljc_tile_sweep<KI, false>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
+            else
+                coul_tile_sweep<KI>(s_a, s_b, JP, xi, yi, zi, ax, ay, az);
 #pragma unroll
             for (int k = 0; k < KI; ++k) {
-                two_sum_acc(hx[k], lx[k], ax[k].x);
-                two_sum_acc(hx[k], lx[k], ax[k].y);
-                two_sum_acc(hy[k], ly[k], ay[k].x);
-                two_sum_acc(hy[k], ly[k], ay[k].y);
-                two_sum_acc(hz[k], lz[k], az[k].x);
-                two_sum_acc(hz[k], lz[k], az[k].y);
+                const float sc = lj_tile ? 1.0f : cst[k].w; // C q_a q_b of the Coulomb-only sum
+                two_sum_acc(hx[k], lx[k], sc * ax[k].x);
+                two_sum_acc(hx[k], lx[k], sc * ax[k].y);
+                two_sum_acc(hy[k], ly[k], sc * ay[k].x);
+                two_sum_acc(hy[k], ly[k], sc * ay[k].y);
+                two_sum_acc(hz[k], lz[k], sc * az[k].x);
+                two_sum_acc(hz[k], lz[k], sc * az[k].y);
             }
         }
 
@@ -258,9 +280,11 @@ const GEntry kLjg[] = {
 
 template <int B, int K, int J>
 cudaError_t launch_l(const StreamK &sk, const float4 *xq, const int *perm, int n_perm,
-                     const int *tblk, const PairTab *tab, float *slots, cudaStream_t st)
+                     const int *tblk, const PairTab *tab, float rc2_lim, int has_coul,
+                     float *slots, cudaStream_t st)
 {
-    k_ljc_grp<B, K, J><<<sk.grid, B, 0, st>>>(xq, perm, n_perm, tblk, tab, sk, slots);
+    k_ljc_grp<B, K, J><<<sk.grid, B, 0, st>>>(xq, perm, n_perm, tblk, tab, rc2_lim, has_coul,
+                                               sk, slots);
     return cudaGetLastError();
 }
 
@@ -310,15 +334,16 @@ int ljg_occupancy(int idx)
 
 cudaError_t launch_allpairs_ljgrp(int idx, const StreamK &sk, const float4 *xq,
                                   const int *perm, int n_perm, const int *tblk,
-                                  const PairTab *tab, float *slots, cudaStream_t st)
+                                  const PairTab *tab, float rc2_lim, int has_coul, float *slots,
+                                  cudaStream_t st)
 {
     switch (idx) {
-    case 0: return launch_l<256, 1, 512>(sk, xq, perm, n_perm, tblk, tab, slots, st);
-    case 1: return launch_l<256, 2, 512>(sk, xq, perm, n_perm, tblk, tab, slots, st);
-    case 2: return launch_l<512, 1, 512>(sk, xq, perm, n_perm, tblk, tab, slots, st);
-    case 3: return launch_l<128, 2, 256>(sk, xq, perm, n_perm, tblk, tab, slots, st);
-    case 4: return launch_l<256, 2, 256>(sk, xq, perm, n_perm, tblk, tab, slots, st);
-    case 5: return launch_l<128, 4, 256>(sk, xq, perm, n_perm, tblk, tab, slots, st);
+    case 0: return launch_l<256, 1, 512>(sk, xq, perm, n_perm, tblk, tab, rc2_lim, has_coul, slots, st);
+    case 1: return launch_l<256, 2, 512>(sk, xq, perm, n_perm, tblk, tab, rc2_lim, has_coul, slots, st);
+    case 2: return launch_l<512, 1, 512>(sk, xq, perm, n_perm, tblk, tab, rc2_lim, has_coul, slots, st);
+    case 3: return launch_l<128, 2, 256>(sk, xq, perm, n_perm, tblk, tab, rc2_lim, has_coul, slots, st);
+    case 4: return launch_l<256, 2, 256>(sk, xq, perm, n_perm, tblk, tab, rc2_lim, has_coul, slots, st);
+    case 5: return launch_l<128, 4, 256>(sk, xq, perm, n_perm, tblk, tab, rc2_lim, has_coul, slots, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -127,6 +127,7 @@ struct npsim_sim {
     double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES]{};
     bool has_ov = false;
     std::vector<int32_t> h_type;
+    std::vector<int32_t> h_rank; // order of each NP inside its type group (grouped kernels)
     double d_mean = 1.0;
     float charge_f[NPSIM_MAX_TYPES]{};
 
@@ -142,6 +143,8 @@ struct npsim_sim {
     float *slots = nullptr;
     float *F_lj = nullptr;                // [6][n]
     PairTab *tab_full = nullptr, *tab_lj = nullptr, *tab_coul = nullptr;
+    float rc2_lim = 0.0f; // largest LJ rc^2 of the table (x 1.0001): tile-culling bound
+    int any_charge = 0;   // Coulomb on and some type charged
     long long *d_step = nullptr;
     float4 *d_spring = nullptr; // [2][NPSIM_MAX_TYPES] spring radius table (spring_entry)
     int *d_flags = nullptr;
@@ -326,7 +329,8 @@ cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, bool coul, const St
     if (shape_ljg(k))
         return launch_allpairs_ljgrp(k - ap_num_configs() - grp_num_configs(), sk, s->xq,
                                      s->perm, s->n_perm, s->tblk, pair_table(s, lj, coul),
-                                     slots, st);
+                                     lj ? s->rc2_lim : 0.0f, coul ? s->any_charge : 0, slots,
+                                     st);
     if (shape_grouped(k))
         return launch_allpairs_grouped(k - ap_num_configs(), sk, s->xq, s->perm, s->n_perm,
                                        s->qblk, slots, st);
@@ -544,12 +548,56 @@ int autotune(npsim_sim *s)
     return NPSIM_OK;
 }
 
+// 3-D Morton (Z-order) key of a point with 10 bits per axis: the bits of the
+// cell indices interleaved, so that points close in the key are close in space.
+uint32_t spread_bits10(uint32_t v)
+{
+    v &= 1023u;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Order of the particles `idx` (AoS positions x) along the Z-order curve of
+// their bounding box; ties keep index order.
+void morton_sort(std::vector<int> &idx, const double *x)
+{
+    if (idx.size() < 2)
+        return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i : idx)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], x[3 * (size_t)i + d]);
+            hi[d] = std::max(hi[d], x[3 * (size_t)i + d]);
+        }
+    std::vector<std::pair<uint32_t, int>> key(idx.size());
+    for (size_t k = 0; k < idx.size(); ++k) {
+        const int i = idx[k];
+        uint32_t c[3];
+        for (int d = 0; d < 3; ++d) {
+            const double ext = hi[d] - lo[d];
+            const double u = ext > 0 ? (x[3 * (size_t)i + d] - lo[d]) / ext : 0.0;
+            c[d] = (uint32_t)std::min(1023.0, std::max(0.0, std::floor(u * 1024.0)));
+        }
+        key[k] = {spread_bits10(c[0]) | (spread_bits10(c[1]) << 1) | (spread_bits10(c[2]) << 2),
+                  i};
+    }
+    std::sort(key.begin(), key.end());
+    for (size_t k = 0; k < idx.size(); ++k)
+        idx[k] = key[k].second;
+}
+
 // Type-grouped order: the charged types first (in type order), then the
-// neutral ones; inside a group NPs keep their index order; every group is
-// padded with -1 to a multiple of 512, so each 256-position block has one type
-// (and one charge).  With skip_neutral and no LJ in the pair sum, the grouped
-// kernels cover only the charged groups and neutral NPs have no pair row.
-int build_grouping(npsim_sim *s, const int32_t *type)
+// neutral ones; inside a group NPs follow the Z-order curve of their positions
+// at creation when LJ is in the pair sum (tiles of nearby NPs let the LJ kernel
+// skip tile pairs beyond the cutoff), else their index order; every group is
+// padded with -1 to a multiple of 512, so each
+// 256-position block has one type (and one charge).  With skip_neutral and no
+// LJ in the pair sum, the grouped kernels cover only the charged groups and
+// neutral NPs have no pair row.
+int build_grouping(npsim_sim *s, const int32_t *type, const double *x0, const int32_t *rank)
 {
     std::vector<int> order;
     for (int t = 0; t < s->T; ++t)
@@ -562,6 +610,13 @@ int build_grouping(npsim_sim *s, const int32_t *type)
     std::vector<std::vector<int>> members(s->T);
     for (int i = 0; i < s->n; ++i)
         members[type[i]].push_back(i);
+    for (auto &m : members) {
+        if (rank) // an order saved with a checkpoint: resume in the same summation order
+            std::stable_sort(m.begin(), m.end(), [&](int a, int b) { return rank[a] < rank[b]; });
+        else if (s->P.lj_mode == 1) // LJ in the pair sum: spatially compact tiles
+            morton_sort(m, x0);
+        // Coulomb only: index order keeps the integrator's partial reads coalesced
+    }
     std::vector<int> perm, tb;
     std::vector<float> qb;
     std::vector<int> pos(s->n, -1);
@@ -584,6 +639,7 @@ int build_grouping(npsim_sim *s, const int32_t *type)
             charged_len = (int)perm.size();
     }
     s->n_perm = (int)perm.size();
+    s->h_rank.assign(pos.begin(), pos.end());
     const bool skip = s->P.skip_neutral && s->P.lj_mode != 1;
     if (skip) {
         s->grp_len = charged_len;
@@ -819,9 +875,15 @@ int npsim_device_info(int *sm_count, int *clock_khz, int *cc_major, int *cc_mino
     return NPSIM_OK;
 }
 
-int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_t n,
-                 const double *x0, const double *v0, const int32_t *type, void *stream,
-                 npsim_sim_t *out)
+} // extern "C"
+
+namespace {
+
+// npsim_create with an optional saved grouping order (rank, n entries: the
+// order of each NP inside its type group, from a checkpoint).
+int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t n,
+                const double *x0, const double *v0, const int32_t *type, void *stream,
+                const int32_t *rank, npsim_sim_t *out)
 {
     if (!out)
         return set_err(NPSIM_ERR_INVALID_ARG, "out is NULL");
@@ -890,8 +952,13 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
     fill_coefs(types, params, sp.tc, s->charge_f);
     PairTab tf{}, tl{}, tc{};
     const double rc_max = fill_tabs(types, params, s->has_ov ? s->eps_ov : nullptr, &tf, &tl);
-    for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) // Coulomb only: no LJ pair in range
+    for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) { // Coulomb only: no LJ pair in range
         tc.e[k] = make_float4(0.0f, 0.0f, 0.0f, tf.e[k].w);
+        if (params->lj_mode != 0 && tf.e[k].y != 0.0f)
+            s->rc2_lim = std::max(s->rc2_lim, tf.e[k].z * 1.0001f);
+        if (tf.e[k].w != 0.0f)
+            s->any_charge = 1;
+    }
 
 #define BAIL_CUDA(call)                                                                 \
     do {                                                                                \
@@ -953,7 +1020,7 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
         BAIL_CUDA(launch_mirror(s->x, s->typ, s->charge_f, s->n, s->xq, s->x_lo, s->user));
     }
     if (s->ap) {
-        rc = build_grouping(s, type);
+        rc = build_grouping(s, type, x0, rank);
         if (rc)
             return bail(rc);
         rc = autotune(s);
@@ -975,6 +1042,17 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
         return bail(rc);
     *out = s;
     return NPSIM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_t n,
+                 const double *x0, const double *v0, const int32_t *type, void *stream,
+                 npsim_sim_t *out)
+{
+    return create_impl(types, params, n, x0, v0, type, stream, nullptr, out);
 }
 
 void npsim_destroy(npsim_sim_t sim)
@@ -1343,8 +1421,9 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
 namespace {
 // Layout: header, then the raw state words so that a resumed run is
 // bit-identical: position hi words [3][n], lo words [3][n], velocities [3][n]
-// (float32 SoA), then the types (int32[n]).
-const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '2'};
+// (float32 SoA), the types (int32[n]) and the order of the NPs inside their
+// type groups (int32[n], the pair kernels' summation order).
+const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '3'};
 
 struct CkptHeader {
     char magic[8];
@@ -1363,7 +1442,7 @@ int npsim_save(npsim_sim_t s, const char *path)
     NP_REQUIRE(s && path, "sim and path are required");
     CkptHeader h{};
     memcpy(h.magic, kMagic, 8);
-    h.version = 2;
+    h.version = 3;
     h.n_types = s->T;
     h.n = s->n;
     h.step = s->step;
@@ -1402,10 +1481,13 @@ int npsim_save(npsim_sim_t s, const char *path)
     FILE *f = fopen(path, "wb");
     if (!f)
         return set_err(NPSIM_ERR_IO, "cannot open %s for writing", path);
+    std::vector<int32_t> rank(s->h_rank);
+    rank.resize(n, 0);
     bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
               fwrite(words.data(), sizeof(float), words.size(), f) == words.size() &&
               fwrite(s->h_type.data(), sizeof(int32_t), s->h_type.size(), f) ==
-                  s->h_type.size();
+                  s->h_type.size() &&
+              fwrite(rank.data(), sizeof(int32_t), rank.size(), f) == rank.size();
     ok = (fclose(f) == 0) && ok;
     if (!ok)
         return set_err(NPSIM_ERR_IO, "short write to %s", path);
@@ -1421,16 +1503,17 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     if (!f)
         return set_err(NPSIM_ERR_IO, "cannot open %s", path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 ||
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 3 ||
         h.n < 1 || h.n > (1ll << 29) || h.n_types < 1 || h.n_types > NPSIM_MAX_TYPES) {
         fclose(f);
         return set_err(NPSIM_ERR_IO, "%s is not an npsim checkpoint", path);
     }
     const size_t n = (size_t)h.n;
     std::vector<float> words(9 * n);
-    std::vector<int32_t> ty(n);
+    std::vector<int32_t> ty(n), rank(n);
     bool ok = fread(words.data(), sizeof(float), words.size(), f) == words.size() &&
-              fread(ty.data(), sizeof(int32_t), ty.size(), f) == ty.size();
+              fread(ty.data(), sizeof(int32_t), ty.size(), f) == ty.size() &&
+              fread(rank.data(), sizeof(int32_t), rank.size(), f) == rank.size();
     fclose(f);
     if (!ok)
         return set_err(NPSIM_ERR_IO, "%s is truncated", path);
@@ -1465,7 +1548,7 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     }
     const npsim_type_t *tys = types_override ? types_override : h.types;
     npsim_sim_t s = nullptr;
-    int rc = npsim_create(tys, &p, h.n, x.data(), v.data(), ty.data(), stream, &s);
+    int rc = create_impl(tys, &p, h.n, x.data(), v.data(), ty.data(), stream, rank.data(), &s);
     if (rc)
         return rc;
     rc = upload_words(s, words.data(), h.step);
@@ -1840,6 +1923,15 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
                 e->h_tabs[d].e[k].y = 0.0f;
                 e->h_tabs[d].e[k].z = 0.0f;
             }
+        g.rc2_lim = 0.0f;
+        g.has_coul = 0;
+        for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) {
+            const float4 t = e->h_tabs[d].e[k];
+            if (t.y != 0.0f)
+                g.rc2_lim = std::max(g.rc2_lim, t.z * 1.0001f);
+            if (t.w != 0.0f)
+                g.has_coul = 1;
+        }
         for (int i = 0; i < n; ++i) {
             for (int k = 0; k < 3; ++k) {
                 xs[(size_t)k * total + off + i] = dr.x0[3 * (size_t)i + k];
@@ -1851,21 +1943,24 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
         }
         off += n;
     }
-    // type-grouped order of every droplet: its types in order, each group padded
-    // with -1 to a multiple of 256 positions
+    // type-grouped order of every droplet: its types in order, each group in
+    // Z-order of the initial positions and padded with -1 to a multiple of 256
     std::vector<int> gperm, gtblk, gpos((size_t)total, -1);
     for (int d = 0; d < n_drops; ++d) {
         EnsDrop &g = e->h_drops[d];
         g.gpos0 = (int)gperm.size();
         for (int t = 0; t < drops[d].params.n_types; ++t) {
-            const size_t start = gperm.size();
+            std::vector<int> mem;
             for (int i = 0; i < e->cnt[d]; ++i)
-                if (drops[d].type[i] == t) {
-                    gpos[(size_t)e->off[d] + i] = (int)gperm.size();
-                    gperm.push_back(e->off[d] + i);
-                }
-            if (gperm.size() == start)
+                if (drops[d].type[i] == t)
+                    mem.push_back(i);
+            if (mem.empty())
                 continue;
+            morton_sort(mem, drops[d].x0);
+            for (int i : mem) {
+                gpos[(size_t)e->off[d] + i] = (int)gperm.size();
+                gperm.push_back(e->off[d] + i);
+            }
             while (gperm.size() % 256)
                 gperm.push_back(-1);
             while (gtblk.size() < gperm.size() / 256)

@@ -53,6 +53,7 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
     __shared__ float4 s_a[JP]; // (-x0, -x1, -y0, -y1)
     __shared__ float2 s_b[JP]; // (-z0, -z1)
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rbox[6 * (BLOCK / 32)], s_jbox[6 * (BLOCK / 32)];
 
     const int c = blockIdx.x;
     const long long p_end = sk_begin(sk, c + 1);
@@ -76,6 +77,7 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
 
         float2 xi[KI], yi[KI], zi[KI];
         int trow[KI];
+        Box3 rb = box_empty();
         float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
 #pragma unroll
         for (int k = 0; k < KI; ++k) {
@@ -90,10 +92,17 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
             zi[k] = make_float2(q.z, q.z);
             trow[k] = (in ? tblk[(D.gpos0 + lpos) >> 8] : 0) * NPSIM_MAX_TYPES;
             hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
+            if (i >= 0)
+                box_add(rb, q.x, q.y, q.z);
         }
+        // the row tile's bounding box (the tile loop's barriers order the reuse of s_rbox)
+        box_warp_store(rb, s_rbox);
+        __syncthreads();
+        rb = box_gather(s_rbox, BLOCK / 32);
 
         for (int jt = jt0; jt < jt1; ++jt) {
             __syncthreads(); // the previous tile has been consumed (and s_tab is loaded)
+            Box3 jb = box_empty();
             for (int m = threadIdx.x; m < JP; m += BLOCK) {
                 const int k0 = D.gpos0 + jt * JT + 2 * m; // npad is a multiple of JT
                 const int j0 = perm[k0], j1 = perm[k0 + 1];
@@ -102,8 +111,14 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
                 const float4 b = j1 >= 0 ? xq[j1] : pad;
                 s_a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
                 s_b[m] = make_float2(-a.z, -b.z);
+                if (j0 >= 0)
+                    box_add(jb, a.x, a.y, a.z);
+                if (j1 >= 0)
+                    box_add(jb, b.x, b.y, b.z);
             }
+            box_warp_store(jb, s_jbox);
             __syncthreads();
+            jb = box_gather(s_jbox, BLOCK / 32);
 
             const int tt = tblk[(D.gpos0 + jt * JT) >> 8]; // one type per tile
             float4 cst[KI];
@@ -113,19 +128,26 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
                 cst[k] = s_tab[trow[k] + tt];
                 ax[k] = ay[k] = az[k] = make_float2(0.0f, 0.0f);
             }
+            // LJ only where the two tiles' boxes come within the largest cutoff
+            const bool lj_tile = D.rc2_lim > 0.0f && box_gap2(rb, jb) <= D.rc2_lim;
+            if (!lj_tile && !D.has_coul)
+                continue; // out of LJ range and no charges: the tile adds exactly 0
             const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
-            if (diag)
+            if (lj_tile && diag)
                 ljc_tile_sweep<KI, true>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
-            else
+            else if (lj_tile)
                 ljc_tile_sweep<KI, false>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
+            else
+                coul_tile_sweep<KI>(s_a, s_b, JP, xi, yi, zi, ax, ay, az);
 #pragma unroll
             for (int k = 0; k < KI; ++k) {
-                two_sum_acc(hx[k], lx[k], ax[k].x);
-                two_sum_acc(hx[k], lx[k], ax[k].y);
-                two_sum_acc(hy[k], ly[k], ay[k].x);
-                two_sum_acc(hy[k], ly[k], ay[k].y);
-                two_sum_acc(hz[k], lz[k], az[k].x);
-                two_sum_acc(hz[k], lz[k], az[k].y);
+                const float sc = lj_tile ? 1.0f : cst[k].w; // C q_a q_b of the Coulomb-only sum
+                two_sum_acc(hx[k], lx[k], sc * ax[k].x);
+                two_sum_acc(hx[k], lx[k], sc * ax[k].y);
+                two_sum_acc(hy[k], ly[k], sc * ay[k].x);
+                two_sum_acc(hy[k], ly[k], sc * ay[k].y);
+                two_sum_acc(hz[k], lz[k], sc * az[k].x);
+                two_sum_acc(hz[k], lz[k], sc * az[k].y);
             }
         }
 

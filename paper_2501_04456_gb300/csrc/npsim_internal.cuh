@@ -85,21 +85,31 @@ constexpr float kPairPad = 1.0e18f;    // padding position: every term with it u
 // partner pairs staged in shared memory as negated coordinates, s_a = (-x0,
 // -x1, -y0, -y1), s_b = (-z0, -z1); cst[k] = (sigma_ab^2, 24 eps_ab, rc_ab^2,
 // C q_a q_b) of row k and the tile's type.  Per pair:
-//   d = x_i - x_j; r^2 = d.d (+ kPairSelfEps); 1/r = rsqrt(r^2);
-//   f = C q_a q_b / r^3 + [r^2 < rc_ab^2] 24 eps_ab / r^2 s^6 (2 s^6 - 1),
-//   s^2 = sigma_ab^2 / r^2;  a += f d,
-// on the packed float32x2 instructions, two partners per register pair.  DIAG
+//   d = x_i - x_j; r^2 = d.d (+ kPairSelfEps); 1/r = rsqrt(r^2); s^6 = (sigma_ab^2/r^2)^3;
+//   f = [C q_a q_b / r + [r^2 < rc_ab^2] s^6 (48 eps_ab s^6 - 24 eps_ab)] / r^2,
+//   a += f d
+// (the bracket is 24 eps_ab (2 s^12 - s^6) r^2 / r^2, the LJ force over r),
+// on the packed float32x2 instructions, two partners per register pair: 17
+// packed instructions per two pairs, two MUFU.RSQ, two cutoff selects.  DIAG
 // (a tile that holds a row's own column) also masks the self pair out of the
 // LJ term, whose r^-14 would overflow there.
 template <int KI, bool DIAG>
 __device__ __forceinline__ void ljc_tile_sweep(const float4 *__restrict__ s_a,
-                                          const float2 *__restrict__ s_b, int JP,
-                                          const float2 (&xi)[KI], const float2 (&yi)[KI],
-                                          const float2 (&zi)[KI], const float4 (&cst)[KI],
-                                          float2 (&ax)[KI], float2 (&ay)[KI], float2 (&az)[KI])
+                                               const float2 *__restrict__ s_b, int JP,
+                                               const float2 (&xi)[KI], const float2 (&yi)[KI],
+                                               const float2 (&zi)[KI], const float4 (&cst)[KI],
+                                               float2 (&ax)[KI], float2 (&ay)[KI],
+                                               float2 (&az)[KI])
 {
     const float2 eps2 = make_float2(kPairSelfEps, kPairSelfEps);
-    const float2 two = make_float2(2.0f, 2.0f), mone = make_float2(-1.0f, -1.0f);
+    float2 sig2[KI], e48[KI], em24[KI], cqq[KI];
+#pragma unroll
+    for (int k = 0; k < KI; ++k) {
+        sig2[k] = make_float2(cst[k].x, cst[k].x);
+        e48[k] = make_float2(2.0f * cst[k].y, 2.0f * cst[k].y);
+        em24[k] = make_float2(-cst[k].y, -cst[k].y);
+        cqq[k] = make_float2(cst[k].w, cst[k].w);
+    }
 #pragma unroll 2
     for (int m = 0; m < JP; ++m) {
         const float4 a = s_a[m];
@@ -115,25 +125,126 @@ __device__ __forceinline__ void ljc_tile_sweep(const float4 *__restrict__ s_a,
             r2 = __ffma2_rn(dx, dx, r2);
             const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
             const float2 ri2 = __fmul2_rn(ri, ri);
-            const float2 s2 = __fmul2_rn(make_float2(cst[k].x, cst[k].x), ri2);
+            const float2 s2 = __fmul2_rn(sig2[k], ri2);
             const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
-            const float2 u = __ffma2_rn(two, s6, mone);
-            const float2 w = __fmul2_rn(make_float2(cst[k].y, cst[k].y), ri2);
-            float2 flj = __fmul2_rn(__fmul2_rn(w, s6), u);
+            float2 t = __fmul2_rn(s6, __ffma2_rn(e48[k], s6, em24[k]));
             if (DIAG) {
-                flj.x = (r2.x < cst[k].z && r2.x > kPairSelfMin) ? flj.x : 0.0f;
-                flj.y = (r2.y < cst[k].z && r2.y > kPairSelfMin) ? flj.y : 0.0f;
+                t.x = (r2.x < cst[k].z && r2.x > kPairSelfMin) ? t.x : 0.0f;
+                t.y = (r2.y < cst[k].z && r2.y > kPairSelfMin) ? t.y : 0.0f;
             } else {
-                flj.x = r2.x < cst[k].z ? flj.x : 0.0f;
-                flj.y = r2.y < cst[k].z ? flj.y : 0.0f;
+                t.x = r2.x < cst[k].z ? t.x : 0.0f;
+                t.y = r2.y < cst[k].z ? t.y : 0.0f;
             }
-            const float2 f =
-                __ffma2_rn(__fmul2_rn(make_float2(cst[k].w, cst[k].w), ri), ri2, flj);
+            const float2 f = __fmul2_rn(__ffma2_rn(cqq[k], ri, t), ri2);
             ax[k] = __ffma2_rn(f, dx, ax[k]);
             ay[k] = __ffma2_rn(f, dy, ay[k]);
             az[k] = __ffma2_rn(f, dz, az[k]);
         }
     }
+}
+
+// One j-tile of the Coulomb-only sum with the charge factored out: a += sum_j
+// d / r^3 (the caller multiplies by the tile's C q_a q_b or q_t): 11 packed
+// lanes per pair (3 sub, 3 for r^2, 2 for 1/r^3, 3 accumulate), one MUFU.RSQ.
+// The self pair contributes exactly 0 (d = 0, r^2 = kPairSelfEps).
+template <int KI>
+__device__ __forceinline__ void coul_tile_sweep(const float4 *__restrict__ s_a,
+                                                const float2 *__restrict__ s_b, int JP,
+                                                const float2 (&xi)[KI], const float2 (&yi)[KI],
+                                                const float2 (&zi)[KI], float2 (&ax)[KI],
+                                                float2 (&ay)[KI], float2 (&az)[KI])
+{
+    const float2 eps2 = make_float2(kPairSelfEps, kPairSelfEps);
+#pragma unroll 2
+    for (int m = 0; m < JP; ++m) {
+        const float4 a = s_a[m];
+        const float2 nz = s_b[m];
+        const float2 nx = make_float2(a.x, a.y), ny = make_float2(a.z, a.w);
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const float2 dx = __fadd2_rn(xi[k], nx);
+            const float2 dy = __fadd2_rn(yi[k], ny);
+            const float2 dz = __fadd2_rn(zi[k], nz);
+            float2 r2 = __ffma2_rn(dz, dz, eps2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dx, dx, r2);
+            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 f = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+            ax[k] = __ffma2_rn(f, dx, ax[k]);
+            ay[k] = __ffma2_rn(f, dy, ay[k]);
+            az[k] = __ffma2_rn(f, dz, az[k]);
+        }
+    }
+}
+
+// Axis-aligned box of points: lo = +inf, hi = -inf when empty.
+struct Box3 {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ __forceinline__ Box3 box_empty()
+{
+    return Box3{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+}
+
+__device__ __forceinline__ void box_add(Box3 &b, float x, float y, float z)
+{
+    b.lx = fminf(b.lx, x);
+    b.ly = fminf(b.ly, y);
+    b.lz = fminf(b.lz, z);
+    b.hx = fmaxf(b.hx, x);
+    b.hy = fmaxf(b.hy, y);
+    b.hz = fmaxf(b.hz, z);
+}
+
+// Warp-reduce b and store lane 0's result as 6 floats at s_red[6 * warp]; the
+// caller synchronises the block and then calls box_gather.
+__device__ __forceinline__ void box_warp_store(Box3 b, float *s_red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        b.lx = fminf(b.lx, __shfl_xor_sync(0xffffffffu, b.lx, o));
+        b.ly = fminf(b.ly, __shfl_xor_sync(0xffffffffu, b.ly, o));
+        b.lz = fminf(b.lz, __shfl_xor_sync(0xffffffffu, b.lz, o));
+        b.hx = fmaxf(b.hx, __shfl_xor_sync(0xffffffffu, b.hx, o));
+        b.hy = fmaxf(b.hy, __shfl_xor_sync(0xffffffffu, b.hy, o));
+        b.hz = fmaxf(b.hz, __shfl_xor_sync(0xffffffffu, b.hz, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        float *r = s_red + 6 * (threadIdx.x >> 5);
+        r[0] = b.lx;
+        r[1] = b.ly;
+        r[2] = b.lz;
+        r[3] = b.hx;
+        r[4] = b.hy;
+        r[5] = b.hz;
+    }
+}
+
+__device__ __forceinline__ Box3 box_gather(const float *s_red, int n_warps)
+{
+    Box3 b = box_empty();
+    for (int w = 0; w < n_warps; ++w) {
+        const float *r = s_red + 6 * w;
+        b.lx = fminf(b.lx, r[0]);
+        b.ly = fminf(b.ly, r[1]);
+        b.lz = fminf(b.lz, r[2]);
+        b.hx = fmaxf(b.hx, r[3]);
+        b.hy = fmaxf(b.hy, r[4]);
+        b.hz = fmaxf(b.hz, r[5]);
+    }
+    return b;
+}
+
+// Squared distance between two boxes (0 if they overlap; +inf if one is empty).
+__device__ __forceinline__ float box_gap2(const Box3 &a, const Box3 &b)
+{
+    if (a.lx > a.hx || b.lx > b.hx)
+        return INFINITY;
+    const float gx = fmaxf(0.0f, fmaxf(b.lx - a.hx, a.lx - b.hx));
+    const float gy = fmaxf(0.0f, fmaxf(b.ly - a.hy, a.ly - b.hy));
+    const float gz = fmaxf(0.0f, fmaxf(b.lz - a.hz, a.lz - b.hz));
+    return gx * gx + gy * gy + gz * gz;
 }
 
 // ---------------------------------------------------------------------------
@@ -357,9 +468,12 @@ cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq
 int ljg_num_configs();
 ApConfig ljg_config(int idx);
 int ljg_occupancy(int idx);
+// rc2_lim: LJ is evaluated only between tiles whose boxes come within
+// sqrt(rc2_lim) (0: no LJ); has_coul = 0 skips the other tiles entirely.
 cudaError_t launch_allpairs_ljgrp(int idx, const StreamK &sk, const float4 *xq,
                                   const int *perm, int n_perm, const int *tblk,
-                                  const PairTab *tab, float *slots, cudaStream_t st);
+                                  const PairTab *tab, float rc2_lim, int has_coul, float *slots,
+                                  cudaStream_t st);
 cudaError_t launch_allpairs(int cfg_idx, bool lj, const StreamK &sk, const float4 *xq,
                             const int *typ, int n, const PairTab *tab, float *slots,
                             cudaStream_t st);
@@ -470,6 +584,8 @@ cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
 struct EnsDrop {
     int offset, n, n_it, n_jt, row0, rot_mode, wall, integrator;
     int gpos0, npad;
+    float rc2_lim;  // LJ only between tiles within this squared distance (0: no LJ)
+    int has_coul;   // 0: tiles out of LJ range add nothing
     long long unit0;
     uint64_t seed;
     double dt, R0, k_evap, g, omega2;
