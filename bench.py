@@ -546,6 +546,12 @@ def run_ours(a):
                "kind": "oracle",
                "sample": f"FP64 oracle pair+external forces of {rows} random rows of the "
                          f"{n}-NP workload (all {n - 1} partners each), {dt:.1f} s"}
+        if ens:
+            # the same oracle rate applied to the ensemble's pair count (context:
+            # the oracle's LJ + Coulomb pairs cost about what its Coulomb pairs do)
+            ens["oracle_droplets_per_s_extrapolated"] = (
+                cpu["value"] / (ens["pairs_per_step"] * ens["steps_per_droplet"]) *
+                ens["droplets"])
 
     if rank == 0:
         out = {

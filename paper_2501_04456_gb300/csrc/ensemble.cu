@@ -49,11 +49,8 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
           StreamK sk, float *__restrict__ slots)
 {
     constexpr int ITILE = BLOCK * KI;
-    constexpr int JP = JT / 2;
-    __shared__ float4 s_a[JP]; // (-x0, -x1, -y0, -y1)
-    __shared__ float2 s_b[JP]; // (-z0, -z1)
+    __shared__ LjcSmem<JT> sm;
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
-    __shared__ float s_rbox[6 * (BLOCK / 32)], s_jbox[6 * (BLOCK / 32)];
 
     const int c = blockIdx.x;
     const long long p_end = sk_begin(sk, c + 1);
@@ -66,7 +63,7 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
         if (d != cur) {
             __syncthreads(); // every thread is done with the previous table
             for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += BLOCK)
-                s_tab[k] = tabs[d].e[k];
+                s_tab[k] = tabs[d].e[k]; // ordered before use by the tile barrier
             cur = d;
         }
         const long long lu = p - D.unit0;
@@ -74,94 +71,9 @@ k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
         const int jt0 = (int)(lu - (long long)r * D.n_jt);
         const long long left = min(p_end, D.unit0 + (long long)D.n_it * D.n_jt) - p;
         const int jt1 = (int)min((long long)D.n_jt, (long long)jt0 + left);
-
-        float2 xi[KI], yi[KI], zi[KI];
-        int trow[KI];
-        Box3 rb = box_empty();
-        float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
-#pragma unroll
-        for (int k = 0; k < KI; ++k) {
-            const int lpos = r * ITILE + k * BLOCK + threadIdx.x;
-            const bool in = lpos < D.npad;
-            const int i = in ? perm[D.gpos0 + lpos] : -1;
-            float4 q = make_float4(kPairPad, kPairPad, kPairPad, 0.0f);
-            if (i >= 0)
-                q = xq[i];
-            xi[k] = make_float2(q.x, q.x);
-            yi[k] = make_float2(q.y, q.y);
-            zi[k] = make_float2(q.z, q.z);
-            trow[k] = (in ? tblk[(D.gpos0 + lpos) >> 8] : 0) * NPSIM_MAX_TYPES;
-            hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
-            if (i >= 0)
-                box_add(rb, q.x, q.y, q.z);
-        }
-        // the row tile's bounding box (the tile loop's barriers order the reuse of s_rbox)
-        box_warp_store(rb, s_rbox);
-        __syncthreads();
-        rb = box_gather(s_rbox, BLOCK / 32);
-
-        for (int jt = jt0; jt < jt1; ++jt) {
-            __syncthreads(); // the previous tile has been consumed (and s_tab is loaded)
-            Box3 jb = box_empty();
-            for (int m = threadIdx.x; m < JP; m += BLOCK) {
-                const int k0 = D.gpos0 + jt * JT + 2 * m; // npad is a multiple of JT
-                const int j0 = perm[k0], j1 = perm[k0 + 1];
-                const float4 pad = make_float4(-kPairPad, -kPairPad, -kPairPad, 0.0f);
-                const float4 a = j0 >= 0 ? xq[j0] : pad;
-                const float4 b = j1 >= 0 ? xq[j1] : pad;
-                s_a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
-                s_b[m] = make_float2(-a.z, -b.z);
-                if (j0 >= 0)
-                    box_add(jb, a.x, a.y, a.z);
-                if (j1 >= 0)
-                    box_add(jb, b.x, b.y, b.z);
-            }
-            box_warp_store(jb, s_jbox);
-            __syncthreads();
-            jb = box_gather(s_jbox, BLOCK / 32);
-
-            const int tt = tblk[(D.gpos0 + jt * JT) >> 8]; // one type per tile
-            float4 cst[KI];
-            float2 ax[KI], ay[KI], az[KI];
-#pragma unroll
-            for (int k = 0; k < KI; ++k) {
-                cst[k] = s_tab[trow[k] + tt];
-                ax[k] = ay[k] = az[k] = make_float2(0.0f, 0.0f);
-            }
-            // LJ only where the two tiles' boxes come within the largest cutoff
-            const bool lj_tile = D.rc2_lim > 0.0f && box_gap2(rb, jb) <= D.rc2_lim;
-            if (!lj_tile && !D.has_coul)
-                continue; // out of LJ range and no charges: the tile adds exactly 0
-            const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
-            if (lj_tile && diag)
-                ljc_tile_sweep<KI, true>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
-            else if (lj_tile)
-                ljc_tile_sweep<KI, false>(s_a, s_b, JP, xi, yi, zi, cst, ax, ay, az);
-            else
-                coul_tile_sweep<KI>(s_a, s_b, JP, xi, yi, zi, ax, ay, az);
-#pragma unroll
-            for (int k = 0; k < KI; ++k) {
-                const float sc = lj_tile ? 1.0f : cst[k].w; // C q_a q_b of the Coulomb-only sum
-                two_sum_acc(hx[k], lx[k], sc * ax[k].x);
-                two_sum_acc(hx[k], lx[k], sc * ax[k].y);
-                two_sum_acc(hy[k], ly[k], sc * ay[k].x);
-                two_sum_acc(hy[k], ly[k], sc * ay[k].y);
-                two_sum_acc(hz[k], lz[k], sc * az[k].x);
-                two_sum_acc(hz[k], lz[k], sc * az[k].y);
-            }
-        }
-
-        float *slot = slots + (size_t)(D.row0 + r + c) * 6 * ITILE; // hi x,y,z, lo x,y,z
-#pragma unroll
-        for (int k = 0; k < KI; ++k) {
-            const int idx = k * BLOCK + threadIdx.x;
-            slot[idx] = hx[k];
-            slot[ITILE + idx] = hy[k];
-            slot[2 * ITILE + idx] = hz[k];
-            slot[3 * ITILE + idx] = lx[k];
-            slot[4 * ITILE + idx] = ly[k];
-            slot[5 * ITILE + idx] = lz[k];
-        }
+        ljc_row_segment<BLOCK, KI, JT>(xq, perm, tblk, D.gpos0, D.npad, s_tab, D.rc2_lim,
+                                       D.has_coul, r, jt0, jt1, sm,
+                                       slots + (size_t)(D.row0 + r + c) * 6 * ITILE);
         p += jt1 - jt0;
     }
 }

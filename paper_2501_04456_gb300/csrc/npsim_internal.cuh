@@ -197,6 +197,21 @@ __device__ __forceinline__ void box_add(Box3 &b, float x, float y, float z)
     b.hz = fmaxf(b.hz, z);
 }
 
+// Box of the points of the whole warp, in every lane.
+__device__ __forceinline__ Box3 box_warp_reduce(Box3 b)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        b.lx = fminf(b.lx, __shfl_xor_sync(0xffffffffu, b.lx, o));
+        b.ly = fminf(b.ly, __shfl_xor_sync(0xffffffffu, b.ly, o));
+        b.lz = fminf(b.lz, __shfl_xor_sync(0xffffffffu, b.lz, o));
+        b.hx = fmaxf(b.hx, __shfl_xor_sync(0xffffffffu, b.hx, o));
+        b.hy = fmaxf(b.hy, __shfl_xor_sync(0xffffffffu, b.hy, o));
+        b.hz = fmaxf(b.hz, __shfl_xor_sync(0xffffffffu, b.hz, o));
+    }
+    return b;
+}
+
 // Warp-reduce b and store lane 0's result as 6 floats at s_red[6 * warp]; the
 // caller synchronises the block and then calls box_gather.
 __device__ __forceinline__ void box_warp_store(Box3 b, float *s_red)
@@ -245,6 +260,118 @@ __device__ __forceinline__ float box_gap2(const Box3 &a, const Box3 &b)
     const float gy = fmaxf(0.0f, fmaxf(b.ly - a.hy, a.ly - b.hy));
     const float gz = fmaxf(0.0f, fmaxf(b.lz - a.hz, a.lz - b.hz));
     return gx * gx + gy * gy + gz * gz;
+}
+
+// Shared memory of ljc_row_segment: one staged j-tile (negated coordinates,
+// two partners per entry) and the box of each 64-partner segment of it.
+template <int JT>
+struct LjcSmem {
+    float4 a[JT / 2]; // (-x0, -x1, -y0, -y1)
+    float2 b[JT / 2]; // (-z0, -z1)
+    Box3 seg[JT / 64];
+};
+
+// Row tile r (rows r*ITILE .. of a grouped order occupying positions [gbase,
+// gbase + glen) of perm / tblk) against its j-tiles jt0 .. jt1-1 of the same
+// order; writes the row partials, as compensated (hi, lo) pairs, to slot
+// [6][ITILE].  For every (warp, 64-partner segment) pair the LJ term is
+// evaluated only when the box of the warp's rows and the box of the segment
+// come within sqrt(rc2_lim); elsewhere the Coulomb-only sweep runs (the charge
+// product applied once per tile), or nothing when has_coul is 0.  s_tab: the
+// 8 x 8 type-pair table (sigma^2, 24 eps, rc^2, C q q) in shared memory.
+template <int BLOCK, int KI, int JT>
+__device__ __forceinline__ void ljc_row_segment(const float4 *__restrict__ xq,
+                                                const int *__restrict__ perm,
+                                                const int *__restrict__ tblk, int gbase,
+                                                int glen, const float4 *__restrict__ s_tab,
+                                                float rc2_lim, int has_coul, int r, int jt0,
+                                                int jt1, LjcSmem<JT> &sm, float *__restrict__ slot)
+{
+    constexpr int ITILE = BLOCK * KI;
+    constexpr int JP = JT / 2;
+    constexpr int NSEG = JT / 64;
+    float2 xi[KI], yi[KI], zi[KI];
+    int trow[KI];
+    float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
+    Box3 wb = box_empty();
+#pragma unroll
+    for (int k = 0; k < KI; ++k) {
+        const int lpos = r * ITILE + k * BLOCK + threadIdx.x;
+        const bool in = lpos < glen;
+        const int i = in ? perm[gbase + lpos] : -1;
+        float4 q = make_float4(kPairPad, kPairPad, kPairPad, 0.0f);
+        if (i >= 0) {
+            q = xq[i];
+            box_add(wb, q.x, q.y, q.z);
+        }
+        xi[k] = make_float2(q.x, q.x);
+        yi[k] = make_float2(q.y, q.y);
+        zi[k] = make_float2(q.z, q.z);
+        trow[k] = (in ? tblk[(gbase + lpos) >> 8] : 0) * NPSIM_MAX_TYPES;
+        hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.0f;
+    }
+    wb = box_warp_reduce(wb); // the box of this warp's rows
+
+    for (int jt = jt0; jt < jt1; ++jt) {
+        __syncthreads(); // the previous tile has been consumed
+        for (int m = threadIdx.x; m < JP; m += BLOCK) { // whole warps take each pass
+            const int k0 = gbase + jt * JT + 2 * m;      // glen is a multiple of JT
+            const int j0 = perm[k0], j1 = perm[k0 + 1];
+            const float4 pad = make_float4(-kPairPad, -kPairPad, -kPairPad, 0.0f);
+            const float4 a = j0 >= 0 ? xq[j0] : pad;
+            const float4 b = j1 >= 0 ? xq[j1] : pad;
+            sm.a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
+            sm.b[m] = make_float2(-a.z, -b.z);
+            Box3 pb = box_empty();
+            if (j0 >= 0)
+                box_add(pb, a.x, a.y, a.z);
+            if (j1 >= 0)
+                box_add(pb, b.x, b.y, b.z);
+            pb = box_warp_reduce(pb); // the 32 entries m of this warp = one segment
+            if ((threadIdx.x & 31) == 0)
+                sm.seg[m >> 5] = pb;
+        }
+        __syncthreads();
+
+        const int tt = tblk[(gbase + jt * JT) >> 8]; // one type per tile
+        float4 cst[KI];
+        float2 ax[KI], ay[KI], az[KI], cx[KI], cy[KI], cz[KI];
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            cst[k] = s_tab[trow[k] + tt];
+            ax[k] = ay[k] = az[k] = cx[k] = cy[k] = cz[k] = make_float2(0.0f, 0.0f);
+        }
+        const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
+        for (int sg = 0; sg < NSEG; ++sg) { // warp-uniform choice per segment
+            const bool lj = rc2_lim > 0.0f && box_gap2(wb, sm.seg[sg]) <= rc2_lim;
+            const float4 *sa = sm.a + 32 * sg;
+            const float2 *sb = sm.b + 32 * sg;
+            if (lj && diag)
+                ljc_tile_sweep<KI, true>(sa, sb, 32, xi, yi, zi, cst, ax, ay, az);
+            else if (lj)
+                ljc_tile_sweep<KI, false>(sa, sb, 32, xi, yi, zi, cst, ax, ay, az);
+            else if (has_coul)
+                coul_tile_sweep<KI>(sa, sb, 32, xi, yi, zi, cx, cy, cz);
+        }
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const float qq = cst[k].w; // C q_a q_b of the Coulomb-only segments
+            two_sum_acc(hx[k], lx[k], fmaf(qq, cx[k].x + cx[k].y, ax[k].x + ax[k].y));
+            two_sum_acc(hy[k], ly[k], fmaf(qq, cy[k].x + cy[k].y, ay[k].x + ay[k].y));
+            two_sum_acc(hz[k], lz[k], fmaf(qq, cz[k].x + cz[k].y, az[k].x + az[k].y));
+        }
+    }
+
+#pragma unroll
+    for (int k = 0; k < KI; ++k) {
+        const int idx = k * BLOCK + threadIdx.x;
+        slot[idx] = hx[k];
+        slot[ITILE + idx] = hy[k];
+        slot[2 * ITILE + idx] = hz[k];
+        slot[3 * ITILE + idx] = lx[k];
+        slot[4 * ITILE + idx] = ly[k];
+        slot[5 * ITILE + idx] = lz[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
