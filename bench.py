@@ -295,12 +295,12 @@ def _ensemble_measure(P, torch, stream, steps, warmup, n_plain=16, steps_per_dro
 INT_BYTES_BA = 16 + 12 + 12 + 4 + 16 + 12 + 12
 INT_BYTES_B = 16 + 12 + 12 + 4 + 24 + 12
 # Cell list per NP: hash (read 16, write key + rank 8), scatter (key, rank,
-# start, sorted: 16), per-cell sort (sorted read + write: 8), gather (sorted 4,
-# hi words 16, type 4, written 20), LJ (own record 20, sorted index 4, force as
-# (hi, lo) pairs 24); per cell: count reset, three scan passes and the sort's
-# range reads (28).
-CELL_BYTES_NP = 24 + 16 + 8 + 44 + 48
-CELL_BYTES_CELL = 28
+# start, arrival slot: 16), in-cell order (arrival slot, key, cell range,
+# sorted: 20), gather (sorted 4, position 16, type 4, record written 16), LJ
+# (own record 16, sorted index 4, force record 24); per cell: count reset and
+# the three scan passes (20).
+CELL_BYTES_NP = 24 + 16 + 20 + 40 + 44
+CELL_BYTES_CELL = 20
 
 
 def _hbm_peak():

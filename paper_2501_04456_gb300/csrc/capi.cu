@@ -222,9 +222,9 @@ struct npsim_sim {
             dfree(b->rank);
             dfree(b->count);
             dfree(b->start);
+            dfree(b->arrived);
             dfree(b->sorted);
             dfree(b->sxq);
-            dfree(b->styp);
             dfree(b->tile_sum);
         }
         dfree(s_hist);
@@ -246,9 +246,9 @@ int alloc_cells(CellGrid &g, CellBufs &b, int n)
     NP_CUDA(dalloc(&b.rank, n));
     NP_CUDA(dalloc(&b.count, g.n_cells));
     NP_CUDA(dalloc(&b.start, (size_t)g.n_cells + 1));
+    NP_CUDA(dalloc(&b.arrived, n));
     NP_CUDA(dalloc(&b.sorted, n));
     NP_CUDA(dalloc(&b.sxq, n));
-    NP_CUDA(dalloc(&b.styp, n));
     NP_CUDA(dalloc(&b.tile_sum, cell_scan_tiles(g.n_cells)));
     return NPSIM_OK;
 }
@@ -1293,7 +1293,7 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
         if (g.n_cells > s->s_cells_cap) {
             CellBufs &b = s->scb;
             dfree(b.key); dfree(b.rank); dfree(b.count); dfree(b.start);
-            dfree(b.sorted); dfree(b.sxq); dfree(b.styp); dfree(b.tile_sum);
+            dfree(b.arrived); dfree(b.sorted); dfree(b.sxq); dfree(b.tile_sum);
             int rc = alloc_cells(g, s->scb, n);
             if (rc)
                 return rc;

@@ -5,11 +5,13 @@
 //   F_i = sum_{j != i, r < rc_ij} 24 eps_ij (2 (s_ij/r)^12 - (s_ij/r)^6) r_ij / r^2.
 //
 // Binning is a counting sort: hash (cell of each NP, its arrival rank from an
-// atomic counter), exclusive scan of the per-cell counts, scatter, then a
-// per-cell sort by NP index so that the order inside a cell -- and therefore
-// the float summation order of the LJ kernel -- does not depend on the atomic
-// arrival order (runs are bit-reproducible).  A gather writes the NP data in
-// cell order so the LJ kernel reads neighbours from contiguous memory.  The
+// atomic counter), exclusive scan of the per-cell counts, scatter, then every
+// NP is placed at its rank by index inside its cell (one thread per NP counts
+// the members of its cell with a smaller index) so that the order inside a
+// cell -- and therefore the float summation order of the LJ kernel -- does not
+// depend on the atomic arrival order (runs are bit-reproducible).  A gather
+// writes the NP records (position, type in the fourth word) in cell order so
+// the LJ kernel reads neighbours from contiguous memory.  The
 // cell edge is at least the largest cutoff (times 1 + 1e-5, so float rounding
 // of the cell index can never separate two NPs within the cutoff by more than
 // one cell); coordinates beyond the grid are clamped into the edge cells,
@@ -151,60 +153,69 @@ k_scan_add(int *__restrict__ start, const int *__restrict__ tile_sum, int m)
 }
 
 __global__ void k_cell_scatter(const int *__restrict__ key, const int *__restrict__ rank,
-                               const int *__restrict__ start, int *__restrict__ sorted,
+                               const int *__restrict__ start, int *__restrict__ arrived,
                                int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    sorted[start[key[i]] + rank[i]] = i;
+    arrived[start[key[i]] + rank[i]] = i;
 }
 
-// Order each cell's members by NP index (insertion sort; cells hold few NPs).
-__global__ void k_cell_sort(const int *__restrict__ start, int *__restrict__ sorted,
-                            int n_cells)
+// Members of every cell in index order: the NP at arrival slot q goes to its
+// cell's start plus the number of members with a smaller index (O(m) per NP for
+// a cell of m members, all NPs in parallel).
+__global__ void k_cell_order(const int *__restrict__ arrived, const int *__restrict__ key,
+                             const int *__restrict__ start, int *__restrict__ sorted, int n)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cells)
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n)
         return;
+    const int i = arrived[q];
+    const int c = key[i];
     const int b = start[c], e = start[c + 1];
-    for (int k = b + 1; k < e; ++k) {
-        const int v = sorted[k];
-        int m = k - 1;
-        while (m >= b && sorted[m] > v) {
-            sorted[m + 1] = sorted[m];
-            --m;
-        }
-        sorted[m + 1] = v;
-    }
+    int rank = 0;
+    for (int k = b; k < e; ++k)
+        rank += arrived[k] < i;
+    sorted[b + rank] = i;
 }
 
+// Cell-ordered records: (x, y, z, type as int bits).
 __global__ void k_cell_gather(const int *__restrict__ sorted, const float4 *__restrict__ xq,
-                              const int *__restrict__ typ, float4 *__restrict__ sxq,
-                              int *__restrict__ styp, int n)
+                              const int *__restrict__ typ, float4 *__restrict__ sxq, int n)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
     const int i = sorted[p];
-    sxq[p] = xq[i];
-    styp[p] = typ[i];
+    const float4 q = xq[i];
+    sxq[p] = make_float4(q.x, q.y, q.z, __int_as_float(typ[i]));
 }
 
 __global__ void __launch_bounds__(128)
 k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
-          const float4 *__restrict__ sxq, const int *__restrict__ styp, int n,
-          const PairTab *__restrict__ tab, float *__restrict__ F_lj)
+          const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab,
+          float *__restrict__ F_lj)
 {
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rcmax[NPSIM_MAX_TYPES]; // largest rc^2 of a row type
     for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += blockDim.x)
         s_tab[k] = tab->e[k];
+    __syncthreads();
+    if (threadIdx.x < NPSIM_MAX_TYPES) {
+        float m = 0.0f;
+        for (int b = 0; b < NPSIM_MAX_TYPES; ++b)
+            m = fmaxf(m, s_tab[threadIdx.x * NPSIM_MAX_TYPES + b].z);
+        s_rcmax[threadIdx.x] = m;
+    }
     __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
     const float4 pi = sxq[p];
-    const int row = styp[p] * NPSIM_MAX_TYPES;
+    const int ti = __float_as_int(pi.w);
+    const int row = ti * NPSIM_MAX_TYPES;
+    const float rcmax = s_rcmax[ti];
     const int cx = cell_coord(pi.x, g), cy = cell_coord(pi.y, g), cz = cell_coord(pi.z, g);
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     for (int dz = -1; dz <= 1; ++dz) {
@@ -219,13 +230,16 @@ k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sor
             const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.dim - 1);
             // cells x0..x1 of this row are contiguous in the sorted order
             const int b = start[base + x0], e = start[base + x1 + 1];
+#pragma unroll 2
             for (int q = b; q < e; ++q) {
-                if (q == p)
-                    continue;
                 const float4 pj = sxq[q];
-                const float4 t = s_tab[row + styp[q]];
                 const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
+                // the row type's largest cutoff first (most candidates stop here);
+                // the NP itself has r2 = 0 and is skipped by q != p
+                if (r2 >= rcmax || q == p)
+                    continue;
+                const float4 t = s_tab[row + __float_as_int(pj.w)];
                 if (r2 < t.z) {
                     const float rinv2 = 1.0f / r2;
                     const float s2 = t.x * rinv2;
@@ -238,18 +252,16 @@ k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sor
             }
         }
     }
-    const int i = sorted[p];
-    F_lj[i] = hx; // hi x, y, z then lo x, y, z ([6][n])
-    F_lj[n + i] = hy;
-    F_lj[2 * n + i] = hz;
-    F_lj[3 * n + i] = lx;
-    F_lj[4 * n + i] = ly;
-    F_lj[5 * n + i] = lz;
+    // one 24-byte record per NP: (hi x, y, z, lo x, y, z)
+    float2 *o = reinterpret_cast<float2 *>(F_lj + 6 * (size_t)sorted[p]);
+    o[0] = make_float2(hx, hy);
+    o[1] = make_float2(hz, lx);
+    o[2] = make_float2(ly, lz);
 }
 
 } // namespace
 
-// kernels per build: hash, three scan passes, scatter, sort, gather
+// kernels per build: hash, three scan passes, scatter, order, gather
 int cell_build_launches() { return 7; }
 
 int cell_scan_tiles(int n_cells) { return (n_cells + kScanTile - 1) / kScanTile; }
@@ -266,9 +278,9 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
     k_scan_tiles<<<nt, kScanThreads, 0, st>>>(b.count, b.start, b.tile_sum, g.n_cells);
     k_scan_totals<<<1, kScanThreads, 0, st>>>(b.tile_sum, nt, b.start, g.n_cells);
     k_scan_add<<<nt, kScanThreads, 0, st>>>(b.start, b.tile_sum, g.n_cells);
-    k_cell_scatter<<<(n + B - 1) / B, B, 0, st>>>(b.key, b.rank, b.start, b.sorted, n);
-    k_cell_sort<<<(g.n_cells + B - 1) / B, B, 0, st>>>(b.start, b.sorted, g.n_cells);
-    k_cell_gather<<<(n + B - 1) / B, B, 0, st>>>(b.sorted, xq, typ, b.sxq, b.styp, n);
+    k_cell_scatter<<<(n + B - 1) / B, B, 0, st>>>(b.key, b.rank, b.start, b.arrived, n);
+    k_cell_order<<<(n + B - 1) / B, B, 0, st>>>(b.arrived, b.key, b.start, b.sorted, n);
+    k_cell_gather<<<(n + B - 1) / B, B, 0, st>>>(b.sorted, xq, typ, b.sxq, n);
     return cudaGetLastError();
 }
 
@@ -276,8 +288,7 @@ cudaError_t launch_cell_lj(const CellGrid &g, const CellBufs &b, int n, const Pa
                            float *F_lj, cudaStream_t st)
 {
     const int B = 128;
-    k_cell_lj<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.sxq, b.styp, n, tab,
-                                             F_lj);
+    k_cell_lj<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.sxq, n, tab, F_lj);
     return cudaGetLastError();
 }
 

@@ -616,14 +616,15 @@ enum IntMode : int {
 // State of the integrator: position = xq.xyz (float32, the word the pair kernels
 // read) + x_lo (float32 SoA [3][n]); velocity float32 SoA [3][n]; force as
 // float32 hi/lo SoA [6][n] (hi x, y, z, then lo x, y, z).  Stream-K partial
-// slots and cell-list LJ forces use the same hi/lo layout.
+// slots use the same hi/lo split; the cell-list LJ forces are one 24-byte
+// (hi x, y, z, lo x, y, z) record per NP (written in cell order).
 struct IntArgs {
     float *x_lo, *v, *F;     // see above
     const int *typ;
     float4 *xq;              // (x hi, y hi, z hi, q)
     const float *slots;      // stream-K partials [slot][6][itile] (or NULL)
     StreamK sk;
-    const float *F_lj;       // cell-list LJ forces [6][n] (or NULL)
+    const float *F_lj;       // cell-list LJ forces [n][6] (hi x, y, z, lo x, y, z) (or NULL)
     const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
                              // no Coulomb partial); NULL: row position = i
     float4 *spring;          // spring radius per type (spring_entry), two buffers
@@ -797,9 +798,8 @@ cudaError_t launch_weights_bf16(const float *w, int rows, int cols, void *wb, vo
 
 // Cell list (celllist.cu)
 struct CellBufs {
-    int *key, *rank, *count, *start, *sorted, *tile_sum;
-    float4 *sxq;
-    int *styp;
+    int *key, *rank, *count, *start, *arrived, *sorted, *tile_sum;
+    float4 *sxq; // cell-ordered (x, y, z, type as int bits)
 };
 cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
                               CellBufs &b, int *flags, cudaStream_t st);
