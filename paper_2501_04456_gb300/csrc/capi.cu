@@ -136,6 +136,7 @@ struct npsim_sim {
     // State: position = xq.xyz (hi words) + x_lo; velocity and force in float32,
     // forces as (hi, lo) pairs.  x is float64 scratch for uploads and statistics.
     double *x = nullptr;                  // [3][n]
+    double *stage = nullptr;              // host-facing AoS copies [x | v | F], 9 n (lazy)
     float *x_lo = nullptr, *v = nullptr;  // [3][n]
     float *F = nullptr, *F_tmp = nullptr; // [6][n]
     float4 *xq = nullptr;
@@ -197,6 +198,7 @@ struct npsim_sim {
                     if (ev[j][k][e])
                         cudaEventDestroy(ev[j][k][e]);
         dfree(x);
+        dfree(stage);
         dfree(x_lo);
         dfree(v);
         dfree(F);
@@ -669,32 +671,23 @@ void to_soa(const double *aos, int n, std::vector<double> &soa)
             soa[(size_t)d * n + i] = aos[3 * (size_t)i + d];
 }
 
-void to_aos(const std::vector<double> &soa, int n, double *aos)
+// Device-side AoS float64 copies of the requested parts of the state (any
+// pointer NULL), then one copy each to the host arrays, on the sim's stream.
+int copy_state_out(npsim_sim *s, const float *F_src, double *x, double *v, double *F)
 {
-    for (int i = 0; i < n; ++i)
-        for (int d = 0; d < 3; ++d)
-            aos[3 * (size_t)i + d] = soa[(size_t)d * n + i];
-}
-
-// Device float32 array -> host float64 vector (count values).
-int fetch_f32(const float *d, size_t count, std::vector<double> &out)
-{
-    std::vector<float> h(count);
-    NP_CUDA(cudaMemcpy(h.data(), d, sizeof(float) * count, cudaMemcpyDeviceToHost));
-    out.assign(h.begin(), h.end());
-    return NPSIM_OK;
-}
-
-// Forces [6][n] as (hi, lo) float pairs -> float64 SoA [3][n].
-int fetch_hilo(const float *d, int n, std::vector<double> &soa)
-{
-    std::vector<double> h;
-    int rc = fetch_f32(d, 6 * (size_t)n, h);
-    if (rc)
-        return rc;
-    soa.resize(3 * (size_t)n);
-    for (size_t k = 0; k < 3 * (size_t)n; ++k)
-        soa[k] = h[k] + h[3 * (size_t)n + k];
+    const size_t n3 = 3 * (size_t)s->n;
+    if (!s->stage)
+        NP_CUDA(dalloc(&s->stage, 3 * n3));
+    double *dx = x ? s->stage : nullptr, *dv = v ? s->stage + n3 : nullptr,
+           *dF = F ? s->stage + 2 * n3 : nullptr;
+    NP_CUDA(launch_state_aos(s->xq, s->x_lo, s->v, F_src, s->n, dx, dv, dF, s->user));
+    if (x)
+        NP_CUDA(cudaMemcpyAsync(x, dx, sizeof(double) * n3, cudaMemcpyDeviceToHost, s->user));
+    if (v)
+        NP_CUDA(cudaMemcpyAsync(v, dv, sizeof(double) * n3, cudaMemcpyDeviceToHost, s->user));
+    if (F)
+        NP_CUDA(cudaMemcpyAsync(F, dF, sizeof(double) * n3, cudaMemcpyDeviceToHost, s->user));
+    NP_CUDA(cudaStreamSynchronize(s->user));
     return NPSIM_OK;
 }
 
@@ -1085,25 +1078,10 @@ int npsim_step(npsim_sim_t s, int64_t n_steps)
 int npsim_get_state(npsim_sim_t s, double *x, double *v, double *F, int64_t *step)
 {
     NP_REQUIRE(s, "sim is NULL");
-    NP_CUDA(cudaStreamSynchronize(s->user));
-    std::vector<double> buf(3 * (size_t)s->n);
-    int rc = NPSIM_OK;
-    if (x) {
-        if ((rc = positions_f64(s)))
+    if (x || v || F) {
+        int rc = copy_state_out(s, s->F, x, v, F);
+        if (rc)
             return rc;
-        NP_CUDA(cudaMemcpy(buf.data(), s->x, sizeof(double) * buf.size(),
-                           cudaMemcpyDeviceToHost));
-        to_aos(buf, s->n, x);
-    }
-    if (v) {
-        if ((rc = fetch_f32(s->v, buf.size(), buf)))
-            return rc;
-        to_aos(buf, s->n, v);
-    }
-    if (F) {
-        if ((rc = fetch_hilo(s->F, s->n, buf)))
-            return rc;
-        to_aos(buf, s->n, F);
     }
     if (step)
         *step = s->step;
@@ -1126,12 +1104,7 @@ int npsim_forces(npsim_sim_t s, int what, double *F)
     int rc = enqueue_pass(s, MODE_FORCES, lj, coul, what == 0, s->F_tmp, s->user);
     if (rc)
         return rc;
-    NP_CUDA(cudaStreamSynchronize(s->user));
-    std::vector<double> buf;
-    if ((rc = fetch_hilo(s->F_tmp, s->n, buf)))
-        return rc;
-    to_aos(buf, s->n, F);
-    return NPSIM_OK;
+    return copy_state_out(s, s->F_tmp, nullptr, nullptr, F);
 }
 
 int npsim_positions_device(npsim_sim_t s, float *dev_xyzq)

@@ -151,7 +151,42 @@ __global__ void k_positions_f64(const float4 *__restrict__ xq, const float *__re
     x[2 * n + i] = (double)h.z + (double)x_lo[2 * n + i];
 }
 
+// Host-facing copy of the state: AoS float64 n x 3 of the position (hi + lo),
+// the velocity and the force (hi + lo); any output may be NULL.
+__global__ void k_state_aos(const float4 *__restrict__ xq, const float *__restrict__ x_lo,
+                            const float *__restrict__ v, const float *__restrict__ F, int n,
+                            double *__restrict__ xo, double *__restrict__ vo,
+                            double *__restrict__ Fo)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    if (xo) {
+        const float4 h = xq[i];
+        xo[3 * (size_t)i + 0] = (double)h.x + (double)x_lo[i];
+        xo[3 * (size_t)i + 1] = (double)h.y + (double)x_lo[n + i];
+        xo[3 * (size_t)i + 2] = (double)h.z + (double)x_lo[2 * n + i];
+    }
+    if (vo) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            vo[3 * (size_t)i + d] = (double)v[d * n + i];
+    }
+    if (Fo) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            Fo[3 * (size_t)i + d] = (double)F[d * n + i] + (double)F[(3 + d) * n + i];
+    }
+}
+
 } // namespace
+
+cudaError_t launch_state_aos(const float4 *xq, const float *x_lo, const float *v, const float *F,
+                             int n, double *xo, double *vo, double *Fo, cudaStream_t st)
+{
+    k_state_aos<<<(n + 255) / 256, 256, 0, st>>>(xq, x_lo, v, F, n, xo, vo, Fo);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mirror(const double *x, const int *typ, const float *charge_by_type,
                           int n, float4 *xq, float *x_lo, cudaStream_t st)

@@ -827,6 +827,10 @@ cudaError_t launch_mirror(const double *x, const int *typ, const float *charge_b
                           int n, float4 *xq, float *x_lo, cudaStream_t st);
 cudaError_t launch_positions_f64(const float4 *xq, const float *x_lo, int n, double *x,
                                  cudaStream_t st);
+// The state as host-facing AoS float64 (n x 3 each; NULL outputs are skipped):
+// position hi + lo, velocity, force hi + lo (F: [6][n] hi/lo SoA).
+cudaError_t launch_state_aos(const float4 *xq, const float *x_lo, const float *v, const float *F,
+                             int n, double *xo, double *vo, double *Fo, cudaStream_t st);
 
 // Test hooks (capi.cu)
 cudaError_t launch_philox(uint64_t seed, const uint32_t ctr[4], long long n_blocks,

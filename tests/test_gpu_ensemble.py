@@ -69,3 +69,28 @@ def test_ensemble_trajectories_match_oracle_and_single_runs(P, drops):
         # run), which 60 steps amplify to a few 1e-8; a wrong key or counter
         # would differ by the noise amplitude itself (~1e-2)
         assert np.abs(xe - xs).max() <= 1e-6, d
+
+
+def test_ensemble_large_droplets_sampled(P):
+    """Droplets large enough that most (warp, segment) pairs are beyond the LJ
+    cutoff (culled to the Coulomb-only sweep): sampled rows of every droplet
+    against the oracle."""
+    scs = wl.ensemble_config(n_droplets=3, master_seed=11, n_min=9000, n_max=16000)
+    drops = []
+    for sc in scs:
+        types, x, v = wl.initial_state(sc, fp32_positions=True)
+        drops.append((sc, x, v, types))
+    rng = np.random.default_rng(2)
+    with P.Ensemble(drops) as ens:
+        for d, (sc, x, v, types) in enumerate(drops):
+            F = ens.forces(d)
+            sel = np.unique(rng.choice(sc.n, 100, replace=False))
+            ref = oracle.pair_forces(x, types, [t.sigma for t in sc.types],
+                                     [t.eps for t in sc.types], [t.charge for t in sc.types],
+                                     sc.bjerrum, lj_cut=sc.lj_cut, lj=sc.lj_mode != 0,
+                                     coulomb=sc.coulomb, eps_override=sc.eps_override, sel=sel)
+            ref = ref + oracle.external_forces(sc, x[sel], types[sel], 0.0)
+            keep = ~cutoff_ambiguous(x, types, sc)[sel]
+            rms = np.sqrt((F ** 2).sum(1).mean())
+            err = np.linalg.norm(F[sel] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
+            assert err[keep].max() <= FORCE_TOL, (d, sc.n, float(err.max()))

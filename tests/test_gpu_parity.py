@@ -191,6 +191,41 @@ def test_forces_full_size_sampled(P):
     assert np.abs(Fp.sum(0)).max() <= 1e-6 * np.abs(Fp).sum()
 
 
+@pytest.mark.parametrize("coul", [True, False])
+def test_lj_in_allpairs_large_droplet_sampled(P, monkeypatch, coul):
+    """LJ inside the all-pairs sum on a droplet large enough that most (warp,
+    64-partner segment) pairs lie beyond the LJ cutoff: those take the culled
+    Coulomb-only sweep (charged types) or are skipped (no charges).  Sampled
+    rows against the oracle row by row, for a type-grouped shape forced and for
+    the autotuned one."""
+    sc = with_(small(wl.config2(), 24000), coulomb=coul)
+    types, x, v = wl.initial_state(sc, fp32_positions=True)
+    rng = np.random.default_rng(5)
+    sel = np.unique(np.concatenate([[0, sc.n - 1], rng.choice(sc.n, 150, replace=False)]))
+    ref = _oracle_pair(sc, x, types, sel=sel)
+    keep = ~cutoff_ambiguous(x, types, sc)[sel]
+    n_cfg = P.npsim_allpairs_num_configs()
+    ljg = None
+    for idx in range(n_cfg - 1, -1, -1):  # the type-grouped shapes close the table
+        monkeypatch.setenv("NPSIM_AUTOTUNE", f"1:{idx}")
+        with P.Sim(sc, x, v, types) as sim:
+            if sim.allpairs_config()["packed"] != 3:
+                break
+            ljg = idx
+    assert ljg is not None
+    for forced in (f"1:{ljg}", None):
+        if forced:
+            monkeypatch.setenv("NPSIM_AUTOTUNE", forced)
+        else:
+            monkeypatch.delenv("NPSIM_AUTOTUNE", raising=False)
+        with P.Sim(sc, x, v, types) as sim:
+            F = sim.forces(1)
+        rms = np.sqrt((F ** 2).sum(1).mean())
+        err = np.linalg.norm(F[sel] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
+        assert err[keep].max() <= FORCE_TOL, (forced, float(err.max()))
+        assert np.abs(F.sum(0)).max() <= 1e-6 * np.abs(F).sum()
+
+
 # --------------------------------------------------------------------------
 # Trajectories
 
