@@ -382,7 +382,11 @@ def _surrogate_measure(P, batch=4096, n_nets=4, reps=7):
     tcgen05 kernels) at batch 4096 through npsim_surr_predict: host inputs in,
     mean and spread out (host copies included)."""
     import numpy as np
-    X = np.random.default_rng(0).standard_normal((batch, 8)).astype(np.float32)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((batch, 8)).astype(np.float32)
+    n_train, epochs, tb = 2048, 3, 256
+    Xt = rng.standard_normal((n_train, 8)).astype(np.float32)
+    Yt = rng.standard_normal((n_train, 65)).astype(np.float32)
     with P.Surrogate(8, 256, 4, 65, n_nets=n_nets, seed=0) as s:
         s.predict(X)
         ts = []
@@ -390,12 +394,19 @@ def _surrogate_measure(P, batch=4096, n_nets=4, reps=7):
             t0 = time.perf_counter()
             s.predict(X)
             ts.append(time.perf_counter() - t0)
+        s.train(Xt, Yt, epochs=1, batch=tb)  # warm-up
+        t0 = time.perf_counter()
+        s.train(Xt, Yt, epochs=epochs, batch=tb)
+        t_train = time.perf_counter() - t0
     ms = 1e3 * statistics.median(ts)
     flops = 2.0 * batch * (16 * 256 + 3 * 256 * 256 + 256 * 80) * n_nets
     return {"batch": batch, "nets": n_nets, "ms_per_batch": ms,
             "predictions_per_s": batch / (ms * 1e-3),
             "tflops_with_host_copies": flops / (ms * 1e-3) / 1e12,
-            "note": "weights untrained: inference cost does not depend on them"}
+            "training": {"samples": n_train, "epochs": epochs, "minibatch": tb,
+                         "s": t_train,
+                         "network_samples_per_s": n_train * epochs * n_nets / t_train},
+            "note": "random weights and data: the cost does not depend on them"}
 
 
 def run_ours(a):
