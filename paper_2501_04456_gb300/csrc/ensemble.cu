@@ -168,7 +168,7 @@ struct EEntry {
 // j-tiles of at most 256 partners: the droplets' type groups are padded to 256
 const EEntry kEns[] = {
     NPSIM_ENS(128, 2, 256), NPSIM_ENS(256, 1, 256), NPSIM_ENS(256, 2, 256),
-    NPSIM_ENS(128, 4, 256), NPSIM_ENS(128, 2, 128), NPSIM_ENS(512, 1, 256),
+    NPSIM_ENS(1024, 1, 256), NPSIM_ENS(256, 1, 128), NPSIM_ENS(512, 1, 256),
 };
 
 template <int B, int K, int J>
@@ -201,8 +201,8 @@ cudaError_t launch_ens_allpairs(int idx, const StreamK &sk, const EnsAllpairsArg
     case 0: return launch_e<128, 2, 256>(sk, a, st);
     case 1: return launch_e<256, 1, 256>(sk, a, st);
     case 2: return launch_e<256, 2, 256>(sk, a, st);
-    case 3: return launch_e<128, 4, 256>(sk, a, st);
-    case 4: return launch_e<128, 2, 128>(sk, a, st);
+    case 3: return launch_e<1024, 1, 256>(sk, a, st);
+    case 4: return launch_e<256, 1, 128>(sk, a, st);
     case 5: return launch_e<512, 1, 256>(sk, a, st);
     default: return cudaErrorInvalidValue;
     }
