@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-surrogate", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-hbm", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-cfg2", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--case", default="step",
                     choices=["step", "integrator", "surrogate", "hbm", "dense"],
                     help=argparse.SUPPRESS)
@@ -377,6 +378,35 @@ def _cell_list_roofline(P, stream, n=1 << 22, chunks=4):
             "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak}
 
 
+def _config2_measure(P, torch, stream, flush, steps, warmup):
+    """The 16384-NP two-type droplet with LJ (2.5 sigma_ab) inside the all-pairs
+    sum: step time over single steps after an L2 flush, CUDA events on the
+    stream, the autotuned all-pairs shape and its share of the step."""
+    import workloads as wl
+    sc = wl.config2()
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types, stream=stream) as sim:
+        sim.profile(True)
+        for _ in range(warmup):
+            flush.zero_()
+            sim.step(1)
+        ts, ap = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            ap.append(sim.kernel_times()[0]["allpairs"])
+        cfg = sim.allpairs_config()
+    ms = sum(ts) / len(ts)
+    return {"workload": sc.name, "n": sc.n, "ms_per_step": ms,
+            "pair_interactions_per_s": sc.n * (sc.n - 1) / (ms * 1e-3),
+            "allpairs_ms": sum(ap) / len(ap), "allpairs_launch": cfg}
+
+
 def _surrogate_measure(P, batch=4096, n_nets=4, reps=7):
     """Inference of the surrogate (deep ensemble of 4 MLPs 8 -> 4 x 256 -> 65, BF16
     tcgen05 kernels) at batch 4096 through npsim_surr_predict: host inputs in,
@@ -520,6 +550,10 @@ def run_ours(a):
         ens = _ensemble_measure(P, torch, stream, max(3, a.steps // 2), a.warmup)
 
     surr = None
+    cfg2 = None
+    if rank == 0 and not a.no_cfg2:
+        cfg2 = _config2_measure(P, torch, stream, flush, a.steps, a.warmup)
+
     hbm = {}
     if not a.no_hbm and rank == 0:
         hbm["integrator"] = _integrator_roofline(P, stream)
@@ -590,6 +624,7 @@ def run_ours(a):
                          "frac_at_sampled_clock": (achieved / (peak_tflops * clk["sm_mhz"] /
                                                                max_mhz)) if clk else None},
             "skip_neutral": skip,
+            "config2": cfg2,
             "ensemble": ens,
             "surrogate": surr,
             **hbm,
