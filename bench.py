@@ -93,6 +93,24 @@ def _oracle_sample(sc, x, types, seconds, max_rows=None):
         rows = min(sc.n, int(rows * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
 
 
+def reduce_max_over_ranks(value, world, device):
+    """Largest value over the ranks (replicas run independently; the slowest one
+    sets the job's time).  One rank: the value itself."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rates(world, n, step_ms):
+    """Whole-job rates of `world` replicas of an n-NP droplet at step_ms each:
+    (pair-interactions/s, particle-steps/s)."""
+    return world * n * (n - 1) / (step_ms * 1e-3), world * n / (step_ms * 1e-3)
+
+
 def _omp_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
@@ -499,17 +517,13 @@ def run_ours(a):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    step_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = reduce_max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps,
+                                    world, dev)
     launches = a.steps * (1 + sim.launches_per_step())
     sim.close()
 
     pairs_per_step = n * (n - 1)
-    value = world * pairs_per_step / (step_ms * 1e-3)
-    psteps = world * n / (step_ms * 1e-3)
+    value, psteps = replica_rates(world, n, step_ms)
 
     # roofline of the dominant kernel (all-pairs, FP32 CUDA-core ALU)
     peaks = _peaks()
