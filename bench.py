@@ -313,13 +313,17 @@ def _ensemble_measure(P, torch, stream, steps, warmup, n_plain=16, steps_per_dro
 # same and writes the force as (hi, lo) pairs (24) and the velocity (12).
 INT_BYTES_BA = 16 + 12 + 12 + 4 + 16 + 12 + 12
 INT_BYTES_B = 16 + 12 + 12 + 4 + 24 + 12
-# Cell list per NP: hash (read 16, write key + rank 8), scatter (key, rank,
-# start, arrival slot: 16), in-cell order (arrival slot, key, cell range,
-# sorted: 20), gather (sorted 4, position 16, type 4, record written 16), LJ
-# (own record 16, sorted index 4, force record 24); per cell: count reset and
-# the three scan passes (20).
-CELL_BYTES_NP = 24 + 16 + 20 + 40 + 44
-CELL_BYTES_CELL = 20
+# Cell list.  Per rebuild and NP: zero/hash (read 16, write key + rank 8),
+# scatter (key, rank, start, arrival slot: 16), in-cell order (arrival slot, key,
+# cell range, sorted: 20), gather (sorted 4, position 16, type 4, record written
+# 16), list build (own record 16, sorted index 4, count 4, build position 16,
+# 4 per list entry); per rebuild and cell: count reset and three scan passes
+# (20).  Per step and NP, the list LJ forces: sorted index 4, current position
+# 16, type record 16, count 4, 4 per list entry, force record 24 (partner
+# positions are re-reads of records already counted).
+CELL_BUILD_BYTES_NP = 24 + 16 + 20 + 40 + 40
+CELL_BUILD_BYTES_CELL = 20
+LIST_LJ_BYTES_NP = 4 + 16 + 16 + 4 + 24
 
 
 def _hbm_peak():
@@ -365,10 +369,11 @@ def _integrator_roofline(P, stream, n=1 << 23, chunks=4):
 
 
 def _cell_list_roofline(P, stream, n=1 << 22, chunks=4):
-    """Cell build + LJ over 27 cells on an LJ-only droplet of n NPs of the
-    paper-scale composition at the paper-scale initial number density (jittered
-    cubic lattice inside R0 - 2, types shuffled), so that the list (~0.5 GB with
-    the cell arrays) exceeds L2."""
+    """The cell-list LJ path (the gated cell and neighbour-list builds, the list
+    LJ forces) on an LJ-only droplet of n NPs of the paper-scale composition at
+    the paper-scale initial number density (jittered cubic lattice inside R0 - 2,
+    types shuffled), a state well beyond L2.  Bytes per step: the list forces
+    every step plus the builds at the rate they ran."""
     import dataclasses
     import numpy as np
     import workloads as wl
@@ -386,14 +391,21 @@ def _cell_list_roofline(P, stream, n=1 << 22, chunks=4):
         sim.profile(True)
         dim, cells = sim.cell_grid()
         sim.step(2 * sim.chunk_steps())
+        _, _, b0 = sim.nbr_info()
+        k = sim.chunk_steps()
         ms, _ = _kernel_chunks(sim, ("cell_build", "cell_lj"), chunks)
         kt, _ = sim.kernel_times()
-    byts = CELL_BYTES_NP * n + CELL_BYTES_CELL * cells
+        cap, mean_len, b1 = sim.nbr_info()
+    steps = chunks * k
+    per_build = (CELL_BUILD_BYTES_NP + 4 * mean_len) * n + CELL_BUILD_BYTES_CELL * cells
+    byts = (LIST_LJ_BYTES_NP + 4 * mean_len) * n + per_build * (b1 - b0) / steps
     gbs = byts / (ms * 1e-3) / 1e9
     peak = _hbm_peak()
-    return {"n": n, "cells": cells, "lattice_spacing": a, "bytes_per_step": byts,
-            "ms_per_step": ms, "ms_build": kt["cell_build"], "ms_lj": kt["cell_lj"],
-            "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak}
+    return {"n": n, "cells": cells, "lattice_spacing": a, "mean_list_length": mean_len,
+            "list_capacity": cap, "rebuilds_per_step": (b1 - b0) / steps,
+            "bytes_per_step": byts, "ms_per_step": ms, "ms_build": kt["cell_build"],
+            "ms_lj": kt["cell_lj"], "bound": "hbm", "achieved": gbs, "peak": peak,
+            "unit": "GB/s", "frac": gbs / peak}
 
 
 def _config2_measure(P, torch, stream, flush, steps, warmup):

@@ -348,6 +348,12 @@ int npsim_launches_per_step(npsim_sim_t sim, int *launches);
  * >= the largest cutoff. */
 int npsim_cell_grid(npsim_sim_t sim, int *dim, int64_t *n_cells);
 
+/* Verlet neighbour lists of the cell-list LJ (lj_mode 2): the list capacity per
+ * NP, the mean list length at the last build, and the number of builds run so
+ * far (a build runs when an NP has moved more than half the skin since the
+ * previous one).  All 0 without a cell list. */
+int npsim_nbr_info(npsim_sim_t sim, int *cap, double *mean_len, int64_t *builds);
+
 /* Steps per captured CUDA graph (npsim_step replays ceil(n / chunk) graphs). */
 int npsim_chunk_steps(npsim_sim_t sim, int *chunk);
 

@@ -111,6 +111,7 @@ def lib():
                                                        C.c_void_p, C.c_void_p]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
             L.npsim_cell_grid.argtypes = [_h, _i32, _i64]
+            L.npsim_nbr_info.argtypes = [_h, _i32, _d, _i64]
             L.npsim_ens_create.argtypes = [C.POINTER(npsim_droplet_t), C.c_int32, C.c_void_p,
                                            C.POINTER(_h)]
             L.npsim_ens_step.argtypes = [_h, C.c_int64]
@@ -346,6 +347,14 @@ def npsim_cell_grid(h):
     return d.value, c.value
 
 
+def npsim_nbr_info(h):
+    """(list capacity, mean list length at the last build, builds so far) of the
+    cell-list LJ neighbour lists; zeros without a cell list."""
+    c, m, b = C.c_int32(), C.c_double(), C.c_int64()
+    _check(lib().npsim_nbr_info(h, C.byref(c), C.byref(m), C.byref(b)))
+    return c.value, m.value, b.value
+
+
 def npsim_chunk_steps(h):
     a = C.c_int32()
     _check(lib().npsim_chunk_steps(h, C.byref(a)))
@@ -411,6 +420,9 @@ class Sim:
 
     def cell_grid(self):
         return npsim_cell_grid(self.h)
+
+    def nbr_info(self):
+        return npsim_nbr_info(self.h)
 
     def profile(self, enable=True):
         npsim_profile(self.h, enable)

@@ -100,6 +100,12 @@ void fill_streamk(StreamK &sk, int n, const ApConfig &c, int grid_target)
 
 // Floats of stream-K partial slots: one slot per (i-tile row, CTA) pair a row
 // can meet, each (hi x, y, z, lo x, y, z) x itile.
+// Verlet skin of the LJ neighbour lists (sigma units of the smallest type = 1),
+// and the squared displacement (half the skin, less 1 % for rounding) that
+// triggers a rebuild.
+constexpr float kSkin = 0.3f;
+constexpr float kHalfSkin2 = (0.5f * kSkin * 0.99f) * (0.5f * kSkin * 0.99f);
+
 size_t slots_floats(const StreamK &sk)
 {
     return (size_t)(sk.n_it + sk.grid) * 6 * (size_t)sk.itile;
@@ -154,6 +160,8 @@ struct npsim_sim {
     CellGrid grid{};
     CellBufs cb{};
     bool cell = false;
+    NbrList nl{};          // Verlet list over the cells (cell-list LJ)
+    int *d_gate = nullptr; // 1: rebuild the cell and neighbour lists at the next pass
 
     bool ap = false, ap_lj = false;
     int ap_idx = 0;
@@ -218,6 +226,11 @@ struct npsim_sim {
         dfree(d_spring);
         dfree(d_flags);
         dfree(d_done);
+        dfree(d_gate);
+        dfree(nl.nbr);
+        dfree(nl.nnbr);
+        dfree(nl.x_ref);
+        dfree(nl.builds);
         CellBufs *bufs[2] = {&cb, &scb};
         for (CellBufs *b : bufs) {
             dfree(b->key);
@@ -367,11 +380,16 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
                     : cudaSuccess;
     };
     if (lj_cell) {
+        // the build kernels run (past their gate check) only after an NP has
+        // moved more than half the skin since the last build
         NP_CUDA(mark(KG_CELL_BUILD, 0));
-        NP_CUDA(launch_cell_build(s->grid, s->xq, s->typ, s->n, s->cb, s->d_flags, st));
+        NP_CUDA(launch_cell_build(s->grid, s->xq, s->typ, s->n, s->cb, s->d_gate, st));
+        NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, kSkin, s->nl, s->d_flags,
+                                 s->d_gate, st));
         NP_CUDA(mark(KG_CELL_BUILD, 1));
         NP_CUDA(mark(KG_CELL_LJ, 0));
-        NP_CUDA(launch_cell_lj(s->grid, s->cb, s->n, s->tab_full, s->F_lj, st));
+        NP_CUDA(launch_lj_nbr(s->grid, s->cb, s->xq, s->n, s->tab_full, s->nl, s->F_lj,
+                              s->d_gate, st));
         NP_CUDA(mark(KG_CELL_LJ, 1));
     }
     if (ap) {
@@ -392,6 +410,9 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     a.field_slots = (ap && !ap_lj && !ljg) ? 1 : 0; // ljg sums C q_a q_b from its table
     a.row_pos = grouped ? s->row_pos : nullptr;
     a.spring = s->d_spring;
+    a.x_ref = s->cell ? s->nl.x_ref : nullptr;
+    a.nbr_gate = s->d_gate;
+    a.half_skin2 = kHalfSkin2;
     a.step = s->d_step;
     a.flags = s->d_flags;
     a.done = s->d_done;
@@ -411,6 +432,9 @@ int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
     a.xq = s->xq;
     a.sk = s->sk;
     a.spring = s->d_spring;
+    a.x_ref = s->cell ? s->nl.x_ref : nullptr;
+    a.nbr_gate = s->d_gate;
+    a.half_skin2 = kHalfSkin2;
     a.step = s->d_step;
     a.flags = s->d_flags;
     a.done = s->d_done;
@@ -451,11 +475,54 @@ int get_graph(npsim_sim *s, int k, cudaGraphExec_t *out)
     return NPSIM_OK;
 }
 
+int set_gate(npsim_sim *s, int v)
+{
+    if (s->d_gate) {
+        NP_CUDA(cudaMemcpyAsync(s->d_gate, &v, sizeof(int), cudaMemcpyHostToDevice, s->user));
+        NP_CUDA(cudaStreamSynchronize(s->user)); // v lives on this stack frame
+    }
+    return NPSIM_OK;
+}
+
+// A neighbour list overflowed (those NPs were summed from the cells, so the
+// forces were exact): grow the list to 1.25 x the longest count plus 8, drop
+// the graphs (they hold the old buffer) and rebuild at the next pass.
+int grow_neighbour_list(npsim_sim *s)
+{
+    std::vector<int> cnt((size_t)s->n);
+    NP_CUDA(cudaMemcpy(cnt.data(), s->nl.nnbr, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost));
+    const int mx = *std::max_element(cnt.begin(), cnt.end());
+    if (mx <= s->nl.cap)
+        return NPSIM_OK;
+    const int cap = mx + mx / 4 + 8;
+    unsigned *nb = nullptr;
+    cudaError_t e = dalloc(&nb, (size_t)cap * s->n);
+    if (e != cudaSuccess)
+        return set_err(NPSIM_ERR_OOM, "neighbour list of %d x %d entries: %s", cap, s->n,
+                       cudaGetErrorString(e));
+    dfree(s->nl.nbr);
+    s->nl.nbr = nb;
+    s->nl.cap = cap;
+    for (auto &g : s->graphs)
+        cudaGraphExecDestroy(g.second);
+    s->graphs.clear();
+    return set_gate(s, 1);
+}
+
 int read_flags(npsim_sim *s)
 {
     int h = 0;
     NP_CUDA(cudaMemcpyAsync(&h, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->user));
     NP_CUDA(cudaStreamSynchronize(s->user));
+    if (h & FLAG_NBR_OVERFLOW) {
+        const int rest = h & ~FLAG_NBR_OVERFLOW;
+        NP_CUDA(cudaMemcpyAsync(s->d_flags, &rest, sizeof(int), cudaMemcpyHostToDevice, s->user));
+        NP_CUDA(cudaStreamSynchronize(s->user));
+        int rc = grow_neighbour_list(s);
+        if (rc)
+            return rc;
+        h = rest;
+    }
     if (h) {
         NP_CUDA(cudaMemsetAsync(s->d_flags, 0, sizeof(int), s->user));
         if (h & FLAG_NONFINITE)
@@ -708,8 +775,13 @@ int positions_f64(npsim_sim *s)
 }
 
 // Set the step counter and recompute the forces of the current state.
-int finish_upload(npsim_sim *s, int64_t step)
+int finish_upload(npsim_sim *s, int64_t step, bool rebuild = true)
 {
+    if (rebuild) {
+        int rc = set_gate(s, 1); // new positions: rebuild the lists at the next pass
+        if (rc)
+            return rc;
+    }
     long long st = step;
     NP_CUDA(cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice,
                             s->user));
@@ -995,12 +1067,19 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
         double L = params->R0;
         for (int64_t i = 0; i < 3 * n; ++i)
             L = std::max(L, std::fabs(x0[i]));
-        L += rc_max;
-        s->grid = make_grid(L, rc_max, std::max<long long>(4 * n + 4096, 1 << 16));
+        L += rc_max + kSkin;
+        s->grid = make_grid(L, rc_max + kSkin, std::max<long long>(4 * n + 4096, 1 << 16));
         rc = alloc_cells(s->grid, s->cb, s->n);
         if (rc)
             return bail(rc);
         BAIL_CUDA(dalloc(&s->F_lj, 2 * n3));
+        s->nl.cap = 32; // grown after the first build if some NP has more partners
+        BAIL_CUDA(dalloc(&s->nl.nbr, (size_t)s->nl.cap * n));
+        BAIL_CUDA(dalloc(&s->nl.nnbr, (size_t)n));
+        BAIL_CUDA(dalloc(&s->nl.x_ref, (size_t)n));
+        BAIL_CUDA(dalloc(&s->nl.builds, 1));
+        BAIL_CUDA(cudaMemset(s->nl.builds, 0, sizeof(unsigned long long)));
+        BAIL_CUDA(dalloc(&s->d_gate, 1));
     }
     s->ap_lj = params->lj_mode == 1;
     s->ap = params->coulomb || s->ap_lj;
@@ -1149,7 +1228,8 @@ int npsim_allpairs_num_configs(int *count)
 int npsim_launches_per_step(npsim_sim_t s, int *launches)
 {
     NP_REQUIRE(s && launches, "sim and launches are required");
-    *launches = 1 + (s->ap ? 1 : 0) + (s->cell ? cell_build_launches() + 1 : 0);
+    // integrator, all-pairs, the gated cell and list builds, the list LJ forces
+    *launches = 1 + (s->ap ? 1 : 0) + (s->cell ? cell_build_launches() + 2 : 0);
     return NPSIM_OK;
 }
 
@@ -1160,6 +1240,35 @@ int npsim_cell_grid(npsim_sim_t s, int *dim, int64_t *n_cells)
         *dim = s->cell ? s->grid.dim : 0;
     if (n_cells)
         *n_cells = s->cell ? s->grid.n_cells : 0;
+    return NPSIM_OK;
+}
+
+int npsim_nbr_info(npsim_sim_t s, int *cap, double *mean_len, int64_t *builds)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    if (cap)
+        *cap = s->cell ? s->nl.cap : 0;
+    if (mean_len)
+        *mean_len = 0.0;
+    if (builds)
+        *builds = 0;
+    if (!s->cell)
+        return NPSIM_OK;
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    if (mean_len) {
+        std::vector<int> cnt((size_t)s->n);
+        NP_CUDA(cudaMemcpy(cnt.data(), s->nl.nnbr, sizeof(int) * cnt.size(),
+                           cudaMemcpyDeviceToHost));
+        double sum = 0.0;
+        for (int c : cnt)
+            sum += c;
+        *mean_len = sum / (double)s->n;
+    }
+    if (builds) {
+        unsigned long long b = 0;
+        NP_CUDA(cudaMemcpy(&b, s->nl.builds, sizeof(b), cudaMemcpyDeviceToHost));
+        *builds = (int64_t)b;
+    }
     return NPSIM_OK;
 }
 
@@ -1278,7 +1387,7 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
             NP_CUDA(dalloc(&s->s_hist, cfg->n_bins));
             s->s_hist_cap = cfg->n_bins;
         }
-        NP_CUDA(launch_cell_build(g, s->xq, s->typ, n, s->scb, s->d_flags, st));
+        NP_CUDA(launch_cell_build(g, s->xq, s->typ, n, s->scb, nullptr, st));
         NP_CUDA(launch_pair_hist(s->x, n, cfg->r_max, cfg->n_bins, g, s->scb, s->s_hist, st));
         std::vector<unsigned long long> h(cfg->n_bins);
         NP_CUDA(cudaMemcpyAsync(h.data(), s->s_hist, sizeof(unsigned long long) * h.size(),
@@ -1395,8 +1504,11 @@ namespace {
 // Layout: header, then the raw state words so that a resumed run is
 // bit-identical: position hi words [3][n], lo words [3][n], velocities [3][n]
 // (float32 SoA), the types (int32[n]) and the order of the NPs inside their
-// type groups (int32[n], the pair kernels' summation order).
-const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '3'};
+// type groups (int32[n], the pair kernels' summation order); with a cell list
+// also the neighbour-list state: the cell grid and list capacity (header), the
+// positions of the last build (float4[n]) and the rebuild gate (header), from
+// which a resumed run rebuilds exactly the list the saved run was using.
+const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '4'};
 
 struct CkptHeader {
     char magic[8];
@@ -1407,7 +1519,50 @@ struct CkptHeader {
     double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut;
     double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     npsim_type_t types[NPSIM_MAX_TYPES];
+    int32_t cell, grid_dim, grid_cells, nbr_cap, gate, pad2_;
+    float grid_inv_h, grid_L;
 };
+
+// Put the neighbour-list state of a checkpoint back: the saved grid and list
+// capacity, a build from the saved build positions (which writes the same
+// lists and x_ref), and the saved gate.
+int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
+{
+    if (!s->cell || !h.cell)
+        return NPSIM_OK;
+    if (h.grid_cells != s->grid.n_cells) {
+        CellBufs &b = s->cb;
+        dfree(b.key); dfree(b.rank); dfree(b.count); dfree(b.start);
+        dfree(b.arrived); dfree(b.sorted); dfree(b.sxq); dfree(b.tile_sum);
+        b = CellBufs{};
+    }
+    CellGrid g{};
+    g.dim = h.grid_dim;
+    g.n_cells = h.grid_cells;
+    g.inv_h = h.grid_inv_h;
+    g.L = h.grid_L;
+    if (!s->cb.key) {
+        int rc = alloc_cells(g, s->cb, s->n);
+        if (rc)
+            return rc;
+    }
+    s->grid = g;
+    if (h.nbr_cap != s->nl.cap) {
+        dfree(s->nl.nbr);
+        NP_CUDA(dalloc(&s->nl.nbr, (size_t)h.nbr_cap * s->n));
+        s->nl.cap = h.nbr_cap;
+    }
+    for (auto &e : s->graphs)
+        cudaGraphExecDestroy(e.second);
+    s->graphs.clear();
+    NP_CUDA(cudaMemcpy(s->nl.x_ref, x_ref_host, sizeof(float4) * (size_t)s->n,
+                       cudaMemcpyHostToDevice));
+    NP_CUDA(launch_cell_build(s->grid, s->nl.x_ref, s->typ, s->n, s->cb, nullptr, s->user));
+    NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, kSkin, s->nl, s->d_flags,
+                             nullptr, s->user));
+    NP_CUDA(cudaStreamSynchronize(s->user));
+    return set_gate(s, h.gate);
+}
 } // namespace
 
 int npsim_save(npsim_sim_t s, const char *path)
@@ -1415,7 +1570,7 @@ int npsim_save(npsim_sim_t s, const char *path)
     NP_REQUIRE(s && path, "sim and path are required");
     CkptHeader h{};
     memcpy(h.magic, kMagic, 8);
-    h.version = 3;
+    h.version = 4;
     h.n_types = s->T;
     h.n = s->n;
     h.step = s->step;
@@ -1456,11 +1611,24 @@ int npsim_save(npsim_sim_t s, const char *path)
         return set_err(NPSIM_ERR_IO, "cannot open %s for writing", path);
     std::vector<int32_t> rank(s->h_rank);
     rank.resize(n, 0);
+    std::vector<float4> xref;
+    if (s->cell) {
+        h.cell = 1;
+        h.grid_dim = s->grid.dim;
+        h.grid_cells = s->grid.n_cells;
+        h.grid_inv_h = s->grid.inv_h;
+        h.grid_L = s->grid.L;
+        h.nbr_cap = s->nl.cap;
+        NP_CUDA(cudaMemcpy(&h.gate, s->d_gate, sizeof(int), cudaMemcpyDeviceToHost));
+        xref.resize(n);
+        NP_CUDA(cudaMemcpy(xref.data(), s->nl.x_ref, sizeof(float4) * n, cudaMemcpyDeviceToHost));
+    }
     bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
               fwrite(words.data(), sizeof(float), words.size(), f) == words.size() &&
               fwrite(s->h_type.data(), sizeof(int32_t), s->h_type.size(), f) ==
                   s->h_type.size() &&
-              fwrite(rank.data(), sizeof(int32_t), rank.size(), f) == rank.size();
+              fwrite(rank.data(), sizeof(int32_t), rank.size(), f) == rank.size() &&
+              fwrite(xref.data(), sizeof(float4), xref.size(), f) == xref.size();
     ok = (fclose(f) == 0) && ok;
     if (!ok)
         return set_err(NPSIM_ERR_IO, "short write to %s", path);
@@ -1476,7 +1644,7 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     if (!f)
         return set_err(NPSIM_ERR_IO, "cannot open %s", path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 3 ||
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 4 ||
         h.n < 1 || h.n > (1ll << 29) || h.n_types < 1 || h.n_types > NPSIM_MAX_TYPES) {
         fclose(f);
         return set_err(NPSIM_ERR_IO, "%s is not an npsim checkpoint", path);
@@ -1484,9 +1652,11 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     const size_t n = (size_t)h.n;
     std::vector<float> words(9 * n);
     std::vector<int32_t> ty(n), rank(n);
+    std::vector<float4> xref(h.cell ? n : 0);
     bool ok = fread(words.data(), sizeof(float), words.size(), f) == words.size() &&
               fread(ty.data(), sizeof(int32_t), ty.size(), f) == ty.size() &&
-              fread(rank.data(), sizeof(int32_t), rank.size(), f) == rank.size();
+              fread(rank.data(), sizeof(int32_t), rank.size(), f) == rank.size() &&
+              fread(xref.data(), sizeof(float4), xref.size(), f) == xref.size();
     fclose(f);
     if (!ok)
         return set_err(NPSIM_ERR_IO, "%s is truncated", path);
@@ -1525,6 +1695,11 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     if (rc)
         return rc;
     rc = upload_words(s, words.data(), h.step);
+    if (!rc && h.cell) { // the saved list state, then the forces from it
+        rc = restore_lists(s, h, xref.data());
+        if (!rc)
+            rc = finish_upload(s, h.step, false);
+    }
     if (rc) {
         npsim_destroy(s);
         return rc;

@@ -11,7 +11,16 @@
 // cell -- and therefore the float summation order of the LJ kernel -- does not
 // depend on the atomic arrival order (runs are bit-reproducible).  A gather
 // writes the NP records (position, type in the fourth word) in cell order so
-// the LJ kernel reads neighbours from contiguous memory.  The
+// the LJ kernel reads neighbours from contiguous memory.
+//
+// The simulation keeps a Verlet neighbour list on top of the cells: the cell
+// edge is the largest cutoff plus a skin, a build lists for every NP the
+// partners within its pair cutoff plus the skin and records the positions it
+// saw; the integrator raises a gate when some NP has moved more than half the
+// skin since then, and only then do the (gated) build kernels run again.  A
+// pair within its cutoff now was within cutoff + skin at the build, so the
+// list (or, for an NP whose list overflowed, the cells of the build) holds
+// every pair that can interact: the forces are those of a rebuild every step.  The
 // cell edge is at least the largest cutoff (times 1 + 1e-5, so float rounding
 // of the cell index can never separate two NPs within the cutoff by more than
 // one cell); coordinates beyond the grid are clamped into the edge cells,
@@ -28,18 +37,30 @@ __device__ __forceinline__ int cell_coord(float x, const CellGrid &g)
     return min(max(c, 0), g.dim - 1);
 }
 
+// Build kernels return at once when a gate is given and reads 0 (no rebuild).
+__device__ __forceinline__ bool gate_closed(const int *gate) { return gate && *gate == 0; }
+
+__global__ void k_cell_zero(int *__restrict__ count, int m, const int *__restrict__ gate)
+{
+    if (gate_closed(gate))
+        return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x)
+        count[c] = 0;
+}
+
 __global__ void k_cell_hash(CellGrid g, const float4 *__restrict__ xq, int n,
                             int *__restrict__ key, int *__restrict__ rank,
-                            int *__restrict__ count)
+                            int *__restrict__ count, const int *__restrict__ gate)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
+    if (gate_closed(gate))
         return;
-    const float4 p = xq[i];
-    const int c = (cell_coord(p.z, g) * g.dim + cell_coord(p.y, g)) * g.dim +
-                  cell_coord(p.x, g);
-    key[i] = c;
-    rank[i] = atomicAdd(&count[c], 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = xq[i];
+        const int c = (cell_coord(p.z, g) * g.dim + cell_coord(p.y, g)) * g.dim +
+                      cell_coord(p.x, g);
+        key[i] = c;
+        rank[i] = atomicAdd(&count[c], 1);
+    }
 }
 
 // Exclusive scan of count[0..m) into start[0..m], start[m] = total, in three
@@ -87,34 +108,42 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *s_warp, int *total
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_tiles(const int *__restrict__ count, int *__restrict__ start, int *__restrict__ tile_sum,
-             int m)
+             int m, const int *__restrict__ gate)
 {
     __shared__ int s_warp[kScanThreads / 32 + 1];
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-    int a[kScanItems];
-    int s = 0;
+    if (gate_closed(gate)) // uniform over the block
+        return;
+    const int n_tiles = (m + kScanTile - 1) / kScanTile;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int base = t * kScanTile + threadIdx.x * kScanItems;
+        int a[kScanItems];
+        int s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        a[k] = base + k < m ? count[base + k] : 0;
-        s += a[k];
-    }
-    int total;
-    int run = cta_exclusive_scan(s, s_warp, &total);
+        for (int k = 0; k < kScanItems; ++k) {
+            a[k] = base + k < m ? count[base + k] : 0;
+            s += a[k];
+        }
+        int total;
+        int run = cta_exclusive_scan(s, s_warp, &total);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < m)
-            start[base + k] = run;
-        run += a[k];
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < m)
+                start[base + k] = run;
+            run += a[k];
+        }
+        if (threadIdx.x == 0)
+            tile_sum[t] = total;
     }
-    if (threadIdx.x == 0)
-        tile_sum[blockIdx.x] = total;
 }
 
 // One CTA: exclusive scan of the tile totals in place; start[m] = grand total.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_totals(int *__restrict__ tile_sum, int n_tiles, int *__restrict__ start, int m)
+k_scan_totals(int *__restrict__ tile_sum, int n_tiles, int *__restrict__ start, int m,
+              const int *__restrict__ gate)
 {
     __shared__ int s_warp[kScanThreads / 32 + 1];
+    if (gate_closed(gate))
+        return;
     int carry = 0;
     for (int b0 = 0; b0 < n_tiles; b0 += kScanTile) {
         const int base = b0 + threadIdx.x * kScanItems;
@@ -140,120 +169,217 @@ k_scan_totals(int *__restrict__ tile_sum, int n_tiles, int *__restrict__ start, 
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_add(int *__restrict__ start, const int *__restrict__ tile_sum, int m)
+k_scan_add(int *__restrict__ start, const int *__restrict__ tile_sum, int m,
+           const int *__restrict__ gate)
 {
-    const int off = tile_sum[blockIdx.x];
-    const int base = blockIdx.x * kScanTile + threadIdx.x;
+    if (gate_closed(gate))
+        return;
+    const int n_tiles = (m + kScanTile - 1) / kScanTile;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int off = tile_sum[t];
+        const int base = t * kScanTile + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int i = base + k * kScanThreads;
-        if (i < m)
-            start[i] += off;
+        for (int k = 0; k < kScanItems; ++k) {
+            const int i = base + k * kScanThreads;
+            if (i < m)
+                start[i] += off;
+        }
     }
 }
 
 __global__ void k_cell_scatter(const int *__restrict__ key, const int *__restrict__ rank,
                                const int *__restrict__ start, int *__restrict__ arrived,
-                               int n)
+                               int n, const int *__restrict__ gate)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
+    if (gate_closed(gate))
         return;
-    arrived[start[key[i]] + rank[i]] = i;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        arrived[start[key[i]] + rank[i]] = i;
 }
 
 // Members of every cell in index order: the NP at arrival slot q goes to its
 // cell's start plus the number of members with a smaller index (O(m) per NP for
 // a cell of m members, all NPs in parallel).
 __global__ void k_cell_order(const int *__restrict__ arrived, const int *__restrict__ key,
-                             const int *__restrict__ start, int *__restrict__ sorted, int n)
+                             const int *__restrict__ start, int *__restrict__ sorted, int n,
+                             const int *__restrict__ gate)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n)
+    if (gate_closed(gate))
         return;
-    const int i = arrived[q];
-    const int c = key[i];
-    const int b = start[c], e = start[c + 1];
-    int rank = 0;
-    for (int k = b; k < e; ++k)
-        rank += arrived[k] < i;
-    sorted[b + rank] = i;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int i = arrived[q];
+        const int c = key[i];
+        const int b = start[c], e = start[c + 1];
+        int rank = 0;
+        for (int k = b; k < e; ++k)
+            rank += arrived[k] < i;
+        sorted[b + rank] = i;
+    }
 }
 
 // Cell-ordered records: (x, y, z, type as int bits).
 __global__ void k_cell_gather(const int *__restrict__ sorted, const float4 *__restrict__ xq,
-                              const int *__restrict__ typ, float4 *__restrict__ sxq, int n)
+                              const int *__restrict__ typ, float4 *__restrict__ sxq, int n,
+                              const int *__restrict__ gate)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
+    if (gate_closed(gate))
         return;
-    const int i = sorted[p];
-    const float4 q = xq[i];
-    sxq[p] = make_float4(q.x, q.y, q.z, __int_as_float(typ[i]));
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int i = sorted[p];
+        const float4 q = xq[i];
+        sxq[p] = make_float4(q.x, q.y, q.z, __int_as_float(typ[i]));
+    }
 }
 
-__global__ void __launch_bounds__(128)
-k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
-          const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab,
-          float *__restrict__ F_lj)
+// Per-row-type tables in shared memory: the pair table and, per row type, its
+// largest squared cutoff (force kernels) or cutoff-plus-skin (list build).
+__device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab, float skin,
+                                            float4 *s_tab, float *s_rl2, float *s_rmax)
 {
-    __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
-    __shared__ float s_rcmax[NPSIM_MAX_TYPES]; // largest rc^2 of a row type
-    for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += blockDim.x)
-        s_tab[k] = tab->e[k];
+    for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += blockDim.x) {
+        const float4 t = tab->e[k];
+        s_tab[k] = t;
+        const float rl = sqrtf(t.z) + skin;
+        s_rl2[k] = t.y != 0.0f ? rl * rl : 0.0f; // no LJ between these types: never listed
+    }
     __syncthreads();
     if (threadIdx.x < NPSIM_MAX_TYPES) {
         float m = 0.0f;
         for (int b = 0; b < NPSIM_MAX_TYPES; ++b)
-            m = fmaxf(m, s_tab[threadIdx.x * NPSIM_MAX_TYPES + b].z);
-        s_rcmax[threadIdx.x] = m;
+            m = fmaxf(m, skin > 0.0f ? s_rl2[threadIdx.x * NPSIM_MAX_TYPES + b]
+                                     : s_tab[threadIdx.x * NPSIM_MAX_TYPES + b].z);
+        s_rmax[threadIdx.x] = m;
     }
     __syncthreads();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
+}
+
+// Neighbour lists (gated): for the NP at cell-ordered position p, the partners
+// within (rc_ab + skin) in the 27 cells, in scan order, as (index << 3 | type)
+// (unsigned: an index below 2^29 fits),
+// column-major nbr[k * n + p] for k < cap; nnbr[p] = the full count (an NP with
+// more than cap partners is summed from the cells instead).  Records the
+// positions of this build in x_ref.
+__global__ void __launch_bounds__(128)
+k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
+            const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab, float skin,
+            int cap, unsigned *__restrict__ nbr, int *__restrict__ nnbr,
+            float4 *__restrict__ x_ref,
+            unsigned long long *__restrict__ builds, int *__restrict__ flags,
+            const int *__restrict__ gate)
+{
+    if (gate_closed(gate))
         return;
-    const float4 pi = sxq[p];
-    const int ti = __float_as_int(pi.w);
-    const int row = ti * NPSIM_MAX_TYPES;
-    const float rcmax = s_rcmax[ti];
-    const int cx = cell_coord(pi.x, g), cy = cell_coord(pi.y, g), cz = cell_coord(pi.z, g);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int z = cz + dz;
-        if (z < 0 || z >= g.dim)
-            continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int y = cy + dy;
-            if (y < 0 || y >= g.dim)
+    if (builds && blockIdx.x == 0 && threadIdx.x == 0)
+        ++*builds;
+    __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rmax[NPSIM_MAX_TYPES];
+    load_tables(tab, skin, s_tab, s_rl2, s_rmax);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const float4 pi = sxq[p];
+        const int ti = __float_as_int(pi.w);
+        const int row = ti * NPSIM_MAX_TYPES;
+        const float rmax = s_rmax[ti];
+        const int cx = cell_coord(pi.x, g), cy = cell_coord(pi.y, g), cz = cell_coord(pi.z, g);
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= g.dim)
                 continue;
-            const int base = (z * g.dim + y) * g.dim;
-            const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.dim - 1);
-            // cells x0..x1 of this row are contiguous in the sorted order
-            const int b = start[base + x0], e = start[base + x1 + 1];
-#pragma unroll 2
-            for (int q = b; q < e; ++q) {
-                const float4 pj = sxq[q];
-                const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
-                // the row type's largest cutoff first (most candidates stop here);
-                // the NP itself has r2 = 0 and is skipped by q != p
-                if (r2 >= rcmax || q == p)
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= g.dim)
                     continue;
-                const float4 t = s_tab[row + __float_as_int(pj.w)];
-                if (r2 < t.z) {
-                    const float rinv2 = 1.0f / r2;
-                    const float s2 = t.x * rinv2;
-                    const float s6 = s2 * s2 * s2;
-                    const float f = t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f);
-                    two_sum_acc(hx, lx, f * dx);
-                    two_sum_acc(hy, ly, f * dy2);
-                    two_sum_acc(hz, lz, f * dz2);
+                const int base = (z * g.dim + y) * g.dim;
+                const int b = start[base + max(cx - 1, 0)];
+                const int e = start[base + min(cx + 1, g.dim - 1) + 1];
+                for (int q = b; q < e; ++q) {
+                    const float4 pj = sxq[q];
+                    const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
+                    if (r2 >= rmax || q == p)
+                        continue;
+                    const int tj = __float_as_int(pj.w);
+                    if (r2 < s_rl2[row + tj]) {
+                        if (cnt < cap)
+                            nbr[(size_t)cnt * n + p] = ((unsigned)sorted[q] << 3) | (unsigned)tj;
+                        ++cnt;
+                    }
                 }
             }
         }
+        nnbr[p] = cnt;
+        if (cnt > cap)
+            atomicOr(flags, FLAG_NBR_OVERFLOW);
+        x_ref[sorted[p]] = make_float4(pi.x, pi.y, pi.z, 0.0f);
     }
-    // one 24-byte record per NP: (hi x, y, z, lo x, y, z)
-    float2 *o = reinterpret_cast<float2 *>(F_lj + 6 * (size_t)sorted[p]);
+}
+
+// LJ forces from the neighbour lists at the current positions xq (threads in
+// the cell order of the last build).  An NP whose list overflowed sums over
+// the 27 cells of that build instead (a superset of its list).  Writes one
+// 24-byte (hi x, y, z, lo x, y, z) record per NP and closes the rebuild gate.
+__global__ void __launch_bounds__(128)
+k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
+         const float4 *__restrict__ sxq, const float4 *__restrict__ xq, int n,
+         const PairTab *__restrict__ tab, int cap, const unsigned *__restrict__ nbr,
+         const int *__restrict__ nnbr, float *__restrict__ F_lj, int *__restrict__ gate)
+{
+    __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rmax[NPSIM_MAX_TYPES];
+    load_tables(tab, 0.0f, s_tab, s_rl2, s_rmax);
+    if (gate && blockIdx.x == 0 && threadIdx.x == 0)
+        *gate = 0; // every build kernel of this step has run; the integrator may reopen it
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    const int i = sorted[p];
+    const float4 pi = xq[i];
+    const int ti = __float_as_int(sxq[p].w);
+    const int row = ti * NPSIM_MAX_TYPES;
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    auto pair = [&](const float4 pj, int tj) {
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float4 t = s_tab[row + tj];
+        if (r2 < t.z) {
+            const float rinv2 = 1.0f / r2;
+            const float s2 = t.x * rinv2;
+            const float s6 = s2 * s2 * s2;
+            const float f = t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f);
+            two_sum_acc(hx, lx, f * dx);
+            two_sum_acc(hy, ly, f * dy);
+            two_sum_acc(hz, lz, f * dz);
+        }
+    };
+    const int cnt = nnbr[p];
+    if (cnt <= cap) {
+        for (int k = 0; k < cnt; ++k) {
+            const unsigned e = nbr[(size_t)k * n + p]; // index < 2^29, type < 8
+            pair(xq[e >> 3], (int)(e & 7u));
+        }
+    } else {
+        const float4 pb = sxq[p]; // cells of the build
+        const int cx = cell_coord(pb.x, g), cy = cell_coord(pb.y, g), cz = cell_coord(pb.z, g);
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= g.dim)
+                continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= g.dim)
+                    continue;
+                const int base = (z * g.dim + y) * g.dim;
+                const int b = start[base + max(cx - 1, 0)];
+                const int e = start[base + min(cx + 1, g.dim - 1) + 1];
+                for (int q = b; q < e; ++q)
+                    if (q != p)
+                        pair(xq[sorted[q]], __float_as_int(sxq[q].w));
+            }
+        }
+    }
+    float2 *o = reinterpret_cast<float2 *>(F_lj + 6 * (size_t)i);
     o[0] = make_float2(hx, hy);
     o[1] = make_float2(hz, lx);
     o[2] = make_float2(ly, lz);
@@ -261,34 +387,60 @@ k_cell_lj(CellGrid g, const int *__restrict__ start, const int *__restrict__ sor
 
 } // namespace
 
-// kernels per build: hash, three scan passes, scatter, order, gather
-int cell_build_launches() { return 7; }
+// kernels per build: zero, hash, three scan passes, scatter, order, gather
+int cell_build_launches() { return 8; }
 
 int cell_scan_tiles(int n_cells) { return (n_cells + kScanTile - 1) / kScanTile; }
 
-cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
-                              CellBufs &b, int * /*flags*/, cudaStream_t st)
+namespace {
+constexpr int kMaxGrid = 1216; // 8 CTAs on each of 152 SMs
+int grid_for(int n, int block)
 {
-    cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(int) * (size_t)g.n_cells, st);
-    if (e != cudaSuccess)
-        return e;
+    const int g = (n + block - 1) / block;
+    return g < 1 ? 1 : (g < kMaxGrid ? g : kMaxGrid);
+}
+} // namespace
+
+cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
+                              CellBufs &b, const int *gate, cudaStream_t st)
+{
+    // grid-stride kernels on at most kMaxGrid CTAs: when the gate is closed a
+    // launch costs little more than its CTAs' start
     const int B = 256;
-    k_cell_hash<<<(n + B - 1) / B, B, 0, st>>>(g, xq, n, b.key, b.rank, b.count);
+    const int gn = grid_for(n, B), gc = grid_for(g.n_cells, B);
+    k_cell_zero<<<gc, B, 0, st>>>(b.count, g.n_cells, gate);
+    k_cell_hash<<<gn, B, 0, st>>>(g, xq, n, b.key, b.rank, b.count, gate);
     const int nt = cell_scan_tiles(g.n_cells);
-    k_scan_tiles<<<nt, kScanThreads, 0, st>>>(b.count, b.start, b.tile_sum, g.n_cells);
-    k_scan_totals<<<1, kScanThreads, 0, st>>>(b.tile_sum, nt, b.start, g.n_cells);
-    k_scan_add<<<nt, kScanThreads, 0, st>>>(b.start, b.tile_sum, g.n_cells);
-    k_cell_scatter<<<(n + B - 1) / B, B, 0, st>>>(b.key, b.rank, b.start, b.arrived, n);
-    k_cell_order<<<(n + B - 1) / B, B, 0, st>>>(b.arrived, b.key, b.start, b.sorted, n);
-    k_cell_gather<<<(n + B - 1) / B, B, 0, st>>>(b.sorted, xq, typ, b.sxq, n);
+    const int gt = nt < kMaxGrid ? nt : kMaxGrid;
+    k_scan_tiles<<<gt, kScanThreads, 0, st>>>(b.count, b.start, b.tile_sum, g.n_cells, gate);
+    k_scan_totals<<<1, kScanThreads, 0, st>>>(b.tile_sum, nt, b.start, g.n_cells, gate);
+    k_scan_add<<<gt, kScanThreads, 0, st>>>(b.start, b.tile_sum, g.n_cells, gate);
+    k_cell_scatter<<<gn, B, 0, st>>>(b.key, b.rank, b.start, b.arrived, n, gate);
+    k_cell_order<<<gn, B, 0, st>>>(b.arrived, b.key, b.start, b.sorted, n, gate);
+    k_cell_gather<<<gn, B, 0, st>>>(b.sorted, xq, typ, b.sxq, n, gate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell_lj(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
-                           float *F_lj, cudaStream_t st)
+cudaError_t launch_nbr_build(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
+                             float skin, const NbrList &l, int *flags, const int *gate,
+                             cudaStream_t st)
+{
+    // heavy per-NP work (every candidate of 27 cells): up to four CTAs of
+    // kMaxGrid, so that a compact droplet's build still has one NP per thread
+    const int B = 128;
+    const int gb = (n + B - 1) / B < 4 * kMaxGrid ? (n + B - 1) / B : 4 * kMaxGrid;
+    k_nbr_build<<<gb > 0 ? gb : 1, B, 0, st>>>(g, b.start, b.sorted, b.sxq, n, tab, skin, l.cap,
+                                               l.nbr, l.nnbr, l.x_ref, l.builds, flags, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq, int n,
+                          const PairTab *tab, const NbrList &l, float *F_lj, int *gate,
+                          cudaStream_t st)
 {
     const int B = 128;
-    k_cell_lj<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.sxq, n, tab, F_lj);
+    k_lj_nbr<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.sxq, xq, n, tab, l.cap,
+                                            l.nbr, l.nnbr, F_lj, gate);
     return cudaGetLastError();
 }
 

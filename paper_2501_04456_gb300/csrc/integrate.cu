@@ -103,7 +103,8 @@ k_integrate(IntArgs a, StepParams p)
         }
 
         advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
-                               step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags);
+                               step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags,
+                               a.x_ref, a.nbr_gate, a.half_skin2);
     }
 
     if (DO_A) {

@@ -16,6 +16,7 @@ enum : int {
     FLAG_NONFINITE = 1,
     FLAG_TIMEOUT = 2,
     FLAG_BAD_CELL = 4,
+    FLAG_NBR_OVERFLOW = 8, // some NP had more list partners than the list holds (not an error)
 };
 
 // ---------------------------------------------------------------------------
@@ -627,6 +628,9 @@ struct IntArgs {
     const float *F_lj;       // cell-list LJ forces [n][6] (hi x, y, z, lo x, y, z) (or NULL)
     const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
                              // no Coulomb partial); NULL: row position = i
+    const float4 *x_ref;     // positions at the last neighbour-list build (or NULL)
+    int *nbr_gate;           // set to 1 when an NP has moved more than half the skin
+    float half_skin2;        // (skin / 2)^2, with margin
     float4 *spring;          // spring radius per type (spring_entry), two buffers
                              // [2][NPSIM_MAX_TYPES]: buffer (step & 1) holds the
                              // current step's; modes that advance the step write
@@ -649,7 +653,9 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
                                                  uint64_t seed, long long step, const float4 &xh,
                                                  float lx, float ly, float lz, const float Fh[3],
                                                  const float Fl[3], float *x_lo, float *v_,
-                                                 float *F, float4 *xq, int *flags)
+                                                 float *F, float4 *xq, int *flags,
+                                                 const float4 *x_ref = nullptr,
+                                                 int *nbr_gate = nullptr, float half_skin2 = 0.f)
 {
     constexpr bool DO_B = (MODE == MODE_BA || MODE == MODE_B);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
@@ -695,6 +701,12 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
         x_lo[2 * n + i] = xlo[2];
         if (!(isfinite(xhi[0]) && isfinite(xhi[1]) && isfinite(xhi[2])))
             atomicOr(flags, FLAG_NONFINITE);
+        if (x_ref) { // moved more than half the skin since the list was built: rebuild
+            const float4 r = x_ref[i];
+            const float ex = xhi[0] - r.x, ey = xhi[1] - r.y, ez = xhi[2] - r.z;
+            if (!(fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= half_skin2))
+                *nbr_gate = 1;
+        }
     }
     v_[i] = v[0];
     v_[n + i] = v[1];
@@ -801,10 +813,25 @@ struct CellBufs {
     int *key, *rank, *count, *start, *arrived, *sorted, *tile_sum;
     float4 *sxq; // cell-ordered (x, y, z, type as int bits)
 };
+// Build the cell list of positions xq (gate: NULL = always, else only when *gate != 0).
 cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
-                              CellBufs &b, int *flags, cudaStream_t st);
-cudaError_t launch_cell_lj(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
-                           float *F_lj, cudaStream_t st);
+                              CellBufs &b, const int *gate, cudaStream_t st);
+// Verlet neighbour list over the cells (celllist.cu): nbr [cap][n] column-major
+// (index << 3 | type) per cell-ordered NP, nnbr [n] the full counts, x_ref [n]
+// the positions of the last build.
+struct NbrList {
+    unsigned *nbr; // (index << 3 | type)
+    int *nnbr;
+    float4 *x_ref;
+    unsigned long long *builds; // number of builds run (device counter)
+    int cap;
+};
+cudaError_t launch_nbr_build(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
+                             float skin, const NbrList &l, int *flags, const int *gate,
+                             cudaStream_t st);
+cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq, int n,
+                          const PairTab *tab, const NbrList &l, float *F_lj, int *gate,
+                          cudaStream_t st);
 int cell_build_launches();
 int cell_scan_tiles(int n_cells);
 

@@ -280,8 +280,12 @@ def test_chunking_and_runs_are_bit_identical(P):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(Fa, Fb)
 
 
-def test_checkpoint_resume_is_bit_exact(P, tmp_path):
-    sc = small(wl.config2(), 1500)
+@pytest.mark.parametrize("which", ["lj_allpairs", "cell_list"])
+def test_checkpoint_resume_is_bit_exact(P, tmp_path, which):
+    # the cell-list case carries neighbour lists (and their rebuilds) across the
+    # checkpoint: kT = 4 makes the NPs fast enough to rebuild several times
+    sc = (small(wl.config2(), 1500) if which == "lj_allpairs"
+          else with_(small(wl.config3(), 3000), kT=4.0))
     types, x, v = wl.initial_state(sc)
     with P.Sim(sc, x, v, types) as a:
         a.step(40)
@@ -301,6 +305,57 @@ def test_checkpoint_resume_is_bit_exact(P, tmp_path):
     finally:
         c.close()
     assert np.array_equal(xa, xc) and np.array_equal(va, vc)
+
+
+def _hi_words(P, sim, n):
+    torch = pytest.importorskip("torch")
+    xq = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    P.npsim_positions_device(sim.h, xq.data_ptr())
+    torch.cuda.synchronize()
+    return xq[:, :3].cpu().double().numpy()
+
+
+def test_neighbour_lists_rebuild_and_stay_exact(P):
+    """The cell-list LJ runs from Verlet lists rebuilt only after an NP has moved
+    half the skin: after several rebuilds the LJ forces still equal the
+    oracle's at the same (float32) positions."""
+    sc = with_(wl.config1(), kT=3.0)
+    types, x, v = wl.initial_state(sc, fp32_positions=True)
+    with P.Sim(sc, x, v, types) as sim:
+        _, _, b0 = sim.nbr_info()
+        sim.step(300)
+        cap, mean_len, b1 = sim.nbr_info()
+        F = sim.forces(2)
+        xh = _hi_words(P, sim, sc.n)
+    assert b1 - b0 >= 2 and mean_len > 0
+    ref = _oracle_pair(sc, xh, types, coul=False)
+    amb = cutoff_ambiguous(xh, types, sc)
+    assert force_error(F, ref)[~amb].max() <= FORCE_TOL
+
+
+def test_neighbour_list_overflow_is_exact_and_grows(P):
+    """A compact lattice has more list partners per NP than the initial list
+    holds: those NPs are summed from the cells (exact) and the list grows."""
+    m, a = 12, 1.12
+    g = (np.arange(m) - (m - 1) / 2) * a
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x = x.astype(np.float32).astype(np.float64)
+    n = len(x)
+    t = wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=100.0)
+    sc = wl.Scenario(name="lattice", types=[t], n=n, seed=4, dt=1e-3, kT=0.1, R0=40.0,
+                     lj_mode=2, coulomb=False)
+    ty = np.zeros(n, np.int32)
+    with P.Sim(sc, x, None, ty) as sim:
+        cap, mean_len, _ = sim.nbr_info()
+        F0 = sim.forces(2)
+        sim.step(40)
+        F1 = sim.forces(2)
+        xh = _hi_words(P, sim, n)
+    assert mean_len > 32 and cap >= mean_len  # grown past the initial 32
+    for F, xx in ((F0, x), (F1, xh)):
+        ref = _oracle_pair(sc, xx, ty, coul=False)
+        amb = cutoff_ambiguous(xx, ty, sc)
+        assert force_error(F, ref)[~amb].max() <= FORCE_TOL
 
 
 # --------------------------------------------------------------------------
