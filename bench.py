@@ -319,8 +319,9 @@ INT_BYTES_B = 16 + 12 + 12 + 4 + 24 + 12
 # 16), list build (own record 16, sorted index 4, count 4, build position 16,
 # 4 per list entry); per rebuild and cell: count reset and three scan passes
 # (20).  Per step and NP, the list LJ forces: sorted index 4, current position
-# 16, type record 16, count 4, 4 per list entry, force record 24 (partner
-# positions are re-reads of records already counted).
+# 16, type record 16, count 4, 4 per list entry, force record 24 (stored as a
+# 32-byte sector, the padding not counted; partner positions are re-reads of
+# records already counted).
 CELL_BUILD_BYTES_NP = 24 + 16 + 20 + 40 + 40
 CELL_BUILD_BYTES_CELL = 20
 LIST_LJ_BYTES_NP = 4 + 16 + 16 + 4 + 24
@@ -728,6 +729,7 @@ def run_dense_case(a, compress_steps=20000):
         for _ in range(a.warmup):
             flush.zero_()
             s2.step(1)
+        _, _, b0 = s2.nbr_info()
         ts, kts = [], []
         for _ in range(a.steps):
             flush.zero_()
@@ -742,13 +744,17 @@ def run_dense_case(a, compress_steps=20000):
         t0 = time.perf_counter()
         st = s2.stats(r_max=10.0, n_bins=128, boxcount=True)  # RDF, R_g, box counting
         t_stats = time.perf_counter() - t0
+        cap, mean_len, b1 = s2.nbr_info()
     km = {k: sum(d[k] for d in kts) / len(kts) for k in kts[0]}
     ms = sum(ts) / len(ts)
     print(json.dumps({"case": "dense", "n": sc.n, "R": Rf, "packing_fraction": phi,
                       "compress_steps": compress_steps, "compress_s": t_comp,
                       "ms_per_step": ms, "pair_interactions_per_s": sc.n * (sc.n - 1) / (ms * 1e-3),
                       "kernel_ms": km, "Df_rg": st["Df_rg"], "Df_box": st["Df_box"],
-                      "Rg": st["Rg"], "stats_ms": 1e3 * t_stats}), flush=True)
+                      "Rg": st["Rg"], "stats_ms": 1e3 * t_stats,
+                      "neighbour_lists": {"mean_length": mean_len, "capacity": cap,
+                                          "rebuilds_per_step": (b1 - b0) / a.steps}}),
+          flush=True)
 
 
 def main():

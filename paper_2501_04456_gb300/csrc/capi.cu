@@ -64,6 +64,19 @@ template <class T> void dfree(T *&p)
     p = nullptr;
 }
 
+void free_cells(CellBufs &b)
+{
+    dfree(b.key);
+    dfree(b.rank);
+    dfree(b.count);
+    dfree(b.start);
+    dfree(b.arrived);
+    dfree(b.sorted);
+    dfree(b.pos);
+    dfree(b.sxq);
+    dfree(b.tile_sum);
+}
+
 int check_device(int *sms)
 {
     int count = 0;
@@ -148,7 +161,7 @@ struct npsim_sim {
     float4 *xq = nullptr;
     int *typ = nullptr;
     float *slots = nullptr;
-    float *F_lj = nullptr;                // [6][n]
+    float *F_lj = nullptr;                // [n][8]: (hi x, y, z, lo x | lo y, z, -, -)
     PairTab *tab_full = nullptr, *tab_lj = nullptr, *tab_coul = nullptr;
     float rc2_lim = 0.0f; // largest LJ rc^2 of the table (x 1.0001): tile-culling bound
     int any_charge = 0;   // Coulomb on and some type charged
@@ -231,17 +244,8 @@ struct npsim_sim {
         dfree(nl.nnbr);
         dfree(nl.x_ref);
         dfree(nl.builds);
-        CellBufs *bufs[2] = {&cb, &scb};
-        for (CellBufs *b : bufs) {
-            dfree(b->key);
-            dfree(b->rank);
-            dfree(b->count);
-            dfree(b->start);
-            dfree(b->arrived);
-            dfree(b->sorted);
-            dfree(b->sxq);
-            dfree(b->tile_sum);
-        }
+        free_cells(cb);
+        free_cells(scb);
         dfree(s_hist);
         dfree(s_rhist);
         dfree(s_part);
@@ -263,6 +267,7 @@ int alloc_cells(CellGrid &g, CellBufs &b, int n)
     NP_CUDA(dalloc(&b.start, (size_t)g.n_cells + 1));
     NP_CUDA(dalloc(&b.arrived, n));
     NP_CUDA(dalloc(&b.sorted, n));
+    NP_CUDA(dalloc(&b.pos, n));
     NP_CUDA(dalloc(&b.sxq, n));
     NP_CUDA(dalloc(&b.tile_sum, cell_scan_tiles(g.n_cells)));
     return NPSIM_OK;
@@ -388,8 +393,8 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
                                  s->d_gate, st));
         NP_CUDA(mark(KG_CELL_BUILD, 1));
         NP_CUDA(mark(KG_CELL_LJ, 0));
-        NP_CUDA(launch_lj_nbr(s->grid, s->cb, s->xq, s->n, s->tab_full, s->nl, s->F_lj,
-                              s->d_gate, st));
+        NP_CUDA(launch_lj_nbr(s->grid, s->cb, s->xq, s->typ, s->n, s->tab_full, s->nl,
+                              s->F_lj, s->d_gate, st));
         NP_CUDA(mark(KG_CELL_LJ, 1));
     }
     if (ap) {
@@ -1072,7 +1077,7 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
         rc = alloc_cells(s->grid, s->cb, s->n);
         if (rc)
             return bail(rc);
-        BAIL_CUDA(dalloc(&s->F_lj, 2 * n3));
+        BAIL_CUDA(dalloc(&s->F_lj, 8 * (size_t)n)); // one 32-byte record per NP
         s->nl.cap = 32; // grown after the first build if some NP has more partners
         BAIL_CUDA(dalloc(&s->nl.nbr, (size_t)s->nl.cap * n));
         BAIL_CUDA(dalloc(&s->nl.nnbr, (size_t)n));
@@ -1373,9 +1378,7 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
         L += cfg->r_max + 1.0;
         CellGrid g = make_grid(L, cfg->r_max * (1.0 + 1e-4) + 1e-3, std::max<long long>(4 * n + 4096, 1 << 16));
         if (g.n_cells > s->s_cells_cap) {
-            CellBufs &b = s->scb;
-            dfree(b.key); dfree(b.rank); dfree(b.count); dfree(b.start);
-            dfree(b.arrived); dfree(b.sorted); dfree(b.sxq); dfree(b.tile_sum);
+            free_cells(s->scb);
             int rc = alloc_cells(g, s->scb, n);
             if (rc)
                 return rc;
@@ -1531,10 +1534,7 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
     if (!s->cell || !h.cell)
         return NPSIM_OK;
     if (h.grid_cells != s->grid.n_cells) {
-        CellBufs &b = s->cb;
-        dfree(b.key); dfree(b.rank); dfree(b.count); dfree(b.start);
-        dfree(b.arrived); dfree(b.sorted); dfree(b.sxq); dfree(b.tile_sum);
-        b = CellBufs{};
+        free_cells(s->cb);
     }
     CellGrid g{};
     g.dim = h.grid_dim;

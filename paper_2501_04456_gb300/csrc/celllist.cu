@@ -201,8 +201,8 @@ __global__ void k_cell_scatter(const int *__restrict__ key, const int *__restric
 // cell's start plus the number of members with a smaller index (O(m) per NP for
 // a cell of m members, all NPs in parallel).
 __global__ void k_cell_order(const int *__restrict__ arrived, const int *__restrict__ key,
-                             const int *__restrict__ start, int *__restrict__ sorted, int n,
-                             const int *__restrict__ gate)
+                             const int *__restrict__ start, int *__restrict__ sorted,
+                             int *__restrict__ pos, int n, const int *__restrict__ gate)
 {
     if (gate_closed(gate))
         return;
@@ -214,6 +214,7 @@ __global__ void k_cell_order(const int *__restrict__ arrived, const int *__restr
         for (int k = b; k < e; ++k)
             rank += arrived[k] < i;
         sorted[b + rank] = i;
+        pos[i] = b + rank;
     }
 }
 
@@ -253,12 +254,13 @@ __device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab, flo
     __syncthreads();
 }
 
-// Neighbour lists (gated): for the NP at cell-ordered position p, the partners
-// within (rc_ab + skin) in the 27 cells, in scan order, as (index << 3 | type)
-// (unsigned: an index below 2^29 fits),
-// column-major nbr[k * n + p] for k < cap; nnbr[p] = the full count (an NP with
-// more than cap partners is summed from the cells instead).  Records the
-// positions of this build in x_ref.
+// Neighbour lists (gated): for NP i (threads in the cell order, so that a
+// warp scans the same cells), the partners within (rc_ab + skin) in the 27
+// cells, in scan order, as (index << 3 | type) (unsigned: an index below 2^29
+// fits), column-major nbr[k * n + i] for k < cap; nnbr[i] = the full count (an
+// NP with more than cap partners is summed from the cells instead).  Lists are
+// written by particle so that the per-step force kernel reads them coalesced.
+// Records the positions of this build in x_ref.
 __global__ void __launch_bounds__(128)
 k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
             const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab, float skin,
@@ -277,6 +279,7 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
     load_tables(tab, skin, s_tab, s_rl2, s_rmax);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const float4 pi = sxq[p];
+        const int i = sorted[p];
         const int ti = __float_as_int(pi.w);
         const int row = ti * NPSIM_MAX_TYPES;
         const float rmax = s_rmax[ti];
@@ -302,26 +305,29 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
                     const int tj = __float_as_int(pj.w);
                     if (r2 < s_rl2[row + tj]) {
                         if (cnt < cap)
-                            nbr[(size_t)cnt * n + p] = ((unsigned)sorted[q] << 3) | (unsigned)tj;
+                            nbr[(size_t)cnt * n + i] = ((unsigned)sorted[q] << 3) | (unsigned)tj;
                         ++cnt;
                     }
                 }
             }
         }
-        nnbr[p] = cnt;
+        nnbr[i] = cnt;
         if (cnt > cap)
             atomicOr(flags, FLAG_NBR_OVERFLOW);
-        x_ref[sorted[p]] = make_float4(pi.x, pi.y, pi.z, 0.0f);
+        x_ref[i] = make_float4(pi.x, pi.y, pi.z, 0.0f);
     }
 }
 
-// LJ forces from the neighbour lists at the current positions xq (threads in
-// the cell order of the last build).  An NP whose list overflowed sums over
-// the 27 cells of that build instead (a superset of its list).  Writes one
-// 24-byte (hi x, y, z, lo x, y, z) record per NP and closes the rebuild gate.
+// LJ forces from the neighbour lists at the current positions xq, one thread
+// per NP in particle order (type-grouped, Morton-ordered within a type: the
+// NP's own record, list and force record are coalesced and a warp's partners
+// are near one another).  An NP whose list overflowed sums over the 27 cells
+// of that build instead (a superset of its list).  Writes one 32-byte (hi x,
+// y, z, lo x, y, z, 0, 0) record per NP and closes the rebuild gate.
 __global__ void __launch_bounds__(128)
 k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
-         const float4 *__restrict__ sxq, const float4 *__restrict__ xq, int n,
+         const int *__restrict__ pos, const float4 *__restrict__ sxq,
+         const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
          const PairTab *__restrict__ tab, int cap, const unsigned *__restrict__ nbr,
          const int *__restrict__ nnbr, float *__restrict__ F_lj, int *__restrict__ gate)
 {
@@ -331,12 +337,11 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
     load_tables(tab, 0.0f, s_tab, s_rl2, s_rmax);
     if (gate && blockIdx.x == 0 && threadIdx.x == 0)
         *gate = 0; // every build kernel of this step has run; the integrator may reopen it
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
         return;
-    const int i = sorted[p];
     const float4 pi = xq[i];
-    const int ti = __float_as_int(sxq[p].w);
+    const int ti = typ[i];
     const int row = ti * NPSIM_MAX_TYPES;
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     auto pair = [&](const float4 pj, int tj) {
@@ -353,13 +358,14 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
             two_sum_acc(hz, lz, f * dz);
         }
     };
-    const int cnt = nnbr[p];
+    const int cnt = nnbr[i];
     if (cnt <= cap) {
         for (int k = 0; k < cnt; ++k) {
-            const unsigned e = nbr[(size_t)k * n + p]; // index < 2^29, type < 8
+            const unsigned e = nbr[(size_t)k * n + i]; // index < 2^29, type < 8
             pair(xq[e >> 3], (int)(e & 7u));
         }
     } else {
+        const int p = pos[i];
         const float4 pb = sxq[p]; // cells of the build
         const int cx = cell_coord(pb.x, g), cy = cell_coord(pb.y, g), cz = cell_coord(pb.z, g);
         for (int dz = -1; dz <= 1; ++dz) {
@@ -379,10 +385,10 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
             }
         }
     }
-    float2 *o = reinterpret_cast<float2 *>(F_lj + 6 * (size_t)i);
-    o[0] = make_float2(hx, hy);
-    o[1] = make_float2(hz, lx);
-    o[2] = make_float2(ly, lz);
+    // one 32-byte record per NP, a whole DRAM sector: (hi x, y, z, lo x), (lo y, z)
+    float4 *o = reinterpret_cast<float4 *>(F_lj + 8 * (size_t)i);
+    o[0] = make_float4(hx, hy, hz, lx);
+    o[1] = make_float4(ly, lz, 0.0f, 0.0f);
 }
 
 } // namespace
@@ -416,7 +422,7 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
     k_scan_totals<<<1, kScanThreads, 0, st>>>(b.tile_sum, nt, b.start, g.n_cells, gate);
     k_scan_add<<<gt, kScanThreads, 0, st>>>(b.start, b.tile_sum, g.n_cells, gate);
     k_cell_scatter<<<gn, B, 0, st>>>(b.key, b.rank, b.start, b.arrived, n, gate);
-    k_cell_order<<<gn, B, 0, st>>>(b.arrived, b.key, b.start, b.sorted, n, gate);
+    k_cell_order<<<gn, B, 0, st>>>(b.arrived, b.key, b.start, b.sorted, b.pos, n, gate);
     k_cell_gather<<<gn, B, 0, st>>>(b.sorted, xq, typ, b.sxq, n, gate);
     return cudaGetLastError();
 }
@@ -434,13 +440,13 @@ cudaError_t launch_nbr_build(const CellGrid &g, const CellBufs &b, int n, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq, int n,
-                          const PairTab *tab, const NbrList &l, float *F_lj, int *gate,
-                          cudaStream_t st)
+cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq,
+                          const int *typ, int n, const PairTab *tab, const NbrList &l,
+                          float *F_lj, int *gate, cudaStream_t st)
 {
     const int B = 128;
-    k_lj_nbr<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.sxq, xq, n, tab, l.cap,
-                                            l.nbr, l.nnbr, F_lj, gate);
+    k_lj_nbr<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.pos, b.sxq, xq, typ, n, tab,
+                                            l.cap, l.nbr, l.nnbr, F_lj, gate);
     return cudaGetLastError();
 }
 

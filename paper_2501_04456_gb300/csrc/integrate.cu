@@ -80,11 +80,11 @@ k_integrate(IntArgs a, StepParams p)
                 }
             }
             if (a.F_lj) {
-                const float2 *r = reinterpret_cast<const float2 *>(a.F_lj + 6 * (size_t)i);
-                const float2 r0 = r[0], r1 = r[1], r2 = r[2]; // (hx, hy) (hz, lx) (ly, lz)
-                df_add_df(Fh[0], Fl[0], r0.x, r1.y);
-                df_add_df(Fh[1], Fl[1], r0.y, r2.x);
-                df_add_df(Fh[2], Fl[2], r1.x, r2.y);
+                const float4 *r = reinterpret_cast<const float4 *>(a.F_lj + 8 * (size_t)i);
+                const float4 r0 = r[0], r1 = r[1]; // (hx, hy, hz, lx) (ly, lz, -, -)
+                df_add_df(Fh[0], Fl[0], r0.x, r0.w);
+                df_add_df(Fh[1], Fl[1], r0.y, r1.x);
+                df_add_df(Fh[2], Fl[2], r0.z, r1.y);
             }
             if (a.ext_on) {
                 float ex, ey, ez;

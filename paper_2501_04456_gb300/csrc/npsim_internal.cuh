@@ -617,15 +617,15 @@ enum IntMode : int {
 // State of the integrator: position = xq.xyz (float32, the word the pair kernels
 // read) + x_lo (float32 SoA [3][n]); velocity float32 SoA [3][n]; force as
 // float32 hi/lo SoA [6][n] (hi x, y, z, then lo x, y, z).  Stream-K partial
-// slots use the same hi/lo split; the cell-list LJ forces are one 24-byte
-// (hi x, y, z, lo x, y, z) record per NP (written in cell order).
+// slots use the same hi/lo split; the cell-list LJ forces are one 32-byte
+// (hi x, y, z, lo x, y, z, 0, 0) record per NP, indexed by particle.
 struct IntArgs {
     float *x_lo, *v, *F;     // see above
     const int *typ;
     float4 *xq;              // (x hi, y hi, z hi, q)
     const float *slots;      // stream-K partials [slot][6][itile] (or NULL)
     StreamK sk;
-    const float *F_lj;       // cell-list LJ forces [n][6] (hi x, y, z, lo x, y, z) (or NULL)
+    const float *F_lj;       // cell-list LJ forces [n][8] (hi x, y, z, lo x, y, z, 0, 0) (or NULL)
     const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
                              // no Coulomb partial); NULL: row position = i
     const float4 *x_ref;     // positions at the last neighbour-list build (or NULL)
@@ -811,14 +811,15 @@ cudaError_t launch_weights_bf16(const float *w, int rows, int cols, void *wb, vo
 // Cell list (celllist.cu)
 struct CellBufs {
     int *key, *rank, *count, *start, *arrived, *sorted, *tile_sum;
+    int *pos;    // cell-ordered position of NP i (the inverse of sorted)
     float4 *sxq; // cell-ordered (x, y, z, type as int bits)
 };
 // Build the cell list of positions xq (gate: NULL = always, else only when *gate != 0).
 cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
                               CellBufs &b, const int *gate, cudaStream_t st);
 // Verlet neighbour list over the cells (celllist.cu): nbr [cap][n] column-major
-// (index << 3 | type) per cell-ordered NP, nnbr [n] the full counts, x_ref [n]
-// the positions of the last build.
+// (index << 3 | type), column i the list of NP i; nnbr [n] the full counts,
+// x_ref [n] the positions of the last build.
 struct NbrList {
     unsigned *nbr; // (index << 3 | type)
     int *nnbr;
@@ -829,9 +830,9 @@ struct NbrList {
 cudaError_t launch_nbr_build(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
                              float skin, const NbrList &l, int *flags, const int *gate,
                              cudaStream_t st);
-cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq, int n,
-                          const PairTab *tab, const NbrList &l, float *F_lj, int *gate,
-                          cudaStream_t st);
+cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq,
+                          const int *typ, int n, const PairTab *tab, const NbrList &l,
+                          float *F_lj, int *gate, cudaStream_t st);
 int cell_build_launches();
 int cell_scan_tiles(int n_cells);
 
