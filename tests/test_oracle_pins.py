@@ -408,6 +408,50 @@ def test_sedimentation_and_centrifugal_drift():
     assert x[0, 2] == pytest.approx(1.0, rel=1e-15)
 
 
+def _boltzmann_wall_cdf(R_eff, k, kT):
+    """CDF of the radius for an ideal gas held by the one-sided interface spring:
+    p(r) ~ r^2 exp(-k max(r - R_eff, 0)^2 / (2 kT)), by trapezoidal quadrature."""
+    w = math.sqrt(kT / k)
+    r = np.linspace(0.0, R_eff + 12.0 * w, 400001)
+    p = r * r * np.exp(-0.5 * np.maximum(r - R_eff, 0.0) ** 2 / (w * w))
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (p[1:] + p[:-1]) * np.diff(r))])
+    return r, cdf / cdf[-1], w
+
+
+@pytest.mark.parametrize("integrator,dt", [(1, 1e-3), (0, 2e-3)])
+def test_wall_ideal_gas_keeps_boltzmann_radial_density(integrator, dt):
+    """An ideal gas (no pair forces) in a static droplet has Boltzmann's stationary
+    radial density under the interface spring (Sec. 2.2 step (iv)): flat inside
+    R - sigma/2, a Gaussian tail of width sqrt(kT/k_wall) beyond it.  Sampled from
+    that law, the gas must stay in it: a wrong spring constant, sign or noise
+    amplitude moves the tail within a few gamma/k_wall (here 0.1 of the 2 time
+    units run).  Checked by a chi-square over radial bins and the tail fraction."""
+    n, k, kT, R, sigma = 20000, 10.0, 1.0, 3.0, 1.0
+    R_eff = R - sigma / 2
+    t = wl.TypeSpec(sigma=sigma, eps=0.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=k)
+    sc = wl.Scenario(name="gas", types=[t], n=n, seed=5, dt=dt, kT=kT, R0=R, k_evap=0.0,
+                     wall=True, lj_mode=0, coulomb=False, integrator=integrator)
+    grid, cdf, w = _boltzmann_wall_cdf(R_eff, k, kT)
+    rng = np.random.default_rng(11)
+    rad = np.interp(rng.random(n), cdf, grid)
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    ty = np.zeros(n, np.int32)
+    v0 = wl.maxwell_velocities(sc, ty, seed=3) if integrator == 0 else np.zeros((n, 3))
+    x, _, _ = oracle.run(sc, rad[:, None] * u, v0, ty, 0, int(round(2.0 / dt)))
+    r = np.linalg.norm(x, axis=1)
+    edges = np.array([0.0, R_eff - 1.0, R_eff - 0.5, R_eff - 0.25, R_eff, R_eff + 0.5 * w,
+                      R_eff + w, R_eff + 1.5 * w, R_eff + 2.0 * w, R_eff + 3.0 * w, np.inf])
+    prob = np.diff(np.interp(edges, grid, cdf, right=1.0))
+    obs = np.histogram(r, bins=edges)[0]
+    chi2 = float((((obs - n * prob) ** 2) / (n * prob)).sum())
+    dof = len(prob) - 1
+    assert chi2 < dof + 6.0 * math.sqrt(2.0 * dof), (chi2, obs, n * prob)
+    p_out = 1.0 - float(np.interp(R_eff, grid, cdf))
+    se = math.sqrt(p_out * (1.0 - p_out) / n)
+    assert abs((r > R_eff).mean() - p_out) < 5.0 * se
+
+
 def test_velocity_verlet_limit_reversible_and_energy():
     """gamma = 0, kT = 0 turns BAOAB into velocity Verlet: running n steps, negating v
     and running n more returns to the start (time reversibility), and the total
