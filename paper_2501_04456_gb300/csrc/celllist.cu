@@ -360,8 +360,24 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
     };
     const int cnt = nnbr[i];
     if (cnt <= cap) {
-        for (int k = 0; k < cnt; ++k) {
-            const unsigned e = nbr[(size_t)k * n + i]; // index < 2^29, type < 8
+        // four list entries, then their four positions, in flight at once; the
+        // pairs are still summed in list order
+        int k = 0;
+        for (; k + 4 <= cnt; k += 4) {
+            unsigned e[4]; // index < 2^29, type < 8
+            float4 pj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                e[u] = nbr[(size_t)(k + u) * n + i];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                pj[u] = xq[e[u] >> 3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                pair(pj[u], (int)(e[u] & 7u));
+        }
+        for (; k < cnt; ++k) {
+            const unsigned e = nbr[(size_t)k * n + i];
             pair(xq[e >> 3], (int)(e & 7u));
         }
     } else {
