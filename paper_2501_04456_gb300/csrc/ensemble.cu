@@ -41,8 +41,11 @@ __device__ __forceinline__ int drop_of_unit(const long long *__restrict__ unit0,
     return lo;
 }
 
+// At least 1024 (one row per thread) or 512 (two rows per thread) threads
+// resident per SM: the register caps this implies (64, 128) hold the sweeps
+// without spills.
 template <int BLOCK, int KI, int JT>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, KI == 1 ? 1024 / BLOCK : 512 / BLOCK)
 k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
           const int *__restrict__ tblk, const EnsDrop *__restrict__ drops,
           const long long *__restrict__ unit0, const PairTab *__restrict__ tabs, int n_drops,

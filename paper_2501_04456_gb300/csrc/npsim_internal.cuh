@@ -263,14 +263,55 @@ __device__ __forceinline__ float box_gap2(const Box3 &a, const Box3 &b)
     return gx * gx + gy * gy + gz * gz;
 }
 
-// Shared memory of ljc_row_segment: one staged j-tile (negated coordinates,
-// two partners per entry) and the box of each 64-partner segment of it.
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only), and its
+// completion by the issuing thread.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_own()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Shared memory of ljc_row_segment: two staged j-tiles (negated coordinates,
+// two partners per entry, and the box of each 64-partner segment) -- one
+// swept while the next is filled -- and the raw partner records of the next
+// tile as gathered by cp.async.
 template <int JT>
 struct LjcSmem {
-    float4 a[JT / 2]; // (-x0, -x1, -y0, -y1)
-    float2 b[JT / 2]; // (-z0, -z1)
-    Box3 seg[JT / 64];
+    float4 raw[JT];      // (x, y, z, q) of the next tile's partners, grouped order
+    float4 a[2][JT / 2]; // (-x0, -x1, -y0, -y1)
+    float2 b[2][JT / 2]; // (-z0, -z1)
+    Box3 seg[2][JT / 64];
 };
+
+// Staging of entry m (partners 2m, 2m + 1) of a j-tile from its raw records:
+// negated, paired coordinates and, by a warp reduction (whole warps stage), the
+// box of the warp's 64 partners.  vmask bit k: partner 2m + k is a particle
+// (not padding).
+template <int JT>
+__device__ __forceinline__ void ljc_stage_entry(LjcSmem<JT> &sm, int buf, int m, float4 a,
+                                                float4 b, int vmask)
+{
+    sm.a[buf][m] = make_float4(-a.x, -b.x, -a.y, -b.y);
+    sm.b[buf][m] = make_float2(-a.z, -b.z);
+    Box3 pb = box_empty();
+    if (vmask & 1)
+        box_add(pb, a.x, a.y, a.z);
+    if (vmask & 2)
+        box_add(pb, b.x, b.y, b.z);
+    pb = box_warp_reduce(pb); // the 32 entries m of this warp = one segment
+    if ((threadIdx.x & 31) == 0)
+        sm.seg[buf][m >> 5] = pb;
+}
 
 // Row tile r (rows r*ITILE .. of a grouped order occupying positions [gbase,
 // gbase + glen) of perm / tblk) against its j-tiles jt0 .. jt1-1 of the same
@@ -280,6 +321,12 @@ struct LjcSmem {
 // come within sqrt(rc2_lim); elsewhere the Coulomb-only sweep runs (the charge
 // product applied once per tile), or nothing when has_coul is 0.  s_tab: the
 // 8 x 8 type-pair table (sigma^2, 24 eps, rc^2, C q q) in shared memory.
+//
+// Staging is software-pipelined: while tile jt is swept, the first JT/2
+// threads have the partner records of tile jt + 1 in flight (cp.async into
+// sm.raw, the partner indices read one tile earlier still) and turn them into
+// the other staged buffer after the sweep, so one barrier per tile remains and
+// the gather's latency hides behind the sweep.
 template <int BLOCK, int KI, int JT>
 __device__ __forceinline__ void ljc_row_segment(const float4 *__restrict__ xq,
                                                 const int *__restrict__ perm,
@@ -291,6 +338,7 @@ __device__ __forceinline__ void ljc_row_segment(const float4 *__restrict__ xq,
     constexpr int ITILE = BLOCK * KI;
     constexpr int JP = JT / 2;
     constexpr int NSEG = JT / 64;
+    static_assert(JP <= BLOCK && JP % 32 == 0, "one staged entry per thread of whole warps");
     float2 xi[KI], yi[KI], zi[KI];
     int trow[KI];
     float hx[KI], hy[KI], hz[KI], lx[KI], ly[KI], lz[KI];
@@ -313,26 +361,43 @@ __device__ __forceinline__ void ljc_row_segment(const float4 *__restrict__ xq,
     }
     wb = box_warp_reduce(wb); // the box of this warp's rows
 
-    for (int jt = jt0; jt < jt1; ++jt) {
-        __syncthreads(); // the previous tile has been consumed
-        for (int m = threadIdx.x; m < JP; m += BLOCK) { // whole warps take each pass
-            const int k0 = gbase + jt * JT + 2 * m;      // glen is a multiple of JT
-            const int j0 = perm[k0], j1 = perm[k0 + 1];
-            const float4 pad = make_float4(-kPairPad, -kPairPad, -kPairPad, 0.0f);
-            const float4 a = j0 >= 0 ? xq[j0] : pad;
-            const float4 b = j1 >= 0 ? xq[j1] : pad;
-            sm.a[m] = make_float4(-a.x, -b.x, -a.y, -b.y);
-            sm.b[m] = make_float2(-a.z, -b.z);
-            Box3 pb = box_empty();
-            if (j0 >= 0)
-                box_add(pb, a.x, a.y, a.z);
-            if (j1 >= 0)
-                box_add(pb, b.x, b.y, b.z);
-            pb = box_warp_reduce(pb); // the 32 entries m of this warp = one segment
-            if ((threadIdx.x & 31) == 0)
-                sm.seg[m >> 5] = pb;
+    const bool stager = threadIdx.x < JP;
+    const int m = threadIdx.x;
+    const float4 pad = make_float4(-kPairPad, -kPairPad, -kPairPad, 0.0f);
+    int pn0 = -1, pn1 = -1; // partner indices of the tile after the one staged next
+    if (stager) {           // tile jt0 staged synchronously (glen is a multiple of JT)
+        const int k0 = gbase + jt0 * JT + 2 * m;
+        const int j0 = perm[k0], j1 = perm[k0 + 1];
+        if (jt0 + 1 < jt1) {
+            pn0 = perm[k0 + JT];
+            pn1 = perm[k0 + JT + 1];
         }
-        __syncthreads();
+        ljc_stage_entry<JT>(sm, 0, m, j0 >= 0 ? xq[j0] : pad, j1 >= 0 ? xq[j1] : pad,
+                            (j0 >= 0) | ((j1 >= 0) << 1));
+    }
+    __syncthreads();
+
+    for (int jt = jt0; jt < jt1; ++jt) {
+        const int cur = (jt - jt0) & 1;
+        const bool next = jt + 1 < jt1; // uniform over the block
+        int vmask = 0;
+        if (stager && next) { // gather tile jt + 1 while this one is swept
+            vmask = (pn0 >= 0) | ((pn1 >= 0) << 1);
+            if (pn0 >= 0)
+                cp_async16(&sm.raw[2 * m], xq + pn0);
+            else
+                sm.raw[2 * m] = pad;
+            if (pn1 >= 0)
+                cp_async16(&sm.raw[2 * m + 1], xq + pn1);
+            else
+                sm.raw[2 * m + 1] = pad;
+            cp_async_commit();
+            if (jt + 2 < jt1) {
+                const int k2 = gbase + (jt + 2) * JT + 2 * m;
+                pn0 = perm[k2];
+                pn1 = perm[k2 + 1];
+            }
+        }
 
         const int tt = tblk[(gbase + jt * JT) >> 8]; // one type per tile
         float4 cst[KI];
@@ -344,9 +409,9 @@ __device__ __forceinline__ void ljc_row_segment(const float4 *__restrict__ xq,
         }
         const bool diag = jt * JT < (r + 1) * ITILE && (jt + 1) * JT > r * ITILE;
         for (int sg = 0; sg < NSEG; ++sg) { // warp-uniform choice per segment
-            const bool lj = rc2_lim > 0.0f && box_gap2(wb, sm.seg[sg]) <= rc2_lim;
-            const float4 *sa = sm.a + 32 * sg;
-            const float2 *sb = sm.b + 32 * sg;
+            const bool lj = rc2_lim > 0.0f && box_gap2(wb, sm.seg[cur][sg]) <= rc2_lim;
+            const float4 *sa = sm.a[cur] + 32 * sg;
+            const float2 *sb = sm.b[cur] + 32 * sg;
             if (lj && diag)
                 ljc_tile_sweep<KI, true>(sa, sb, 32, xi, yi, zi, cst, ax, ay, az);
             else if (lj)
@@ -361,6 +426,12 @@ __device__ __forceinline__ void ljc_row_segment(const float4 *__restrict__ xq,
             two_sum_acc(hy[k], ly[k], fmaf(qq, cy[k].x + cy[k].y, ay[k].x + ay[k].y));
             two_sum_acc(hz[k], lz[k], fmaf(qq, cz[k].x + cz[k].y, az[k].x + az[k].y));
         }
+
+        if (stager && next) { // this thread's copies have landed: stage tile jt + 1
+            cp_async_wait_own();
+            ljc_stage_entry<JT>(sm, cur ^ 1, m, sm.raw[2 * m], sm.raw[2 * m + 1], vmask);
+        }
+        __syncthreads(); // tile jt + 1 staged; tile jt's buffer free again
     }
 
 #pragma unroll
