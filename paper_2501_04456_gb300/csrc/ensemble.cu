@@ -87,7 +87,22 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
 {
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
-    const long long step = *a.step;
+    // the step counter as in k_integrate: read by thread 0 before the CTA's
+    // one barrier, the CTA counted in right after, the last one advances it
+    __shared__ long long s_step;
+    if (threadIdx.x == 0)
+        s_step = *a.step;
+    __syncthreads();
+    const long long step = s_step;
+    if (DO_A && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done, 1u);
+        if (prev == gridDim.x - 1) {
+            *a.step = step + 1;
+            *a.done = 0u;
+            __threadfence();
+        }
+    }
     const int i0 = blockIdx.x * blockDim.x;
     if (DO_A) {
         // spring radii of step + 1 for every (droplet, type), spread over the
@@ -146,18 +161,6 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
         }
         advance_particle<MODE>(i, n, (uint32_t)li, tc, D.integrator, 0.5f * (float)D.dt, D.seed,
                                step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags);
-    }
-    if (DO_A) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(a.done, 1u);
-            if (prev == gridDim.x - 1) {
-                *a.step = step + 1;
-                *a.done = 0u;
-                __threadfence();
-            }
-        }
     }
 }
 

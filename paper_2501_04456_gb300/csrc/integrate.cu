@@ -26,7 +26,10 @@
 // the external forces at t = step*dt, and applies the B half kick and/or the
 // BAOA part of the next step.  The step counter lives in device memory and is
 // advanced by the last CTA to finish, so a captured CUDA graph replays without
-// parameter updates.
+// parameter updates: thread 0 of every CTA reads it into shared memory before
+// the CTA's one barrier and counts the CTA in right after, so the CTA that
+// counts last -- every CTA has the step by then -- advances it, and threads
+// then run to completion without waiting for one another.
 #include "npsim_internal.cuh"
 
 namespace npsim {
@@ -38,15 +41,27 @@ __global__ void __launch_bounds__(256, 6)
 k_integrate(IntArgs a, StepParams p)
 {
     __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
-    const long long step = *a.step; // positions are x_step at t = step * dt
+    __shared__ long long s_step;
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    if (threadIdx.x == 0)
+        s_step = *a.step;
     if (threadIdx.x < NPSIM_MAX_TYPES)
         s_tc[threadIdx.x] = p.tc[threadIdx.x];
+    __syncthreads();
+    const long long step = s_step; // positions are x_step at t = step * dt
+    if (DO_A && threadIdx.x == 0) { // this CTA has the step: count it in
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done, 1u);
+        if (prev == gridDim.x - 1) { // the last: advance the step
+            *a.step = step + 1;
+            *a.done = 0u;
+            __threadfence();
+        }
+    }
     if (DO_A && blockIdx.x == 0 && threadIdx.x < p.n_types) // spring radius of step + 1
         a.spring[((step + 1) & 1) * NPSIM_MAX_TYPES + threadIdx.x] =
             spring_entry(p.R0, p.k_evap, p.dt, step + 1, p.tc[threadIdx.x].half_sigma);
-    __syncthreads();
 
     const int n = p.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,21 +120,6 @@ k_integrate(IntArgs a, StepParams p)
         advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
                                step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags,
                                a.x_ref, a.nbr_gate, a.half_skin2);
-    }
-
-    if (DO_A) {
-        // The last CTA to finish advances the step counter: every CTA has read
-        // it by the time it counts itself done.
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(a.done, 1u);
-            if (prev == gridDim.x - 1) {
-                *a.step = step + 1;
-                *a.done = 0u;
-                __threadfence();
-            }
-        }
     }
 }
 
