@@ -87,6 +87,25 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
 {
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // this thread's state first (in flight during the barrier below)
+    int d = 0, ti = 0;
+    float4 xh = make_float4(0.f, 0.f, 0.f, 0.f);
+    float lx = 0.f, ly = 0.f, lz = 0.f;
+    float v[3] = {0.f, 0.f, 0.f};
+    if (i < n_total) {
+        d = a.drop_of[i];
+        ti = a.typ[i];
+        xh = a.xq[i];
+        lx = a.x_lo[i];
+        ly = a.x_lo[n_total + i];
+        lz = a.x_lo[2 * n_total + i];
+        if (MODE != MODE_FORCES) {
+            v[0] = a.v[i];
+            v[1] = a.v[n_total + i];
+            v[2] = a.v[2 * n_total + i];
+        }
+    }
     // the step counter as in k_integrate: read by thread 0 before the CTA's
     // one barrier, the CTA counted in right after, the last one advances it
     __shared__ long long s_step;
@@ -103,7 +122,6 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
             __threadfence();
         }
     }
-    const int i0 = blockIdx.x * blockDim.x;
     if (DO_A) {
         // spring radii of step + 1 for every (droplet, type), spread over the
         // first CTAs of the launch (one entry per thread)
@@ -117,16 +135,11 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
     }
     const float4 *spring = a.spring + (size_t)(step & 1) * n_drops * NPSIM_MAX_TYPES;
 
-    const int i = i0 + threadIdx.x;
     if (i < n_total) {
         const int n = n_total;
-        const int d = a.drop_of[i];
         const EnsDrop &D = a.drops[d];
         const int li = i - D.offset;
-        const int ti = a.typ[i];
         const TypeCoef tc = D.tc[ti];
-        const float4 xh = a.xq[i];
-        const float lx = a.x_lo[i], ly = a.x_lo[n + i], lz = a.x_lo[2 * n + i];
         float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
         if (ASSEMBLE) {
             if (a.slots) {
@@ -160,7 +173,7 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
             }
         }
         advance_particle<MODE>(i, n, (uint32_t)li, tc, D.integrator, 0.5f * (float)D.dt, D.seed,
-                               step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags);
+                               step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq, a.flags);
     }
 }
 

@@ -37,13 +37,39 @@ namespace npsim {
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 6)
+__global__ void __launch_bounds__(256, 5)
 k_integrate(IntArgs a, StepParams p)
 {
     __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
     __shared__ long long s_step;
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    const int n = p.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // this thread's state first: its loads do not depend on the step, so they
+    // are in flight while the CTA waits for the counter at the barrier
+    int ti = 0;
+    float4 xh = make_float4(0.f, 0.f, 0.f, 0.f);
+    float lx = 0.f, ly = 0.f, lz = 0.f;
+    float v[3] = {0.f, 0.f, 0.f};
+    float4 flj0 = make_float4(0.f, 0.f, 0.f, 0.f), flj1 = flj0;
+    if (i < n) {
+        ti = a.typ[i];
+        xh = a.xq[i];
+        lx = a.x_lo[i];
+        ly = a.x_lo[n + i];
+        lz = a.x_lo[2 * n + i];
+        if (MODE != MODE_FORCES) {
+            v[0] = a.v[i];
+            v[1] = a.v[n + i];
+            v[2] = a.v[2 * n + i];
+        }
+        if (ASSEMBLE && a.F_lj) {
+            const float4 *r = reinterpret_cast<const float4 *>(a.F_lj + 8 * (size_t)i);
+            flj0 = r[0]; // (hx, hy, hz, lx)
+            flj1 = r[1]; // (ly, lz, -, -)
+        }
+    }
     if (threadIdx.x == 0)
         s_step = *a.step;
     if (threadIdx.x < NPSIM_MAX_TYPES)
@@ -63,15 +89,10 @@ k_integrate(IntArgs a, StepParams p)
         a.spring[((step + 1) & 1) * NPSIM_MAX_TYPES + threadIdx.x] =
             spring_entry(p.R0, p.k_evap, p.dt, step + 1, p.tc[threadIdx.x].half_sigma);
 
-    const int n = p.n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float4 *spring = a.spring + (step & 1) * NPSIM_MAX_TYPES;
 
     if (i < n) {
-        const int ti = a.typ[i];
         const TypeCoef &tc = s_tc[ti];
-        float4 xh = a.xq[i];
-        float lx = a.x_lo[i], ly = a.x_lo[n + i], lz = a.x_lo[2 * n + i];
         float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
         if (ASSEMBLE) {
             const int pos = a.row_pos ? a.row_pos[i] : i;
@@ -95,11 +116,9 @@ k_integrate(IntArgs a, StepParams p)
                 }
             }
             if (a.F_lj) {
-                const float4 *r = reinterpret_cast<const float4 *>(a.F_lj + 8 * (size_t)i);
-                const float4 r0 = r[0], r1 = r[1]; // (hx, hy, hz, lx) (ly, lz, -, -)
-                df_add_df(Fh[0], Fl[0], r0.x, r0.w);
-                df_add_df(Fh[1], Fl[1], r0.y, r1.x);
-                df_add_df(Fh[2], Fl[2], r0.z, r1.y);
+                df_add_df(Fh[0], Fl[0], flj0.x, flj0.w);
+                df_add_df(Fh[1], Fl[1], flj0.y, flj1.x);
+                df_add_df(Fh[2], Fl[2], flj0.z, flj1.y);
             }
             if (a.ext_on) {
                 float ex, ey, ez;
@@ -118,8 +137,8 @@ k_integrate(IntArgs a, StepParams p)
         }
 
         advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
-                               step, xh, lx, ly, lz, Fh, Fl, a.x_lo, a.v, a.F, a.xq, a.flags,
-                               a.x_ref, a.nbr_gate, a.half_skin2);
+                               step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq,
+                               a.flags, a.x_ref, a.nbr_gate, a.half_skin2);
     }
 }
 

@@ -723,8 +723,9 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
                                                  const TypeCoef &tc, int integrator, float hdt,
                                                  uint64_t seed, long long step, const float4 &xh,
                                                  float lx, float ly, float lz, const float Fh[3],
-                                                 const float Fl[3], float *x_lo, float *v_,
-                                                 float *F, float4 *xq, int *flags,
+                                                 const float Fl[3], const float (&v0)[3],
+                                                 float *x_lo, float *v_, float *F, float4 *xq,
+                                                 int *flags,
                                                  const float4 *x_ref = nullptr,
                                                  int *nbr_gate = nullptr, float half_skin2 = 0.f)
 {
@@ -741,7 +742,7 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
         return;
     const float f[3] = {__fadd_rn(Fh[0], Fl[0]), __fadd_rn(Fh[1], Fl[1]),
                         __fadd_rn(Fh[2], Fl[2])};
-    float v[3] = {v_[i], v_[n + i], v_[2 * n + i]};
+    float v[3] = {v0[0], v0[1], v0[2]}; // v_ at i, read by the caller
     const bool baoab = integrator == 0;
     if (DO_B && baoab) {
 #pragma unroll
