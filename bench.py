@@ -315,16 +315,16 @@ INT_BYTES_BA = 16 + 12 + 12 + 4 + 16 + 12 + 12
 INT_BYTES_B = 16 + 12 + 12 + 4 + 24 + 12
 # Cell list.  Per rebuild and NP: zero/hash (read 16, write key + rank 8),
 # scatter (key, rank, start, arrival slot: 16), in-cell order (arrival slot, key,
-# cell range, sorted: 20), gather (sorted 4, position 16, type 4, record written
-# 16), list build (own record 16, sorted index 4, count 4, build position 16,
-# 4 per list entry); per rebuild and cell: count reset and three scan passes
-# (20).  Per step and NP, the list LJ forces: sorted index 4, current position
-# 16, type record 16, count 4, 4 per list entry, force record 24 (stored as a
-# 32-byte sector, the padding not counted; partner positions are re-reads of
-# records already counted).
-CELL_BUILD_BYTES_NP = 24 + 16 + 20 + 40 + 40
+# cell range, sorted, cell-ordered position: 24), gather (sorted 4, position 16,
+# type 4, record written 16), list build (own record 16, sorted index 4, count
+# 4, build position 16, 4 per list entry); per rebuild and cell: count reset
+# and three scan passes (20).  Per step and NP, the list LJ forces (one thread
+# per particle): current position 16, type 4, count 4, 4 per list entry, force
+# record 24 (stored as a 32-byte sector, the padding not counted; partner
+# positions are re-reads of records already counted).
+CELL_BUILD_BYTES_NP = 24 + 16 + 24 + 40 + 40
 CELL_BUILD_BYTES_CELL = 20
-LIST_LJ_BYTES_NP = 4 + 16 + 16 + 4 + 24
+LIST_LJ_BYTES_NP = 16 + 4 + 4 + 24
 
 
 def _hbm_peak():
