@@ -324,7 +324,7 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
 // are near one another).  An NP whose list overflowed sums over the 27 cells
 // of that build instead (a superset of its list).  Writes one 32-byte (hi x,
 // y, z, lo x, y, z, 0, 0) record per NP and closes the rebuild gate.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
          const int *__restrict__ pos, const float4 *__restrict__ sxq,
          const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
@@ -358,28 +358,42 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
             two_sum_acc(hz, lz, f * dz);
         }
     };
+    // List entries are read four at a time, one block ahead of their use (rows
+    // below cap exist whatever the count), so each block's partner positions
+    // are gathered as soon as the count is known; the pairs are summed in
+    // list order.  Entries are index << 3 | type (index < 2^29).
+    unsigned e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        e[u] = u < cap ? nbr[(size_t)u * n + i] : 0u;
     const int cnt = nnbr[i];
     if (cnt <= cap) {
-        // four list entries, then their four positions, in flight at once; the
-        // pairs are still summed in list order
         int k = 0;
         for (; k + 4 <= cnt; k += 4) {
-            unsigned e[4]; // index < 2^29, type < 8
             float4 pj[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                e[u] = nbr[(size_t)(k + u) * n + i];
+            unsigned en[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 pj[u] = xq[e[u] >> 3];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
+                en[u] = k + 4 + u < cap ? nbr[(size_t)(k + 4 + u) * n + i] : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
                 pair(pj[u], (int)(e[u] & 7u));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                e[u] = en[u];
         }
-        for (; k < cnt; ++k) {
-            const unsigned e = nbr[(size_t)k * n + i];
-            pair(xq[e >> 3], (int)(e & 7u));
-        }
+        float4 pj[4]; // the last cnt - k < 4 entries
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k + u < cnt)
+                pj[u] = xq[e[u] >> 3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k + u < cnt)
+                pair(pj[u], (int)(e[u] & 7u));
     } else {
         const int p = pos[i];
         const float4 pb = sxq[p]; // cells of the build
