@@ -2,7 +2,7 @@
 // parameters to the statistics of the final aggregate (fractal dimension and
 // RDF), trained and evaluated on the GPU by the BF16 tcgen05 kernels of
 // mlp.cu.  The paper has no learned component; the plain simulation is the
-// surrogate's fallback and the judge of its error.
+// surrogate's fallback and the measure of its error.
 //
 // Network: n_in inputs (padded to 16) -> n_layers hidden layers of width H
 // with SiLU -> n_out outputs (padded to a multiple of 16).  Weights and
