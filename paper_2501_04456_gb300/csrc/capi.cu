@@ -1732,8 +1732,9 @@ struct npsim_ens {
     int *perm = nullptr, *tblk = nullptr, *row_pos = nullptr; // type-grouped order
     EnsDrop *drops = nullptr;
     PairTab *tabs = nullptr;
-    long long *unit0 = nullptr;
-    float *slots = nullptr;
+    long long *item0 = nullptr;  // work-item prefix per droplet (n_drops + 1)
+    unsigned *d_work = nullptr;  // work-item counters of the all-pairs launch
+    float *slots = nullptr;      // one [6][itile] slot per work item
     long long *d_step = nullptr;
     float4 *d_spring = nullptr; // [2][D][NPSIM_MAX_TYPES]
     int *d_flags = nullptr;
@@ -1741,6 +1742,8 @@ struct npsim_ens {
 
     int shape = 0;
     StreamK sk{};
+    int chunk = 1;          // j-tiles per work item
+    long long n_items = 0;  // work items of one all-pairs launch
     std::map<int, cudaGraphExec_t> graphs;
     int64_t step = 0;
 
@@ -1760,7 +1763,8 @@ struct npsim_ens {
         dfree(row_pos);
         dfree(drops);
         dfree(tabs);
-        dfree(unit0);
+        dfree(item0);
+        dfree(d_work);
         dfree(slots);
         dfree(d_step);
         dfree(d_spring);
@@ -1773,46 +1777,60 @@ struct npsim_ens {
 
 namespace {
 
-// Droplet geometry for launch shape `shape`: rows and (i-tile x j-tile) units of
-// every droplet laid end to end.  Returns the total number of units.
-long long ens_geometry(npsim_ens *e, int shape, std::vector<long long> &unit0, long long *rows)
+// Work items per CTA that the chunk size aims at: enough that the last items
+// drawn (the only imbalance of dynamic scheduling) are short, few enough that
+// the per-item slots stay small.
+constexpr int kItemsPerCta = 32;
+
+// Droplet geometry for launch shape `shape` on grid_target CTAs: row tiles and
+// j-tiles of every droplet, the chunk size (j-tiles per work item) and the
+// work items laid end to end (item0).  Returns the number of items; *chunk_out
+// receives the chunk size.
+long long ens_geometry(npsim_ens *e, int shape, int grid_target, std::vector<long long> &item0,
+                       int *chunk_out)
 {
     const ApConfig c = ens_config(shape);
     const int itile = c.block * c.ki;
-    long long u = 0, r = 0;
-    unit0.assign(e->D + 1, 0);
+    long long W = 0;
     for (int d = 0; d < e->D; ++d) {
         EnsDrop &g = e->h_drops[d];
         g.n_it = (g.npad + itile - 1) / itile;
         g.n_jt = g.npad / c.jt; // npad is a multiple of 256, jt divides 256
-        g.row0 = (int)r;
-        g.unit0 = u;
-        unit0[d] = u;
-        u += (long long)g.n_it * g.n_jt;
-        r += g.n_it;
+        W += (long long)g.n_it * g.n_jt;
     }
-    unit0[e->D] = u;
-    if (rows)
-        *rows = r;
-    return u;
+    const long long target = (long long)std::max(grid_target, 1) * kItemsPerCta;
+    const int chunk = (int)std::max<long long>(1, (W + target - 1) / target);
+    long long it = 0;
+    item0.assign(e->D + 1, 0);
+    for (int d = 0; d < e->D; ++d) {
+        EnsDrop &g = e->h_drops[d];
+        g.n_ch = (g.n_jt + chunk - 1) / chunk;
+        g.item0 = it;
+        item0[d] = it;
+        it += (long long)g.n_it * g.n_ch;
+    }
+    item0[e->D] = it;
+    if (chunk_out)
+        *chunk_out = chunk;
+    return it;
 }
 
-void ens_streamk(long long W, const ApConfig &c, int grid_target, StreamK &sk)
+void ens_streamk(long long n_items, const ApConfig &c, int grid_target, StreamK &sk)
 {
     sk.itile = c.block * c.ki;
     sk.jtile = c.jt;
     sk.n_it = 0;
     sk.n_jt = 0;
-    sk.W = W;
-    sk.grid = (int)std::min<long long>(std::max(grid_target, 1), W);
+    sk.W = n_items;
+    sk.grid = (int)std::min<long long>(std::max(grid_target, 1), n_items);
     sk.pad_ = 0;
 }
 
-int ens_upload_geometry(npsim_ens *e, const std::vector<long long> &unit0)
+int ens_upload_geometry(npsim_ens *e, const std::vector<long long> &item0)
 {
     NP_CUDA(cudaMemcpyAsync(e->drops, e->h_drops.data(), sizeof(EnsDrop) * e->D,
                             cudaMemcpyHostToDevice, e->user));
-    NP_CUDA(cudaMemcpyAsync(e->unit0, unit0.data(), sizeof(long long) * unit0.size(),
+    NP_CUDA(cudaMemcpyAsync(e->item0, item0.data(), sizeof(long long) * item0.size(),
                             cudaMemcpyHostToDevice, e->user));
     NP_CUDA(cudaStreamSynchronize(e->user));
     return NPSIM_OK;
@@ -1825,9 +1843,12 @@ EnsAllpairsArgs ens_ap_args(npsim_ens *e, float *slots)
     a.perm = e->perm;
     a.tblk = e->tblk;
     a.drops = e->drops;
-    a.unit0 = e->unit0;
+    a.item0 = e->item0;
     a.tabs = e->tabs;
     a.n_drops = e->D;
+    a.chunk = e->chunk;
+    a.n_items = e->n_items;
+    a.work = e->d_work;
     a.slots = slots;
     return a;
 }
@@ -1911,7 +1932,7 @@ int ens_autotune(npsim_ens *e)
 {
     const int nc = ens_num_configs();
     const char *env = getenv("NPSIM_ENS_SHAPE");
-    std::vector<long long> unit0;
+    std::vector<long long> item0;
     int best = -1;
     if (env) {
         const int idx = atoi(env);
@@ -1924,11 +1945,9 @@ int ens_autotune(npsim_ens *e)
             const int occ = ens_occupancy(c);
             if (occ <= 0)
                 continue;
-            long long rows = 0;
-            const long long W = ens_geometry(e, c, unit0, &rows);
-            StreamK sk;
-            ens_streamk(W, ens_config(c), occ * e->sms, sk);
-            need = std::max(need, (size_t)(rows + sk.grid) * 6 * (size_t)sk.itile);
+            const long long items = ens_geometry(e, c, occ * e->sms, item0, nullptr);
+            const ApConfig cc = ens_config(c);
+            need = std::max(need, (size_t)items * 6 * (size_t)(cc.block * cc.ki));
         }
         float *tmp = nullptr;
         NP_CUDA(dalloc(&tmp, need));
@@ -1940,14 +1959,14 @@ int ens_autotune(npsim_ens *e)
             const int occ = ens_occupancy(c);
             if (occ <= 0)
                 continue;
-            const long long W = ens_geometry(e, c, unit0, nullptr);
-            int rc = ens_upload_geometry(e, unit0);
+            e->n_items = ens_geometry(e, c, occ * e->sms, item0, &e->chunk);
+            int rc = ens_upload_geometry(e, item0);
             if (rc) {
                 cudaFree(tmp);
                 return rc;
             }
             StreamK sk;
-            ens_streamk(W, ens_config(c), occ * e->sms, sk);
+            ens_streamk(e->n_items, ens_config(c), occ * e->sms, sk);
             e->shape = c;
             if (launch_ens_allpairs(c, sk, ens_ap_args(e, tmp), e->user) != cudaSuccess)
                 continue;
@@ -1974,13 +1993,13 @@ int ens_autotune(npsim_ens *e)
             best = 0;
     }
     e->shape = best;
-    long long rows = 0;
-    const long long W = ens_geometry(e, best, unit0, &rows);
-    ens_streamk(W, ens_config(best), std::max(1, ens_occupancy(best)) * e->sms, e->sk);
-    int rc = ens_upload_geometry(e, unit0);
+    const int grid_target = std::max(1, ens_occupancy(best)) * e->sms;
+    e->n_items = ens_geometry(e, best, grid_target, item0, &e->chunk);
+    ens_streamk(e->n_items, ens_config(best), grid_target, e->sk);
+    int rc = ens_upload_geometry(e, item0);
     if (rc)
         return rc;
-    NP_CUDA(dalloc(&e->slots, (size_t)(rows + e->sk.grid) * 6 * (size_t)e->sk.itile));
+    NP_CUDA(dalloc(&e->slots, (size_t)e->n_items * 6 * (size_t)e->sk.itile));
     return NPSIM_OK;
 }
 
@@ -2135,7 +2154,9 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
     EBAIL(dalloc(&e->drop_of, (size_t)total));
     EBAIL(dalloc(&e->drops, (size_t)n_drops));
     EBAIL(dalloc(&e->tabs, (size_t)n_drops));
-    EBAIL(dalloc(&e->unit0, (size_t)n_drops + 1));
+    EBAIL(dalloc(&e->item0, (size_t)n_drops + 1));
+    EBAIL(dalloc(&e->d_work, 2));
+    EBAIL(cudaMemset(e->d_work, 0, 2 * sizeof(unsigned)));
     EBAIL(dalloc(&e->d_step, 1));
     EBAIL(dalloc(&e->d_spring, (size_t)2 * n_drops * NPSIM_MAX_TYPES));
     EBAIL(dalloc(&e->d_flags, 1));

@@ -5,11 +5,14 @@
 // charges, LJ table, radius law, seed).  Particles of all droplets are stored
 // back to back (structure of arrays over the concatenation).  The all-pairs
 // work of droplet d is a rectangle of n_it(d) x n_jt(d) (i-tile x j-tile)
-// units; the rectangles are laid end to end and the resulting unit sequence is
-// split evenly over the CTAs (stream-K), so a 512-NP droplet and a 32768-NP
-// droplet share the GPU in proportion to their N^2 work within one launch.
-// A CTA writes one compensated (hi, lo) float32 partial per (global row, CTA)
-// segment into slot row + CTA; the integrator sums a row's partials in CTA order.
+// units; every row tile is cut into work items of at most `chunk` j-tiles,
+// the items of all droplets are numbered end to end, and the CTAs of one
+// launch draw items from a device counter until none are left, so a 512-NP
+// and a 32768-NP droplet share the GPU in proportion to their work within one
+// launch and items rich in LJ segments (which cost more than Coulomb-only
+// ones) are balanced as they run.  An item writes one compensated (hi, lo)
+// float32 partial per row into its own slot; the integrator sums a row's items
+// in item order, so the result does not depend on which CTA ran which item.
 //
 // Inside the ensemble each droplet's particles are listed in a type-grouped
 // order (each type's group padded to 256 positions), so every j-tile holds
@@ -26,14 +29,14 @@ namespace npsim {
 
 namespace {
 
-// Droplet whose unit range contains global unit u (unit0 has n_drops + 1 entries).
-__device__ __forceinline__ int drop_of_unit(const long long *__restrict__ unit0, int n_drops,
+// Droplet whose item range contains item u (item0 has n_drops + 1 entries).
+__device__ __forceinline__ int drop_of_item(const long long *__restrict__ item0, int n_drops,
                                             long long u)
 {
     int lo = 0, hi = n_drops - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (unit0[mid] <= u)
+        if (item0[mid] <= u)
             lo = mid;
         else
             hi = mid - 1;
@@ -46,38 +49,46 @@ __device__ __forceinline__ int drop_of_unit(const long long *__restrict__ unit0,
 // without spills.
 template <int BLOCK, int KI, int JT>
 __global__ void __launch_bounds__(BLOCK, KI == 1 ? 1024 / BLOCK : 512 / BLOCK)
-k_ens_ljc(const float4 *__restrict__ xq, const int *__restrict__ perm,
-          const int *__restrict__ tblk, const EnsDrop *__restrict__ drops,
-          const long long *__restrict__ unit0, const PairTab *__restrict__ tabs, int n_drops,
-          StreamK sk, float *__restrict__ slots)
+k_ens_ljc(EnsAllpairsArgs a)
 {
     constexpr int ITILE = BLOCK * KI;
     __shared__ LjcSmem<JT> sm;
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
-
-    const int c = blockIdx.x;
-    const long long p_end = sk_begin(sk, c + 1);
-    long long p = sk_begin(sk, c);
+    __shared__ long long s_item;
     int cur = -1;
 
-    while (p < p_end) {
-        const int d = drop_of_unit(unit0, n_drops, p);
-        const EnsDrop &D = drops[d];
-        if (d != cur) {
-            __syncthreads(); // every thread is done with the previous table
+    for (;;) {
+        __syncthreads(); // every thread has read s_item and finished the last item
+        if (threadIdx.x == 0)
+            s_item = (long long)atomicAdd(a.work, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= a.n_items)
+            break;
+        const int d = drop_of_item(a.item0, a.n_drops, item);
+        const EnsDrop &D = a.drops[d];
+        if (d != cur) { // ordered before use by the staging barrier
             for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += BLOCK)
-                s_tab[k] = tabs[d].e[k]; // ordered before use by the tile barrier
+                s_tab[k] = a.tabs[d].e[k];
             cur = d;
         }
-        const long long lu = p - D.unit0;
-        const int r = (int)(lu / D.n_jt);
-        const int jt0 = (int)(lu - (long long)r * D.n_jt);
-        const long long left = min(p_end, D.unit0 + (long long)D.n_it * D.n_jt) - p;
-        const int jt1 = (int)min((long long)D.n_jt, (long long)jt0 + left);
-        ljc_row_segment<BLOCK, KI, JT>(xq, perm, tblk, D.gpos0, D.npad, s_tab, D.rc2_lim,
+        const int li = (int)(item - D.item0);
+        const int r = li / D.n_ch;
+        const int jt0 = (li - r * D.n_ch) * a.chunk;
+        const int jt1 = min(D.n_jt, jt0 + a.chunk);
+        ljc_row_segment<BLOCK, KI, JT>(a.xq, a.perm, a.tblk, D.gpos0, D.npad, s_tab, D.rc2_lim,
                                        D.has_coul, r, jt0, jt1, sm,
-                                       slots + (size_t)(D.row0 + r + c) * 6 * ITILE);
-        p += jt1 - jt0;
+                                       a.slots + (size_t)item * 6 * ITILE);
+    }
+    // the last CTA out resets the counters for the next launch (every CTA has
+    // drawn its last item by the time it counts itself out)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.work + 1, 1u) == gridDim.x - 1) {
+            a.work[0] = 0u;
+            a.work[1] = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -146,11 +157,9 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 const int lpos = a.row_pos[i] - D.gpos0; // row in the droplet's grouped order
                 const int r = lpos / sk.itile;
                 const int idx = lpos - r * sk.itile;
-                const long long u0 = D.unit0 + (long long)r * D.n_jt;
-                const int c0 = sk_cta_of(sk, u0);
-                const int c1 = sk_cta_of(sk, u0 + D.n_jt - 1);
-                for (int c = c0; c <= c1; ++c) {
-                    const float *slot = a.slots + (size_t)(D.row0 + r + c) * 6 * sk.itile + idx;
+                const long long it0 = D.item0 + (long long)r * D.n_ch; // the row's items
+                for (int c = 0; c < D.n_ch; ++c) {
+                    const float *slot = a.slots + (size_t)(it0 + c) * 6 * sk.itile + idx;
 #pragma unroll
                     for (int k = 0; k < 3; ++k)
                         df_add_df(Fh[k], Fl[k], slot[k * sk.itile], slot[(3 + k) * sk.itile]);
@@ -193,8 +202,7 @@ const EEntry kEns[] = {
 template <int B, int K, int J>
 cudaError_t launch_e(const StreamK &sk, const EnsAllpairsArgs &a, cudaStream_t st)
 {
-    k_ens_ljc<B, K, J><<<sk.grid, B, 0, st>>>(a.xq, a.perm, a.tblk, a.drops, a.unit0, a.tabs,
-                                               a.n_drops, sk, a.slots);
+    k_ens_ljc<B, K, J><<<sk.grid, B, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -791,14 +791,16 @@ cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
 // Ensemble of droplets (ensemble.cu).  Each droplet's particles are listed in a
 // type-grouped order (groups padded to 256 positions) at positions [gpos0,
 // gpos0 + npad) of the ensemble's grouped order.  Geometry depends on the
-// launch shape: n_it = ceil(npad / itile), n_jt = npad / jtile; row0 and unit0
-// are prefix sums of n_it and n_it * n_jt over the droplets.
+// launch shape: n_it = ceil(npad / itile) row tiles, n_jt = npad / jtile
+// j-tiles, each row tile cut into n_ch = ceil(n_jt / chunk) work items of at
+// most `chunk` consecutive j-tiles; item0 is the prefix sum of n_it * n_ch
+// over the droplets (item = item0 + row * n_ch + chunk index).
 struct EnsDrop {
-    int offset, n, n_it, n_jt, row0, rot_mode, wall, integrator;
+    int offset, n, n_it, n_jt, n_ch, rot_mode, wall, integrator;
     int gpos0, npad;
     float rc2_lim;  // LJ only between tiles within this squared distance (0: no LJ)
     int has_coul;   // 0: tiles out of LJ range add nothing
-    long long unit0;
+    long long item0;
     uint64_t seed;
     double dt, R0, k_evap, g, omega2;
     TypeCoef tc[NPSIM_MAX_TYPES];
@@ -809,11 +811,13 @@ struct EnsAllpairsArgs {
     const int *perm;        // grouped position -> particle (-1: padding)
     const int *tblk;        // type of each 256-position block
     const EnsDrop *drops;
-    const long long *unit0; // n_drops + 1 entries
+    const long long *item0; // n_drops + 1 entries
     const PairTab *tabs;    // one table per droplet
     int n_drops;
-    int pad_;
-    float *slots;
+    int chunk;              // j-tiles per work item
+    long long n_items;
+    unsigned *work;         // [0] next item, [1] CTAs done (both 0 between launches)
+    float *slots;           // one [6][itile] slot per work item
 };
 
 struct EnsIntArgs {
