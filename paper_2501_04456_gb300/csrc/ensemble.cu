@@ -197,6 +197,7 @@ struct EEntry {
 const EEntry kEns[] = {
     NPSIM_ENS(128, 2, 256), NPSIM_ENS(256, 1, 256), NPSIM_ENS(256, 2, 256),
     NPSIM_ENS(1024, 1, 256), NPSIM_ENS(256, 1, 128), NPSIM_ENS(512, 1, 256),
+    NPSIM_ENS(128, 1, 256), NPSIM_ENS(128, 1, 128),
 };
 
 template <int B, int K, int J>
@@ -231,6 +232,8 @@ cudaError_t launch_ens_allpairs(int idx, const StreamK &sk, const EnsAllpairsArg
     case 3: return launch_e<1024, 1, 256>(sk, a, st);
     case 4: return launch_e<256, 1, 128>(sk, a, st);
     case 5: return launch_e<512, 1, 256>(sk, a, st);
+    case 6: return launch_e<128, 1, 256>(sk, a, st);
+    case 7: return launch_e<128, 1, 128>(sk, a, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -38,7 +38,7 @@ def test_ensemble_forces_match_oracle(P, drops):
 def test_ensemble_every_shape(P, drops, monkeypatch):
     sc, x, v, types = drops[2]
     ref = [oracle.total_forces(s, xx, tt, 0.0) for s, xx, _, tt in drops]
-    for idx in range(6):
+    for idx in range(8):  # the ensemble kernel's eight launch shapes
         monkeypatch.setenv("NPSIM_ENS_SHAPE", str(idx))
         with P.Ensemble(drops) as ens:
             assert ens.config()["index"] == idx
