@@ -99,6 +99,8 @@ int check_device(int *sms)
 std::mutex g_tune_mu;
 // (n, lj, grouped length, skip_neutral) -> launch shape
 std::map<std::array<long long, 4>, int> g_tune_cache;
+// ensembles: (grouped length, LJ on, Coulomb on) of every droplet -> launch shape
+std::map<std::vector<long long>, int> g_ens_tune_cache;
 
 void fill_streamk(StreamK &sk, int n, const ApConfig &c, int grid_target)
 {
@@ -1939,6 +1941,22 @@ int ens_autotune(npsim_ens *e)
         if (idx >= 0 && idx < nc && ens_occupancy(idx) > 0)
             best = idx;
     }
+    // the same ensemble geometry gets the same shape within a process (so
+    // that repeated runs of one ensemble sum in the same order)
+    std::vector<long long> key;
+    for (int d = 0; d < e->D; ++d) {
+        const EnsDrop &g = e->h_drops[d];
+        key.push_back(((long long)g.npad << 2) | (g.rc2_lim > 0.0f ? 2 : 0) |
+                      (g.has_coul ? 1 : 0));
+    }
+    const bool pinned = best >= 0;
+    if (!pinned) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_ens_tune_cache.find(key);
+        if (it != g_ens_tune_cache.end())
+            best = it->second;
+    }
+    const bool cached = !pinned && best >= 0;
     if (best < 0) {
         size_t need = 0;
         for (int c = 0; c < nc; ++c) {
@@ -1991,6 +2009,10 @@ int ens_autotune(npsim_ens *e)
             return set_err(NPSIM_ERR_CUDA, "ensemble autotune: %s", cudaGetErrorString(ce));
         if (best < 0)
             best = 0;
+    }
+    if (!pinned && !cached) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_ens_tune_cache[key] = best;
     }
     e->shape = best;
     const int grid_target = std::max(1, ens_occupancy(best)) * e->sms;

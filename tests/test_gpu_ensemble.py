@@ -94,3 +94,21 @@ def test_ensemble_large_droplets_sampled(P):
             rms = np.sqrt((F ** 2).sum(1).mean())
             err = np.linalg.norm(F[sel] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
             assert err[keep].max() <= FORCE_TOL, (d, sc.n, float(err.max()))
+
+
+def test_ensemble_runs_are_bit_reproducible(P, drops):
+    """CTAs draw work items in whatever order they reach the counter, but every
+    item writes its own slot and a row's items are summed in item order: two
+    runs of the same ensemble agree bit for bit (and the item counter is reset
+    between launches, or the second run would find no work).  The second
+    ensemble of the same geometry reuses the first one's launch shape."""
+    states, shapes = [], []
+    for _ in range(2):
+        with P.Ensemble(drops) as ens:
+            shapes.append(ens.config()["index"])
+            ens.step(25)
+            states.append([ens.state(d) for d in range(len(drops))])
+    assert shapes[0] == shapes[1]
+    for a, b in zip(*states):
+        for u, w in zip(a[:3], b[:3]):
+            assert np.array_equal(u, w)
