@@ -391,6 +391,11 @@ class Sim:
         s.h, s.n, s.scenario = h, n, scenario
         return s
 
+    @classmethod
+    def load(cls, path, n, scenario=None, stream=None):
+        """Resume a simulation of n NPs from a checkpoint written by save()."""
+        return cls._wrap(npsim_load(path, stream=stream), n, scenario)
+
     def step(self, n_steps=1):
         npsim_step(self.h, n_steps)
 

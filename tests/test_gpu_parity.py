@@ -294,8 +294,7 @@ def test_checkpoint_resume_is_bit_exact(P, tmp_path, which):
     with P.Sim(sc, x, v, types) as b:
         b.step(20)
         b.save(path)
-    h = P.npsim_load(path)
-    c = P.Sim._wrap(h, sc.n, sc)
+    c = P.Sim.load(path, sc.n, sc)
     try:
         _, _, _, st = c.state()
         assert st == 20
