@@ -197,7 +197,8 @@ int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out);
  * if it is the packed Coulomb kernel over partners grouped by charge value, 3
  * if it is the packed LJ + Coulomb kernel over partners grouped by type (0: the
  * scalar kernel).  Any pointer may be NULL.  The environment variable NPSIM_AUTOTUNE=1:<index>
- * forces a shape at npsim_create (NPSIM_AUTOTUNE=0: the first shape). */
+ * forces a shape at npsim_create (NPSIM_AUTOTUNE=0: the first shape); with
+ * NPSIM_AUTOTUNE_LOG set, the autotuners print every candidate's time to stderr. */
 int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j_tile,
                           int *grid, int *index, int *packed);
 

@@ -589,6 +589,7 @@ int autotune(npsim_sim *s)
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
         const bool coul = s->P.coulomb != 0;
+        const bool log = getenv("NPSIM_AUTOTUNE_LOG") != nullptr; // per-shape times to stderr
         for (int c = 0; c < nc; ++c) {
             const int occ = shape_occupancy(s, c, lj);
             if (occ <= 0)
@@ -606,6 +607,11 @@ int autotune(npsim_sim *s)
                 continue;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
+            if (log) {
+                const ApConfig cf = shape_config(c);
+                fprintf(stderr, "npsim autotune n=%d shape %d <%d,%d,%d> grid %d: %.4f ms\n",
+                        s->n, c, cf.block, cf.ki, cf.jt, sk.grid, ms / reps);
+            }
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -1996,6 +2002,11 @@ int ens_autotune(npsim_ens *e)
                 continue;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
+            if (getenv("NPSIM_AUTOTUNE_LOG")) {
+                const ApConfig cf = ens_config(c);
+                fprintf(stderr, "npsim ensemble autotune shape %d <%d,%d,%d> grid %d: %.4f ms\n",
+                        c, cf.block, cf.ki, cf.jt, sk.grid, ms / 2);
+            }
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
