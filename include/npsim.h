@@ -157,6 +157,7 @@ typedef struct {
     int32_t n_scales;
     int32_t pad_;
     int64_t nbox[NPSIM_MAX_SCALES];
+    int64_t n_surf;  /* NPs at the surface: | |x_i| - R(t) | < r_i (Sec. 1, Sec. 2.2 (iv)) */
 } npsim_stats_t;
 
 /*

@@ -95,6 +95,8 @@ def _declare(lib):
     lib.or_radial_hist.argtypes = [C.c_int64, _d, C.c_double, C.c_int, C.c_double,
                                    i64p, _d]
     lib.or_rg.argtypes = [C.c_int64, _d, C.c_double, C.c_double, _d, _d, _d]
+    lib.or_surface_count.argtypes = [C.c_int64, _d, i32p, _d, C.c_double]
+    lib.or_surface_count.restype = C.c_int64
     lib.or_boxcount.argtypes = [C.c_int64, _d, C.c_double, C.c_int, i64p]
     lib.or_boxcount_df.argtypes = [C.c_int64, _d, C.c_double, C.c_double, C.c_int,
                                    i64p, _d]
@@ -294,6 +296,16 @@ def radial_concentration(x, r_max, n_bins, R):
     lib.or_radial_hist(x.shape[0], _ptr(x, C.c_double), r_max, n_bins, R,
                        _ptr(c, C.c_int64), _ptr(Cc, C.c_double))
     return c, Cc
+
+
+def surface_count(x, types, sigma, R):
+    """N_surf: NPs with | |x_i| - R | < sigma_i / 2 (Sec. 1, Sec. 2.2 step iv)."""
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    t = _i32(types)
+    s = _f64(sigma)
+    return int(lib.or_surface_count(x.shape[0], _ptr(x, C.c_double), _ptr(t, C.c_int32),
+                                    _ptr(s, C.c_double), R))
 
 
 def rg(x, d_mean, k_f=K_F):

@@ -31,6 +31,7 @@
  *   or_boxcount ............. pinned (lattices of dimension 1, 2, 3)
  *   or_rg ................... pinned (solid ball R_g, fractal equation)
  *   or_radial_hist .......... pinned (uniform ball -> flat profile)
+ *   or_surface_count ........ pinned (hand-placed NPs on both sides of the band edges)
  */
 #include <math.h>
 #include <stdint.h>
@@ -385,6 +386,23 @@ void or_rdf(int64_t n, const double *x, double r_max, int n_bins, double R,
         double dV = 4.0 / 3.0 * pi * (r1 * r1 * r1 - r0 * r0 * r0);
         g[b] = ((double)counts[b] / (double)n) / ((double)(n - 1) * dV / V);
     }
+}
+
+/* N_surf, the number of NPs at the droplet surface (Sec. 1, where the
+ * scattered intensity grows with N_surf^2): NP i counts when its centre lies in
+ * the band (-r_i, r_i) about the surface of radius R, the band of Sec. 2.2
+ * step (iv):  | |x_i| - R | < r_i,  r_i = sigma_{type i} / 2.               */
+int64_t or_surface_count(int64_t n, const double *x, const int32_t *type, const double *sigma,
+                         double R)
+{
+    int64_t count = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = sqrt(x[3 * i] * x[3 * i] + x[3 * i + 1] * x[3 * i + 1] +
+                        x[3 * i + 2] * x[3 * i + 2]);
+        if (fabs(r - R) < 0.5 * sigma[type[i]])
+            ++count;
+    }
+    return count;
 }
 
 /* Radial concentration about the droplet centre, Sec. 3.2:

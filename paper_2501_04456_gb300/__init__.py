@@ -64,7 +64,7 @@ class npsim_stats_t(C.Structure):
     _fields_ = [("R", C.c_double), ("d_mean", C.c_double), ("Rg", C.c_double),
                 ("Df_rg", C.c_double), ("Df_box", C.c_double), ("center", C.c_double * 3),
                 ("n_scales", C.c_int32), ("pad_", C.c_int32),
-                ("nbox", C.c_int64 * MAX_SCALES)]
+                ("nbox", C.c_int64 * MAX_SCALES), ("n_surf", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -282,7 +282,7 @@ def npsim_stats(h, r_max=10.0, n_bins=128, radial_bins=0, boxcount=True,
     ns = out.n_scales
     return {"R": out.R, "d_mean": out.d_mean, "Rg": out.Rg, "Df_rg": out.Df_rg,
             "Df_box": out.Df_box, "center": np.array(out.center[:]),
-            "nbox": np.array(out.nbox[:ns], np.int64),
+            "nbox": np.array(out.nbox[:ns], np.int64), "n_surf": int(out.n_surf),
             "rdf_counts": counts[:n_bins], "rdf_g": g[:n_bins],
             "radial_counts": rc_[:radial_bins], "radial_c": rcc[:radial_bins]}
 

@@ -209,6 +209,7 @@ struct npsim_sim {
     unsigned long long *s_table = nullptr;
     unsigned long long s_table_size = 0;
     int *s_count = nullptr;
+    unsigned long long *s_surf = nullptr; // N_surf counter
 
     ~npsim_sim()
     {
@@ -254,6 +255,7 @@ struct npsim_sim {
         dfree(s_vec);
         dfree(s_table);
         dfree(s_count);
+        dfree(s_surf);
         if (cap)
             cudaStreamDestroy(cap);
     }
@@ -1360,6 +1362,7 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
         NP_CUDA(dalloc(&s->s_part, 3 * (size_t)nblk));
         NP_CUDA(dalloc(&s->s_vec, 8));
         NP_CUDA(dalloc(&s->s_count, 1));
+        NP_CUDA(dalloc(&s->s_surf, 1));
     }
     int rc0 = positions_f64(s);
     if (rc0)
@@ -1436,6 +1439,17 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
                 radial_c[b] = ((double)h[b] / (double)n) / (dV / V);
             }
         }
+    }
+    // N_surf: NPs in the band (-r_i, r_i) about the surface
+    {
+        SurfHalf hs{};
+        for (int t = 0; t < s->P.n_types; ++t)
+            hs.h[t] = 0.5 * s->types[t].sigma;
+        unsigned long long cnt = 0;
+        NP_CUDA(launch_surface_count(s->x, s->typ, n, R, hs, s->s_surf, st));
+        NP_CUDA(cudaMemcpyAsync(&cnt, s->s_surf, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        NP_CUDA(cudaStreamSynchronize(st));
+        out->n_surf = (int64_t)cnt;
     }
     // centre of mass and radius of gyration (Eqs. r0, Rg), fractal equation (Eq. N)
     NP_CUDA(launch_block_reduce(0, s->x, n, nullptr, s->s_part, st));

@@ -920,6 +920,12 @@ cudaError_t launch_radial_hist(const double *x, int n, double r_max, int n_bins,
                                unsigned long long *hist, cudaStream_t st);
 // mode 0: per-CTA sums of x; 1: sums of |x - c|^2; 2: componentwise minima.
 // part holds 3 doubles per CTA of 256 threads.
+// Half diameter of every type (surface band of N_surf).
+struct SurfHalf {
+    double h[NPSIM_MAX_TYPES];
+};
+cudaError_t launch_surface_count(const double *x, const int *typ, int n, double R,
+                                 const SurfHalf &hs, unsigned long long *count, cudaStream_t st);
 cudaError_t launch_block_reduce(int mode, const double *x, int n, const double *c,
                                 double *part, cudaStream_t st);
 cudaError_t launch_boxcount(const double *x, int n, const double *origin, double eps,

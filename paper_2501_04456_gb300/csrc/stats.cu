@@ -6,6 +6,10 @@
 //    sqrt(dx*dx + dy*dy + dz*dz) and floor(r / dr) rounded one by one (no fused
 //    multiply-add), so integer counts are exact;
 //  * radial histogram of |x| for the concentration C_NPs(r) of Sec. 3.2;
+//  * N_surf, the number of NPs at the droplet surface (Sec. 1: the scattered
+//    intensity grows with N_surf^2), counted as the NPs whose centre lies in
+//    the band (-r_i, r_i) about the surface, | |x_i| - R(t) | < r_i, the band
+//    in which Sec. 2.2 step (iv) applies the interface force;
 //  * per-CTA partial sums (centre of mass, squared deviations) and minima,
 //    finished on the host in CTA order (deterministic);
 //  * box counting: the number of distinct integer triples floor((x - o)/eps)
@@ -117,6 +121,23 @@ k_radial_hist(const double *__restrict__ x, int n, double dr, int n_bins,
         for (int b = threadIdx.x; b < n_bins; b += blockDim.x)
             if (s_h[b])
                 atomicAdd(&hist[b], (unsigned long long)s_h[b]);
+}
+
+// NPs with | |x_i| - R | < half_sigma[type_i] (|x| and the difference in
+// float64, rounded operation by operation as in the radial histogram).
+__global__ void __launch_bounds__(256)
+k_surface_count(const double *__restrict__ x, const int *__restrict__ typ, int n, double R,
+                SurfHalf hs, unsigned long long *__restrict__ count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int in = 0;
+    if (i < n) {
+        const double r = dist_rn(x[i], x[n + i], x[2 * n + i], 0.0, 0.0, 0.0);
+        in = fabs(__dsub_rn(r, R)) < hs.h[typ[i]];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0 && m)
+        atomicAdd(count, (unsigned long long)__popc(m));
 }
 
 // Per-CTA partials: mode 0 -> sum of x (3 values), 1 -> sum of |x - c|^2
@@ -244,6 +265,16 @@ cudaError_t launch_radial_hist(const double *x, int n, double r_max, int n_bins,
     if (e != cudaSuccess)
         return e;
     k_radial_hist<<<(n + 255) / 256, 256, 0, st>>>(x, n, dr, n_bins, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surface_count(const double *x, const int *typ, int n, double R,
+                                 const SurfHalf &hs, unsigned long long *count, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess)
+        return e;
+    k_surface_count<<<(n + 255) / 256, 256, 0, st>>>(x, typ, n, R, hs, count);
     return cudaGetLastError();
 }
 

@@ -384,6 +384,28 @@ def test_stats_parity(P):
     Dfb, nb = oracle.boxcount_df(xg, st["d_mean"], Rg)
     assert np.array_equal(st["nbox"], nb)
     assert st["Df_box"] == pytest.approx(Dfb, rel=1e-10)
+    # the surface band is decided in float64 on both sides, at the library's R
+    sig = [t.sigma for t in sc.types]
+    assert st["n_surf"] == oracle.surface_count(xg, types, sig, st["R"])
+
+
+def test_stats_surface_count_hand_placed(P):
+    """N_surf on the GPU for NPs placed on both sides of both band edges."""
+    ts = [wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=10.0),
+          wl.TypeSpec(sigma=3.0, eps=1.0, mass=27.0, charge=0.0, gamma=1.0 / 9, k_wall=10.0)]
+    cases = [(0, 9.4, 0), (0, 9.6, 1), (0, 10.0, 1), (0, 10.4, 1), (0, 10.6, 0),
+             (1, 8.4, 0), (1, 8.6, 1), (1, 11.4, 1), (1, 11.6, 0), (1, 0.0, 0)]
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((len(cases), 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    ty = np.array([c[0] for c in cases], np.int32)
+    x = u * np.array([c[1] for c in cases])[:, None]
+    sc = wl.Scenario(name="band", types=ts, n=len(cases), R0=10.0, k_evap=0.0,
+                     lj_mode=0, coulomb=False)
+    with P.Sim(sc, x, None, ty) as sim:
+        st = sim.stats(r_max=2.0, n_bins=4, boxcount=False)
+    assert st["R"] == 10.0
+    assert st["n_surf"] == sum(c[2] for c in cases) == 5
 
 
 def test_stats_boxcount_lattice_on_gpu(P):

@@ -583,6 +583,25 @@ def test_radial_concentration_uniform_ball_flat():
         assert abs(Cc[b] - 1) < 5 / math.sqrt(counts[b])
 
 
+def test_surface_count_band_edges():
+    """N_surf counts NP i when | |x_i| - R | < sigma_i / 2: NPs placed just
+    inside and just outside both edges of the band, for two diameters, in random
+    directions (a band of sigma instead of sigma/2, or a one-sided test, fails)."""
+    R = 10.0
+    sigma = np.array([1.0, 3.0])
+    cases = [(0, 9.4, 0), (0, 9.6, 1), (0, 10.0, 1), (0, 10.4, 1), (0, 10.6, 0),
+             (1, 8.4, 0), (1, 8.6, 1), (1, 11.4, 1), (1, 11.6, 0), (1, 0.0, 0),
+             (0, 12.0, 0), (1, 10.0, 1)]
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((len(cases), 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    ty = np.array([c[0] for c in cases], np.int32)
+    x = u * np.array([c[1] for c in cases])[:, None]
+    assert oracle.surface_count(x, ty, sigma, R) == sum(c[2] for c in cases)
+    for k in range(len(cases)):  # one NP at a time
+        assert oracle.surface_count(x[k:k + 1], ty[k:k + 1], sigma, R) == cases[k][2]
+
+
 def test_rg_closed_forms_and_fractal_equation():
     golden = json.load(open(GOLDEN))
     assert oracle.K_F == golden["fractal_prefactor_k_f"]["value"]
