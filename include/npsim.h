@@ -63,8 +63,12 @@ typedef struct {
     int32_t rot_mode;   /* centrifugal force: 0 none, 1 rotation about z, 2 isotropic */
     int32_t lj_mode;    /* LJ: 0 off, 1 inside the all-pairs kernel, 2 cell list */
     int32_t coulomb;    /* 1: all-pairs Coulomb (not truncated), 0: off */
-    int32_t wall;       /* 1: interface spring on, 0: off (bulk liquid) */
-    int32_t integrator; /* 0: BAOAB Langevin, 1: overdamped (Brownian dynamics) */
+    int32_t wall;       /* interface spring (Sec. 2.2 iv): 0 off (bulk liquid); 1 on every
+                           NP beyond its equilibrium point R(t) - r_i; 2 only within
+                           the band (-r_i, r_i) about the surface, as step (iv) prints it */
+    int32_t integrator; /* 0: BAOAB Langevin; 1: overdamped (Brownian dynamics); 2: the
+                           step (vi) as printed: v += dt (F/m - gamma v), then a random
+                           velocity of magnitude v_kick in a uniform direction, x += dt v */
     int32_t skip_neutral; /* 1: leave NPs of charge 0 out of the all-pairs Coulomb sum
                              (their terms are exactly zero); 0: sum over all pairs */
     int32_t reserved_;    /* set to 0 */
@@ -79,6 +83,8 @@ typedef struct {
     double lj_cut;      /* LJ cutoff in units of sigma_ab (2.5 typical) */
     const double *eps_override; /* n_types x n_types LJ eps matrix, or NULL for
                                    Lorentz-Berthelot eps_ab = sqrt(eps_a eps_b) */
+    double v_kick;      /* integrator 2: magnitude of the random velocity added each step */
+    double coulomb_cut; /* coulomb 2: Coulomb truncated (not shifted) at coulomb_cut * sigma_ab */
 } npsim_params_t;
 
 typedef struct npsim_sim *npsim_sim_t;

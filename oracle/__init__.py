@@ -65,6 +65,7 @@ class Params(C.Structure):
         ("gamma", C.c_double * MAX_TYPES), ("k_wall", C.c_double * MAX_TYPES),
         ("eps_override", C.c_double * (MAX_TYPES * MAX_TYPES)),
         ("has_eps_override", C.c_int32), ("pad_", C.c_int32),
+        ("v_kick", C.c_double), ("coul_cut", C.c_double),
     ]
 
 
@@ -207,8 +208,10 @@ def make_params(sc) -> Params:
     p.rot_mode = sc.rot_mode
     p.lj_on = int(sc.lj_mode != 0)
     p.coul_on = int(sc.coulomb)
-    p.wall_on = int(sc.wall)
+    p.wall_on = 0 if not sc.wall else (2 if getattr(sc, "wall_band", False) else 1)
     p.integrator = sc.integrator
+    p.v_kick = float(getattr(sc, "v_kick", 0.0))
+    p.coul_cut = float(getattr(sc, "coulomb_cut", 0.0))
     p.seed = sc.seed
     p.dt, p.kT, p.R0, p.k_evap = sc.dt, sc.kT, sc.R0, sc.k_evap
     p.g, p.omega, p.bjerrum, p.lj_cut = sc.g, sc.omega, sc.bjerrum, sc.lj_cut

@@ -215,8 +215,8 @@ typedef struct {
     int32_t rot_mode;   /* 0 none, 1 about z, 2 isotropic */
     int32_t lj_on;
     int32_t coul_on;
-    int32_t wall_on;
-    int32_t integrator; /* 0 BAOAB Langevin, 1 overdamped (Brownian) */
+    int32_t wall_on;    /* 0 off, 1 beyond the equilibrium point, 2 within the band only */
+    int32_t integrator; /* 0 BAOAB Langevin, 1 overdamped (Brownian), 2 printed step vi */
     uint64_t seed;
     double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut;
     double sigma[OR_MAX_TYPES];
@@ -228,15 +228,19 @@ typedef struct {
     double eps_override[OR_MAX_TYPES * OR_MAX_TYPES];
     int32_t has_eps_override;
     int32_t pad_;
+    double v_kick;      /* integrator 2: magnitude of the random velocity per step */
+    double coul_cut;    /* > 0: Coulomb truncated (not shifted) at coul_cut * sigma_ab */
 } or_params_t;
 
 /* External forces on one particle at time t (steps iv and v):
  *  - interface wall (Sec. 2.1: a spring whose equilibrium point lies one NP
  *    radius inside the surface; spring constant per type).  With
  *    s = |x| - (R(t) - sigma/2), a particle with s > 0 feels -k_wall s x/|x|.
- *    Reading taken: the spring acts on every particle beyond its equilibrium
- *    point, with no outer limit (the literal band (-r, r) of step iv would let
- *    particles that the moving interface outruns escape).
+ *    Reading taken (wall_on = 1): the spring acts on every particle beyond its
+ *    equilibrium point, with no outer limit (the literal band (-r, r) of step
+ *    iv would let particles that the moving interface outruns escape).
+ *    wall_on = 2 is the band as printed: the spring acts only for
+ *    -r < |x| - R < r, i.e. 0 < s < sigma.
  *  - gravity -m g z^ (Sec. 1.2, step v; buoyancy folded into g).
  *  - centrifugal m w^2 (x, y, 0) for rotation about z, or m w^2 x for the
  *    isotropic tumbling of Sec. 1.2.                                        */
@@ -251,7 +255,8 @@ void or_external_forces(const or_params_t *p, int64_t n, const double *x,
         if (p->wall_on) {
             double r = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
             double s = r - (R - 0.5 * p->sigma[ti]);
-            if (s > 0.0 && r > 0.0) {
+            int in_band = p->wall_on != 2 || s < p->sigma[ti];
+            if (s > 0.0 && r > 0.0 && in_band) {
                 double f = -p->k_wall[ti] * s / r;
                 F[3 * i + 0] += f * xi[0];
                 F[3 * i + 1] += f * xi[1];
@@ -296,6 +301,8 @@ void or_total_forces(const or_params_t *p, int64_t n, const double *x,
  *     x += dt/2 v;  F <- F(x_{n+1}, t_{n+1});  v += dt/2 F/m.
  *   Overdamped mode (Brownian dynamics, Euler-Maruyama):
  *     x += F(x_n, t_n) dt/(m gamma) + sqrt(2 kT dt/(m gamma)) xi_n.
+ *   Printed mode (integrator 2, step vi as the paper states it):
+ *     v += dt (F(x_n, t_n)/m - gamma v);  v += v_kick xi_n/|xi_n|;  x += dt v.
  * xi_n are the three normals of particle i at step n, purpose 0.  In the
  * overdamped mode velocities are not a state and v is left unchanged.
  * x, v (n x 3) are updated in place from step `step0` for n_steps steps;
@@ -324,11 +331,25 @@ void or_run(const or_params_t *p, int64_t n, double *x, double *v,
                     v[3 * i + d] = vi;
                     x[3 * i + d] = xv;
                 }
-            } else {
+            } else if (p->integrator == 1) {
                 double mob = 1.0 / (m * gam);
                 double sd = sqrt(2.0 * p->kT * dt * mob);
                 for (int d = 0; d < 3; ++d)
                     x[3 * i + d] += F[3 * i + d] * dt * mob + sd * xi[3 * i + d];
+            } else {
+                /* step (vi) as printed: the force with the drag -m gamma v
+                 * changes the velocity, a random velocity of fixed magnitude
+                 * v_kick along the unit vector n/|n| of this step's normals is
+                 * added, and the position moves with the new velocity.     */
+                const double *nrm = xi + 3 * i;
+                double len = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+                double a = len > 0.0 ? p->v_kick / len : 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double vi = v[3 * i + d] + dt * (F[3 * i + d] / m - gam * v[3 * i + d]);
+                    vi += a * nrm[d];
+                    v[3 * i + d] = vi;
+                    x[3 * i + d] += dt * vi;
+                }
             }
         }
         memset(F, 0, sizeof(double) * 3 * (size_t)n);

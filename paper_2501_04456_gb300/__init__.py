@@ -46,7 +46,8 @@ class npsim_params_t(C.Structure):
                 ("seed", C.c_uint64), ("dt", C.c_double), ("kT", C.c_double),
                 ("R0", C.c_double), ("k_evap", C.c_double), ("g", C.c_double),
                 ("omega", C.c_double), ("bjerrum", C.c_double), ("lj_cut", C.c_double),
-                ("eps_override", C.POINTER(C.c_double))]
+                ("eps_override", C.POINTER(C.c_double)), ("v_kick", C.c_double),
+                ("coulomb_cut", C.c_double)]
 
 
 class npsim_droplet_t(C.Structure):
@@ -194,9 +195,12 @@ def params_from(sc):
     p.n_types = len(sc.types)
     p.rot_mode = sc.rot_mode
     p.lj_mode = sc.lj_mode
-    p.coulomb = int(bool(sc.coulomb))
-    p.wall = int(bool(sc.wall))
+    ccut = float(getattr(sc, "coulomb_cut", 0.0))
+    p.coulomb = 0 if not sc.coulomb else (2 if ccut > 0 else 1)
+    p.coulomb_cut = ccut
+    p.wall = 0 if not sc.wall else (2 if getattr(sc, "wall_band", False) else 1)
     p.integrator = sc.integrator
+    p.v_kick = float(getattr(sc, "v_kick", 0.0))
     p.skip_neutral = int(bool(getattr(sc, "skip_neutral", False)))
     p.seed = sc.seed
     p.dt, p.kT, p.R0, p.k_evap = sc.dt, sc.kT, sc.R0, sc.k_evap

@@ -878,6 +878,9 @@ void fill_coefs(const npsim_type_t *types, const npsim_params_t *params, TypeCoe
         c.mw2 = (float)(ty.mass * params->omega * params->omega);
         c.kw = (float)ty.k_wall;
         c.hs = (float)c.half_sigma;
+        c.dt_m = (float)(params->dt / ty.mass);
+        c.gdt = (float)(ty.gamma * params->dt);
+        c.kick = (float)params->v_kick;
         if (charge_f)
             charge_f[t] = (float)ty.charge;
     }
@@ -918,14 +921,18 @@ int validate(const npsim_type_t *types, const npsim_params_t *p, int64_t n)
     NP_REQUIRE(p->kT >= 0, "kT must be >= 0");
     NP_REQUIRE(p->rot_mode >= 0 && p->rot_mode <= 2, "rot_mode must be 0, 1 or 2");
     NP_REQUIRE(p->lj_mode >= 0 && p->lj_mode <= 2, "lj_mode must be 0, 1 or 2");
-    NP_REQUIRE(p->integrator == 0 || p->integrator == 1, "integrator must be 0 or 1");
+    NP_REQUIRE(p->integrator >= 0 && p->integrator <= 2, "integrator must be 0, 1 or 2");
+    NP_REQUIRE(p->wall >= 0 && p->wall <= 2, "wall must be 0, 1 or 2");
+    NP_REQUIRE(p->coulomb == 0 || p->coulomb == 1, "coulomb must be 0 or 1");
     NP_REQUIRE(p->R0 > 0 || !p->wall, "R0 must be positive when the wall is on");
+    NP_REQUIRE(p->integrator != 2 || (p->v_kick >= 0 && std::isfinite(p->v_kick)),
+               "v_kick must be finite and >= 0");
     NP_REQUIRE(p->lj_mode == 0 || p->lj_cut > 0, "lj_cut must be positive");
     for (int t = 0; t < p->n_types; ++t) {
         NP_REQUIRE(types[t].sigma > 0 && types[t].mass > 0, "type %d: sigma, mass > 0", t);
         NP_REQUIRE(types[t].gamma >= 0 && types[t].eps >= 0 && types[t].k_wall >= 0,
                    "type %d: gamma, eps, k_wall >= 0", t);
-        NP_REQUIRE(p->integrator == 0 || types[t].gamma > 0,
+        NP_REQUIRE(p->integrator != 1 || types[t].gamma > 0,
                    "type %d: the overdamped integrator needs gamma > 0", t);
     }
     return NPSIM_OK;
@@ -1541,7 +1548,7 @@ struct CkptHeader {
     int64_t n, step;
     int32_t rot_mode, lj_mode, coulomb, wall, integrator, has_ov, skip_neutral, pad_;
     uint64_t seed;
-    double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut;
+    double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut, v_kick, coulomb_cut;
     double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     npsim_type_t types[NPSIM_MAX_TYPES];
     int32_t cell, grid_dim, grid_cells, nbr_cap, gate, pad2_;
@@ -1592,7 +1599,7 @@ int npsim_save(npsim_sim_t s, const char *path)
     NP_REQUIRE(s && path, "sim and path are required");
     CkptHeader h{};
     memcpy(h.magic, kMagic, 8);
-    h.version = 4;
+    h.version = 5;
     h.n_types = s->T;
     h.n = s->n;
     h.step = s->step;
@@ -1612,6 +1619,8 @@ int npsim_save(npsim_sim_t s, const char *path)
     h.omega = s->P.omega;
     h.bjerrum = s->P.bjerrum;
     h.lj_cut = s->P.lj_cut;
+    h.v_kick = s->P.v_kick;
+    h.coulomb_cut = s->P.coulomb_cut;
     memcpy(h.eps_ov, s->eps_ov, sizeof(h.eps_ov));
     memcpy(h.types, s->types, sizeof(h.types));
     const size_t n = (size_t)s->n;
@@ -1666,7 +1675,7 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     if (!f)
         return set_err(NPSIM_ERR_IO, "cannot open %s", path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 4 ||
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 5 ||
         h.n < 1 || h.n > (1ll << 29) || h.n_types < 1 || h.n_types > NPSIM_MAX_TYPES) {
         fclose(f);
         return set_err(NPSIM_ERR_IO, "%s is not an npsim checkpoint", path);
@@ -1706,6 +1715,8 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     p.omega = h.omega;
     p.bjerrum = h.bjerrum;
     p.lj_cut = h.lj_cut;
+    p.v_kick = h.v_kick;
+    p.coulomb_cut = h.coulomb_cut;
     p.eps_override = h.has_ov ? h.eps_ov : nullptr;
     if (params_override) {
         p = *params_override;

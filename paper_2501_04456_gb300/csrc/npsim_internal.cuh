@@ -457,8 +457,10 @@ struct TypeCoef {
     // float32 copies used by the integrator (all of its arithmetic is float32 or
     // compensated float32): dt/(2m), c1 as hi + lo (its rounding error would
     // otherwise compound over the 1/(gamma dt) steps a velocity remembers),
-    // sd_o, dt*mob, sd_bd, C q, m g, m w^2, k_wall, sigma/2
+    // sd_o, dt*mob, sd_bd, C q, m g, m w^2, k_wall, sigma/2; for the printed
+    // step (vi) dt/m, gamma dt and the kick magnitude
     float hdt_m, c1f, c1lo, sd_of, dt_mob, sd_bdf, qc, mg, mw2, kw, hs;
+    float dt_m, gdt, kick;
 };
 
 // ---------------------------------------------------------------------------
@@ -513,7 +515,8 @@ __device__ __forceinline__ void df_mul(float &h, float &l, float b)
 // Equilibrium radius of the interface spring for a particle of half-diameter
 // hs at t = step dt: R_eff = R(t) - hs with R(t)^2 = R0^2 - k t (radius-square
 // law, 0 once the droplet has gone).  Returned as (R_eff^2 hi, R_eff^2 lo,
-// R_eff, 0) from one float64 evaluation.  Host and device both call this (the
+// R_eff, 2 hs = the width of the band (-r, r) about the surface) from one
+// float64 evaluation.  Host and device both call this (the
 // explicit fma fixes the rounding), so a table set by the host equals the one
 // the integrator writes for the same step bit for bit.
 __host__ __device__ inline float4 spring_entry(double R0, double k_evap, double dt,
@@ -525,7 +528,7 @@ __host__ __device__ inline float4 spring_entry(double R0, double k_evap, double 
     const double re = R - hs;
     const double re2 = re * re;
     const float h = (float)re2;
-    return make_float4(h, (float)(re2 - (double)h), (float)re, 0.0f);
+    return make_float4(h, (float)(re2 - (double)h), (float)re, (float)(2.0 * hs));
 }
 
 // External forces (interface spring, gravity, centrifugal) on a particle at
@@ -533,7 +536,8 @@ __host__ __device__ inline float4 spring_entry(double R0, double k_evap, double 
 // difference of two nearly equal numbers; it is formed as
 // (|x|^2 - R_eff^2) / (|x| + R_eff) with |x|^2 from exact products and sums
 // (the lo^2 terms lie below the precision kept), so s keeps float32 relative
-// precision however large |x| is.
+// precision however large |x| is.  wall = 2 limits the spring to the band
+// (-r, r) about the surface, 0 < s < 2 r (spring.w = 2 r).
 __device__ __forceinline__ void external_force(const float4 &xh, float lx, float ly, float lz,
                                                float kw, float mg, float mw2, float4 spring,
                                                int wall, int rot_mode, float &fx,
@@ -561,7 +565,7 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
         } else {
             s = rr - reff;
         }
-        if (s > 0.0f && r2h > 0.0f) {
+        if (s > 0.0f && r2h > 0.0f && (wall != 2 || s < spring.w)) {
             const float f = -kw * s * rinv;
             fx = f * xh.x;
             fy = f * xh.y;
@@ -762,10 +766,21 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
                                  __fmaf_rn(tc.c1lo, v[d], __fmul_rn(tc.sd_of, nz[d]))); // O
                 df_add(xhi[d], xlo[d], __fmul_rn(hdt, v[d]));         // A
             }
-        } else {
+        } else if (integrator == 1) {
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 df_add(xhi[d], xlo[d], __fmaf_rn(f[d], tc.dt_mob, __fmul_rn(tc.sd_bdf, nz[d])));
+        } else { // step (vi) as printed: drag and force, a kick of fixed size, drift
+            const float nn = sqrtf(__fmaf_rn(nz[0], nz[0], __fmaf_rn(nz[1], nz[1],
+                                                                     __fmul_rn(nz[2], nz[2]))));
+            const float a = nn > 0.0f ? __fdiv_rn(tc.kick, nn) : 0.0f; // kick / |n|
+            const float dt = 2.0f * hdt;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                v[d] = __fmaf_rn(tc.dt_m, f[d], __fmaf_rn(-tc.gdt, v[d], v[d]));
+                v[d] = __fmaf_rn(a, nz[d], v[d]);
+                df_add(xhi[d], xlo[d], __fmul_rn(dt, v[d]));
+            }
         }
         xq[i] = make_float4(xhi[0], xhi[1], xhi[2], xh.w);
         x_lo[i] = xlo[0];

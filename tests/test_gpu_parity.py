@@ -231,7 +231,7 @@ def test_lj_in_allpairs_large_droplet_sampled(P, monkeypatch, coul):
 
 
 TRAJ = ["lj1000_cell", "coul_lj_allpairs_2048", "coul_allpairs_lj_cell_4096",
-        "overdamped_lj_1000"]
+        "overdamped_lj_1000", "printed_kick_band_coul_lj_2048", "printed_kick_band_lj1000_cell"]
 
 
 def _traj_scen(name):
@@ -243,6 +243,11 @@ def _traj_scen(name):
         return small(wl.config3(), 4096)
     if name == "overdamped_lj_1000":
         return with_(wl.config1(), integrator=1)
+    # the paper's printed steps (iv) and (vi): band-limited wall, drag + fixed kick
+    if name == "printed_kick_band_coul_lj_2048":
+        return with_(small(wl.config2(), 2048), integrator=2, v_kick=0.05, wall_band=True)
+    if name == "printed_kick_band_lj1000_cell":
+        return with_(wl.config1(), integrator=2, v_kick=0.1, wall_band=True)
     raise KeyError(name)
 
 
@@ -257,7 +262,7 @@ def test_trajectory_parity_100_steps(P, name):
     xo, vo, Fo = oracle.run(sc, x, v, types, 0, 100)
     dx = np.abs(xg - xo).max()
     assert dx <= TRAJ_TOL, dx
-    if sc.integrator == 0:
+    if sc.integrator != 1:
         assert np.abs(vg - vo).max() <= 1e-2
     assert force_error(Fg, Fo).max() <= 1e-3
 
@@ -475,6 +480,44 @@ def test_invalid_arguments_are_errors(P):
     assert e.value.code == -1
     with pytest.raises(P.NpsimError):
         P.Sim(with_(sc, dt=0.0), x, v, types)
+
+
+def test_band_wall_forces_match_oracle(P):
+    """The printed step (iv) wall on the GPU: NPs of two sizes placed inside,
+    across and beyond the band (-r, r) about the surface."""
+    ts = [wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=40.0),
+          wl.TypeSpec(sigma=3.0, eps=1.0, mass=27.0, charge=0.0, gamma=1.0 / 9, k_wall=90.0)]
+    rng = np.random.default_rng(8)
+    n = 400
+    ty = (np.arange(n) % 2).astype(np.int32)
+    rad = 10.0 + rng.uniform(-2.5, 2.5, n)
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    x = wl.fp32_representable(u * rad[:, None])
+    for band in (False, True):
+        sc = wl.Scenario(name="band", types=ts, n=n, R0=10.0, k_evap=0.0, lj_mode=0,
+                         coulomb=False, g=0.3, wall_band=band)
+        with P.Sim(sc, x, None, ty) as sim:
+            F = sim.forces(0)
+        ref = oracle.total_forces(sc, x, ty, 0.0)
+        assert force_error(F, ref).max() <= FORCE_TOL, band
+
+
+def test_printed_kick_has_fixed_magnitude_gpu(P):
+    """Printed step (vi) on the GPU with gamma = 0 and no force: one step from
+    rest gives |v| = v_kick for every NP, in the oracle's directions."""
+    n, A = 4096, 0.3
+    t = wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.5, charge=0.0, gamma=0.0, k_wall=0.0)
+    sc = wl.Scenario(name="kick", types=[t], n=n, seed=23, kT=0.0, R0=1e9, wall=False,
+                     lj_mode=0, coulomb=False, integrator=2, v_kick=A)
+    ty = np.zeros(n, np.int32)
+    x0 = np.zeros((n, 3))
+    with P.Sim(sc, x0, None, ty) as sim:
+        sim.step(1)
+        _, v, _, _ = sim.state()
+    assert np.allclose(np.linalg.norm(v, axis=1), A, rtol=1e-6)
+    _, vo, _ = oracle.run(sc, x0, np.zeros((n, 3)), ty, 0, 1)
+    assert np.abs(v - vo).max() <= 1e-6 * A
 
 
 def test_free_particles_msd_and_equipartition_gpu(P):

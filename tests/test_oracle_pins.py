@@ -335,6 +335,25 @@ def test_wall_spring_closed_form():
     assert F[0, 2] == pytest.approx(-50.0 * 0.25, rel=1e-12)
 
 
+def test_band_wall_closed_form():
+    """wall_band: the spring acts only within the band (-r, r) about the surface,
+    i.e. for 0 < s < sigma with s = |x| - (R - r); beyond it the force is 0, where
+    the default wall keeps pulling (-k s x/|x|)."""
+    import dataclasses
+    sc1 = _one_type_scenario()                       # sigma 2, k_wall 50, R 10
+    sc2 = dataclasses.replace(sc1, wall_band=True)
+    u = np.array([0.48, -0.6, 0.64])
+    for rad, in_band in ((8.5, False), (9.5, True), (10.5, True), (10.99, True),
+                         (11.01, False), (11.5, False)):
+        x = (rad * u)[None]
+        s = rad - 9.0
+        full = -50.0 * max(s, 0.0) * u
+        F1 = oracle.external_forces(sc1, x, np.zeros(1, np.int32), 0.0)[0]
+        F2 = oracle.external_forces(sc2, x, np.zeros(1, np.int32), 0.0)[0]
+        assert np.allclose(F1, full, rtol=1e-14, atol=1e-14)
+        assert np.allclose(F2, full if in_band else 0.0 * u, rtol=1e-14, atol=1e-14)
+
+
 def test_gravity_and_centrifugal_closed_form():
     x = np.array([[1.0, -2.0, 3.0]])
     ty = np.zeros(1, np.int32)
@@ -450,6 +469,56 @@ def test_wall_ideal_gas_keeps_boltzmann_radial_density(integrator, dt):
     p_out = 1.0 - float(np.interp(R_eff, grid, cdf))
     se = math.sqrt(p_out * (1.0 - p_out) / n)
     assert abs((r > R_eff).mean() - p_out) < 5.0 * se
+
+
+def _kick_scenario(n, v_kick, gamma, g=0.0, dt=2e-3, mass=1.5):
+    t = wl.TypeSpec(sigma=1.0, eps=1.0, mass=mass, charge=0.0, gamma=gamma, k_wall=0.0)
+    return wl.Scenario(name="kick", types=[t], n=n, seed=23, dt=dt, kT=0.0, R0=1e9,
+                       wall=False, lj_mode=0, coulomb=False, integrator=2,
+                       v_kick=v_kick, g=g)
+
+
+def test_printed_step_drag_closed_form():
+    """Printed step (vi) without kick: v_{k+1} = (1 - gamma dt) v_k, so
+    v_n = q^n v_0 and x_n = x_0 + dt v_0 q (1 - q^n)/(1 - q), q = 1 - gamma dt;
+    under a constant force -m g the terminal velocity -g/gamma is a fixed point."""
+    n_p, steps, gam, dt = 50, 300, 2.0, 2e-3
+    sc = _kick_scenario(n_p, 0.0, gam, dt=dt)
+    rng = np.random.default_rng(3)
+    x0, v0 = rng.standard_normal((n_p, 3)), rng.standard_normal((n_p, 3))
+    ty = np.zeros(n_p, np.int32)
+    x, v, _ = oracle.run(sc, x0, v0, ty, 0, steps)
+    q = 1.0 - gam * dt
+    assert np.allclose(v, v0 * q ** steps, rtol=1e-12, atol=1e-15)
+    assert np.allclose(x, x0 + dt * v0 * q * (1 - q ** steps) / (1 - q), rtol=1e-11, atol=1e-13)
+    sc = _kick_scenario(n_p, 0.0, gam, g=0.8, dt=dt)
+    vt = np.tile([[0.0, 0.0, -0.8 / gam]], (n_p, 1))
+    _, v, _ = oracle.run(sc, x0, vt, ty, 0, 50)
+    assert np.allclose(v, vt, rtol=1e-13, atol=1e-15)
+
+
+def test_printed_step_kick_has_fixed_magnitude_and_uniform_direction():
+    """Printed step (vi) with gamma = 0 and no force: every step adds exactly
+    v_kick in a direction uniform on the sphere (mean 0, second moment I/3), so
+    |v_n|^2 grows by v_kick^2 per step on average."""
+    n_p, A = 20000, 0.3
+    sc = _kick_scenario(n_p, A, 0.0)
+    ty = np.zeros(n_p, np.int32)
+    x0 = np.zeros((n_p, 3))
+    v0 = np.zeros((n_p, 3))
+    _, v1, _ = oracle.run(sc, x0, v0, ty, 0, 1)
+    assert np.allclose(np.linalg.norm(v1, axis=1), A, rtol=1e-13)
+    _, v2, _ = oracle.run(sc, x0, v1, ty, 1, 1)        # the next step, alone
+    assert np.allclose(np.linalg.norm(v2 - v1, axis=1), A, rtol=1e-12)
+    u = v1 / A
+    se = 1.0 / math.sqrt(3 * n_p)
+    assert np.all(np.abs(u.mean(0)) < 5 * se)
+    M = u.T @ u / n_p
+    assert np.allclose(M, np.eye(3) / 3, atol=5 * math.sqrt(2.0 / 15 / n_p) + 1e-3)
+    steps = 40
+    _, v, _ = oracle.run(sc, x0, v0, ty, 0, steps)
+    s2 = (v ** 2).sum(1)
+    assert abs(s2.mean() - steps * A * A) < 5 * s2.std() / math.sqrt(n_p)
 
 
 def test_velocity_verlet_limit_reversible_and_energy():

@@ -65,8 +65,11 @@ class Scenario:
     lj_cut: float = 2.5          # LJ cutoff in units of sigma_ab
     coulomb: bool = False
     lj_mode: int = 1             # 0 off, 1 inside the all-pairs kernel, 2 cell list
-    integrator: int = 0          # 0 BAOAB Langevin, 1 overdamped
+    integrator: int = 0          # 0 BAOAB Langevin, 1 overdamped, 2 printed step (vi) + kick
     wall: bool = True
+    wall_band: bool = False      # spring only within (-r, r) of the surface (printed step iv)
+    v_kick: float = 0.0          # integrator 2: magnitude of the random velocity per step
+    coulomb_cut: float = 0.0     # > 0: Coulomb truncated at coulomb_cut * sigma_ab (cell list)
     eps_override: Optional[np.ndarray] = None
     n_steps: int = 1000          # length of the full run
     min_gap: float = 0.9         # placement: no pair closer than min_gap*sigma_ab
