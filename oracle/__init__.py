@@ -81,7 +81,7 @@ def _declare(lib):
     lib.or_philox_blocks.argtypes = [C.c_uint64, u32p, C.c_int64, u32p]
     lib.or_normals.argtypes = [C.c_uint64, C.c_int64, C.c_uint32, C.c_int64, _d]
     lib.or_mix_tables.argtypes = [C.c_int, _d, _d, _d, C.c_double, _d, _d, _d]
-    lib.or_pair_forces.argtypes = [C.c_int64, _d, i32p, C.c_int, _d, _d, _d, _d,
+    lib.or_pair_forces.argtypes = [C.c_int64, _d, i32p, C.c_int, _d, _d, _d, _d, _d,
                                    C.c_double, C.c_int, C.c_int, C.c_int64, i64p, _d]
     lib.or_radius.argtypes = [C.c_double, C.c_double, C.c_double]
     lib.or_radius.restype = C.c_double
@@ -174,8 +174,9 @@ def mix_tables(sigma, eps, eps_override=None, lj_cut=2.5):
 
 
 def pair_forces(x, types, sigma, eps, charge, bjerrum, lj_cut=2.5, lj=True,
-                coulomb=True, eps_override=None, sel=None):
-    """Pair forces of Sec. 2.2 step (ii) on rows `sel` (all rows if None)."""
+                coulomb=True, eps_override=None, sel=None, coulomb_cut=0.0):
+    """Pair forces of Sec. 2.2 step (ii) on rows `sel` (all rows if None); with
+    coulomb_cut > 0 the Coulomb term is truncated at coulomb_cut * sigma_ab."""
     lib = _load()
     x = _f64(x, (-1, 3))
     types = _i32(types)
@@ -188,8 +189,10 @@ def pair_forces(x, types, sigma, eps, charge, bjerrum, lj_cut=2.5, lj=True,
         sel_arr = np.ascontiguousarray(sel, dtype=np.int64)
         n_sel, selp = len(sel_arr), _ptr(sel_arr, C.c_int64)
     F = np.zeros((n_sel, 3))
+    rcc = np.ascontiguousarray(coulomb_cut * s) if coulomb_cut > 0 else None
     lib.or_pair_forces(n, _ptr(x, C.c_double), _ptr(types, C.c_int32), len(q),
                        _ptr(s, C.c_double), _ptr(e, C.c_double), _ptr(r, C.c_double),
+                       None if rcc is None else _ptr(rcc, C.c_double),
                        _ptr(q, C.c_double), bjerrum, int(lj), int(coulomb), n_sel,
                        selp, _ptr(F, C.c_double))
     return F

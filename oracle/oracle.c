@@ -153,12 +153,15 @@ void or_mix_tables(int T, const double *sigma, const double *eps,
  *                       + 24 eps_ij (2 (s/r)^12 - (s/r)^6) r_ij / r^2 * [r < rc_ij] ]
  * with r_ij = x_i - x_j, s = sigma_ij, C = Bjerrum length (energy unit kT = 1).
  * LJ is truncated and not shifted (Sec. 2.2 step ii).  Coulomb is summed over
- * all pairs (no truncation).  x is row-major n x 3.  sel (length n_sel) picks
- * the rows to evaluate; NULL means rows 0..n_sel-1.  F is n_sel x 3.        */
+ * all pairs (no truncation) when rcc_ab is NULL; otherwise the Coulomb term of
+ * a pair counts only for r < rcc_ab (truncated, not shifted: the paper's
+ * "pure" Coulomb with the interaction range of step i).  x is row-major n x 3.
+ * sel (length n_sel) picks the rows to evaluate; NULL means rows 0..n_sel-1.
+ * F is n_sel x 3.                                                           */
 void or_pair_forces(int64_t n, const double *x, const int32_t *type, int T,
                     const double *sig_ab, const double *eps_ab, const double *rc_ab,
-                    const double *charge, double bjerrum, int lj_on, int coul_on,
-                    int64_t n_sel, const int64_t *sel, double *F)
+                    const double *rcc_ab, const double *charge, double bjerrum, int lj_on,
+                    int coul_on, int64_t n_sel, const int64_t *sel, double *F)
 {
     if (!lj_on && !coul_on) { /* every term of the sum is zero */
         memset(F, 0, sizeof(double) * 3 * (size_t)n_sel);
@@ -179,7 +182,7 @@ void or_pair_forces(int64_t n, const double *x, const int32_t *type, int T,
             double r2 = dx * dx + dy * dy + dz * dz;
             double r = sqrt(r2);
             double f = 0.0; /* force / |r_ij| times 1/r, i.e. F = f * r_ij */
-            if (coul_on)
+            if (coul_on && (!rcc_ab || r < rcc_ab[ti * T + tj]))
                 f += bjerrum * charge[ti] * charge[tj] / (r2 * r);
             if (lj_on) {
                 int p = ti * T + tj;
@@ -285,8 +288,12 @@ void or_total_forces(const or_params_t *p, int64_t n, const double *x,
     or_mix_tables(p->n_types, p->sigma, p->eps,
                   p->has_eps_override ? p->eps_override : NULL, p->lj_cut, sig_ab,
                   eps_ab, rc_ab);
-    or_pair_forces(n, x, type, p->n_types, sig_ab, eps_ab, rc_ab, p->charge,
-                   p->bjerrum, p->lj_on, p->coul_on, n, NULL, F);
+    double rcc_ab[OR_MAX_TYPES * OR_MAX_TYPES];
+    for (int k = 0; k < p->n_types * p->n_types; ++k)
+        rcc_ab[k] = p->coul_cut * sig_ab[k];
+    or_pair_forces(n, x, type, p->n_types, sig_ab, eps_ab, rc_ab,
+                   p->coul_cut > 0.0 ? rcc_ab : NULL, p->charge, p->bjerrum, p->lj_on,
+                   p->coul_on, n, NULL, F);
     or_external_forces(p, n, x, type, t, F);
 }
 

@@ -167,6 +167,7 @@ struct npsim_sim {
     PairTab *tab_full = nullptr, *tab_lj = nullptr, *tab_coul = nullptr;
     float rc2_lim = 0.0f; // largest LJ rc^2 of the table (x 1.0001): tile-culling bound
     int any_charge = 0;   // Coulomb on and some type charged
+    float *d_rcc2 = nullptr; // coulomb mode 2: squared Coulomb cutoff per type pair (8 x 8)
     long long *d_step = nullptr;
     float4 *d_spring = nullptr; // [2][NPSIM_MAX_TYPES] spring radius table (spring_entry)
     int *d_flags = nullptr;
@@ -256,6 +257,7 @@ struct npsim_sim {
         dfree(s_table);
         dfree(s_count);
         dfree(s_surf);
+        dfree(d_rcc2);
         if (cap)
             cudaStreamDestroy(cap);
     }
@@ -369,12 +371,14 @@ enum { KG_ALLPAIRS = 0, KG_CELL_BUILD = 1, KG_CELL_LJ = 2, KG_INTEGRATE = 3 };
 int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext, float *Fout,
                  cudaStream_t st, int prof_slot = -1)
 {
-    const bool lj_cell = want_lj && s->cell;
     const bool ap_lj = want_lj && s->P.lj_mode == 1;
     // with every charged NP left out (skip_neutral and no charges) the grouped
     // Coulomb sum is empty
-    const bool ap_coul = want_coul && s->P.coulomb &&
+    const bool ap_coul = want_coul && s->P.coulomb == 1 &&
                          !(shape_grouped(s->ap_idx) && s->grp_len == 0);
+    // coulomb mode 2: Coulomb truncated at its cutoff, summed with LJ from the lists
+    const bool cell_coul = want_coul && s->P.coulomb == 2;
+    const bool lj_cell = s->cell && (want_lj || cell_coul);
     const bool ap = ap_lj || ap_coul;
     const bool ljg = shape_ljg(s->ap_idx);
     // the ungrouped kernels also serve a Coulomb-only pass of an LJ simulation
@@ -393,12 +397,13 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
         // moved more than half the skin since the last build
         NP_CUDA(mark(KG_CELL_BUILD, 0));
         NP_CUDA(launch_cell_build(s->grid, s->xq, s->typ, s->n, s->cb, s->d_gate, st));
-        NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, kSkin, s->nl, s->d_flags,
-                                 s->d_gate, st));
+        NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, s->d_rcc2, kSkin, s->nl,
+                                 s->d_flags, s->d_gate, st));
         NP_CUDA(mark(KG_CELL_BUILD, 1));
         NP_CUDA(mark(KG_CELL_LJ, 0));
-        NP_CUDA(launch_lj_nbr(s->grid, s->cb, s->xq, s->typ, s->n, s->tab_full, s->nl,
-                              s->F_lj, s->d_gate, st));
+        NP_CUDA(launch_lj_nbr(s->grid, s->cb, s->xq, s->typ, s->n,
+                              want_lj ? s->tab_full : s->tab_coul,
+                              cell_coul ? s->d_rcc2 : nullptr, s->nl, s->F_lj, s->d_gate, st));
         NP_CUDA(mark(KG_CELL_LJ, 1));
     }
     if (ap) {
@@ -590,7 +595,7 @@ int autotune(npsim_sim *s)
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
-        const bool coul = s->P.coulomb != 0;
+        const bool coul = s->P.coulomb == 1;
         const bool log = getenv("NPSIM_AUTOTUNE_LOG") != nullptr; // per-shape times to stderr
         for (int c = 0; c < nc; ++c) {
             const int occ = shape_occupancy(s, c, lj);
@@ -923,7 +928,11 @@ int validate(const npsim_type_t *types, const npsim_params_t *p, int64_t n)
     NP_REQUIRE(p->lj_mode >= 0 && p->lj_mode <= 2, "lj_mode must be 0, 1 or 2");
     NP_REQUIRE(p->integrator >= 0 && p->integrator <= 2, "integrator must be 0, 1 or 2");
     NP_REQUIRE(p->wall >= 0 && p->wall <= 2, "wall must be 0, 1 or 2");
-    NP_REQUIRE(p->coulomb == 0 || p->coulomb == 1, "coulomb must be 0 or 1");
+    NP_REQUIRE(p->coulomb >= 0 && p->coulomb <= 2, "coulomb must be 0, 1 or 2");
+    NP_REQUIRE(p->coulomb != 2 || p->lj_mode == 2,
+               "coulomb 2 (truncated, through the cell list) needs lj_mode 2");
+    NP_REQUIRE(p->coulomb != 2 || (p->coulomb_cut > 0 && std::isfinite(p->coulomb_cut)),
+               "coulomb 2 needs coulomb_cut > 0");
     NP_REQUIRE(p->R0 > 0 || !p->wall, "R0 must be positive when the wall is on");
     NP_REQUIRE(p->integrator != 2 || (p->v_kick >= 0 && std::isfinite(p->v_kick)),
                "v_kick must be finite and >= 0");
@@ -1085,12 +1094,28 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
     BAIL_CUDA(cudaStreamSynchronize(s->user));
 
     s->cell = params->lj_mode == 2;
+    double rc_cell = rc_max; // largest cutoff of the cell-list terms
+    if (params->coulomb == 2) {
+        // truncated Coulomb: cutoff coulomb_cut * sigma_ab for every charged pair
+        float rcc2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES] = {};
+        const int T = params->n_types;
+        for (int a = 0; a < T; ++a)
+            for (int b = 0; b < T; ++b) {
+                if (types[a].charge == 0.0 || types[b].charge == 0.0)
+                    continue;
+                const double rcc = params->coulomb_cut * 0.5 * (types[a].sigma + types[b].sigma);
+                rcc2[a * NPSIM_MAX_TYPES + b] = (float)(rcc * rcc);
+                rc_cell = std::max(rc_cell, rcc);
+            }
+        BAIL_CUDA(dalloc(&s->d_rcc2, (size_t)NPSIM_MAX_TYPES * NPSIM_MAX_TYPES));
+        BAIL_CUDA(cudaMemcpy(s->d_rcc2, rcc2, sizeof(rcc2), cudaMemcpyHostToDevice));
+    }
     if (s->cell) {
         double L = params->R0;
         for (int64_t i = 0; i < 3 * n; ++i)
             L = std::max(L, std::fabs(x0[i]));
-        L += rc_max + kSkin;
-        s->grid = make_grid(L, rc_max + kSkin, std::max<long long>(4 * n + 4096, 1 << 16));
+        L += rc_cell + kSkin;
+        s->grid = make_grid(L, rc_cell + kSkin, std::max<long long>(4 * n + 4096, 1 << 16));
         rc = alloc_cells(s->grid, s->cb, s->n);
         if (rc)
             return bail(rc);
@@ -1104,7 +1129,7 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
         BAIL_CUDA(dalloc(&s->d_gate, 1));
     }
     s->ap_lj = params->lj_mode == 1;
-    s->ap = params->coulomb || s->ap_lj;
+    s->ap = params->coulomb == 1 || s->ap_lj;
 
     // positions for the mirror (needed before tuning)
     {
@@ -1587,7 +1612,8 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
     NP_CUDA(cudaMemcpy(s->nl.x_ref, x_ref_host, sizeof(float4) * (size_t)s->n,
                        cudaMemcpyHostToDevice));
     NP_CUDA(launch_cell_build(s->grid, s->nl.x_ref, s->typ, s->n, s->cb, nullptr, s->user));
-    NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, kSkin, s->nl, s->d_flags,
+    NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, s->d_rcc2, kSkin, s->nl,
+                             s->d_flags,
                              nullptr, s->user));
     NP_CUDA(cudaStreamSynchronize(s->user));
     return set_gate(s, h.gate);

@@ -234,14 +234,24 @@ __global__ void k_cell_gather(const int *__restrict__ sorted, const float4 *__re
 
 // Per-row-type tables in shared memory: the pair table and, per row type, its
 // largest squared cutoff (force kernels) or cutoff-plus-skin (list build).
-__device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab, float skin,
-                                            float4 *s_tab, float *s_rl2, float *s_rmax)
+// rcc2 (or NULL): squared cutoffs of the truncated Coulomb term per type pair
+// (coulomb mode 2); a pair is listed within max(LJ cutoff, Coulomb cutoff) +
+// skin, counting only the terms that act (eps_ab != 0, C q_a q_b != 0).
+__device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab,
+                                            const float *__restrict__ rcc2, float skin,
+                                            float4 *s_tab, float *s_rl2, float *s_rmax,
+                                            float *s_rcc2 = nullptr)
 {
     for (int k = threadIdx.x; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; k += blockDim.x) {
         const float4 t = tab->e[k];
         s_tab[k] = t;
-        const float rl = sqrtf(t.z) + skin;
-        s_rl2[k] = t.y != 0.0f ? rl * rl : 0.0f; // no LJ between these types: never listed
+        const float rcc = rcc2 ? rcc2[k] : 0.0f;
+        if (s_rcc2)
+            s_rcc2[k] = rcc;
+        const float r_lj = t.y != 0.0f ? sqrtf(t.z) : 0.0f;
+        const float r_c = (rcc > 0.0f && t.w != 0.0f) ? sqrtf(rcc) : 0.0f;
+        const float r = fmaxf(r_lj, r_c);
+        s_rl2[k] = r > 0.0f ? (r + skin) * (r + skin) : 0.0f; // 0: never listed
     }
     __syncthreads();
     if (threadIdx.x < NPSIM_MAX_TYPES) {
@@ -263,7 +273,8 @@ __device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab, flo
 // Records the positions of this build in x_ref.
 __global__ void __launch_bounds__(128)
 k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
-            const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab, float skin,
+            const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab,
+            const float *__restrict__ rcc2, float skin,
             int cap, unsigned *__restrict__ nbr, int *__restrict__ nnbr,
             float4 *__restrict__ x_ref,
             unsigned long long *__restrict__ builds, int *__restrict__ flags,
@@ -276,7 +287,7 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     __shared__ float s_rmax[NPSIM_MAX_TYPES];
-    load_tables(tab, skin, s_tab, s_rl2, s_rmax);
+    load_tables(tab, rcc2, skin, s_tab, s_rl2, s_rmax);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const float4 pi = sxq[p];
         const int i = sorted[p];
@@ -318,23 +329,26 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
     }
 }
 
-// LJ forces from the neighbour lists at the current positions xq, one thread
-// per NP in particle order (type-grouped, Morton-ordered within a type: the
-// NP's own record, list and force record are coalesced and a warp's partners
-// are near one another).  An NP whose list overflowed sums over the 27 cells
-// of that build instead (a superset of its list).  Writes one 32-byte (hi x,
-// y, z, lo x, y, z, 0, 0) record per NP and closes the rebuild gate.
+// LJ forces (and, with rcc2, the truncated Coulomb term) from the neighbour
+// lists at the current positions xq, one thread per NP in particle index
+// order: the NP's own record, list column and force record are coalesced, the
+// partners' records are gathered.  An NP whose list overflowed sums over the
+// 27 cells of that build instead (a superset of its list).  Writes one 32-byte
+// (hi x, y, z, lo x, y, z, 0, 0) record per NP and closes the rebuild gate.
+template <bool COUL>
 __global__ void __launch_bounds__(128, 8)
 k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
          const int *__restrict__ pos, const float4 *__restrict__ sxq,
          const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
-         const PairTab *__restrict__ tab, int cap, const unsigned *__restrict__ nbr,
-         const int *__restrict__ nnbr, float *__restrict__ F_lj, int *__restrict__ gate)
+         const PairTab *__restrict__ tab, const float *__restrict__ rcc2, int cap,
+         const unsigned *__restrict__ nbr, const int *__restrict__ nnbr,
+         float *__restrict__ F_lj, int *__restrict__ gate)
 {
     __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rcc2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     __shared__ float s_rmax[NPSIM_MAX_TYPES];
-    load_tables(tab, 0.0f, s_tab, s_rl2, s_rmax);
+    load_tables(tab, COUL ? rcc2 : nullptr, 0.0f, s_tab, s_rl2, s_rmax, s_rcc2);
     if (gate && blockIdx.x == 0 && threadIdx.x == 0)
         *gate = 0; // every build kernel of this step has run; the integrator may reopen it
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -348,7 +362,24 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float4 t = s_tab[row + tj];
-        if (r2 < t.z) {
+        if (COUL) { // LJ (r < rc_ab) plus Coulomb truncated at its own cutoff
+            float f = 0.0f;
+            if (r2 < t.z) {
+                const float rinv2 = 1.0f / r2;
+                const float s2 = t.x * rinv2;
+                const float s6 = s2 * s2 * s2;
+                f = t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f);
+            }
+            if (r2 < s_rcc2[row + tj]) {
+                const float ri = rsqrtf(r2);
+                f = fmaf(t.w * ri, ri * ri, f); // C q_a q_b / r^3
+            }
+            if (f != 0.0f) {
+                two_sum_acc(hx, lx, f * dx);
+                two_sum_acc(hy, ly, f * dy);
+                two_sum_acc(hz, lz, f * dz);
+            }
+        } else if (r2 < t.z) {
             const float rinv2 = 1.0f / r2;
             const float s2 = t.x * rinv2;
             const float s6 = s2 * s2 * s2;
@@ -458,25 +489,31 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
 }
 
 cudaError_t launch_nbr_build(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
-                             float skin, const NbrList &l, int *flags, const int *gate,
-                             cudaStream_t st)
+                             const float *rcc2, float skin, const NbrList &l, int *flags,
+                             const int *gate, cudaStream_t st)
 {
     // heavy per-NP work (every candidate of 27 cells): up to four CTAs of
     // kMaxGrid, so that a compact droplet's build still has one NP per thread
     const int B = 128;
     const int gb = (n + B - 1) / B < 4 * kMaxGrid ? (n + B - 1) / B : 4 * kMaxGrid;
-    k_nbr_build<<<gb > 0 ? gb : 1, B, 0, st>>>(g, b.start, b.sorted, b.sxq, n, tab, skin, l.cap,
-                                               l.nbr, l.nnbr, l.x_ref, l.builds, flags, gate);
+    k_nbr_build<<<gb > 0 ? gb : 1, B, 0, st>>>(g, b.start, b.sorted, b.sxq, n, tab, rcc2, skin,
+                                               l.cap, l.nbr, l.nnbr, l.x_ref, l.builds, flags,
+                                               gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq,
-                          const int *typ, int n, const PairTab *tab, const NbrList &l,
-                          float *F_lj, int *gate, cudaStream_t st)
+                          const int *typ, int n, const PairTab *tab, const float *rcc2,
+                          const NbrList &l, float *F_lj, int *gate, cudaStream_t st)
 {
     const int B = 128;
-    k_lj_nbr<<<(n + B - 1) / B, B, 0, st>>>(g, b.start, b.sorted, b.pos, b.sxq, xq, typ, n, tab,
-                                            l.cap, l.nbr, l.nnbr, F_lj, gate);
+    const int grid = (n + B - 1) / B;
+    if (rcc2)
+        k_lj_nbr<true><<<grid, B, 0, st>>>(g, b.start, b.sorted, b.pos, b.sxq, xq, typ, n, tab,
+                                           rcc2, l.cap, l.nbr, l.nnbr, F_lj, gate);
+    else
+        k_lj_nbr<false><<<grid, B, 0, st>>>(g, b.start, b.sorted, b.pos, b.sxq, xq, typ, n, tab,
+                                            nullptr, l.cap, l.nbr, l.nnbr, F_lj, gate);
     return cudaGetLastError();
 }
 

@@ -918,12 +918,15 @@ struct NbrList {
     unsigned long long *builds; // number of builds run (device counter)
     int cap;
 };
+// rcc2 (or NULL): squared cutoffs of the truncated Coulomb term per type pair
+// (8 x 8); with it the lists cover both cutoffs and the list force kernel adds
+// C q_a q_b r_ij / r^3 within the Coulomb cutoff to the LJ term.
 cudaError_t launch_nbr_build(const CellGrid &g, const CellBufs &b, int n, const PairTab *tab,
-                             float skin, const NbrList &l, int *flags, const int *gate,
-                             cudaStream_t st);
+                             const float *rcc2, float skin, const NbrList &l, int *flags,
+                             const int *gate, cudaStream_t st);
 cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq,
-                          const int *typ, int n, const PairTab *tab, const NbrList &l,
-                          float *F_lj, int *gate, cudaStream_t st);
+                          const int *typ, int n, const PairTab *tab, const float *rcc2,
+                          const NbrList &l, float *F_lj, int *gate, cudaStream_t st);
 int cell_build_launches();
 int cell_scan_tiles(int n_cells);
 

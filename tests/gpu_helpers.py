@@ -35,23 +35,30 @@ def force_error(F_gpu, F_ref, rows=None):
 
 
 def cutoff_ambiguous(x, types, sc, rel=2e-6):
-    """Rows with an LJ pair whose distance lies within float32 rounding of its cutoff:
-    both classifications of such a pair are correct, so the strict comparison
-    leaves these rows out (the caller checks they are few)."""
-    if sc.lj_mode == 0:
-        return np.zeros(len(x), bool)
+    """Rows with a pair whose distance lies within float32 rounding of its LJ
+    cutoff (or of its Coulomb cutoff, when Coulomb is truncated): both
+    classifications of such a pair are correct, so the strict comparison leaves
+    these rows out (the caller checks they are few)."""
     sig = np.array([t.sigma for t in sc.types])
-    rc = sc.lj_cut * 0.5 * (sig[:, None] + sig[None, :])
+    sab = 0.5 * (sig[:, None] + sig[None, :])
+    cuts = []
+    if sc.lj_mode != 0:
+        cuts.append(sc.lj_cut * sab)
+    if sc.coulomb and getattr(sc, "coulomb_cut", 0.0) > 0:
+        cuts.append(sc.coulomb_cut * sab)
     out = np.zeros(len(x), bool)
+    if not cuts:
+        return out
     from scipy.spatial import cKDTree
     tree = cKDTree(x)
-    pairs = tree.query_pairs(rc.max() * (1 + 1e-4), output_type="ndarray")
+    pairs = tree.query_pairs(max(c.max() for c in cuts) * (1 + 1e-4), output_type="ndarray")
     if len(pairs):
         d = np.linalg.norm(x[pairs[:, 0]] - x[pairs[:, 1]], axis=1)
-        r = rc[types[pairs[:, 0]], types[pairs[:, 1]]]
-        amb = np.abs(d - r) <= rel * r
-        out[pairs[amb, 0]] = True
-        out[pairs[amb, 1]] = True
+        for rc in cuts:
+            r = rc[types[pairs[:, 0]], types[pairs[:, 1]]]
+            amb = np.abs(d - r) <= rel * r
+            out[pairs[amb, 0]] = True
+            out[pairs[amb, 1]] = True
     return out
 
 

@@ -65,11 +65,14 @@ def _scen(name):
     if name == "eps_matrix_1200":
         sc = small(wl.config2(), 1200)
         return with_(sc, eps_override=np.array([[0.155, 1.26], [1.26, 0.155]]) * 4)
+    if name == "truncated_coul_lj_cell_5003":  # the printed range 4 sigma_ab, cell list
+        return with_(small(wl.config3(), 5003), coulomb_cut=4.0)
     raise KeyError(name)
 
 
 SCENARIOS = ["lj1000_cell", "coul_lj_allpairs_3001", "coul_allpairs_lj_cell_5003",
-             "lj_allpairs_only_1537", "coul_only_2049", "eps_matrix_1200"]
+             "lj_allpairs_only_1537", "coul_only_2049", "eps_matrix_1200",
+             "truncated_coul_lj_cell_5003"]
 
 
 def _oracle_pair(sc, x, types, lj=True, coul=True, sel=None):
@@ -78,7 +81,8 @@ def _oracle_pair(sc, x, types, lj=True, coul=True, sel=None):
     q = [t.charge for t in sc.types]
     return oracle.pair_forces(x, types, sig, eps, q, sc.bjerrum, lj_cut=sc.lj_cut,
                               lj=lj and sc.lj_mode != 0, coulomb=coul and sc.coulomb,
-                              eps_override=sc.eps_override, sel=sel)
+                              eps_override=sc.eps_override, sel=sel,
+                              coulomb_cut=sc.coulomb_cut)
 
 
 @pytest.mark.parametrize("name", SCENARIOS)
@@ -231,7 +235,8 @@ def test_lj_in_allpairs_large_droplet_sampled(P, monkeypatch, coul):
 
 
 TRAJ = ["lj1000_cell", "coul_lj_allpairs_2048", "coul_allpairs_lj_cell_4096",
-        "overdamped_lj_1000", "printed_kick_band_coul_lj_2048", "printed_kick_band_lj1000_cell"]
+        "overdamped_lj_1000", "printed_kick_band_coul_lj_2048", "printed_kick_band_lj1000_cell",
+        "truncated_coul_lj_cell_4096"]
 
 
 def _traj_scen(name):
@@ -248,6 +253,8 @@ def _traj_scen(name):
         return with_(small(wl.config2(), 2048), integrator=2, v_kick=0.05, wall_band=True)
     if name == "printed_kick_band_lj1000_cell":
         return with_(wl.config1(), integrator=2, v_kick=0.1, wall_band=True)
+    if name == "truncated_coul_lj_cell_4096":
+        return with_(small(wl.config3(), 4096), coulomb_cut=4.0)
     raise KeyError(name)
 
 
@@ -517,7 +524,10 @@ def test_printed_kick_has_fixed_magnitude_gpu(P):
         _, v, _, _ = sim.state()
     assert np.allclose(np.linalg.norm(v, axis=1), A, rtol=1e-6)
     _, vo, _ = oracle.run(sc, x0, np.zeros((n, 3)), ty, 0, 1)
-    assert np.abs(v - vo).max() <= 1e-6 * A
+    # directions: the float32 Box-Muller normals differ from the float64 ones by
+    # ~1e-7 relative, rarely ~1e-5 at small radii (test_normals_match_oracle)
+    assert np.abs(v - vo).max() <= 2e-5 * A
+    assert np.median(np.abs(v - vo)) <= 1e-6 * A
 
 
 def test_free_particles_msd_and_equipartition_gpu(P):

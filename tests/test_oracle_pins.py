@@ -201,6 +201,47 @@ def test_coulomb_two_body_inverse_square(r):
     assert np.all(F[:, 1:] == 0)
 
 
+@pytest.mark.parametrize("frac,inside", [(0.5, True), (0.999, True), (1.001, False),
+                                           (1.5, False)])
+def test_coulomb_truncated_two_body(frac, inside):
+    """Truncated Coulomb (the printed range 4 sigma_ab, not shifted): inside the
+    range the force is the full C q1 q2 / r^2, beyond it exactly 0; sigma_ab of
+    a 1-3 pair is 2, so the range is 8."""
+    q, lb, cut = (0.5, -2.0), 0.7, 4.0
+    sig = (1.0, 3.0)
+    r = frac * cut * 2.0
+    x = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    F = oracle.pair_forces(x, np.array([0, 1]), sig, (1.0, 1.0), q, lb, lj=False,
+                           coulomb=True, coulomb_cut=cut)
+    expect = lb * q[0] * q[1] / (r * r) if inside else 0.0
+    assert F[1, 0] == pytest.approx(expect, rel=1e-13, abs=1e-300)
+    assert F[0, 0] == -F[1, 0]
+
+
+def test_coulomb_truncated_cluster_newton_and_subset():
+    """Truncated Coulomb on a random cluster: Newton's third law holds and every
+    pair's contribution is either the untruncated one (r < 4 sigma_ab) or 0,
+    checked by removing the far pairs one NP at a time."""
+    rng = np.random.default_rng(6)
+    n = 40
+    x = rng.uniform(-6, 6, (n, 3))
+    ty = rng.integers(0, 2, n).astype(np.int32)
+    sig, q = (1.0, 3.0), (0.7, -0.4)
+    Ft = oracle.pair_forces(x, ty, sig, (1.0, 1.0), q, 0.7, lj=False, coulomb=True,
+                            coulomb_cut=4.0)
+    assert np.abs(Ft.sum(0)).max() <= 1e-12 * np.abs(Ft).sum()
+    s = np.array(sig)
+    for i in range(0, n, 7):
+        d = np.linalg.norm(x - x[i], axis=1)
+        near = d < 4.0 * 0.5 * (s[ty[i]] + s[ty])
+        keep = near.copy()
+        keep[i] = True
+        Fi = oracle.pair_forces(x[keep], ty[keep], sig, (1.0, 1.0), q, 0.7, lj=False,
+                                coulomb=True)            # untruncated, near partners only
+        assert np.allclose(Ft[i], Fi[np.flatnonzero(keep).tolist().index(i)], rtol=1e-12,
+                           atol=1e-14)
+
+
 def test_coulomb_ring_axis_exact():
     """M equal charges on a ring of radius a: on the axis at height z the force is
     exactly C q Q z / (a^2 + z^2)^(3/2) along z (transverse parts cancel)."""
