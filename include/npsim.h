@@ -178,6 +178,20 @@ int npsim_stats(npsim_sim_t sim, const npsim_stats_cfg_t *cfg, int64_t *rdf_coun
                 double *rdf_g, int64_t *radial_counts, double *radial_c,
                 npsim_stats_t *out);
 
+/*
+ * Light scattered by the NPs (Sec. 3.3): the intensity as the Fourier transform
+ * of the RDF, I(q) = N_surf^2 * integral of exp(i q.r) g(r) d^3r, for g constant
+ * on each of the n_bins bins of [0, r_max) (the g of npsim_stats):
+ *   I(q) = N_surf^2 4 pi sum_b g_b [G(q r_{b+1}) - G(q r_b)] / q^3,
+ *   G(u) = sin u - u cos u,  and  N_surf^2 4 pi sum_b g_b (r_{b+1}^3 - r_b^3)/3 at q = 0;
+ * with I_frac (or NULL) also the fractal form I_frac(q) = N_surf^2 (q R_g)^(-D_f).
+ * g (n_bins), q (n_q, >= 0), I and I_frac (n_q) are host arrays; the sums run on
+ * the GPU in float64 (one warp per q, bins reduced in a fixed order).  Errors:
+ * INVALID_ARG (NULL arrays, n_bins or n_q < 1, r_max <= 0, q < 0), CUDA.
+ */
+int npsim_scattering(const double *g, int32_t n_bins, double r_max, double n_surf, double Rg,
+                     double Df, const double *q, int32_t n_q, double *I, double *I_frac);
+
 /* Checkpoint (Sec. 2.2: a run can be halted and resumed from its saved NP
  * configuration, possibly with other parameters): the raw state words
  * (position hi and lo float32 words, float32 velocities), types, step counter,

@@ -314,6 +314,42 @@ def surface_count(x, types, sigma, R):
                                     _ptr(s, C.c_double), R))
 
 
+def _sin_minus_ucos(u):
+    """sin u - u cos u, by its Taylor series sum_k (-1)^(k+1) 2k u^(2k+1)/(2k+1)!
+    below u = 0.5 (where the two terms cancel), directly above."""
+    u = np.asarray(u, np.float64)
+    out = np.sin(u) - u * np.cos(u)
+    small = u < 0.5
+    if np.any(small):
+        us = u[small]
+        term_sum = np.zeros_like(us)
+        fact = 1.0  # (2k+1)!
+        for k in range(1, 13):
+            fact *= (2 * k) * (2 * k + 1)
+            term_sum += (-1) ** (k + 1) * 2 * k * us ** (2 * k + 1) / fact
+        out[small] = term_sum
+    return out
+
+
+def scattering(g, r_max, n_surf, q):
+    """Light scattered by the NPs, Sec. 3.3: I(q) = N_surf^2 * integral of
+    exp(i q.r) g(r) d^3r = N_surf^2 4 pi integral g(r) r^2 sin(qr)/(qr) dr, with g
+    constant on the bins of [0, r_max): each bin contributes
+    g_b [G(q r_{b+1}) - G(q r_b)]/q^3, G(u) = sin u - u cos u (the antiderivative
+    of u sin u), and g_b (r_{b+1}^3 - r_b^3)/3 at q = 0."""
+    g = np.asarray(g, np.float64)
+    q = np.asarray(q, np.float64)
+    edges = np.arange(len(g) + 1) * (r_max / len(g))
+    out = np.empty(len(q))
+    for k, qq in enumerate(q):
+        if qq > 0:
+            G = _sin_minus_ucos(qq * edges)
+            out[k] = 4 * np.pi * np.sum(g * np.diff(G)) / qq ** 3
+        else:
+            out[k] = 4 * np.pi * np.sum(g * np.diff(edges ** 3)) / 3
+    return n_surf ** 2 * out
+
+
 def rg(x, d_mean, k_f=K_F):
     """(R_g, D_f, r0) from Eqs. N, Rg, r0 of Sec. 3.1."""
     lib = _load()

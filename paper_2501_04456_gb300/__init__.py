@@ -101,6 +101,8 @@ def lib():
             L.npsim_positions_device.argtypes = [_h, C.c_void_p]
             L.npsim_stats.argtypes = [_h, C.POINTER(npsim_stats_cfg_t), _i64, _d, _i64, _d,
                                       C.POINTER(npsim_stats_t)]
+            L.npsim_scattering.argtypes = [_d, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, _d, C.c_int32, _d, _d]
             L.npsim_save.argtypes = [_h, C.c_char_p]
             L.npsim_load.argtypes = [C.c_char_p, C.POINTER(npsim_type_t),
                                      C.POINTER(npsim_params_t), C.c_void_p, C.POINTER(_h)]
@@ -289,6 +291,19 @@ def npsim_stats(h, r_max=10.0, n_bins=128, radial_bins=0, boxcount=True,
             "nbox": np.array(out.nbox[:ns], np.int64), "n_surf": int(out.n_surf),
             "rdf_counts": counts[:n_bins], "rdf_g": g[:n_bins],
             "radial_counts": rc_[:radial_bins], "radial_c": rcc[:radial_bins]}
+
+
+def npsim_scattering(g, r_max, n_surf, q, Rg=1.0, Df=3.0):
+    """I(q) of the NPs from the RDF g (Sec. 3.3) and the fractal form
+    N_surf^2 (q R_g)^(-D_f); returns (I, I_frac) for the wave numbers q."""
+    g = np.ascontiguousarray(g, np.float64)
+    q = np.ascontiguousarray(q, np.float64)
+    I = np.zeros(len(q))
+    If = np.zeros(len(q))
+    _check(lib().npsim_scattering(_p(g, C.c_double), len(g), r_max, float(n_surf), Rg, Df,
+                                  _p(q, C.c_double), len(q), _p(I, C.c_double),
+                                  _p(If, C.c_double)))
+    return I, If
 
 
 def npsim_save(h, path):

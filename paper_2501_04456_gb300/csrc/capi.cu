@@ -1620,6 +1620,47 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
 }
 } // namespace
 
+int npsim_scattering(const double *g, int32_t n_bins, double r_max, double n_surf, double Rg,
+                     double Df, const double *q, int32_t n_q, double *I, double *I_frac)
+{
+    NP_REQUIRE(g && q && I, "g, q and I are required");
+    NP_REQUIRE(n_bins >= 1 && n_q >= 1, "n_bins and n_q must be >= 1");
+    NP_REQUIRE(r_max > 0 && std::isfinite(r_max), "r_max must be positive");
+    for (int k = 0; k < n_q; ++k)
+        NP_REQUIRE(q[k] >= 0 && std::isfinite(q[k]), "q[%d] must be finite and >= 0", k);
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1)
+        return set_err(NPSIM_ERR_NO_DEVICE, "no CUDA device visible");
+    double *dg = nullptr, *dq = nullptr, *dI = nullptr, *dF = nullptr;
+    auto release = [&]() {
+        dfree(dg);
+        dfree(dq);
+        dfree(dI);
+        dfree(dF);
+    };
+    cudaError_t e = dalloc(&dg, (size_t)n_bins);
+    if (e == cudaSuccess)
+        e = dalloc(&dq, (size_t)n_q);
+    if (e == cudaSuccess)
+        e = dalloc(&dI, (size_t)n_q);
+    if (e == cudaSuccess && I_frac)
+        e = dalloc(&dF, (size_t)n_q);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dg, g, sizeof(double) * n_bins, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dq, q, sizeof(double) * n_q, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_scattering(dg, n_bins, r_max, dq, n_q, n_surf, Rg, Df, dI, dF, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(I, dI, sizeof(double) * n_q, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && I_frac)
+        e = cudaMemcpy(I_frac, dF, sizeof(double) * n_q, cudaMemcpyDeviceToHost);
+    release();
+    if (e != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "npsim_scattering: %s", cudaGetErrorString(e));
+    return NPSIM_OK;
+}
+
 int npsim_save(npsim_sim_t s, const char *path)
 {
     NP_REQUIRE(s && path, "sim and path are required");

@@ -938,6 +938,11 @@ cudaError_t launch_radial_hist(const double *x, int n, double r_max, int n_bins,
                                unsigned long long *hist, cudaStream_t st);
 // mode 0: per-CTA sums of x; 1: sums of |x - c|^2; 2: componentwise minima.
 // part holds 3 doubles per CTA of 256 threads.
+// I(q) of Sec. 3.3 for a piecewise-constant g on [0, r_max), and its fractal form
+// N_surf^2 (q R_g)^(-D_f) into out_frac (or NULL); device arrays.
+cudaError_t launch_scattering(const double *g, int n_bins, double r_max, const double *q, int n_q,
+                              double n_surf, double Rg, double Df, double *out,
+                              double *out_frac, cudaStream_t st);
 // Half diameter of every type (surface band of N_surf).
 struct SurfHalf {
     double h[NPSIM_MAX_TYPES];

@@ -6,6 +6,7 @@
 //    sqrt(dx*dx + dy*dy + dz*dz) and floor(r / dr) rounded one by one (no fused
 //    multiply-add), so integer counts are exact;
 //  * radial histogram of |x| for the concentration C_NPs(r) of Sec. 3.2;
+//  * the scattered intensity I(q) of Sec. 3.3 as the transform of g(r);
 //  * N_surf, the number of NPs at the droplet surface (Sec. 1: the scattered
 //    intensity grows with N_surf^2), counted as the NPs whose centre lies in
 //    the band (-r_i, r_i) about the surface, | |x_i| - R(t) | < r_i, the band
@@ -140,6 +141,56 @@ k_surface_count(const double *__restrict__ x, const int *__restrict__ typ, int n
         atomicAdd(count, (unsigned long long)__popc(m));
 }
 
+// G(u) = sin u - u cos u (the antiderivative of u sin u): by its series below
+// u = 0.5, where the difference of the two terms would cancel.
+__device__ __forceinline__ double scat_G(double u)
+{
+    if (u < 0.5) {
+        const double u2 = u * u;
+        // u^3/3 - u^5/30 + u^7/840 - u^9/45360 + u^11/3991680 - u^13/518918400
+        double s = -1.0 / 518918400.0;
+        s = s * u2 + 1.0 / 3991680.0;
+        s = s * u2 - 1.0 / 45360.0;
+        s = s * u2 + 1.0 / 840.0;
+        s = s * u2 - 1.0 / 30.0;
+        s = s * u2 + 1.0 / 3.0;
+        return s * u2 * u;
+    }
+    return sin(u) - u * cos(u);
+}
+
+// One warp per q: I(q) = N_surf^2 4 pi sum_b g_b [G(q r_{b+1}) - G(q r_b)] / q^3
+// (q = 0: N_surf^2 4 pi sum_b g_b (r_{b+1}^3 - r_b^3) / 3); lane l sums bins l,
+// l + 32, ... and the lanes are combined in a fixed butterfly order.  out_frac
+// (or NULL): the fractal form N_surf^2 (q R_g)^(-D_f).
+__global__ void k_scattering(const double *__restrict__ g, int n_bins, double dr,
+                             const double *__restrict__ q, int n_q, double n_surf, double Rg,
+                             double Df, double *__restrict__ out, double *__restrict__ out_frac)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_q)
+        return;
+    const double qq = q[w];
+    double acc = 0.0;
+    for (int b = lane; b < n_bins; b += 32) {
+        const double r0 = b * dr, r1 = (b + 1) * dr;
+        const double t = qq > 0.0 ? scat_G(qq * r1) - scat_G(qq * r0)
+                                  : (r1 * r1 * r1 - r0 * r0 * r0) / 3.0;
+        acc += g[b] * t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const double four_pi = 12.566370614359172953850573533118;
+        const double n2 = n_surf * n_surf;
+        out[w] = n2 * (qq > 0.0 ? four_pi * acc / (qq * qq * qq) : four_pi * acc);
+        if (out_frac)
+            out_frac[w] = n2 * pow(qq * Rg, -Df);
+    }
+}
+
 // Per-CTA partials: mode 0 -> sum of x (3 values), 1 -> sum of |x - c|^2
 // (1 value), 2 -> componentwise minimum (3 values).  Tree reduction in a fixed
 // order inside the CTA.
@@ -265,6 +316,17 @@ cudaError_t launch_radial_hist(const double *x, int n, double r_max, int n_bins,
     if (e != cudaSuccess)
         return e;
     k_radial_hist<<<(n + 255) / 256, 256, 0, st>>>(x, n, dr, n_bins, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scattering(const double *g, int n_bins, double r_max, const double *q, int n_q,
+                              double n_surf, double Rg, double Df, double *out,
+                              double *out_frac, cudaStream_t st)
+{
+    const int threads = 128;
+    const int grid = (n_q * 32 + threads - 1) / threads;
+    k_scattering<<<grid, threads, 0, st>>>(g, n_bins, r_max / (double)n_bins, q, n_q, n_surf, Rg,
+                                           Df, out, out_frac);
     return cudaGetLastError();
 }
 

@@ -401,6 +401,23 @@ def test_stats_parity(P):
     assert st["n_surf"] == oracle.surface_count(xg, types, sig, st["R"])
 
 
+def test_scattering_matches_oracle(P):
+    """I(q) of Sec. 3.3 on the GPU from a simulated RDF, and the fractal form."""
+    sc = small(wl.config3(), 4000)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as sim:
+        sim.step(5)
+        st = sim.stats(r_max=12.0, n_bins=96, boxcount=False)
+    q = np.concatenate([[0.0, 1e-3, 0.02], np.linspace(0.1, 12.0, 61)])
+    n_surf = max(st["n_surf"], 7)
+    I, If = P.npsim_scattering(st["rdf_g"], 12.0, n_surf, q, Rg=st["Rg"], Df=st["Df_rg"])
+    ref = oracle.scattering(st["rdf_g"], 12.0, n_surf, q)
+    assert np.allclose(I, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
+    with np.errstate(divide="ignore"):
+        frac = n_surf ** 2 * (q * st["Rg"]) ** (-st["Df_rg"])
+    assert np.allclose(If[1:], frac[1:], rtol=1e-12)
+
+
 def test_stats_surface_count_hand_placed(P):
     """N_surf on the GPU for NPs placed on both sides of both band edges."""
     ts = [wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=10.0),

@@ -712,6 +712,39 @@ def test_surface_count_band_edges():
         assert oracle.surface_count(x[k:k + 1], ty[k:k + 1], sigma, R) == cases[k][2]
 
 
+def test_scattering_uniform_sphere_closed_form():
+    """g = 1 on [0, R): the transform is the volume integral of a uniform sphere,
+    4 pi (sin qR - qR cos qR)/q^3, and 4 pi R^3/3 at q = 0 (whatever the binning),
+    times N_surf^2."""
+    R = 7.5
+    q = np.array([0.05, 0.3, 1.0, 2.7, 9.0])
+    for n_bins in (1, 16, 128):
+        I = oracle.scattering(np.ones(n_bins), R, 3, q)
+        ref = 9 * 4 * np.pi * (np.sin(q * R) - q * R * np.cos(q * R)) / q ** 3
+        assert np.allclose(I, ref, rtol=1e-11, atol=0)
+        assert oracle.scattering(np.ones(n_bins), R, 3, [0.0])[0] == pytest.approx(
+            9 * 4 * np.pi * R ** 3 / 3, rel=1e-13)
+
+
+def test_scattering_matches_numerical_quadrature():
+    """A random piecewise-constant g: every bin's r^2 sin(qr)/(qr) integral by
+    adaptive quadrature agrees with the oracle's antiderivative form, small q
+    (series branch) included."""
+    integrate = pytest.importorskip("scipy.integrate")
+    rng = np.random.default_rng(12)
+    n_bins, r_max = 24, 6.0
+    g = rng.uniform(0.0, 3.0, n_bins)
+    dr = r_max / n_bins
+    for q in (0.01, 0.08, 0.37, 2.5, 11.0):
+        tot = 0.0
+        for b in range(n_bins):
+            val, _ = integrate.quad(lambda r: r * r * np.sinc(q * r / np.pi), b * dr,
+                                    (b + 1) * dr, epsabs=0, epsrel=1e-13, limit=200)
+            tot += g[b] * val
+        assert oracle.scattering(g, r_max, 1, [q])[0] == pytest.approx(4 * np.pi * tot,
+                                                                       rel=1e-10)
+
+
 def test_rg_closed_forms_and_fractal_equation():
     golden = json.load(open(GOLDEN))
     assert oracle.K_F == golden["fractal_prefactor_k_f"]["value"]
