@@ -464,8 +464,22 @@ def _truncated_measure(P, torch, stream, flush, steps, warmup, n=250000):
             ts.append(e0.elapsed_time(e1))
             kts.append(sim.kernel_times()[0])
         cap, mean_len, b1 = sim.nbr_info()
+        # the frame recorder: 200 steps plain, then recording every 10th and every
+        # step (float32 positions, asynchronous copies into page-locked frames)
+        rec = {}
+        sim.profile(False)
+        buf = P.frame_buffer(200, sc.n)  # page-locked, allocated outside the timing
+        for every in (0, 10, 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if every:
+                sim.record(200, every=every, out=buf)
+            else:
+                sim.step(200)
+            rec[f"every_{every}" if every else "plain"] = 1e3 * (time.perf_counter() - t0) / 200
     ms = sum(ts) / len(ts)
     return {"workload": sc.name + "_coulomb_cut4", "n": sc.n, "ms_per_step": ms,
+            "recorder_ms_per_step": rec,
             "particle_steps_per_s": sc.n / (ms * 1e-3),
             "kernel_ms": {k: sum(d[k] for d in kts) / len(kts) for k in kts[0]},
             "neighbour_lists": {"mean_length": mean_len, "capacity": cap,

@@ -124,6 +124,18 @@ void npsim_destroy(npsim_sim_t sim);
  */
 int npsim_step(npsim_sim_t sim, int64_t n_steps);
 
+/* Run n_steps steps and record every `every`-th frame (Sec. 2.2: only every
+ * j-th frame of a fine-step run is recorded): after steps every, 2 every, ...
+ * the float32 position mirror (x, y, z hi words, charge) of all NPs goes to
+ * frames[k] (host, n_frames x n x 4 floats, caller-owned), copied by a side
+ * stream from a device staging ring while the next steps compute.  frames is
+ * registered as page-locked memory for the call unless it already is.
+ * n_frames >= n_steps / every.  Returns after the last frame has arrived and
+ * the error flags were read, as npsim_step.  Errors: as npsim_step,
+ * INVALID_ARG (every < 1, frames too short). */
+int npsim_step_record(npsim_sim_t sim, int64_t n_steps, int64_t every, float *frames,
+                      int64_t n_frames);
+
 /* Copy the state to host arrays (any may be NULL): x, v (n x 3), F (n x 3 total
  * force at x and the current time), *step (steps taken since t = 0).  On the
  * device a position is kept as a pair of float32 words (hi + lo, about 48

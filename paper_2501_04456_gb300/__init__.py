@@ -103,6 +103,8 @@ def lib():
                                       C.POINTER(npsim_stats_t)]
             L.npsim_scattering.argtypes = [_d, C.c_int32, C.c_double, C.c_double, C.c_double,
                                            C.c_double, _d, C.c_int32, _d, _d]
+            L.npsim_step_record.argtypes = [_h, C.c_int64, C.c_int64, C.POINTER(C.c_float),
+                                            C.c_int64]
             L.npsim_save.argtypes = [_h, C.c_char_p]
             L.npsim_load.argtypes = [C.c_char_p, C.POINTER(npsim_type_t),
                                      C.POINTER(npsim_params_t), C.c_void_p, C.POINTER(_h)]
@@ -306,6 +308,29 @@ def npsim_scattering(g, r_max, n_surf, q, Rg=1.0, Df=3.0):
     return I, If
 
 
+def frame_buffer(n_frames, n):
+    """A float32 (n_frames, n, 4) array for recorded frames, in page-locked memory
+    when torch can provide it (the library registers any other array per call)."""
+    shape = (max(n_frames, 1), n, 4)
+    try:
+        import torch
+        return torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
+    except Exception:  # no torch or no pinned memory: a plain array
+        return np.zeros(shape, np.float32)
+
+
+def npsim_step_record(h, n, n_steps, every, out=None):
+    """Advance n_steps steps recording every every-th frame: float32 (n_frames, n, 4)
+    of (x, y, z, charge), into out (from frame_buffer) or a new buffer."""
+    nf = n_steps // every
+    frames = frame_buffer(nf, n) if out is None else out
+    if frames.dtype != np.float32 or not frames.flags.c_contiguous or \
+            frames.shape[1:] != (n, 4) or frames.shape[0] < nf:
+        raise ValueError("out must be a C-contiguous float32 (>= n_frames, n, 4) array")
+    _check(lib().npsim_step_record(h, n_steps, every, _p(frames, C.c_float), nf))
+    return frames[:nf]
+
+
 def npsim_save(h, path):
     _check(lib().npsim_save(h, os.fsencode(path)))
 
@@ -417,6 +442,10 @@ class Sim:
 
     def step(self, n_steps=1):
         npsim_step(self.h, n_steps)
+
+    def record(self, n_steps, every=1, out=None):
+        """Advance n_steps, returning every every-th frame of the float32 positions."""
+        return npsim_step_record(self.h, self.n, n_steps, every, out)
 
     def state(self):
         return npsim_get_state(self.h, self.n)

@@ -199,6 +199,11 @@ struct npsim_sim {
     // per-kernel timing: events around each kernel group of each step of a chunk
     bool profiling = false;
     cudaEvent_t ev[kChunk][4][2]{};
+    // frame recorder: device staging ring, copy stream, per-slot events
+    static constexpr int kRecSlots = 3;
+    float4 *rec_ring = nullptr;
+    cudaStream_t rec_stream = nullptr;
+    cudaEvent_t rec_ready[kRecSlots]{}, rec_done[kRecSlots]{};
 
     // statistics (allocated on first use)
     CellGrid sgrid{};
@@ -217,6 +222,15 @@ struct npsim_sim {
         for (auto &g : graphs)
             cudaGraphExecDestroy(g.second);
         graphs.clear();
+        for (int k = 0; k < kRecSlots; ++k) {
+            if (rec_ready[k])
+                cudaEventDestroy(rec_ready[k]);
+            if (rec_done[k])
+                cudaEventDestroy(rec_done[k]);
+        }
+        if (rec_stream)
+            cudaStreamDestroy(rec_stream);
+        dfree(rec_ring);
         for (int j = 0; j < kChunk; ++j)
             for (int k = 0; k < 4; ++k)
                 for (int e = 0; e < 2; ++e)
@@ -1182,10 +1196,12 @@ void npsim_destroy(npsim_sim_t sim)
     delete sim;
 }
 
-int npsim_step(npsim_sim_t s, int64_t n_steps)
+} // extern "C"
+
+namespace {
+// Queue n_steps steps as graph chunks of at most kChunk steps (no host wait).
+int enqueue_steps(npsim_sim *s, int64_t n_steps)
 {
-    NP_REQUIRE(s, "sim is NULL");
-    NP_REQUIRE(n_steps >= 0, "n_steps must be >= 0");
     int64_t rem = n_steps;
     while (rem > 0) {
         const int k = (int)std::min<int64_t>(rem, kChunk);
@@ -1198,6 +1214,85 @@ int npsim_step(npsim_sim_t s, int64_t n_steps)
         rem -= k;
         s->step += k;
     }
+    return NPSIM_OK;
+}
+} // namespace
+
+extern "C" {
+
+int npsim_step(npsim_sim_t s, int64_t n_steps)
+{
+    NP_REQUIRE(s, "sim is NULL");
+    NP_REQUIRE(n_steps >= 0, "n_steps must be >= 0");
+    int rc = enqueue_steps(s, n_steps);
+    if (rc)
+        return rc;
+    return read_flags(s);
+}
+
+int npsim_step_record(npsim_sim_t s, int64_t n_steps, int64_t every, float *frames,
+                      int64_t n_frames)
+{
+    NP_REQUIRE(s && frames, "sim and frames are required");
+    NP_REQUIRE(n_steps >= 0 && every >= 1, "n_steps >= 0 and every >= 1 are required");
+    const int64_t nf = n_steps / every;
+    NP_REQUIRE(n_frames >= nf, "frames holds %lld frames, %lld are recorded",
+               (long long)n_frames, (long long)nf);
+    const size_t bytes = sizeof(float4) * (size_t)s->n;
+    constexpr int R = npsim_sim::kRecSlots;
+    if (!s->rec_ring) {
+        NP_CUDA(dalloc(&s->rec_ring, (size_t)R * s->n));
+        NP_CUDA(cudaStreamCreateWithFlags(&s->rec_stream, cudaStreamNonBlocking));
+        for (int k = 0; k < R; ++k) {
+            NP_CUDA(cudaEventCreateWithFlags(&s->rec_ready[k], cudaEventDisableTiming));
+            NP_CUDA(cudaEventCreateWithFlags(&s->rec_done[k], cudaEventDisableTiming));
+        }
+    }
+    // copies are asynchronous only into page-locked memory: register the
+    // caller's buffer for the call unless it already is
+    bool registered = false;
+    if (nf > 0) {
+        cudaPointerAttributes at{};
+        const bool locked = cudaPointerGetAttributes(&at, frames) == cudaSuccess &&
+                            at.type == cudaMemoryTypeHost;
+        cudaGetLastError(); // a plain host pointer may leave an error behind
+        if (!locked) {
+            NP_CUDA(cudaHostRegister(frames, bytes * (size_t)nf, cudaHostRegisterDefault));
+            registered = true;
+        }
+    }
+    int rc = NPSIM_OK;
+    cudaError_t e = cudaSuccess;
+    for (int64_t f = 0; f < nf && rc == NPSIM_OK && e == cudaSuccess; ++f) {
+        rc = enqueue_steps(s, every);
+        if (rc)
+            break;
+        const int slot = (int)(f % R);
+        if (f >= R) // the slot's previous frame has reached the host
+            e = cudaStreamWaitEvent(s->user, s->rec_done[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->rec_ring + (size_t)slot * s->n, s->xq, bytes,
+                                cudaMemcpyDeviceToDevice, s->user);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(s->rec_ready[slot], s->user);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s->rec_stream, s->rec_ready[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(frames + (size_t)f * 4 * s->n, s->rec_ring + (size_t)slot * s->n,
+                                bytes, cudaMemcpyDeviceToHost, s->rec_stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(s->rec_done[slot], s->rec_stream);
+    }
+    if (rc == NPSIM_OK && e == cudaSuccess)
+        rc = enqueue_steps(s, n_steps - nf * every);
+    const cudaError_t e2 = cudaStreamSynchronize(s->rec_stream);
+    if (registered)
+        cudaHostUnregister(frames);
+    if (rc)
+        return rc;
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return set_err(NPSIM_ERR_CUDA, "frame recorder: %s",
+                       cudaGetErrorString(e != cudaSuccess ? e : e2));
     return read_flags(s);
 }
 

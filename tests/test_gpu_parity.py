@@ -418,6 +418,31 @@ def test_scattering_matches_oracle(P):
     assert np.allclose(If[1:], frac[1:], rtol=1e-12)
 
 
+def test_frame_recorder_matches_stepping(P):
+    """Frames recorded every 5 steps (asynchronous copies) are the float32 position
+    words and charges of the states reached by plain stepping, and recording
+    leaves the trajectory bit-identical."""
+    sc = small(wl.config3(), 3000)
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as a:
+        frames = a.record(23, every=5)           # after steps 5, 10, 15, 20; then 3 more
+        xa, va, _, st = a.state()
+    assert frames.shape == (4, sc.n, 4) and st == 23
+    q = np.array([t.charge for t in sc.types], np.float32)[types]
+    with P.Sim(sc, x, v, types) as b:
+        for k in range(4):
+            b.step(5)
+            xb, _, _, _ = b.state()
+            x32 = xb.astype(np.float32)           # the hi word is the float nearest x
+            f = frames[k, :, :3]
+            assert np.mean(f == x32) >= 0.9999
+            assert np.all(np.abs(f - x32) <= np.spacing(np.abs(x32)))
+            assert np.array_equal(frames[k, :, 3], q)
+        b.step(3)
+        xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
 def test_stats_surface_count_hand_placed(P):
     """N_surf on the GPU for NPs placed on both sides of both band edges."""
     ts = [wl.TypeSpec(sigma=1.0, eps=1.0, mass=1.0, charge=0.0, gamma=1.0, k_wall=10.0),
