@@ -314,6 +314,245 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                      "r"(g.tmem_cols));
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference of the whole network: one CTA runs every layer of one
+// network on 128 rows of the batch, so activations never leave the SM.
+//  * the A operand of every layer lives in shared memory (`abuf`, canonical
+//    no-swizzle K-major layout): layer 0's input arrives by TMA, the epilogue
+//    of layer l writes the BF16 activations of layer l + 1 into the same
+//    buffer once layer l's MMAs have completed;
+//  * weights stream by TMA through a ring of kInferStages stages of up to
+//    N x 64 BF16 (one producer thread, running ahead across layers);
+//  * one thread issues tcgen05.mma (M = 128, N = layer width, K = 16) into
+//    one TMEM accumulator that every layer reuses;
+//  * 8 epilogue warps read the accumulator (tcgen05.ld), add the bias, apply
+//    SiLU and write BF16 activations (hidden layers) or FP32 outputs (last
+//    layer, to the network's slice of y); they release the next layer with
+//    an mbarrier after a proxy fence (generic writes -> tensor-core reads).
+// The arithmetic is that of the layer-by-layer GEMM path (same MMA sequence,
+// same epilogue operations), so both give the same bits.
+constexpr int kInferThreads = 320; // warp 0 producer, warp 1 MMA, warps 2-9 epilogue
+constexpr int kInferStages = 3;
+
+// Tensor maps of the fused inference: the batch input (rows x in_p) and, per
+// layer, the weights of every network stacked along the rows (n_nets * N x K).
+struct MlpMaps {
+    CUtensorMap x;
+    CUtensorMap w[kMaxMlpLayers + 1];
+};
+
+struct MlpDev {
+    int NL, in_p, H, out_p, bp, tmem_cols, abuf_bytes, stage_bytes;
+    const float *bias[kMaxMlpLayers + 1]; // per layer, n_nets * N stacked
+    float *y;                              // [n_nets][bp][out_p]
+    int *flags;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ int infer_k(const MlpDev &d, int l) { return l == 0 ? d.in_p : d.H; }
+__device__ __forceinline__ int infer_n(const MlpDev &d, int l) { return l == d.NL ? d.out_p : d.H; }
+
+__global__ void __launch_bounds__(kInferThreads, 1)
+k_mlp_infer(const __grid_constant__ MlpMaps maps, MlpDev d)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[kInferStages], empty[kInferStages], x_full, acc_full,
+        act_ready, drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_issued, s_x_issued;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int net = blockIdx.y;
+    const int m0 = blockIdx.x * kTileM;
+    const uint32_t abuf = smem_addr(smem);
+    const uint32_t ring = abuf + (uint32_t)d.abuf_bytes;
+    const uint32_t sbytes = (uint32_t)d.stage_bytes;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&s_tmem)),
+                     "r"(d.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kInferStages; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            mbar_init(smem_addr(&empty[s]), 1);
+        }
+        mbar_init(smem_addr(&x_full), 1);
+        mbar_init(smem_addr(&acc_full), 1);
+        mbar_init(smem_addr(&act_ready), 8); // one arrival per epilogue warp
+        mbar_init(smem_addr(&drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort = 0;
+        s_issued = 0;
+        s_x_issued = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) { // TMA producer: the input tile, then every layer's weights
+            const uint32_t xb = smem_addr(&x_full);
+            mbar_expect_tx(xb, (uint32_t)(kTileM * d.in_p * 2));
+            for (int kg = 0; kg < d.in_p / 8; ++kg)
+                tma_load_2d(abuf + (uint32_t)(kg * kTileM * 16), &maps.x, kg * 8, m0, xb);
+            s_x_issued = 1;
+            int c = 0;
+            bool ok = true;
+            for (int l = 0; l <= d.NL && ok; ++l) {
+                const int K = infer_k(d, l), N = infer_n(d, l);
+                const int row0 = net * N;
+                for (int k0 = 0; k0 < K; k0 += kChunkK, ++c) {
+                    const int s = c % kInferStages, u = c / kInferStages;
+                    if (u > 0 && !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((u - 1) & 1))) {
+                        atomicExch(&s_abort, 1);
+                        ok = false;
+                        break;
+                    }
+                    const int kc = min(kChunkK, K - k0);
+                    const uint32_t sb = ring + (uint32_t)s * sbytes, fb = smem_addr(&full[s]);
+                    mbar_expect_tx(fb, (uint32_t)(N * kc * 2));
+                    for (int kg = 0; kg < kc / 8; ++kg)
+                        tma_load_2d(sb + (uint32_t)(kg * N * 16), &maps.w[l], k0 + kg * 8, row0, fb);
+                }
+            }
+            s_issued = c;
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) { // MMA issuer
+            int c = 0;
+            bool ok = true;
+            for (int l = 0; l <= d.NL && ok; ++l) {
+                const uint32_t gate = l == 0 ? smem_addr(&x_full) : smem_addr(&act_ready);
+                const uint32_t par = l == 0 ? 0u : (uint32_t)((l - 1) & 1);
+                if (!mbar_wait_bounded(gate, par)) {
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int K = infer_k(d, l), N = infer_n(d, l);
+                const uint32_t idesc = idesc_bf16(kTileM, N);
+                for (int k0 = 0; k0 < K; k0 += kChunkK, ++c) {
+                    const int s = c % kInferStages, u = c / kInferStages;
+                    if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)(u & 1))) {
+                        atomicExch(&s_abort, 1);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const int kc = min(kChunkK, K - k0);
+                    const uint32_t sb = ring + (uint32_t)s * sbytes;
+                    for (int ks = 0; ks < kc; ks += 16) {
+                        const int k = k0 + ks;
+                        const uint64_t ad = smem_desc(abuf + (uint32_t)((k / 8) * kTileM * 16),
+                                                      kTileM * 16, 128);
+                        const uint64_t bd = smem_desc(sb + (uint32_t)((ks / 8) * N * 16),
+                                                      (uint32_t)(N * 16), 128);
+                        const uint32_t acc = k > 0 ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                         tmem),
+                                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                    mma_commit(smem_addr(&empty[s]));
+                }
+                mma_commit(smem_addr(&acc_full)); // this layer's accumulator is complete
+            }
+            mma_commit(smem_addr(&drain)); // every MMA issued has completed (also after an abort)
+        }
+        __syncwarp();
+    } else { // epilogue warps 2..9: TMEM lanes 32 (warp mod 4) .. +31, alternate 16-column groups
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int r = quad * 32 + lane; // row inside the tile
+        for (int l = 0; l <= d.NL; ++l) {
+            if (!mbar_wait_bounded(smem_addr(&acc_full), (uint32_t)(l & 1))) {
+                atomicExch(&s_abort, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int N = infer_n(d, l);
+            const float *bias = d.bias[l] + (size_t)net * N;
+            const bool last = l == d.NL;
+            float *yrow = last ? d.y + ((size_t)net * d.bp + m0 + r) * d.out_p : nullptr;
+            for (int j = half * 16; j < N; j += 32) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)j;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
+                               "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]),
+                               "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                               "=r"(v[15])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (last) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4 *>(yrow + j + q) = make_float4(
+                            __uint_as_float(v[q]) + bias[j + q],
+                            __uint_as_float(v[q + 1]) + bias[j + q + 1],
+                            __uint_as_float(v[q + 2]) + bias[j + q + 2],
+                            __uint_as_float(v[q + 3]) + bias[j + q + 3]);
+                } else {
+#pragma unroll
+                    for (int h8 = 0; h8 < 2; ++h8) { // two 8-column core-matrix rows
+                        uint32_t p[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = h8 * 8 + 2 * e;
+                            const float a0 = silu(__uint_as_float(v[q]) + bias[j + q]);
+                            const float a1 = silu(__uint_as_float(v[q + 1]) + bias[j + q + 1]);
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
+                            p[e] = *reinterpret_cast<const uint32_t *>(&b2);
+                        }
+                        const int col = j + h8 * 8;
+                        uint8_t *dst = smem + (size_t)(col / 8) * kTileM * 16 + (size_t)r * 16;
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
+                    }
+                }
+            }
+            if (!last) { // the activations are the next layer's A operand
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_addr(&act_ready));
+            }
+        }
+    }
+
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) {
+            atomicOr(d.flags, FLAG_TIMEOUT);
+            // copies still in flight land before the CTA leaves (at most the
+            // last one issued per stage, and the input tile)
+            const int issued = s_issued;
+            for (int s = 0; s < kInferStages && s < issued; ++s) {
+                const int u_last = (issued - 1 - s) / kInferStages;
+                mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)(u_last & 1));
+            }
+            if (s_x_issued)
+                mbar_wait_bounded(smem_addr(&x_full), 0);
+            mbar_wait_bounded(smem_addr(&drain), 0);
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(d.tmem_cols));
+}
+
 // out[c][r] = in[r][c] for an R x C BF16 matrix (32 x 32 tiles in shared memory).
 __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int R, int C, int ldi,
                                  __nv_bfloat16 *__restrict__ out, int ldo)
@@ -496,6 +735,57 @@ cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t st)
     stages = stages < nchunks ? stages : nchunks;
     dim3 grid((g.M + kTileM - 1) / kTileM, (g.N + g.n_tile - 1) / g.n_tile);
     k_gemm_bf16<<<grid, kGemmThreads, dyn_smem_bytes(g.n_tile, stages), st>>>(ta, tb, g, stages);
+    return cudaGetLastError();
+}
+
+bool mlp_infer_supported(int NL, int in_p, int H, int out_p)
+{
+    return NL >= 1 && NL <= kMaxMlpLayers && H >= 16 && H <= 256 && H % 16 == 0 &&
+           out_p >= 16 && out_p <= 256 && out_p % 16 == 0 && in_p >= 16 && in_p <= 256 &&
+           in_p % 16 == 0;
+}
+
+cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t st)
+{
+    if (!mlp_infer_supported(a.NL, a.in_p, a.H, a.out_p) || a.bp < kTileM || a.bp % kTileM ||
+        a.n_nets < 1 || !a.X || !a.y)
+        return cudaErrorInvalidValue;
+    const int kmax = a.in_p > a.H ? a.in_p : a.H;
+    const int nmax = a.H > a.out_p ? a.H : a.out_p;
+    MlpDev d{};
+    d.NL = a.NL;
+    d.in_p = a.in_p;
+    d.H = a.H;
+    d.out_p = a.out_p;
+    d.bp = a.bp;
+    d.tmem_cols = 32;
+    while (d.tmem_cols < nmax) // TMEM columns: a power of two >= 32
+        d.tmem_cols *= 2;
+    d.abuf_bytes = (kTileM * kmax * 2 + 1023) / 1024 * 1024;
+    d.stage_bytes = nmax * kChunkK * 2;
+    d.y = a.y;
+    d.flags = a.flags;
+    MlpMaps maps{};
+    if (!encode_operand(&maps.x, a.X, a.bp, a.in_p, a.in_p, kTileM))
+        return cudaErrorInvalidValue;
+    for (int l = 0; l <= a.NL; ++l) {
+        const int K = l == 0 ? a.in_p : a.H, N = l == a.NL ? a.out_p : a.H;
+        if (!a.W[l] || !a.b[l] || ((uintptr_t)a.W[l] % 16) ||
+            !encode_operand(&maps.w[l], a.W[l], a.n_nets * N, K, K, N))
+            return cudaErrorInvalidValue;
+        d.bias[l] = a.b[l];
+    }
+    const int smem = d.abuf_bytes + kInferStages * d.stage_bytes;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kTileM * 256 * 2 + kInferStages * 256 * kChunkK * 2);
+        if (e != cudaSuccess)
+            return e;
+        attr_done = true;
+    }
+    dim3 grid(a.bp / kTileM, a.n_nets);
+    k_mlp_infer<<<grid, kInferThreads, smem, st>>>(maps, d);
     return cudaGetLastError();
 }
 

@@ -886,6 +886,22 @@ struct AdamArgs {
 
 int gemm_smem_bytes(int n_tile);
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t st);
+
+// Fused inference of a whole MLP (mlp.cu): every layer of every network in one
+// launch, activations kept in shared memory, one CTA per (128 rows, network).
+// W[l] / b[l]: layer l's BF16 weights (N_l x K_l, K-major) and FP32 biases of
+// all networks stacked (network k at rows k N_l); y: [n_nets][bp][out_p].
+constexpr int kMaxMlpLayers = 6; // hidden layers the fused kernel takes
+struct MlpInferArgs {
+    const __nv_bfloat16 *X;                    // bp x in_p
+    const __nv_bfloat16 *W[kMaxMlpLayers + 1]; // layer l: n_nets * N_l x K_l
+    const float *b[kMaxMlpLayers + 1];         // layer l: n_nets * N_l
+    int NL, in_p, H, out_p, bp, n_nets;
+    float *y;
+    int *flags;
+};
+bool mlp_infer_supported(int NL, int in_p, int H, int out_p);
+cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const void *in, int R, int C, int ldi, void *out, int ldo,
                                   cudaStream_t st);
 cudaError_t launch_mse_grad(const float *y, const float *t, const float *w, int M, int m_valid,

@@ -64,6 +64,10 @@ struct npsim_surr {
     int n_in = 0, n_in_p = 0, H = 0, NL = 0, n_out = 0, n_out_p = 0, n_nets = 0;
     int bcap = 0; // batch capacity (multiple of 128)
     std::vector<std::vector<Layer>> nets;
+    // per layer, the BF16 weights and FP32 biases of all networks in one block
+    // (network k at rows k out_p): Layer::Wb and Layer::b point into these
+    std::vector<__nv_bfloat16 *> Wb_stack;
+    std::vector<float *> b_stack;
     std::vector<float> xm, xs, ym, ys; // normalisation
     cudaStream_t st = nullptr;
     // activations and gradients for one batch
@@ -90,9 +94,9 @@ struct npsim_surr {
     {
         for (auto &net : nets)
             for (auto &L : net) {
+                L.b = nullptr; // inside b_stack / Wb_stack
+                L.Wb = nullptr;
                 dfree2(L.W);
-                dfree2(L.b);
-                dfree2(L.Wb);
                 dfree2(L.Wt);
                 dfree2(L.mW);
                 dfree2(L.vW);
@@ -127,6 +131,10 @@ struct npsim_surr {
         dfree2(flags);
         dfree2(dsx);
         dfree2(dsy);
+        for (auto *p : Wb_stack)
+            dfree2(p);
+        for (auto *p : b_stack)
+            dfree2(p);
         if (st)
             cudaStreamDestroy(st);
     }
@@ -397,6 +405,15 @@ int npsim_surr_create(int32_t n_in, int32_t n_hidden, int32_t n_layers, int32_t 
     if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess)
         return bail(report_error(NPSIM_ERR_CUDA, "stream create failed"));
     std::mt19937_64 rng(seed);
+    s->Wb_stack.assign(n_layers + 1, nullptr);
+    s->b_stack.assign(n_layers + 1, nullptr);
+    for (int l = 0; l <= n_layers; ++l) {
+        const size_t in_p = l == 0 ? s->n_in_p : n_hidden;
+        const size_t out_p = l == n_layers ? s->n_out_p : n_hidden;
+        if (dmalloc(&s->Wb_stack[l], (size_t)n_nets * out_p * in_p) != cudaSuccess ||
+            dmalloc(&s->b_stack[l], (size_t)n_nets * out_p) != cudaSuccess)
+            return bail(report_error(NPSIM_ERR_OOM, "surrogate weights"));
+    }
     s->nets.resize(n_nets);
     for (int k = 0; k < n_nets; ++k) {
         s->nets[k].resize(n_layers + 1);
@@ -427,8 +444,8 @@ int npsim_surr_create(int32_t n_in, int32_t n_hidden, int32_t n_layers, int32_t 
             rc = report_error(NPSIM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
             SRB(dmalloc(&L.W, nw));
-            SRB(dmalloc(&L.b, L.out_p));
-            SRB(dmalloc(&L.Wb, nw));
+            L.b = s->b_stack[l] + (size_t)k * L.out_p;
+            L.Wb = s->Wb_stack[l] + (size_t)k * nw;
             SRB(dmalloc(&L.Wt, nw));
             SRB(dmalloc(&L.mW, nw));
             SRB(dmalloc(&L.vW, nw));
@@ -691,10 +708,31 @@ int npsim_surr_predict(npsim_surr_t s, const float *X, int32_t B, float *Y_mean,
     rc = upload_batch(s, X, nullptr, B, bp);
     if (rc)
         return rc;
-    for (int k = 0; k < s->n_nets; ++k) {
-        rc = forward(s, k, bp, s->y_all + (size_t)k * bp * s->n_out_p);
-        if (rc)
-            return rc;
+    // NPSIM_SURR_LAYERED selects the layer-by-layer GEMM path (same arithmetic)
+    const bool layered = getenv("NPSIM_SURR_LAYERED") != nullptr;
+    if (!layered && mlp_infer_supported(s->NL, s->n_in_p, s->H, s->n_out_p)) {
+        // every layer of every network in one launch
+        MlpInferArgs f{};
+        f.X = s->a[0];
+        for (int l = 0; l <= s->NL; ++l) {
+            f.W[l] = s->Wb_stack[l];
+            f.b[l] = s->b_stack[l];
+        }
+        f.NL = s->NL;
+        f.in_p = s->n_in_p;
+        f.H = s->H;
+        f.out_p = s->n_out_p;
+        f.bp = bp;
+        f.n_nets = s->n_nets;
+        f.y = s->y_all;
+        f.flags = s->flags;
+        SR_CUDA(launch_mlp_infer(f, s->st));
+    } else {
+        for (int k = 0; k < s->n_nets; ++k) {
+            rc = forward(s, k, bp, s->y_all + (size_t)k * bp * s->n_out_p);
+            if (rc)
+                return rc;
+        }
     }
     float *d_mean = s->ystat, *d_spread = s->ystat + (size_t)B * s->n_out;
     const int ne = B * s->n_out;

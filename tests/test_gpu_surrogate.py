@@ -62,6 +62,29 @@ def test_surrogate_forward_backward_vs_oracle(P):
         assert np.linalg.norm(gb - ob) <= 1e-2 * np.linalg.norm(ob) + 1e-12, l
 
 
+def test_fused_inference_equals_layered_and_oracle(P, monkeypatch):
+    """Prediction runs every layer of every network in one fused tcgen05 launch;
+    it gives the same bits as the layer-by-layer GEMMs (same MMA sequence, same
+    epilogue) and matches the float64 oracle's networks within BF16 rounding.
+    300 rows: three 128-row tiles, the last one ragged."""
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((300, 8)).astype(np.float32)
+    with P.Surrogate(n_in=8, n_hidden=256, n_layers=4, n_out=65, n_nets=3, seed=5) as s:
+        m_f, sp_f = s.predict(X)
+        monkeypatch.setenv("NPSIM_SURR_LAYERED", "1")
+        m_l, sp_l = s.predict(X)
+        monkeypatch.delenv("NPSIM_SURR_LAYERED")
+        flats = [s.get_params(k)[0] for k in range(3)]
+    assert np.array_equal(m_f, m_l) and np.array_equal(sp_f, sp_l)
+    outs = []
+    for flat in flats:
+        _, _, yo = mlp.loss_and_grads(mlp.unflatten(flat, DIMS), _pad(X, 16),
+                                      np.zeros((300, 80)), n_valid=65, m_valid=300, bf=True)
+        outs.append(yo[:, :65])
+    mean_o = np.mean(outs, axis=0)
+    assert np.abs(m_f - mean_o).max() <= 1e-2 * max(1.0, np.abs(mean_o).max())
+
+
 def test_surrogate_adamw_step_vs_oracle(P):
     lr, wd = 1e-3, 1e-2
     with P.Surrogate(n_in=8, n_hidden=256, n_layers=4, n_out=65, n_nets=1, seed=5) as s:
