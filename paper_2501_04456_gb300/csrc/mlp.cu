@@ -361,9 +361,10 @@ k_mlp_infer(const __grid_constant__ MlpMaps maps, MlpDev d)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[kInferStages], empty[kInferStages], x_full, acc_full,
-        act_ready, drain;
+        act_ready, drain, bias_ready;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort, s_issued, s_x_issued;
+    __shared__ float s_bias[2][256]; // the epilogue's bias, by layer parity
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int net = blockIdx.y;
@@ -387,6 +388,7 @@ k_mlp_infer(const __grid_constant__ MlpMaps maps, MlpDev d)
         mbar_init(smem_addr(&acc_full), 1);
         mbar_init(smem_addr(&act_ready), 8); // one arrival per epilogue warp
         mbar_init(smem_addr(&drain), 1);
+        mbar_init(smem_addr(&bias_ready), kInferThreads - 64); // every epilogue thread
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
         s_issued = 0;
@@ -473,13 +475,21 @@ k_mlp_infer(const __grid_constant__ MlpMaps maps, MlpDev d)
         const int quad = warp & 3, half = (warp - 2) >> 2;
         const int r = quad * 32 + lane; // row inside the tile
         for (int l = 0; l <= d.NL; ++l) {
-            if (!mbar_wait_bounded(smem_addr(&acc_full), (uint32_t)(l & 1))) {
+            const int N = infer_n(d, l);
+            // this layer's bias into shared memory while its MMAs run.  Every
+            // epilogue thread arrives after its store and waits for all 256
+            // (bounded): the completed phase also shows that every thread has
+            // left the previous layer, so the other parity's buffer is free
+            float *bias = s_bias[l & 1];
+            if (tid - 64 < N)
+                bias[tid - 64] = d.bias[l][(size_t)net * N + (tid - 64)];
+            mbar_arrive(smem_addr(&bias_ready));
+            if (!mbar_wait_bounded(smem_addr(&bias_ready), (uint32_t)(l & 1)) ||
+                !mbar_wait_bounded(smem_addr(&acc_full), (uint32_t)(l & 1))) {
                 atomicExch(&s_abort, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int N = infer_n(d, l);
-            const float *bias = d.bias[l] + (size_t)net * N;
             const bool last = l == d.NL;
             float *yrow = last ? d.y + ((size_t)net * d.bp + m0 + r) * d.out_p : nullptr;
             for (int j = half * 16; j < N; j += 32) {
