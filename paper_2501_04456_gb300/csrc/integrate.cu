@@ -1,15 +1,18 @@
 // integrate.cu -- steps (iii)-(vi) of the loop in arXiv 2501.04456 Sec. 2.2,
 // fused into one pass over the particles:
 //   (iii) droplet radius by the radius-square law R(t)^2 = R0^2 - k t;
-//   (iv)  interface spring: s = |x| - (R(t) - sigma/2), F += -k_wall s x/|x| if s > 0;
+//   (iv)  interface spring: s = |x| - (R(t) - sigma/2), F += -k_wall s x/|x| if s > 0
+//         (wall mode 2, as printed: only while s < sigma, the band (-r, r));
 //   (v)   gravity -m g z^, centrifugal m w^2 (x, y, 0) (about z) or m w^2 x
 //         (isotropic tumbling), viscous drag inside the Langevin O step;
 //   (vi)  velocity and position update with Brownian noise:
 //         BAOAB  v += dt/2 F/m; x += dt/2 v; v = c1 v + sqrt((1-c1^2) kT/m) xi;
 //                x += dt/2 v; [forces at x_{n+1}]; v += dt/2 F/m,  c1 = exp(-gamma dt)
-//         or overdamped  x += F dt/(m gamma) + sqrt(2 kT dt/(m gamma)) xi.
+//         or overdamped  x += F dt/(m gamma) + sqrt(2 kT dt/(m gamma)) xi,
+//         or as printed  v += dt (F/m - gamma v); v += v_kick xi/|xi|; x += dt v.
 // The paper adds a fixed-magnitude random vector and has no temperature; the
-// thermostat here is the fluctuation-dissipation-consistent reading of it.
+// thermostat (BAOAB, overdamped) is the fluctuation-dissipation-consistent
+// reading of it, integrator mode 2 the step as printed.
 //
 // Precision without float64 arithmetic (GB300's FP64 rate is ~1/64 of FP32):
 // the position is the unevaluated sum of two floats, hi (the float32 word the
@@ -22,10 +25,11 @@
 // the first CTA of the launch that advances the step, for the next step).
 //
 // One kernel serves four modes (see IntMode): it sums the stream-K partials of
-// the all-pairs kernel (and the cell-list LJ forces) into the total force, adds
-// the external forces at t = step*dt, and applies the B half kick and/or the
-// BAOA part of the next step.  The step counter lives in device memory and is
-// advanced by the last CTA to finish, so a captured CUDA graph replays without
+// the all-pairs kernel (and the list forces: LJ, and the truncated Coulomb term
+// in coulomb mode 2) into the total force, adds the external forces at
+// t = step*dt, and applies the B half kick and/or the BAOA part of the next
+// step (or the overdamped step, or step (vi) as printed).  The step counter
+// lives in device memory so that a captured CUDA graph replays without
 // parameter updates: thread 0 of every CTA reads it into shared memory before
 // the CTA's one barrier and counts the CTA in right after, so the CTA that
 // counts last -- every CTA has the step by then -- advances it, and threads
