@@ -62,7 +62,9 @@ typedef struct {
     int32_t n_types;    /* 1 .. NPSIM_MAX_TYPES */
     int32_t rot_mode;   /* centrifugal force: 0 none, 1 rotation about z, 2 isotropic */
     int32_t lj_mode;    /* LJ: 0 off, 1 inside the all-pairs kernel, 2 cell list */
-    int32_t coulomb;    /* 1: all-pairs Coulomb (not truncated), 0: off */
+    int32_t coulomb;    /* 0 off; 1 all-pairs Coulomb (not truncated); 2 Coulomb truncated
+                           (not shifted) at coulomb_cut * sigma_ab, summed with LJ from
+                           the cell list (needs lj_mode 2; the paper prints 4 sigma_ab) */
     int32_t wall;       /* interface spring (Sec. 2.2 iv): 0 off (bulk liquid); 1 on every
                            NP beyond its equilibrium point R(t) - r_i; 2 only within
                            the band (-r_i, r_i) about the surface, as step (iv) prints it */
