@@ -238,19 +238,24 @@ def kernel_source_hash(packed):
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def _traffic_from_profile(packed):
-    """dram bytes per launch recorded by the committed ncu summary, if it was taken
-    on the current source of the all-pairs kernel in use (else null)."""
+def _traffic_from_profile(cfg):
+    """dram bytes per launch recorded by the committed ncu summary for the launch
+    in use (its shape's index in the autotuner's table and its number of
+    stream-K ranges), if it was taken on the current source of the all-pairs
+    kernel (else null)."""
     path = os.path.join(ROOT, "profiles", "allpairs_paper_scale250000.md")
     try:
         txt = open(path).read()
-        h = kernel_source_hash(packed)
+        h = kernel_source_hash(cfg.get("packed", 0))
     except OSError:
         return None
     m_h = re.search(r"source sha256\[:16\]:\s*([0-9a-f]{16})", txt)
-    m_t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
-    if m_h and m_t and m_h.group(1) == h:
-        return float(m_t.group(1))
+    if not (m_h and m_h.group(1) == h):
+        return None
+    pat = r"dram bytes per full launch, shape (\d+), (\d+) ranges:\s*([0-9.eE+]+)"
+    for idx, ranges, val in re.findall(pat, txt):
+        if int(idx) == cfg.get("index") and int(ranges) == cfg.get("ranges"):
+            return float(val)
     return None
 
 
@@ -594,7 +599,7 @@ def run_ours(a):
     peak_tflops = info["sm_count"] * 128 * 2 * max_mhz * 1e6 / 1e12
     ap_avg = sum(ap_ms) / len(ap_ms)
     achieved = FLOPS_PER_PAIR * pairs_per_step / (ap_avg * 1e-3) / 1e12
-    traffic = _traffic_from_profile(cfg.get("packed", 0))
+    traffic = _traffic_from_profile(cfg)
 
     # the same workload with the neutral NPs left out of the Coulomb sum (their
     # Coulomb terms are exactly zero): reported beside the headline, which sums

@@ -227,15 +227,24 @@ int npsim_philox(uint64_t seed, const uint32_t ctr[4], int64_t n_blocks, uint32_
 int npsim_normals(uint64_t seed, int64_t step, int64_t n, double *out);
 
 /* Launch shape of the all-pairs kernel chosen by the autotuner: threads per
- * CTA, particles i per thread, j-tile length, CTAs, the index of the shape in
+ * CTA, particles i per thread, j-tile length, CTAs launched, the index of the shape in
  * the autotuner's table, and 1 if it is the packed float32x2 Coulomb kernel, 2
  * if it is the packed Coulomb kernel over partners grouped by charge value, 3
  * if it is the packed LJ + Coulomb kernel over partners grouped by type (0: the
- * scalar kernel).  Any pointer may be NULL.  The environment variable NPSIM_AUTOTUNE=1:<index>
- * forces a shape at npsim_create (NPSIM_AUTOTUNE=0: the first shape); with
+ * scalar kernel).  Any pointer may be NULL.  The grouped kernels (2, 3) cut
+ * their work into a number of ranges per CTA that the autotuner also picks and
+ * hand the ranges out at run time.  The environment variable
+ * NPSIM_AUTOTUNE=1:<index>[:<ranges per CTA>] forces a shape at npsim_create
+ * (NPSIM_AUTOTUNE=0: the first shape); with
  * NPSIM_AUTOTUNE_LOG set, the autotuners print every candidate's time to stderr. */
 int npsim_allpairs_config(npsim_sim_t sim, int *block, int *i_per_thread, int *j_tile,
                           int *grid, int *index, int *packed);
+
+/* Number of stream-K ranges the all-pairs work is cut into (each writes its
+ * own partial slot; equal to the CTAs launched unless the shape is a grouped
+ * one, whose CTAs take further ranges from a device counter as they finish);
+ * 0 without an all-pairs sum. */
+int npsim_allpairs_ranges(npsim_sim_t sim, int *ranges);
 
 /* Number of launch shapes in the autotuner's table. */
 int npsim_allpairs_num_configs(int *count);

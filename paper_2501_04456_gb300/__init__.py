@@ -112,6 +112,7 @@ def lib():
             L.npsim_normals.argtypes = [C.c_uint64, C.c_int64, C.c_int64, _d]
             L.npsim_allpairs_config.argtypes = [_h, _i32, _i32, _i32, _i32, _i32, _i32]
             L.npsim_allpairs_num_configs.argtypes = [_i32]
+            L.npsim_allpairs_ranges.argtypes = [_h, _i32]
             L.npsim_coulomb_forces_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_double,
                                                        C.c_void_p, C.c_void_p]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
@@ -361,7 +362,11 @@ def npsim_allpairs_config(h):
     v = [C.c_int32() for _ in range(6)]
     _check(lib().npsim_allpairs_config(h, *[C.byref(x) for x in v]))
     keys = ("block", "i_per_thread", "j_tile", "grid", "index", "packed")
-    return {k: x.value for k, x in zip(keys, v)}
+    out = {k: x.value for k, x in zip(keys, v)}
+    r = C.c_int32()
+    _check(lib().npsim_allpairs_ranges(h, C.byref(r)))
+    out["ranges"] = r.value
+    return out
 
 
 def npsim_allpairs_num_configs():

@@ -97,8 +97,12 @@ int check_device(int *sms)
 }
 
 std::mutex g_tune_mu;
-// (n, lj, grouped length, skip_neutral) -> launch shape
-std::map<std::array<long long, 4>, int> g_tune_cache;
+// (n, lj, grouped length, skip_neutral) -> (launch shape, ranges per CTA)
+std::map<std::array<long long, 4>, std::pair<int, int>> g_tune_cache;
+// Ranges per CTA the autotuner tries for the grouped kernels (dynamic
+// launches), and the one a forced shape gets by default.
+constexpr int kRangesPerCta[] = {1, 4, 16};
+constexpr int kDefaultRangesPerCta = 4;
 // ensembles: (grouped length, LJ on, Coulomb on) of every droplet -> launch shape
 std::map<std::vector<long long>, int> g_ens_tune_cache;
 
@@ -110,11 +114,11 @@ void fill_streamk(StreamK &sk, int n, const ApConfig &c, int grid_target)
     sk.n_jt = (n + c.jt - 1) / c.jt;
     sk.W = (long long)sk.n_it * sk.n_jt;
     sk.grid = (int)std::min<long long>(std::max(grid_target, 1), sk.W);
-    sk.pad_ = 0;
+    sk.ctas = 0;
 }
 
-// Floats of stream-K partial slots: one slot per (i-tile row, CTA) pair a row
-// can meet, each (hi x, y, z, lo x, y, z) x itile.
+// Floats of stream-K partial slots: one slot per (i-tile row, range) pair a
+// row can meet, each (hi x, y, z, lo x, y, z) x itile.
 // Verlet skin of the LJ neighbour lists (sigma units of the smallest type = 1),
 // and the squared displacement (half the skin, less 1 % for rounding) that
 // triggers a rebuild.
@@ -163,6 +167,7 @@ struct npsim_sim {
     float4 *xq = nullptr;
     int *typ = nullptr;
     float *slots = nullptr;
+    unsigned *ap_work = nullptr;          // range counters of the grouped kernels [2]
     float *F_lj = nullptr;                // [n][8]: (hi x, y, z, lo x | lo y, z, -, -)
     PairTab *tab_full = nullptr, *tab_lj = nullptr, *tab_coul = nullptr;
     float rc2_lim = 0.0f; // largest LJ rc^2 of the table (x 1.0001): tile-culling bound
@@ -181,6 +186,7 @@ struct npsim_sim {
 
     bool ap = false, ap_lj = false;
     int ap_idx = 0;
+    int ap_per_cta = kDefaultRangesPerCta; // stream-K ranges per CTA (grouped kernels)
 
     // type-grouped order for the grouped kernels (built when pair sums are on)
     int *perm = nullptr;    // [n_perm] particle at each grouped position, -1 = padding
@@ -245,6 +251,7 @@ struct npsim_sim {
         dfree(xq);
         dfree(typ);
         dfree(slots);
+        dfree(ap_work);
         dfree(perm);
         dfree(qblk);
         dfree(tblk);
@@ -340,11 +347,13 @@ int shape_occupancy(const npsim_sim *s, int k, bool lj)
     return ap_occupancy(k, lj);
 }
 
-void shape_streamk(const npsim_sim *s, int k, int grid_target, StreamK &sk)
+// Stream-K split of shape k on `ctas` CTAs; the grouped kernels cut the
+// units into per_cta ranges per CTA and hand them out at run time.
+void shape_streamk(const npsim_sim *s, int k, int ctas, int per_cta, StreamK &sk)
 {
     const ApConfig c = shape_config(k);
     if (!shape_grouped(k)) {
-        fill_streamk(sk, s->n, c, grid_target);
+        fill_streamk(sk, s->n, c, ctas);
         return;
     }
     // rows and columns over the grouped order (grp_len is a multiple of 512)
@@ -353,8 +362,9 @@ void shape_streamk(const npsim_sim *s, int k, int grid_target, StreamK &sk)
     sk.n_it = (s->grp_len + sk.itile - 1) / sk.itile;
     sk.n_jt = s->grp_len / c.jt;
     sk.W = (long long)sk.n_it * sk.n_jt;
-    sk.grid = (int)std::min<long long>(std::max(grid_target, 1), sk.W);
-    sk.pad_ = 0;
+    ctas = std::max(ctas, 1);
+    sk.grid = (int)std::min<long long>((long long)ctas * std::max(per_cta, 1), sk.W);
+    sk.ctas = std::min(ctas, sk.grid);
 }
 
 // Type-pair table of a pair sum: LJ + Coulomb, LJ only or Coulomb only.
@@ -369,11 +379,11 @@ cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, bool coul, const St
     if (shape_ljg(k))
         return launch_allpairs_ljgrp(k - ap_num_configs() - grp_num_configs(), sk, s->xq,
                                      s->perm, s->n_perm, s->tblk, pair_table(s, lj, coul),
-                                     lj ? s->rc2_lim : 0.0f, coul ? s->any_charge : 0, slots,
-                                     st);
+                                     lj ? s->rc2_lim : 0.0f, coul ? s->any_charge : 0,
+                                     s->ap_work, slots, st);
     if (shape_grouped(k))
         return launch_allpairs_grouped(k - ap_num_configs(), sk, s->xq, s->perm, s->n_perm,
-                                       s->qblk, slots, st);
+                                       s->qblk, s->ap_work, slots, st);
     return launch_allpairs(k, lj, sk, s->xq, s->typ, s->n, lj ? pair_table(s, lj, coul) : nullptr,
                            slots, st);
 }
@@ -562,22 +572,27 @@ int read_flags(npsim_sim *s)
     return NPSIM_OK;
 }
 
-// Pick the all-pairs launch shape: time each candidate on the current positions.
+// Pick the all-pairs launch shape (and, for the grouped kernels, the ranges
+// per CTA): time each candidate on the current positions.
 int autotune(npsim_sim *s)
 {
     const bool lj = s->ap_lj;
     const int nc = shape_count();
-    // NPSIM_AUTOTUNE=0 takes the first shape; NPSIM_AUTOTUNE=1:<index> forces one
-    // (ignored if that shape cannot run this sum); neither touches the cache.
+    // NPSIM_AUTOTUNE=0 takes the first shape; NPSIM_AUTOTUNE=1:<index>[:<ranges per
+    // CTA>] forces one (ignored if that shape cannot run this sum); neither
+    // touches the cache.
     const char *env = getenv("NPSIM_AUTOTUNE");
     if (env && env[0] == '0') {
         s->ap_idx = 0;
+        s->ap_per_cta = kDefaultRangesPerCta;
         return NPSIM_OK;
     }
     if (env && env[0] == '1' && env[1] == ':') {
         const int idx = atoi(env + 2);
+        const char *m = strchr(env + 2, ':');
         if (idx >= 0 && idx < nc && shape_occupancy(s, idx, lj) > 0) {
             s->ap_idx = idx;
+            s->ap_per_cta = m ? std::max(1, atoi(m + 1)) : kDefaultRangesPerCta;
             return NPSIM_OK;
         }
     }
@@ -587,11 +602,13 @@ int autotune(npsim_sim *s)
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            s->ap_idx = it->second;
+            s->ap_idx = it->second.first;
+            s->ap_per_cta = it->second.second;
             return NPSIM_OK;
         }
     }
-    int best = 0;
+    const int n_m = (int)(sizeof(kRangesPerCta) / sizeof(kRangesPerCta[0]));
+    int best = 0, best_m = kDefaultRangesPerCta;
     {
         // scratch big enough for every candidate
         size_t need = 0;
@@ -600,7 +617,7 @@ int autotune(npsim_sim *s)
             if (occ <= 0)
                 continue;
             StreamK sk;
-            shape_streamk(s, c, occ * s->sms, sk);
+            shape_streamk(s, c, occ * s->sms, kRangesPerCta[n_m - 1], sk);
             need = std::max(need, slots_floats(sk));
         }
         float *tmp = nullptr;
@@ -615,27 +632,36 @@ int autotune(npsim_sim *s)
             const int occ = shape_occupancy(s, c, lj);
             if (occ <= 0)
                 continue;
-            StreamK sk;
-            shape_streamk(s, c, occ * s->sms, sk);
-            if (shape_launch(s, c, lj, coul, sk, tmp, s->user) != cudaSuccess)
-                continue;
-            const int reps = s->n > 100000 ? 2 : 5;
-            cudaEventRecord(e0, s->user);
-            for (int r = 0; r < reps; ++r)
-                shape_launch(s, c, lj, coul, sk, tmp, s->user);
-            cudaEventRecord(e1, s->user);
-            if (cudaEventSynchronize(e1) != cudaSuccess)
-                continue;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (log) {
-                const ApConfig cf = shape_config(c);
-                fprintf(stderr, "npsim autotune n=%d shape %d <%d,%d,%d> grid %d: %.4f ms\n",
-                        s->n, c, cf.block, cf.ki, cf.jt, sk.grid, ms / reps);
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
+            for (int mi = 0; mi < (shape_grouped(c) ? n_m : 1); ++mi) {
+                const int m = shape_grouped(c) ? kRangesPerCta[mi] : 1;
+                StreamK sk;
+                shape_streamk(s, c, occ * s->sms, m, sk);
+                if (shape_grouped(c) && mi > 0 && sk.grid == sk.ctas)
+                    break; // no more ranges than CTAs: the same launch as m = 1
+                if (shape_launch(s, c, lj, coul, sk, tmp, s->user) != cudaSuccess)
+                    continue;
+                const int reps = s->n > 100000 ? 2 : 5;
+                cudaEventRecord(e0, s->user);
+                for (int r = 0; r < reps; ++r)
+                    shape_launch(s, c, lj, coul, sk, tmp, s->user);
+                cudaEventRecord(e1, s->user);
+                if (cudaEventSynchronize(e1) != cudaSuccess)
+                    continue;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (log) {
+                    const ApConfig cf = shape_config(c);
+                    fprintf(stderr,
+                            "npsim autotune n=%d shape %d <%d,%d,%d> grid %d ranges %d: "
+                            "%.4f ms\n",
+                            s->n, c, cf.block, cf.ki, cf.jt, sk.ctas > 0 ? sk.ctas : sk.grid,
+                            sk.grid, ms / reps);
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                    best_m = m;
+                }
             }
         }
         cudaEventDestroy(e0);
@@ -646,8 +672,9 @@ int autotune(npsim_sim *s)
             return set_err(NPSIM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
     }
     s->ap_idx = best;
+    s->ap_per_cta = best_m;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_cache[key] = best;
+    g_tune_cache[key] = std::make_pair(best, best_m);
     return NPSIM_OK;
 }
 
@@ -1156,11 +1183,13 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
         rc = build_grouping(s, type, x0, rank);
         if (rc)
             return bail(rc);
+        BAIL_CUDA(dalloc(&s->ap_work, 2));
+        BAIL_CUDA(cudaMemset(s->ap_work, 0, 2 * sizeof(unsigned)));
         rc = autotune(s);
         if (rc)
             return bail(rc);
         const int occ = std::max(1, shape_occupancy(s, s->ap_idx, s->ap_lj));
-        shape_streamk(s, s->ap_idx, occ * s->sms, s->sk);
+        shape_streamk(s, s->ap_idx, occ * s->sms, s->ap_per_cta, s->sk);
         BAIL_CUDA(dalloc(&s->slots, slots_floats(s->sk)));
     } else {
         s->sk = StreamK{};
@@ -1348,7 +1377,7 @@ int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_t
     if (j_tile)
         *j_tile = s->ap ? c.jt : 0;
     if (grid)
-        *grid = s->ap ? s->sk.grid : 0;
+        *grid = !s->ap ? 0 : s->sk.ctas > 0 ? s->sk.ctas : s->sk.grid;
     if (index)
         *index = s->ap ? s->ap_idx : -1;
     if (packed)
@@ -1357,6 +1386,13 @@ int npsim_allpairs_config(npsim_sim_t s, int *block, int *i_per_thread, int *j_t
                   : shape_grouped(s->ap_idx) ? 2
                   : ap_packed(s->ap_idx)     ? 1
                                              : 0;
+    return NPSIM_OK;
+}
+
+int npsim_allpairs_ranges(npsim_sim_t s, int *ranges)
+{
+    NP_REQUIRE(s && ranges, "sim and ranges are required");
+    *ranges = s->ap ? s->sk.grid : 0;
     return NPSIM_OK;
 }
 
@@ -2018,7 +2054,7 @@ void ens_streamk(long long n_items, const ApConfig &c, int grid_target, StreamK 
     sk.n_jt = 0;
     sk.W = n_items;
     sk.grid = (int)std::min<long long>(std::max(grid_target, 1), n_items);
-    sk.pad_ = 0;
+    sk.ctas = 0;
 }
 
 int ens_upload_geometry(npsim_ens *e, const std::vector<long long> &item0)

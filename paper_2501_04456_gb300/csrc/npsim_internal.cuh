@@ -596,17 +596,21 @@ struct StepParams {
 };
 
 // Stream-K decomposition of the all-pairs sum: W = n_it * n_jt work units
-// (i-tile x j-tile) split evenly over `grid` CTAs; CTA c covers units
-// [W c / grid, W (c+1) / grid).  The part of i-tile row r computed by CTA c is
-// written to partial slot r + c (unique: rows and CTAs both advance along
-// the unit order).
+// (i-tile x j-tile) split evenly into `grid` ranges; range c covers units
+// [W c / grid, W (c+1) / grid).  The part of i-tile row r computed in range c
+// is written to partial slot r + c (unique: rows and ranges both advance
+// along the unit order).  A static launch runs range c on CTA c; a dynamic
+// launch (the grouped kernels) starts `ctas` CTAs on ranges 0 .. ctas - 1 and
+// hands out the rest from a device counter, so a CTA that runs ahead of the
+// others on its SM takes more ranges.  Slots depend only on the range, so the
+// sums do not depend on which CTA ran which range.
 struct StreamK {
     int itile;   // i per CTA tile = block * ki
     int jtile;   // j per shared-memory tile
     int n_it;    // number of i tiles
     int n_jt;    // number of j tiles
-    int grid;    // CTAs
-    int pad_;
+    int grid;    // ranges (= CTAs of a static launch)
+    int ctas;    // CTAs of a dynamic launch (<= grid; 0 for static launches)
     long long W; // n_it * n_jt
 };
 
@@ -662,9 +666,11 @@ bool ap_packed(int idx); // float32x2 Coulomb-only kernel
 int grp_num_configs();
 ApConfig grp_config(int idx);
 int grp_occupancy(int idx);
+// work: two zeroed device counters (ranges handed out, CTAs done), reset to 0
+// by the last CTA of each launch; launches sharing one pair must not overlap.
 cudaError_t launch_allpairs_grouped(int idx, const StreamK &sk, const float4 *xq,
                                     const int *perm, int n_perm, const float *qblk,
-                                    float *slots, cudaStream_t st);
+                                    unsigned *work, float *slots, cudaStream_t st);
 // Type-grouped packed LJ + Coulomb kernel (allpairs_grouped.cu): rows and
 // columns follow perm (grouped by type, groups padded to 512), tblk = type of
 // each 256-position block; the table selects LJ + Coulomb, LJ or Coulomb.
@@ -675,8 +681,8 @@ int ljg_occupancy(int idx);
 // sqrt(rc2_lim) (0: no LJ); has_coul = 0 skips the other tiles entirely.
 cudaError_t launch_allpairs_ljgrp(int idx, const StreamK &sk, const float4 *xq,
                                   const int *perm, int n_perm, const int *tblk,
-                                  const PairTab *tab, float rc2_lim, int has_coul, float *slots,
-                                  cudaStream_t st);
+                                  const PairTab *tab, float rc2_lim, int has_coul,
+                                  unsigned *work, float *slots, cudaStream_t st);
 cudaError_t launch_allpairs(int cfg_idx, bool lj, const StreamK &sk, const float4 *xq,
                             const int *typ, int n, const PairTab *tab, float *slots,
                             cudaStream_t st);

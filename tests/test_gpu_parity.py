@@ -149,6 +149,39 @@ def test_every_launch_shape(P, monkeypatch):
     assert seen == {0, 1, 2, 3, 10, 13}
 
 
+def test_dynamic_ranges(P, monkeypatch):
+    """The grouped kernels cut their work into several ranges per CTA and hand
+    them out at run time.  For 1, 3 and 16 ranges per CTA, on droplets large
+    enough that there are more ranges than CTAs, every grouped shape gives the
+    oracle's forces on sampled rows, and a second evaluation (the CTAs taking
+    other ranges) is bit-identical."""
+    sc_c = with_(small(wl.config3(), 60001), lj_mode=0)      # Coulomb only
+    sc_l = with_(small(wl.config2(), 20011), coulomb=True)   # Coulomb + LJ
+    rng = np.random.default_rng(5)
+    checked = set()
+    for sc, packed in ((sc_c, 2), (sc_l, 3)):
+        types, x, v = wl.initial_state(sc, fp32_positions=True)
+        sel = np.unique(np.concatenate([[0, sc.n - 1], rng.choice(sc.n, 150, replace=False)]))
+        ref = _oracle_pair(sc, x, types, sel=sel)
+        amb = cutoff_ambiguous(x, types, sc)[sel]
+        for idx in range(P.npsim_allpairs_num_configs()):
+            for m in (1, 3, 16):
+                monkeypatch.setenv("NPSIM_AUTOTUNE", f"1:{idx}:{m}")
+                with P.Sim(sc, x, v, types) as sim:
+                    cfg = sim.allpairs_config()
+                    if cfg["index"] != idx or cfg["packed"] != packed:
+                        break
+                    F1 = sim.forces(1)
+                    F2 = sim.forces(1)
+                assert np.array_equal(F1, F2), (idx, m)
+                rms = np.sqrt((F1 ** 2).sum(1).mean())
+                err = np.linalg.norm(F1[sel] - ref, axis=1) / np.maximum(
+                    np.linalg.norm(ref, axis=1), rms)
+                assert err[~amb].max() <= FORCE_TOL, (idx, m, float(err.max()))
+                checked.add((packed, m))
+    assert checked == {(p, m) for p in (2, 3) for m in (1, 3, 16)}
+
+
 def test_skip_neutral_forces_and_steps(P):
     """Leaving the neutral NPs out of the Coulomb sum (their terms are exactly zero)
     gives the oracle's forces, and the same trajectory to rounding."""
