@@ -335,8 +335,11 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
 // partners' records are gathered.  An NP whose list overflowed sums over the
 // 27 cells of that build instead (a superset of its list).  Writes one 32-byte
 // (hi x, y, z, lo x, y, z, 0, 0) record per NP and closes the rebuild gate.
+// 10 CTAs of 128 per SM for the LJ-only kernel (48 registers): the partner
+// gathers are latency-bound, and more threads in flight help (0.114 -> 0.100 ms
+// per step on 4.2 M NPs; 12 CTAs spill).  The truncated-Coulomb variant keeps 8.
 template <bool COUL>
-__global__ void __launch_bounds__(128, 8)
+__global__ void __launch_bounds__(128, COUL ? 8 : 10)
 k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
          const int *__restrict__ pos, const float4 *__restrict__ sxq,
          const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
@@ -358,36 +361,29 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
     const int ti = typ[i];
     const int row = ti * NPSIM_MAX_TYPES;
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    auto pair = [&](const float4 pj, int tj) {
+    // One pair's force added into (sx, sy, sz); 1/r^2 as rsqrt(r^2)^2, as in
+    // the all-pairs kernels.  The block sums go into the compensated (hi, lo)
+    // totals by flush(), once per block of up to four partners.
+    auto pair = [&](const float4 pj, int tj, float &sx, float &sy, float &sz) {
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float4 t = s_tab[row + tj];
-        if (COUL) { // LJ (r < rc_ab) plus Coulomb truncated at its own cutoff
-            float f = 0.0f;
-            if (r2 < t.z) {
-                const float rinv2 = 1.0f / r2;
-                const float s2 = t.x * rinv2;
-                const float s6 = s2 * s2 * s2;
-                f = t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f);
-            }
-            if (r2 < s_rcc2[row + tj]) {
-                const float ri = rsqrtf(r2);
-                f = fmaf(t.w * ri, ri * ri, f); // C q_a q_b / r^3
-            }
-            if (f != 0.0f) {
-                two_sum_acc(hx, lx, f * dx);
-                two_sum_acc(hy, ly, f * dy);
-                two_sum_acc(hz, lz, f * dz);
-            }
-        } else if (r2 < t.z) {
-            const float rinv2 = 1.0f / r2;
-            const float s2 = t.x * rinv2;
-            const float s6 = s2 * s2 * s2;
-            const float f = t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f);
-            two_sum_acc(hx, lx, f * dx);
-            two_sum_acc(hy, ly, f * dy);
-            two_sum_acc(hz, lz, f * dz);
-        }
+        const float ri = rsqrtf(r2);
+        const float rinv2 = ri * ri;
+        const float s2 = t.x * rinv2;
+        const float s6 = s2 * s2 * s2;
+        // LJ (r < rc_ab) plus, with COUL, Coulomb truncated at its own cutoff
+        float f = r2 < t.z ? t.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f) : 0.0f;
+        if (COUL && r2 < s_rcc2[row + tj])
+            f = fmaf(t.w * ri, rinv2, f); // C q_a q_b / r^3
+        sx = fmaf(f, dx, sx);
+        sy = fmaf(f, dy, sy);
+        sz = fmaf(f, dz, sz);
+    };
+    auto flush = [&](float sx, float sy, float sz) {
+        two_sum_acc(hx, lx, sx);
+        two_sum_acc(hy, ly, sy);
+        two_sum_acc(hz, lz, sz);
     };
     // List entries are read four at a time, one block ahead of their use (rows
     // below cap exist whatever the count), so each block's partner positions
@@ -409,22 +405,28 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 en[u] = k + 4 + u < cap ? nbr[(size_t)(k + 4 + u) * n + i] : 0u;
+            float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                pair(pj[u], (int)(e[u] & 7u));
+                pair(pj[u], (int)(e[u] & 7u), sx, sy, sz);
+            flush(sx, sy, sz);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 e[u] = en[u];
         }
-        float4 pj[4]; // the last cnt - k < 4 entries
+        if (k < cnt) { // the last cnt - k < 4 entries
+            float4 pj[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (k + u < cnt)
-                pj[u] = xq[e[u] >> 3];
+            for (int u = 0; u < 4; ++u)
+                if (k + u < cnt)
+                    pj[u] = xq[e[u] >> 3];
+            float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (k + u < cnt)
-                pair(pj[u], (int)(e[u] & 7u));
+            for (int u = 0; u < 4; ++u)
+                if (k + u < cnt)
+                    pair(pj[u], (int)(e[u] & 7u), sx, sy, sz);
+            flush(sx, sy, sz);
+        }
     } else {
         const int p = pos[i];
         const float4 pb = sxq[p]; // cells of the build
@@ -441,8 +443,11 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
                 const int b = start[base + max(cx - 1, 0)];
                 const int e = start[base + min(cx + 1, g.dim - 1) + 1];
                 for (int q = b; q < e; ++q)
-                    if (q != p)
-                        pair(xq[sorted[q]], __float_as_int(sxq[q].w));
+                    if (q != p) {
+                        float sx = 0.f, sy = 0.f, sz = 0.f;
+                        pair(xq[sorted[q]], __float_as_int(sxq[q].w), sx, sy, sz);
+                        flush(sx, sy, sz);
+                    }
             }
         }
     }
