@@ -250,10 +250,17 @@ def npsim_step(h, n_steps):
     _check(lib().npsim_step(h, int(n_steps)))
 
 
-def npsim_get_state(h, n):
-    x = np.empty((n, 3))
-    v = np.empty((n, 3))
-    F = np.empty((n, 3))
+def npsim_get_state(h, n, out=None):
+    """Positions, velocities and forces (n x 3 float64 each) and the step.  out:
+    optional (x, v, F) arrays to fill, e.g. views of page-locked host memory,
+    which the device copies reach faster than pageable memory."""
+    if out is None:
+        x, v, F = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+    else:
+        x, v, F = out
+        for a in (x, v, F):
+            if a.shape != (n, 3) or a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("out arrays must be C-contiguous float64 of shape (n, 3)")
     st = C.c_int64()
     _check(lib().npsim_get_state(h, _p(x, C.c_double), _p(v, C.c_double),
                                  _p(F, C.c_double), C.byref(st)))
