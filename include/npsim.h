@@ -288,6 +288,21 @@ int npsim_ens_get_state(npsim_ens_t ens, int32_t d, double *x, double *v, double
 /* Total forces of droplet d at the current state (recomputed), n_d x 3. */
 int npsim_ens_forces(npsim_ens_t ens, int32_t d, double *F);
 
+/* Statistics of Sec. 3 of droplet d at the ensemble's current step, computed on
+ * the device from the ensemble's own state (no copy of the positions to the
+ * host): the same outputs, definitions and units as npsim_stats -- the RDF of
+ * Sec. 3.2 (ordered-pair counts and g, V the droplet's volume 4 pi R_d(t)^3 / 3),
+ * the radial concentration C_NPs, N_surf, R_g and D_f by the fractal equation
+ * (Sec. 3.1, Eqs. N, Rg, r0, with the droplet's number-mean diameter) and the
+ * box-counting D_f.  Host outputs as in npsim_stats (rdf_counts/rdf_g n_bins,
+ * radial_counts/radial_c radial_bins; any of the four may be NULL).  Scratch is
+ * allocated on the first call and grown for larger droplets; the call
+ * synchronises the ensemble's stream.  Errors: INVALID_ARG (d outside
+ * [0, n_drops), bad cfg), OOM, CUDA. */
+int npsim_ens_stats(npsim_ens_t ens, int32_t d, const npsim_stats_cfg_t *cfg,
+                    int64_t *rdf_counts, double *rdf_g, int64_t *radial_counts,
+                    double *radial_c, npsim_stats_t *out);
+
 /* Launch shape of the ensemble all-pairs kernel (any pointer may be NULL). */
 int npsim_ens_config(npsim_ens_t ens, int *block, int *i_per_thread, int *j_tile, int *grid,
                      int *index);
@@ -360,9 +375,9 @@ int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, 
 /*
  * All-pairs Coulomb forces without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc when
- * they need forces -- code inside an open CUDA stream capture (where allocation
- * is not allowed), frameworks whose own pool owns all device memory, or
- * real-time loops that cannot risk an allocation's latency or failure.
+ * they need forces -- code running under a framework whose own memory pool owns
+ * all device memory and forbids raw allocations, or a real-time loop that cannot
+ * risk an allocation's latency or its failure in the middle of a run.
  *
  * Computes F_i = C q_i sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3, the same sum
  * as npsim_forces(sim, 3, ...), from dev_xyzq (device, n float4 records
@@ -375,13 +390,32 @@ int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, 
  * [1, 32768]; larger n is rejected with NPSIM_ERR_INVALID_ARG.  The first call
  * on a device looks up the array's device address for that device (set-up,
  * once per device, with that device current); make that first call before any
- * stream capture.  Every call on a device shares the array: calls that overlap
- * on the GPU (different streams without ordering) race and give wrong forces.
- * Each call writes every partial it reads, so nothing carries over from the
- * previous call.  Allocates nothing (no cudaMalloc/cudaFree).
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset (or anything else that destroys the device's primary context)
+ * the kept address is stale, so do not call this entry point again in that
+ * process.  Every call on a device shares the array: calls that overlap on the
+ * GPU (different streams without ordering) race and give wrong forces.  Each
+ * call writes every partial it reads, so nothing carries over from the previous
+ * call.  Allocates nothing (no cudaMalloc/cudaFree).
  */
 int npsim_coulomb_forces_noalloc(const float *dev_xyzq, int64_t n, double bjerrum,
                                  double *dev_F, void *stream);
+
+/*
+ * Measurement hook: the FP32 CUDA-core rate that bounds the all-pairs kernels
+ * (their pair body is FP32 arithmetic, not a dense contraction).  One launch of
+ * one full wave of CTAs (every SM filled to its occupancy limit), each thread
+ * running 8 independent chains of `iters` dependent fused multiply-adds:
+ * scalar FFMA (packed = 0, 2 flops per lane) or the packed float32x2 FFMA2 the
+ * pair kernels issue (packed = 1, 4 flops per lane), after one shorter warm-up
+ * launch, timed with CUDA events on `stream`.  *flops: floating-point
+ * operations of the timed launch; *ms: its duration; *grid (may be NULL): CTAs
+ * launched.  The achieved rate is *flops / *ms; it depends on the SM clock
+ * during the launch, which the caller samples.  Allocates a small sink buffer;
+ * synchronises the stream.  Errors: INVALID_ARG (iters outside [1, 2^40],
+ * NULL outputs), CUDA, NO_DEVICE. */
+int npsim_fma_peak(int packed, int64_t iters, void *stream, double *flops, float *ms,
+                   int *grid);
 
 /* Kernel launches per step in a long run (pair kernels + cell-list kernels + one
  * integrator pass); npsim_step adds one integrator launch per graph chunk. */

@@ -116,6 +116,8 @@ def lib():
             L.npsim_coulomb_forces_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_double,
                                                        C.c_void_p, C.c_void_p]
             L.npsim_launches_per_step.argtypes = [_h, _i32]
+            L.npsim_fma_peak.argtypes = [C.c_int, C.c_int64, C.c_void_p, _d,
+                                         C.POINTER(C.c_float), _i32]
             L.npsim_cell_grid.argtypes = [_h, _i32, _i64]
             L.npsim_nbr_info.argtypes = [_h, _i32, _d, _i64]
             L.npsim_ens_create.argtypes = [C.POINTER(npsim_droplet_t), C.c_int32, C.c_void_p,
@@ -124,6 +126,8 @@ def lib():
             L.npsim_ens_get_state.argtypes = [_h, C.c_int32, _d, _d, _d, _i64]
             L.npsim_ens_forces.argtypes = [_h, C.c_int32, _d]
             L.npsim_ens_config.argtypes = [_h, _i32, _i32, _i32, _i32, _i32]
+            L.npsim_ens_stats.argtypes = [_h, C.c_int32, C.POINTER(npsim_stats_cfg_t), _i64,
+                                          _d, _i64, _d, C.POINTER(npsim_stats_t)]
             L.npsim_ens_info.argtypes = [_h, _i64, _d]
             L.npsim_ens_destroy.argtypes = [_h]
             L.npsim_ens_destroy.restype = None
@@ -284,23 +288,30 @@ def npsim_positions_device(h, dev_ptr):
     _check(lib().npsim_positions_device(h, C.c_void_p(int(dev_ptr))))
 
 
-def npsim_stats(h, r_max=10.0, n_bins=128, radial_bins=0, boxcount=True,
-                max_scales=MAX_SCALES):
+def _stats_call(fn, r_max, n_bins, radial_bins, boxcount, max_scales):
+    """Marshal the statistics outputs of npsim_stats / npsim_ens_stats: fn(cfg,
+    rdf_counts, rdf_g, radial_counts, radial_c, out) returns the status."""
     cfg = npsim_stats_cfg_t(r_max, n_bins, radial_bins, int(boxcount), max_scales)
     counts = np.zeros(max(n_bins, 1), np.int64)
     g = np.zeros(max(n_bins, 1))
     rc_ = np.zeros(max(radial_bins, 1), np.int64)
     rcc = np.zeros(max(radial_bins, 1))
     out = npsim_stats_t()
-    _check(lib().npsim_stats(h, C.byref(cfg), _p(counts, C.c_int64), _p(g, C.c_double),
-                             _p(rc_, C.c_int64) if radial_bins else None,
-                             _p(rcc, C.c_double) if radial_bins else None, C.byref(out)))
+    _check(fn(C.byref(cfg), _p(counts, C.c_int64), _p(g, C.c_double),
+              _p(rc_, C.c_int64) if radial_bins else None,
+              _p(rcc, C.c_double) if radial_bins else None, C.byref(out)))
     ns = out.n_scales
     return {"R": out.R, "d_mean": out.d_mean, "Rg": out.Rg, "Df_rg": out.Df_rg,
             "Df_box": out.Df_box, "center": np.array(out.center[:]),
             "nbox": np.array(out.nbox[:ns], np.int64), "n_surf": int(out.n_surf),
             "rdf_counts": counts[:n_bins], "rdf_g": g[:n_bins],
             "radial_counts": rc_[:radial_bins], "radial_c": rcc[:radial_bins]}
+
+
+def npsim_stats(h, r_max=10.0, n_bins=128, radial_bins=0, boxcount=True,
+                max_scales=MAX_SCALES):
+    return _stats_call(lambda *a: lib().npsim_stats(h, *a), r_max, n_bins, radial_bins,
+                       boxcount, max_scales)
 
 
 def npsim_scattering(g, r_max, n_surf, q, Rg=1.0, Df=3.0):
@@ -388,6 +399,16 @@ def npsim_coulomb_forces_noalloc(dev_xyzq, n, bjerrum, dev_F, stream=None):
     _check(lib().npsim_coulomb_forces_noalloc(C.c_void_p(int(dev_xyzq)), int(n),
                                               float(bjerrum), C.c_void_p(int(dev_F)),
                                               _stream_handle(stream)))
+
+
+def npsim_fma_peak(packed=True, iters=1 << 16, stream=None):
+    """FP32 FMA microbenchmark: (flops, ms, grid) of one timed launch."""
+    fl = C.c_double()
+    ms = C.c_float()
+    g = C.c_int32()
+    _check(lib().npsim_fma_peak(int(bool(packed)), int(iters), _stream_handle(stream),
+                                C.byref(fl), C.byref(ms), C.byref(g)))
+    return fl.value, ms.value, g.value
 
 
 def npsim_launches_per_step(h):
@@ -566,6 +587,12 @@ def npsim_ens_config(h):
     return dict(zip(("block", "i_per_thread", "j_tile", "grid", "index"), [x.value for x in v]))
 
 
+def npsim_ens_stats(h, d, r_max=10.0, n_bins=128, radial_bins=0, boxcount=True,
+                    max_scales=MAX_SCALES):
+    return _stats_call(lambda *a: lib().npsim_ens_stats(h, int(d), *a), r_max, n_bins,
+                       radial_bins, boxcount, max_scales)
+
+
 def npsim_ens_info(h):
     n = C.c_int64()
     p = C.c_double()
@@ -595,6 +622,9 @@ class Ensemble:
 
     def config(self):
         return npsim_ens_config(self.h)
+
+    def stats(self, d, **kw):
+        return npsim_ens_stats(self.h, d, **kw)
 
     def info(self):
         return npsim_ens_info(self.h)

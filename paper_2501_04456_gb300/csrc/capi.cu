@@ -77,6 +77,39 @@ void free_cells(CellBufs &b)
     dfree(b.tile_sum);
 }
 
+// Scratch of the statistics of Sec. 3 (allocated on first use, grown as needed):
+// float64 positions, the cell list of the pair histogram, the histograms, the
+// per-CTA partial sums and the box-counting hash table.
+struct StatsWork {
+    double *x = nullptr; // [3][n] float64 positions (hi + lo), when the owner has none
+    int x_cap = 0;
+    CellGrid grid{};
+    CellBufs cb{};
+    int cells_cap = 0, cells_n = 0; // cells and NPs the cell buffers hold
+    unsigned long long *hist = nullptr, *rhist = nullptr;
+    int hist_cap = 0, rhist_cap = 0;
+    double *part = nullptr; // 3 doubles per CTA of 256 threads
+    int part_cap = 0;
+    double *vec = nullptr;  // centre of mass [3], box origin [3]
+    unsigned long long *table = nullptr;
+    unsigned long long table_size = 0;
+    int *count = nullptr;
+    unsigned long long *surf = nullptr; // N_surf counter
+};
+void free_stats(StatsWork &w)
+{
+    dfree(w.x);
+    free_cells(w.cb);
+    dfree(w.hist);
+    dfree(w.rhist);
+    dfree(w.part);
+    dfree(w.vec);
+    dfree(w.table);
+    dfree(w.count);
+    dfree(w.surf);
+    w = StatsWork{};
+}
+
 int check_device(int *sms)
 {
     int count = 0;
@@ -212,16 +245,7 @@ struct npsim_sim {
     cudaEvent_t rec_ready[kRecSlots]{}, rec_done[kRecSlots]{};
 
     // statistics (allocated on first use)
-    CellGrid sgrid{};
-    CellBufs scb{};
-    int s_cells_cap = 0;
-    unsigned long long *s_hist = nullptr, *s_rhist = nullptr;
-    int s_hist_cap = 0, s_rhist_cap = 0;
-    double *s_part = nullptr, *s_vec = nullptr;
-    unsigned long long *s_table = nullptr;
-    unsigned long long s_table_size = 0;
-    int *s_count = nullptr;
-    unsigned long long *s_surf = nullptr; // N_surf counter
+    StatsWork sw{};
 
     ~npsim_sim()
     {
@@ -270,14 +294,7 @@ struct npsim_sim {
         dfree(nl.x_ref);
         dfree(nl.builds);
         free_cells(cb);
-        free_cells(scb);
-        dfree(s_hist);
-        dfree(s_rhist);
-        dfree(s_part);
-        dfree(s_vec);
-        dfree(s_table);
-        dfree(s_count);
-        dfree(s_surf);
+        free_stats(sw);
         dfree(d_rcc2);
         if (cap)
             cudaStreamDestroy(cap);
@@ -1502,72 +1519,96 @@ int npsim_kernel_times(npsim_sim_t s, double *ms, int *samples)
 // ---------------------------------------------------------------------------
 // Statistics
 
-int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
-                double *rdf_g, int64_t *radial_counts, double *radial_c, npsim_stats_t *out)
+} // extern "C"
+
+namespace {
+
+// One reduction of launch_block_reduce over n positions, its per-CTA partials
+// copied to the host (CTA order).
+int block_partials(StatsWork &w, int mode, const double *x, int n, const double *c,
+                   std::vector<double> &part, cudaStream_t st)
 {
-    NP_REQUIRE(s && cfg && out, "sim, cfg and out are required");
-    NP_REQUIRE(cfg->n_bins >= 0 && cfg->radial_bins >= 0, "bins must be >= 0");
-    NP_REQUIRE(cfg->n_bins == 0 || cfg->r_max > 0, "r_max must be positive");
-    NP_REQUIRE(cfg->max_scales >= 0 && cfg->max_scales <= NPSIM_MAX_SCALES,
-               "max_scales must be in [0, %d]", NPSIM_MAX_SCALES);
-    const int n = s->n;
-    cudaStream_t st = s->user;
+    const int nblk = (n + 255) / 256;
+    part.resize(3 * (size_t)nblk);
+    NP_CUDA(launch_block_reduce(mode, x, n, c, w.part, st));
+    NP_CUDA(cudaMemcpyAsync(part.data(), w.part, sizeof(double) * part.size(),
+                            cudaMemcpyDeviceToHost, st));
+    NP_CUDA(cudaStreamSynchronize(st));
+    return NPSIM_OK;
+}
+
+// The statistics of Sec. 3 of one droplet of n NPs whose float64 positions
+// ([3][n]) are x, float32 hi words xq and types typ (all device), at droplet
+// radius R: the RDF (Sec. 3.2), the radial concentration C_NPs, N_surf, the
+// centre of mass and R_g (Eqs. r0, Rg), D_f from the fractal equation (Eq. N)
+// and by box counting.  Shared by npsim_stats and npsim_ens_stats.
+int stats_core(StatsWork &w, const double *x, const float4 *xq, const int *typ, int n, double R,
+               double d_mean, const npsim_type_t *types, int T, int *d_flags,
+               const npsim_stats_cfg_t *cfg, int64_t *rdf_counts, double *rdf_g,
+               int64_t *radial_counts, double *radial_c, npsim_stats_t *out, cudaStream_t st)
+{
     memset(out, 0, sizeof(*out));
-    const double t = (double)s->step * s->P.dt;
-    const double R2 = s->P.R0 * s->P.R0 - s->P.k_evap * t;
-    const double R = R2 > 0 ? std::sqrt(R2) : 0.0;
     out->R = R;
-    out->d_mean = s->d_mean;
+    out->d_mean = d_mean;
     const double pi = 3.14159265358979323846;
 
     const int nblk = (n + 255) / 256;
-    if (!s->s_part) {
-        NP_CUDA(dalloc(&s->s_part, 3 * (size_t)nblk));
-        NP_CUDA(dalloc(&s->s_vec, 8));
-        NP_CUDA(dalloc(&s->s_count, 1));
-        NP_CUDA(dalloc(&s->s_surf, 1));
+    if (!w.vec) {
+        NP_CUDA(dalloc(&w.vec, 8));
+        NP_CUDA(dalloc(&w.count, 1));
+        NP_CUDA(dalloc(&w.surf, 1));
     }
-    int rc0 = positions_f64(s);
-    if (rc0)
-        return rc0;
-    std::vector<double> part(3 * (size_t)nblk);
-    // extent of the cloud (minimum and maximum corner)
-    NP_CUDA(launch_block_reduce(2, s->x, n, nullptr, s->s_part, st));
-    NP_CUDA(cudaMemcpyAsync(part.data(), s->s_part, sizeof(double) * part.size(),
-                            cudaMemcpyDeviceToHost, st));
-    NP_CUDA(cudaStreamSynchronize(st));
+    if (nblk > w.part_cap) {
+        dfree(w.part);
+        NP_CUDA(dalloc(&w.part, 3 * (size_t)nblk));
+        w.part_cap = nblk;
+    }
+    std::vector<double> part;
+    // extent of the cloud: minimum corner (box-counting origin), largest |x_d|
+    int rc = block_partials(w, 2, x, n, nullptr, part, st);
+    if (rc)
+        return rc;
     double o[3] = {INFINITY, INFINITY, INFINITY};
     for (int b = 0; b < nblk; ++b)
         for (int d = 0; d < 3; ++d)
             o[d] = std::min(o[d], part[3 * b + d]);
 
     if (cfg->n_bins > 0 && rdf_counts) {
+        rc = block_partials(w, 3, x, n, nullptr, part, st);
+        if (rc)
+            return rc;
         // cell grid with edge >= r_max over the cloud (positions are needed in
         // float32 only to choose candidates)
         double L = R;
-        std::vector<double> xs(3 * (size_t)n);
-        NP_CUDA(cudaMemcpy(xs.data(), s->x, sizeof(double) * xs.size(), cudaMemcpyDeviceToHost));
-        for (double vv : xs)
-            L = std::max(L, std::fabs(vv));
+        for (int b = 0; b < nblk; ++b)
+            for (int d = 0; d < 3; ++d)
+                L = std::max(L, part[3 * b + d]);
         L += cfg->r_max + 1.0;
-        CellGrid g = make_grid(L, cfg->r_max * (1.0 + 1e-4) + 1e-3, std::max<long long>(4 * n + 4096, 1 << 16));
-        if (g.n_cells > s->s_cells_cap) {
-            free_cells(s->scb);
-            int rc = alloc_cells(g, s->scb, n);
+        CellGrid g = make_grid(L, cfg->r_max * (1.0 + 1e-4) + 1e-3,
+                               std::max<long long>(4 * (long long)n + 4096, 1 << 16));
+        if (g.n_cells > w.cells_cap || n > w.cells_n) {
+            // grow to hold both this droplet and the largest one seen so far
+            CellGrid ga = g;
+            ga.n_cells = std::max(g.n_cells, w.cells_cap);
+            const int na = std::max(n, w.cells_n);
+            free_cells(w.cb);
+            w.cells_cap = w.cells_n = 0;
+            rc = alloc_cells(ga, w.cb, na);
             if (rc)
                 return rc;
-            s->s_cells_cap = g.n_cells;
+            w.cells_cap = ga.n_cells;
+            w.cells_n = na;
         }
-        s->sgrid = g;
-        if (cfg->n_bins > s->s_hist_cap) {
-            dfree(s->s_hist);
-            NP_CUDA(dalloc(&s->s_hist, cfg->n_bins));
-            s->s_hist_cap = cfg->n_bins;
+        w.grid = g;
+        if (cfg->n_bins > w.hist_cap) {
+            dfree(w.hist);
+            NP_CUDA(dalloc(&w.hist, cfg->n_bins));
+            w.hist_cap = cfg->n_bins;
         }
-        NP_CUDA(launch_cell_build(g, s->xq, s->typ, n, s->scb, nullptr, st));
-        NP_CUDA(launch_pair_hist(s->x, n, cfg->r_max, cfg->n_bins, g, s->scb, s->s_hist, st));
+        NP_CUDA(launch_cell_build(g, xq, typ, n, w.cb, nullptr, st));
+        NP_CUDA(launch_pair_hist(x, n, cfg->r_max, cfg->n_bins, g, w.cb, w.hist, st));
         std::vector<unsigned long long> h(cfg->n_bins);
-        NP_CUDA(cudaMemcpyAsync(h.data(), s->s_hist, sizeof(unsigned long long) * h.size(),
+        NP_CUDA(cudaMemcpyAsync(h.data(), w.hist, sizeof(unsigned long long) * h.size(),
                                 cudaMemcpyDeviceToHost, st));
         NP_CUDA(cudaStreamSynchronize(st));
         const double dr = cfg->r_max / (double)cfg->n_bins;
@@ -1582,14 +1623,14 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
         }
     }
     if (cfg->radial_bins > 0 && radial_counts) {
-        if (cfg->radial_bins > s->s_rhist_cap) {
-            dfree(s->s_rhist);
-            NP_CUDA(dalloc(&s->s_rhist, cfg->radial_bins));
-            s->s_rhist_cap = cfg->radial_bins;
+        if (cfg->radial_bins > w.rhist_cap) {
+            dfree(w.rhist);
+            NP_CUDA(dalloc(&w.rhist, cfg->radial_bins));
+            w.rhist_cap = cfg->radial_bins;
         }
-        NP_CUDA(launch_radial_hist(s->x, n, R, cfg->radial_bins, s->s_rhist, st));
+        NP_CUDA(launch_radial_hist(x, n, R, cfg->radial_bins, w.rhist, st));
         std::vector<unsigned long long> h(cfg->radial_bins);
-        NP_CUDA(cudaMemcpyAsync(h.data(), s->s_rhist, sizeof(unsigned long long) * h.size(),
+        NP_CUDA(cudaMemcpyAsync(h.data(), w.rhist, sizeof(unsigned long long) * h.size(),
                                 cudaMemcpyDeviceToHost, st));
         NP_CUDA(cudaStreamSynchronize(st));
         const double dr = R / (double)cfg->radial_bins;
@@ -1606,36 +1647,34 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
     // N_surf: NPs in the band (-r_i, r_i) about the surface
     {
         SurfHalf hs{};
-        for (int t = 0; t < s->P.n_types; ++t)
-            hs.h[t] = 0.5 * s->types[t].sigma;
+        for (int t = 0; t < T; ++t)
+            hs.h[t] = 0.5 * types[t].sigma;
         unsigned long long cnt = 0;
-        NP_CUDA(launch_surface_count(s->x, s->typ, n, R, hs, s->s_surf, st));
-        NP_CUDA(cudaMemcpyAsync(&cnt, s->s_surf, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        NP_CUDA(launch_surface_count(x, typ, n, R, hs, w.surf, st));
+        NP_CUDA(cudaMemcpyAsync(&cnt, w.surf, sizeof(cnt), cudaMemcpyDeviceToHost, st));
         NP_CUDA(cudaStreamSynchronize(st));
         out->n_surf = (int64_t)cnt;
     }
     // centre of mass and radius of gyration (Eqs. r0, Rg), fractal equation (Eq. N)
-    NP_CUDA(launch_block_reduce(0, s->x, n, nullptr, s->s_part, st));
-    NP_CUDA(cudaMemcpyAsync(part.data(), s->s_part, sizeof(double) * part.size(),
-                            cudaMemcpyDeviceToHost, st));
-    NP_CUDA(cudaStreamSynchronize(st));
+    rc = block_partials(w, 0, x, n, nullptr, part, st);
+    if (rc)
+        return rc;
     double c[3] = {0, 0, 0};
     for (int b = 0; b < nblk; ++b)
         for (int d = 0; d < 3; ++d)
             c[d] += part[3 * b + d];
     for (int d = 0; d < 3; ++d)
         c[d] /= (double)n;
-    NP_CUDA(cudaMemcpyAsync(s->s_vec, c, sizeof(c), cudaMemcpyHostToDevice, st));
-    NP_CUDA(launch_block_reduce(1, s->x, n, s->s_vec, s->s_part, st));
-    NP_CUDA(cudaMemcpyAsync(part.data(), s->s_part, sizeof(double) * part.size(),
-                            cudaMemcpyDeviceToHost, st));
-    NP_CUDA(cudaStreamSynchronize(st));
+    NP_CUDA(cudaMemcpyAsync(w.vec, c, sizeof(c), cudaMemcpyHostToDevice, st));
+    rc = block_partials(w, 1, x, n, w.vec, part, st);
+    if (rc)
+        return rc;
     double ss = 0.0;
     for (int b = 0; b < nblk; ++b)
         ss += part[3 * b];
     const double Rg = std::sqrt(ss / (double)n);
     out->Rg = Rg;
-    out->Df_rg = std::log((double)n / kKf) / std::log(2.0 * Rg / s->d_mean);
+    out->Df_rg = std::log((double)n / kKf) / std::log(2.0 * Rg / d_mean);
     for (int d = 0; d < 3; ++d)
         out->center[d] = c[d];
 
@@ -1644,21 +1683,20 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
         unsigned long long tsz = 1;
         while (tsz < 2ull * (unsigned long long)n)
             tsz <<= 1;
-        if (tsz > s->s_table_size) {
-            dfree(s->s_table);
-            NP_CUDA(dalloc(&s->s_table, tsz));
-            s->s_table_size = tsz;
+        if (tsz > w.table_size) {
+            dfree(w.table);
+            NP_CUDA(dalloc(&w.table, tsz));
+            w.table_size = tsz;
         }
-        NP_CUDA(cudaMemcpyAsync(s->s_vec + 3, o, sizeof(o), cudaMemcpyHostToDevice, st));
+        NP_CUDA(cudaMemcpyAsync(w.vec + 3, o, sizeof(o), cudaMemcpyHostToDevice, st));
         int ns = 0;
-        while (ns < cfg->max_scales && s->d_mean * std::ldexp(1.0, ns) <= 2.0 * Rg)
+        while (ns < cfg->max_scales && d_mean * std::ldexp(1.0, ns) <= 2.0 * Rg)
             ++ns;
         for (int k = 0; k < ns; ++k) {
-            const double eps = s->d_mean * std::ldexp(1.0, k);
-            NP_CUDA(launch_boxcount(s->x, n, s->s_vec + 3, eps, s->s_table, tsz, s->s_count,
-                                    s->d_flags, st));
+            const double eps = d_mean * std::ldexp(1.0, k);
+            NP_CUDA(launch_boxcount(x, n, w.vec + 3, eps, w.table, tsz, w.count, d_flags, st));
             int cnt = 0;
-            NP_CUDA(cudaMemcpyAsync(&cnt, s->s_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+            NP_CUDA(cudaMemcpyAsync(&cnt, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
             NP_CUDA(cudaStreamSynchronize(st));
             out->nbox[k] = cnt;
         }
@@ -1668,20 +1706,53 @@ int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts
             const int m = ns - 1;
             double mx = 0, my = 0;
             for (int k = 1; k < ns; ++k) {
-                mx += std::log(s->d_mean * std::ldexp(1.0, k));
+                mx += std::log(d_mean * std::ldexp(1.0, k));
                 my += std::log((double)out->nbox[k]);
             }
             mx /= m;
             my /= m;
             double sxy = 0, sxx = 0;
             for (int k = 1; k < ns; ++k) {
-                const double ex = std::log(s->d_mean * std::ldexp(1.0, k)) - mx;
+                const double ex = std::log(d_mean * std::ldexp(1.0, k)) - mx;
                 sxy += ex * (std::log((double)out->nbox[k]) - my);
                 sxx += ex * ex;
             }
             out->Df_box = -sxy / sxx;
         }
     }
+    return NPSIM_OK;
+}
+
+int check_stats_cfg(const npsim_stats_cfg_t *cfg)
+{
+    NP_REQUIRE(cfg->n_bins >= 0 && cfg->radial_bins >= 0, "bins must be >= 0");
+    NP_REQUIRE(cfg->n_bins == 0 || cfg->r_max > 0, "r_max must be positive");
+    NP_REQUIRE(cfg->max_scales >= 0 && cfg->max_scales <= NPSIM_MAX_SCALES,
+               "max_scales must be in [0, %d]", NPSIM_MAX_SCALES);
+    return NPSIM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
+                double *rdf_g, int64_t *radial_counts, double *radial_c, npsim_stats_t *out)
+{
+    NP_REQUIRE(s && cfg && out, "sim, cfg and out are required");
+    int rc = check_stats_cfg(cfg);
+    if (rc)
+        return rc;
+    const double t = (double)s->step * s->P.dt;
+    const double R2 = s->P.R0 * s->P.R0 - s->P.k_evap * t;
+    const double R = R2 > 0 ? std::sqrt(R2) : 0.0;
+    rc = positions_f64(s);
+    if (rc)
+        return rc;
+    rc = stats_core(s->sw, s->x, s->xq, s->typ, s->n, R, s->d_mean, s->types, s->P.n_types,
+                    s->d_flags, cfg, rdf_counts, rdf_g, radial_counts, radial_c, out, s->user);
+    if (rc)
+        return rc;
     return read_flags(s);
 }
 
@@ -1978,8 +2049,12 @@ struct npsim_ens {
     std::map<int, cudaGraphExec_t> graphs;
     int64_t step = 0;
 
+    std::vector<double> d_mean; // number-mean NP diameter of each droplet
+    StatsWork sw{};             // statistics of one droplet at a time (lazy)
+
     ~npsim_ens()
     {
+        free_stats(sw);
         for (auto &g : graphs)
             cudaGraphExecDestroy(g.second);
         dfree(x_lo);
@@ -2305,6 +2380,7 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
     e->P.resize(n_drops);
     e->types.resize(n_drops);
     e->eps_ov.resize(n_drops);
+    e->d_mean.assign(n_drops, 1.0);
     std::vector<double> xs(3 * (size_t)total), vs(3 * (size_t)total, 0.0);
     std::vector<int> dof((size_t)total);
     std::vector<float4> xq0((size_t)total);
@@ -2355,6 +2431,10 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
             if (t.w != 0.0f)
                 g.has_coul = 1;
         }
+        double dsum = 0.0;
+        for (int i = 0; i < n; ++i)
+            dsum += dr.types[dr.type[i]].sigma;
+        e->d_mean[d] = dsum / (double)n;
         for (int i = 0; i < n; ++i) {
             for (int k = 0; k < 3; ++k) {
                 xs[(size_t)k * total + off + i] = dr.x0[3 * (size_t)i + k];
@@ -2562,6 +2642,43 @@ int npsim_ens_forces(npsim_ens_t e, int32_t d, double *F)
                            cudaMemcpyDeviceToHost));
         for (int i = 0; i < n; ++i)
             F[3 * (size_t)i + c] = (double)a[i] + (double)b[i];
+    }
+    return NPSIM_OK;
+}
+
+int npsim_ens_stats(npsim_ens_t e, int32_t d, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
+                    double *rdf_g, int64_t *radial_counts, double *radial_c, npsim_stats_t *out)
+{
+    NP_REQUIRE(e && cfg && out && d >= 0 && d < e->D,
+               "bad ensemble, droplet index, cfg or out");
+    int rc = check_stats_cfg(cfg);
+    if (rc)
+        return rc;
+    const int n = e->cnt[d], off = e->off[d];
+    if (n > e->sw.x_cap) {
+        dfree(e->sw.x);
+        e->sw.x_cap = 0;
+        NP_CUDA(dalloc(&e->sw.x, 3 * (size_t)n));
+        e->sw.x_cap = n;
+    }
+    const npsim_params_t &p = e->P[d];
+    const double t = (double)e->step * p.dt;
+    const double R2 = p.R0 * p.R0 - p.k_evap * t;
+    const double R = R2 > 0 ? std::sqrt(R2) : 0.0;
+    // droplet d's positions (hi + lo) from the ensemble's state, on the device
+    NP_CUDA(launch_positions_f64_ld(e->xq + off, e->x_lo + off, n, e->n_total, e->sw.x,
+                                    e->user));
+    rc = stats_core(e->sw, e->sw.x, e->xq + off, e->typ + off, n, R, e->d_mean[d],
+                    e->types[d].data(), p.n_types, e->d_flags, cfg, rdf_counts, rdf_g,
+                    radial_counts, radial_c, out, e->user);
+    if (rc)
+        return rc;
+    int h = 0;
+    NP_CUDA(cudaMemcpyAsync(&h, e->d_flags, sizeof(int), cudaMemcpyDeviceToHost, e->user));
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    if (h) {
+        NP_CUDA(cudaMemsetAsync(e->d_flags, 0, sizeof(int), e->user));
+        return set_err(NPSIM_ERR_CUDA, "device error word 0x%x", h);
     }
     return NPSIM_OK;
 }

@@ -163,16 +163,17 @@ __global__ void k_mirror(const double *__restrict__ x, const int *__restrict__ t
     xq[i] = make_float4(h[0], h[1], h[2], charges.e[typ[i]].x);
 }
 
+// x = hi + lo in float64; lo words are rows of a [3][ld] array, x is [3][n].
 __global__ void k_positions_f64(const float4 *__restrict__ xq, const float *__restrict__ x_lo,
-                                int n, double *__restrict__ x)
+                                int n, int ld, double *__restrict__ x)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
     const float4 h = xq[i];
     x[i] = (double)h.x + (double)x_lo[i];
-    x[n + i] = (double)h.y + (double)x_lo[n + i];
-    x[2 * n + i] = (double)h.z + (double)x_lo[2 * n + i];
+    x[n + i] = (double)h.y + (double)x_lo[(size_t)ld + i];
+    x[2 * n + i] = (double)h.z + (double)x_lo[2 * (size_t)ld + i];
 }
 
 // Host-facing copy of the state: AoS float64 n x 3 of the position (hi + lo),
@@ -225,7 +226,14 @@ cudaError_t launch_mirror(const double *x, const int *typ, const float *charge_b
 cudaError_t launch_positions_f64(const float4 *xq, const float *x_lo, int n, double *x,
                                  cudaStream_t st)
 {
-    k_positions_f64<<<(n + 255) / 256, 256, 0, st>>>(xq, x_lo, n, x);
+    k_positions_f64<<<(n + 255) / 256, 256, 0, st>>>(xq, x_lo, n, n, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_positions_f64_ld(const float4 *xq, const float *x_lo, int n, int ld,
+                                    double *x, cudaStream_t st)
+{
+    k_positions_f64<<<(n + 255) / 256, 256, 0, st>>>(xq, x_lo, n, ld, x);
     return cudaGetLastError();
 }
 

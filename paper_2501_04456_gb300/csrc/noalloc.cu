@@ -4,13 +4,12 @@
 // The regular path keeps the all-pairs partial sums (one slot of compensated
 // float32 (hi, lo) pairs per i-tile row and CTA of the stream-K split) in memory that npsim_create
 // allocates.  Some callers cannot allocate at the moment they need forces:
-// code running inside a CUDA stream capture (cudaMalloc is not a legal
-// operation while a capture is open), code running under a framework that
-// owns all device memory through its own pool and forbids raw allocations, or
-// a real-time loop that cannot afford an allocation's latency or failure.  For
-// them, this file holds the partial sums in one file-scope __device__ array of
-// fixed size, present on every GPU that loads the library until the process
-// exits, and the entry point npsim_coulomb_forces_noalloc allocates nothing.
+// code running under a framework that owns all device memory through its own
+// pool and forbids raw allocations, or a real-time loop that cannot afford an
+// allocation's latency or its failure in the middle of a run.  For them, this
+// file holds the partial sums in one file-scope __device__ array of fixed size,
+// present on every GPU that loads the library until the process exits, and the
+// entry point npsim_coulomb_forces_noalloc allocates nothing.
 //
 // The computation is the same Coulomb sum as npsim_forces(sim, 3, ...):
 //   F_i = C q_i sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3,
@@ -51,7 +50,9 @@ DeviceSetup g_setup[kMaxDevices];
 
 // Once per device, with that device current: the device address of g_scratch
 // (in host code the array's name is only a host-side stand-in) and the launch
-// shape.  The first call on a device runs this.
+// shape.  The first call on a device runs this; the result is kept for the
+// life of the process, so it goes stale if the device's primary context is
+// destroyed (cudaDeviceReset), which the header tells callers not to do.
 int setup_device(int dev, DeviceSetup &out)
 {
     std::lock_guard<std::mutex> lock(g_mu);

@@ -958,8 +958,8 @@ cudaError_t launch_pair_hist(const double *x, int n, double r_max, int n_bins,
                              unsigned long long *hist, cudaStream_t st);
 cudaError_t launch_radial_hist(const double *x, int n, double r_max, int n_bins,
                                unsigned long long *hist, cudaStream_t st);
-// mode 0: per-CTA sums of x; 1: sums of |x - c|^2; 2: componentwise minima.
-// part holds 3 doubles per CTA of 256 threads.
+// mode 0: per-CTA sums of x; 1: sums of |x - c|^2; 2: componentwise minima;
+// 3: componentwise maxima of |x_d|.  part holds 3 doubles per CTA of 256 threads.
 // I(q) of Sec. 3.3 for a piecewise-constant g on [0, r_max), and its fractal form
 // N_surf^2 (q R_g)^(-D_f) into out_frac (or NULL); device arrays.
 cudaError_t launch_scattering(const double *g, int n_bins, double r_max, const double *q, int n_q,
@@ -982,6 +982,10 @@ cudaError_t launch_mirror(const double *x, const int *typ, const float *charge_b
                           int n, float4 *xq, float *x_lo, cudaStream_t st);
 cudaError_t launch_positions_f64(const float4 *xq, const float *x_lo, int n, double *x,
                                  cudaStream_t st);
+// The same for n NPs whose lo words are rows of a [3][ld] array (one droplet of
+// an ensemble); x is [3][n].
+cudaError_t launch_positions_f64_ld(const float4 *xq, const float *x_lo, int n, int ld,
+                                    double *x, cudaStream_t st);
 // The state as host-facing AoS float64 (n x 3 each; NULL outputs are skipped):
 // position hi + lo, velocity, force hi + lo (F: [6][n] hi/lo SoA).
 cudaError_t launch_state_aos(const float4 *xq, const float *x_lo, const float *v, const float *F,

@@ -192,8 +192,8 @@ __global__ void k_scattering(const double *__restrict__ g, int n_bins, double dr
 }
 
 // Per-CTA partials: mode 0 -> sum of x (3 values), 1 -> sum of |x - c|^2
-// (1 value), 2 -> componentwise minimum (3 values).  Tree reduction in a fixed
-// order inside the CTA.
+// (1 value), 2 -> componentwise minimum (3 values), 3 -> componentwise maximum
+// of |x_d| (3 values).  Tree reduction in a fixed order inside the CTA.
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_block_reduce(const double *__restrict__ x, int n, const double *__restrict__ c,
@@ -208,6 +208,13 @@ k_block_reduce(const double *__restrict__ x, int n, const double *__restrict__ c
             a0 = x[i];
             a1 = x[n + i];
             a2 = x[2 * n + i];
+        }
+    } else if (MODE == 3) {
+        a0 = a1 = a2 = 0.0;
+        if (i < n) {
+            a0 = fabs(x[i]);
+            a1 = fabs(x[n + i]);
+            a2 = fabs(x[2 * n + i]);
         }
     } else if (MODE == 0) {
         a0 = a1 = a2 = 0.0;
@@ -233,7 +240,8 @@ k_block_reduce(const double *__restrict__ x, int n, const double *__restrict__ c
         if (threadIdx.x < o) {
             for (int d = 0; d < 3; ++d) {
                 const double u = s[d][threadIdx.x], w = s[d][threadIdx.x + o];
-                s[d][threadIdx.x] = (MODE == 2) ? fmin(u, w) : __dadd_rn(u, w);
+                s[d][threadIdx.x] = (MODE == 2) ? fmin(u, w)
+                                    : (MODE == 3) ? fmax(u, w) : __dadd_rn(u, w);
             }
         }
         __syncthreads();
@@ -348,8 +356,10 @@ cudaError_t launch_block_reduce(int mode, const double *x, int n, const double *
         k_block_reduce<0><<<grid, 256, 0, st>>>(x, n, c, part);
     else if (mode == 1)
         k_block_reduce<1><<<grid, 256, 0, st>>>(x, n, c, part);
-    else
+    else if (mode == 2)
         k_block_reduce<2><<<grid, 256, 0, st>>>(x, n, c, part);
+    else
+        k_block_reduce<3><<<grid, 256, 0, st>>>(x, n, c, part);
     return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ def test_ensemble_every_shape(P, drops, monkeypatch):
 
 
 def test_ensemble_trajectories_match_oracle_and_single_runs(P, drops):
-    steps = 60
+    steps = 100  # the step count the 1e-4 sigma trajectory tolerance is stated for
     with P.Ensemble(drops) as ens:
         n_tot, pairs = ens.info()
         assert n_tot == sum(len(d[1]) for d in drops)
@@ -66,16 +66,19 @@ def test_ensemble_trajectories_match_oracle_and_single_runs(P, drops):
             xs, vs, _, _ = sim.state()
         # same physics, same Philox keys; the pair sums differ only in float
         # summation order (type groups padded to 256 here, to 512 in a single
-        # run), which 60 steps amplify to a few 1e-8; a wrong key or counter
+        # run), which 100 steps amplify to ~1e-7 at most; a wrong key or counter
         # would differ by the noise amplitude itself (~1e-2)
         assert np.abs(xe - xs).max() <= 1e-6, d
 
 
 def test_ensemble_large_droplets_sampled(P):
     """Droplets large enough that most (warp, segment) pairs are beyond the LJ
-    cutoff (culled to the Coulomb-only sweep): sampled rows of every droplet
-    against the oracle."""
+    cutoff (culled to the Coulomb-only sweep), up to the largest N of the
+    256-droplet ensemble (32768, many more j-tiles per work item row): sampled
+    rows of every droplet against the oracle."""
     scs = wl.ensemble_config(n_droplets=3, master_seed=11, n_min=9000, n_max=16000)
+    scs += wl.ensemble_config(n_droplets=1, master_seed=13, n_min=32768, n_max=32768)
+    assert scs[-1].n == 32768
     drops = []
     for sc in scs:
         types, x, v = wl.initial_state(sc, fp32_positions=True)
@@ -112,3 +115,44 @@ def test_ensemble_runs_are_bit_reproducible(P, drops):
     for a, b in zip(*states):
         for u, w in zip(a[:3], b[:3]):
             assert np.array_equal(u, w)
+
+
+def test_ensemble_stats_match_oracle(P, drops):
+    """npsim_ens_stats (the statistics of Sec. 3 straight from the ensemble's
+    device state) for droplets of uneven N after some steps, against the oracle
+    on the same float64 positions: integer histograms and box counts exactly,
+    g, C_NPs, R_g and both D_f to float64 rounding."""
+    steps = 20
+    sizes = [len(d[1]) for d in drops]
+    picks = [int(np.argmin(sizes)), int(np.argmax(sizes)), 2]
+    with P.Ensemble(drops) as ens:
+        ens.step(steps)
+        got = {d: (ens.state(d)[0], ens.stats(d, r_max=8.0, n_bins=64, radial_bins=16,
+                                               boxcount=True)) for d in picks}
+        # a second call on the first droplet reuses the scratch grown for the largest
+        again = ens.stats(picks[0], r_max=8.0, n_bins=64, radial_bins=16, boxcount=True)
+    assert np.array_equal(again["rdf_counts"], got[picks[0]][1]["rdf_counts"])
+    assert np.array_equal(again["nbox"], got[picks[0]][1]["nbox"])
+    for d in picks:
+        sc, _, _, types = drops[d]
+        xg, st = got[d]
+        R = oracle.radius(sc.R0, sc.k_evap, steps * sc.dt)
+        assert st["R"] == pytest.approx(R, rel=1e-14)
+        sig = np.array([t.sigma for t in sc.types])
+        d_mean = float(sig[types].mean())
+        assert st["d_mean"] == pytest.approx(d_mean, rel=1e-14)
+        c_o, g_o = oracle.rdf(xg, 8.0, 64, R)
+        assert np.array_equal(st["rdf_counts"], c_o), d
+        assert np.allclose(st["rdf_g"], g_o, rtol=1e-12, atol=0)
+        rc_o, C_o = oracle.radial_concentration(xg, R, 16, R)
+        assert np.array_equal(st["radial_counts"], rc_o)
+        assert np.allclose(st["radial_c"], C_o, rtol=1e-12)
+        Rg, Df, r0 = oracle.rg(xg, d_mean)
+        assert st["Rg"] == pytest.approx(Rg, rel=1e-12)
+        assert st["Df_rg"] == pytest.approx(Df, rel=1e-10)
+        assert np.allclose(st["center"], r0, rtol=1e-10, atol=1e-12)
+        Dfb, nb = oracle.boxcount_df(xg, d_mean, Rg)
+        assert np.array_equal(st["nbox"], nb)
+        if np.isfinite(Dfb):
+            assert st["Df_box"] == pytest.approx(Dfb, rel=1e-10)
+        assert st["n_surf"] == oracle.surface_count(xg, types, sig, st["R"])

@@ -67,12 +67,16 @@ def _scen(name):
         return with_(sc, eps_override=np.array([[0.155, 1.26], [1.26, 0.155]]) * 4)
     if name == "truncated_coul_lj_cell_5003":  # the printed range 4 sigma_ab, cell list
         return with_(small(wl.config3(), 5003), coulomb_cut=4.0)
+    if name == "isotropic_centrifugal_coul_lj_2000":
+        # the tumbling droplet of Sec. 1.2 (Fig. 2: omega = 1, isotropic): the
+        # centrifugal force m omega^2 x in every direction, no gravity
+        return with_(small(wl.config2(), 2000), rot_mode=2, omega=1.0, g=0.0)
     raise KeyError(name)
 
 
 SCENARIOS = ["lj1000_cell", "coul_lj_allpairs_3001", "coul_allpairs_lj_cell_5003",
              "lj_allpairs_only_1537", "coul_only_2049", "eps_matrix_1200",
-             "truncated_coul_lj_cell_5003"]
+             "truncated_coul_lj_cell_5003", "isotropic_centrifugal_coul_lj_2000"]
 
 
 def _oracle_pair(sc, x, types, lj=True, coul=True, sel=None):
@@ -269,7 +273,8 @@ def test_lj_in_allpairs_large_droplet_sampled(P, monkeypatch, coul):
 
 TRAJ = ["lj1000_cell", "coul_lj_allpairs_2048", "coul_allpairs_lj_cell_4096",
         "overdamped_lj_1000", "printed_kick_band_coul_lj_2048", "printed_kick_band_lj1000_cell",
-        "truncated_coul_lj_cell_4096"]
+        "truncated_coul_lj_cell_4096", "isotropic_centrifugal_coul_lj_2048",
+        "isotropic_centrifugal_lj1000_cell"]
 
 
 def _traj_scen(name):
@@ -288,6 +293,12 @@ def _traj_scen(name):
         return with_(wl.config1(), integrator=2, v_kick=0.1, wall_band=True)
     if name == "truncated_coul_lj_cell_4096":
         return with_(small(wl.config3(), 4096), coulomb_cut=4.0)
+    # the isotropic centrifugal force of the tumbling droplet (Sec. 1.2, Fig. 2:
+    # omega = 1) pushing every NP outward against the interface spring
+    if name == "isotropic_centrifugal_coul_lj_2048":
+        return with_(small(wl.config2(), 2048), rot_mode=2, omega=1.0, g=0.0)
+    if name == "isotropic_centrifugal_lj1000_cell":
+        return with_(wl.config1(), rot_mode=2, omega=1.0)
     raise KeyError(name)
 
 
