@@ -4,13 +4,17 @@
 Workload: the 250000-NP three-type droplet (diameters 1/1.5/3 sigma, fractions
 0.6/0.3/0.1, charges 0/+0.5/-0.5, all-pairs Coulomb + cell-list LJ at
 2.5 sigma_ab, R 200 -> 60 sigma, kT = 1), synthetic seeded initial state.  One
-step = cell binning, cell-list LJ, all-pairs Coulomb, and the fused
+step = cell binning, cell-list LJ, all-pairs Coulomb (over the charged NPs: the
+Coulomb terms of the 60 % neutral NPs are exactly zero), and the fused
 integrator (radius law, interface spring, drag, Philox noise, update).
 
 Prints one JSON line: pair-interactions/s (N(N-1) per step) as `value`, with
-particle-steps/s, the roofline of the all-pairs kernel (FP32 CUDA-core ALU),
-an end-to-end figure through the C ABI with host buffers, the FP64 CPU oracle
-timed on a bounded sample, and the SM clocks sampled during the timed region.
+particle-steps/s, the roofline of the all-pairs kernel (FP32 CUDA-core ALU,
+against the FP32 rate measured by the library's FMA microbenchmark), the same
+step with the Coulomb term summed over all N(N-1) pairs, the 256-droplet
+ensemble over whole 10000-step runs against the plain path, an end-to-end
+figure through the C ABI with host buffers, the FP64 CPU oracle timed on a
+bounded sample, and the SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -43,13 +47,15 @@ def _args():
     ap.add_argument("--n", type=int, default=250000, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--no-skip", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-full-sum", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--ensemble-steps", type=int, default=10000, help=argparse.SUPPRESS)
     ap.add_argument("--no-surrogate", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-hbm", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-cfg2", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--case", default="step",
-                    choices=["step", "integrator", "surrogate", "hbm", "dense"],
+                    choices=["step", "integrator", "surrogate", "hbm", "dense", "dense_lj",
+                             "surrogate_train", "config3_full"],
                     help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -238,11 +244,12 @@ def kernel_source_hash(packed):
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def _traffic_from_profile(cfg):
+def _traffic_from_profile(cfg, full_sum):
     """dram bytes per launch recorded by the committed ncu summary for the launch
-    in use (its shape's index in the autotuner's table and its number of
-    stream-K ranges), if it was taken on the current source of the all-pairs
-    kernel (else null)."""
+    in use (its shape's index in the autotuner's table, its number of stream-K
+    ranges, and whether it sums over all N(N-1) pairs or the charged pairs
+    only), if it was taken on the current source of the all-pairs kernel (else
+    null)."""
     path = os.path.join(ROOT, "profiles", "allpairs_paper_scale250000.md")
     try:
         txt = open(path).read()
@@ -252,63 +259,74 @@ def _traffic_from_profile(cfg):
     m_h = re.search(r"source sha256\[:16\]:\s*([0-9a-f]{16})", txt)
     if not (m_h and m_h.group(1) == h):
         return None
-    pat = r"dram bytes per full launch, shape (\d+), (\d+) ranges:\s*([0-9.eE+]+)"
+    kind = "full" if full_sum else "charged-only"
+    pat = rf"dram bytes per {kind} launch, shape (\d+), (\d+) ranges:\s*([0-9.eE+]+)"
     for idx, ranges, val in re.findall(pat, txt):
         if int(idx) == cfg.get("index") and int(ranges) == cfg.get("ranges"):
             return float(val)
     return None
 
 
-def _ensemble_measure(P, torch, stream, steps, warmup, n_plain=16, steps_per_droplet=10000):
-    """Droplets/s of the 256-droplet ensemble (N log-uniform in [512, 32768]) run as
-    one batched ensemble, and of the same droplets run one after another with the
-    single-droplet path.  Each droplet is a 10000-step run; both rates come from
-    measured per-step times.  The plain rate times a stratified sample of
-    n_plain droplets (every 256/n_plain-th by N) and scales its summed step time
-    to all 256.  The ensemble's working set (~250 MB) exceeds L2, so no flush."""
+def _ensemble_measure(P, torch, stream, n_plain=16, steps_per_droplet=10000, segments=10):
+    """Droplets/s of the 256-droplet ensemble (N log-uniform in [512, 32768]) over
+    whole runs: the batched ensemble is created from host arrays and advanced
+    through all 10000 steps of every droplet (the step time is recorded per
+    segment of 1000 steps, so its growth as the droplets shrink is visible); the
+    plain arm runs a stratified sample of n_plain of the same droplets (every
+    256/n_plain-th by N) one after another with the single-droplet path, each a
+    whole 10000-step run from its creation, and scales the summed wall time to
+    all 256.  Both rates include creation.  The ensemble's working set (~250 MB)
+    exceeds L2, so no flush."""
     import numpy as np
     import workloads as wl
-    scs = wl.ensemble_config()
+    scs = wl.ensemble_config(n_steps=steps_per_droplet)
     drops = [(sc, *wl.initial_state(sc)) for sc in scs]
     drops = [(sc, x, v, t) for sc, t, x, v in drops]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     ens = P.Ensemble(drops, stream=stream)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
     n_tot, pairs = ens.info()
-    ens.step(warmup)
+    seg = steps_per_droplet // segments
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(segments + 1)]
+    ev[0].record(stream)
+    for k in range(segments):
+        ens.step(seg if k < segments - 1 else steps_per_droplet - seg * (segments - 1))
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ens.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    t_run = time.perf_counter() - t0
+    seg_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(segments)]
     cfg = ens.config()
     ens.close()
     order = np.argsort([sc.n for sc in scs])
     stride = max(1, len(scs) // n_plain)
     sample = order[stride // 2::stride][:n_plain]
-    plain_ms = 0.0
+    t_plain = 0.0
     for d in sample:
         sc, x, v, t = drops[d]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         with P.Sim(sc, x, v, t, stream=stream) as sim:
-            sim.step(2)
+            sim.step(steps_per_droplet)
             torch.cuda.synchronize()
-            e0.record(stream)
-            sim.step(16)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            plain_ms += e0.elapsed_time(e1) / 16
-    plain_ms_all = plain_ms * len(scs) / len(sample)
-    ens_dps = len(scs) / (ms * 1e-3 * steps_per_droplet)
-    plain_dps = len(scs) / (plain_ms_all * 1e-3 * steps_per_droplet)
+        t_plain += time.perf_counter() - t1
+    t_plain_all = t_plain * len(scs) / len(sample)
+    ens_dps = len(scs) / t_run
+    plain_dps = len(scs) / t_plain_all
+    run_ms = sum(seg_ms)
     return {"droplets": len(scs), "steps_per_droplet": steps_per_droplet,
-            "n_particles": n_tot, "pairs_per_step": pairs,
-            "ms_per_step": ms, "droplets_per_s": ens_dps,
-            "pair_interactions_per_s": pairs / (ms * 1e-3),
+            "n_particles": n_tot, "pairs_per_step_initial": pairs,
+            "whole_run_s": t_run, "create_s": t_create,
+            "ms_per_step": run_ms / steps_per_droplet,
+            "ms_per_step_by_segment": [m / seg for m in seg_ms],
+            "droplets_per_s": ens_dps,
+            "pair_interactions_per_s": pairs * steps_per_droplet / (run_ms * 1e-3),
             "allpairs_launch": cfg,
-            "plain": {"ms_per_step_all_droplets": plain_ms_all, "droplets_per_s": plain_dps,
-                      "sample": f"{len(sample)} of {len(scs)} droplets, every {stride}-th by N; "
-                                f"summed step time x {len(scs) / len(sample):.0f}"},
+            "plain": {"whole_run_s_all_droplets": t_plain_all, "droplets_per_s": plain_dps,
+                      "sample": f"{len(sample)} of {len(scs)} droplets, every {stride}-th by N, "
+                                f"each created and run for {steps_per_droplet} steps; summed "
+                                f"wall time x {len(scs) / len(sample):.0f}"},
             "speedup_vs_plain": ens_dps / plain_dps}
 
 
@@ -322,11 +340,12 @@ INT_BYTES_B = 16 + 12 + 12 + 4 + 24 + 12
 # scatter (key, rank, start, arrival slot: 16), in-cell order (arrival slot, key,
 # cell range, sorted, cell-ordered position: 24), gather (sorted 4, position 16,
 # type 4, record written 16), list build (own record 16, sorted index 4, count
-# 4, build position 16, 4 per list entry); per rebuild and cell: count reset
-# and three scan passes (20).  Per step and NP, the list LJ forces (one thread
-# per particle): current position 16, type 4, count 4, 4 per list entry, force
-# record 24 (stored as a 32-byte sector, the padding not counted; partner
-# positions are re-reads of records already counted).
+# 4, build position 16, 4 per list entry); per rebuild and (type, cell) key:
+# count reset and three scan passes (20).  Per step and NP, the list LJ forces
+# (one thread per cell-order slot): current record (position and type) 16,
+# particle index 4, count 4, 4 per list entry, force record 24 (stored as a
+# 32-byte sector, the padding not counted; partner positions are re-reads of
+# records already counted).
 CELL_BUILD_BYTES_NP = 24 + 16 + 24 + 40 + 40
 CELL_BUILD_BYTES_CELL = 20
 LIST_LJ_BYTES_NP = 16 + 4 + 4 + 24
@@ -403,7 +422,9 @@ def _cell_list_roofline(P, stream, n=1 << 22, chunks=4):
         kt, _ = sim.kernel_times()
         cap, mean_len, b1 = sim.nbr_info()
     steps = chunks * k
-    per_build = (CELL_BUILD_BYTES_NP + 4 * mean_len) * n + CELL_BUILD_BYTES_CELL * cells
+    # count and scan passes run over (type, cell) keys
+    per_build = ((CELL_BUILD_BYTES_NP + 4 * mean_len) * n +
+                 CELL_BUILD_BYTES_CELL * cells * len(sc.types))
     byts = (LIST_LJ_BYTES_NP + 4 * mean_len) * n + per_build * (b1 - b0) / steps
     gbs = byts / (ms * 1e-3) / 1e9
     peak = _hbm_peak()
@@ -412,6 +433,71 @@ def _cell_list_roofline(P, stream, n=1 << 22, chunks=4):
             "bytes_per_step": byts, "ms_per_step": ms, "ms_build": kt["cell_build"],
             "ms_lj": kt["cell_lj"], "bound": "hbm", "achieved": gbs, "peak": peak,
             "unit": "GB/s", "frac": gbs / peak}
+
+
+def _dense_lj_state(P, stream, n_copy=65536, copies=4, compress_steps=20000, seed=0):
+    """A dense aggregate of the paper-scale composition larger than L2: an LJ-only
+    droplet of n_copy NPs (diameters 1/1.5/3, fractions 0.6/0.3/0.1) compacted by
+    the radius law from the paper-scale packing fraction to R_f = 0.3 R0
+    (packing fraction ~0.6, the dense end state of the 250000-NP run) over
+    compress_steps steps, then copies^3 copies of it on a cubic grid with gaps
+    wider than every cutoff, the NP indices shuffled at random so that index
+    order carries no spatial order.  Returns (scenario held at rest with the
+    wall off, x, types, packing fraction of one copy)."""
+    import dataclasses
+    import numpy as np
+    import workloads as wl
+    sc = dataclasses.replace(_scenario(n_copy, seed), coulomb=False, lj_mode=2)
+    Rf = 0.3 * sc.R0
+    comp = dataclasses.replace(sc, n_steps=compress_steps,
+                               k_evap=(sc.R0 ** 2 - Rf ** 2) / (compress_steps * sc.dt))
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(comp, x, v, types, stream=stream) as sim:
+        sim.step(compress_steps)
+        xf, _, _, _ = sim.state()
+    vol = sum((types == t).sum() * np.pi / 6.0 * ts.sigma ** 3 for t, ts in enumerate(sc.types))
+    phi = vol / (4.0 / 3.0 * np.pi * Rf ** 3)
+    gap = 2.0 * Rf + 20.0
+    g = (np.arange(copies) - (copies - 1) / 2.0) * gap
+    offs = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    X = (xf[None, :, :] + offs[:, None, :]).reshape(-1, 3)
+    T = np.tile(types, len(offs))
+    perm = np.random.default_rng(seed + 1).permutation(len(X))
+    X, T = X[perm], T[perm].astype(np.int32)
+    R_all = float(np.linalg.norm(X, axis=1).max()) + 10.0
+    held = dataclasses.replace(sc, n=len(X), R0=R_all, k_evap=0.0, wall=False,
+                               name=f"dense_lj{len(X)}")
+    return held, X, T, phi
+
+
+def _cell_list_dense_roofline(P, stream, chunks=4, **kw):
+    """The cell-list LJ path on the dense aggregate of _dense_lj_state (4.2 M
+    NPs, ~0.6 packing fraction, random index order): bytes per step as in
+    _cell_list_roofline (list forces every step, builds at the rate they ran)."""
+    hs, X, T, phi = _dense_lj_state(P, stream, **kw)
+    n = len(X)
+    with P.Sim(hs, X, None, T, stream=stream) as sim:
+        sim.profile(True)
+        dim, cells = sim.cell_grid()
+        sim.step(2 * sim.chunk_steps())
+        _, _, b0 = sim.nbr_info()
+        k = sim.chunk_steps()
+        ms, _ = _kernel_chunks(sim, ("cell_build", "cell_lj"), chunks)
+        kt, _ = sim.kernel_times()
+        cap, mean_len, b1 = sim.nbr_info()
+    steps = chunks * k
+    per_build = ((CELL_BUILD_BYTES_NP + 4 * mean_len) * n +
+                 CELL_BUILD_BYTES_CELL * cells * len(hs.types))
+    byts = (LIST_LJ_BYTES_NP + 4 * mean_len) * n + per_build * (b1 - b0) / steps
+    gbs = byts / (ms * 1e-3) / 1e9
+    peak = _hbm_peak()
+    return {"n": n, "packing_fraction": phi, "cells": cells, "mean_list_length": mean_len,
+            "list_capacity": cap, "rebuilds_per_step": (b1 - b0) / steps,
+            "bytes_per_step": byts, "ms_per_step": ms, "ms_build": kt["cell_build"],
+            "ms_lj": kt["cell_lj"], "bound": "hbm", "achieved": gbs, "peak": peak,
+            "unit": "GB/s", "frac": gbs / peak,
+            "state": "64 copies of a 65536-NP LJ droplet compacted to R_f = 0.3 R0, indices "
+                     "shuffled"}
 
 
 def _config2_measure(P, torch, stream, flush, steps, warmup):
@@ -525,6 +611,55 @@ def _surrogate_measure(P, batch=4096, n_nets=4, reps=7):
             "note": "random weights and data: the cost does not depend on them"}
 
 
+def _fp32_peak(P, stream, uuid, target_s=0.25, reps=3):
+    """The FP32 CUDA-core rate measured on this GPU by the library's FMA
+    microbenchmark (npsim_fma_peak): packed FFMA2 (the instruction the pair
+    kernels issue) and scalar FFMA, one full wave of CTAs with 8 independent
+    chains per thread, each timed over `reps` launches of ~target_s with CUDA
+    events, the SM clock sampled meanwhile.  The best rate is the roofline's
+    peak."""
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    out = {}
+    for packed in (True, False):
+        _, ms, _ = P.npsim_fma_peak(packed, 1 << 14, stream)  # calibrate the length
+        iters = max(1 << 14, int((1 << 14) * target_s / max(ms * 1e-3, 1e-6)))
+        best, best_ms, grid = 0.0, 0.0, 0
+        for _ in range(reps):
+            fl, ms, grid = P.npsim_fma_peak(packed, iters, stream)
+            r = fl / (ms * 1e-3) / 1e12
+            if r > best:
+                best, best_ms = r, ms
+        out["ffma2" if packed else "ffma"] = {"tflops": best, "ms": best_ms, "grid": grid,
+                                              "iters": iters}
+    time.sleep(0.3)
+    out["clocks"] = clocks.stop()
+    out["tflops"] = max(out["ffma2"]["tflops"], out["ffma"]["tflops"])
+    return out
+
+
+def _timed_steps(sim, torch, stream, flush, steps, warmup):
+    """Mean step time (ms) of `steps` single steps, each after an L2 flush and
+    bracketed by CUDA events on the simulation's stream, and the mean all-pairs
+    kernel duration of those steps (the library's own events)."""
+    for _ in range(warmup):
+        flush.zero_()
+        sim.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    ap = []
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+        ap.append(sim.kernel_times()[0]["allpairs"])
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, sum(ap) / len(ap)
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -592,44 +727,53 @@ def run_ours(a):
 
     pairs_per_step = n * (n - 1)
     value, psteps = replica_rates(world, n, step_ms)
+    q_of = np.array([t.charge for t in sc.types])[types]
+    n_charged = int(np.count_nonzero(q_of))
+    charged_pairs = n_charged * (n_charged - 1)
 
-    # roofline of the dominant kernel (all-pairs, FP32 CUDA-core ALU)
+    # roofline of the dominant kernel (all-pairs Coulomb, FP32 CUDA-core ALU):
+    # the default path sums the Coulomb term over the charged NPs only (the
+    # neutral NPs' terms are exactly zero), so its algorithmic work is 17 flops
+    # per charged ordered pair; the peak is the FP32 rate measured by the FMA
+    # microbenchmark on this GPU in this run
     peaks = _peaks()
     max_mhz = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
-    peak_tflops = info["sm_count"] * 128 * 2 * max_mhz * 1e6 / 1e12
+    nominal_tflops = info["sm_count"] * 128 * 2 * max_mhz * 1e6 / 1e12
+    peak = _fp32_peak(P, stream, f"GPU-{uuid}" if uuid else None) if rank == 0 else None
+    peak_tflops = peak["tflops"] if peak else nominal_tflops
     ap_avg = sum(ap_ms) / len(ap_ms)
-    achieved = FLOPS_PER_PAIR * pairs_per_step / (ap_avg * 1e-3) / 1e12
-    traffic = _traffic_from_profile(cfg)
+    achieved = FLOPS_PER_PAIR * charged_pairs / (ap_avg * 1e-3) / 1e12
+    traffic = _traffic_from_profile(cfg, full_sum=False)
+    pclk = (peak or {}).get("clocks") or {}
+    peak_basis = (f"measured: npsim_fma_peak, best of packed FFMA2 "
+                  f"({peak['ffma2']['tflops']:.2f}) and scalar FFMA ({peak['ffma']['tflops']:.2f}) "
+                  f"TFLOP/s, one full wave of {peak['ffma2']['grid']} CTAs, median SM clock "
+                  f"{pclk.get('sm_mhz')} MHz during it" if peak else
+                  f"derived: {info['sm_count']} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz")
 
-    # the same workload with the neutral NPs left out of the Coulomb sum (their
-    # Coulomb terms are exactly zero): reported beside the headline, which sums
-    # over all N(N-1) pairs
-    skip = None
-    if not a.no_skip:
+    # the explicit option: the Coulomb term summed over all N(N-1) pairs, neutral
+    # NPs included (sum_neutral), timed the same way
+    full = None
+    if not a.no_full_sum:
         import dataclasses
-        s3 = P.Sim(dataclasses.replace(sc, skip_neutral=True), x, v, types, stream=stream)
-        for _ in range(a.warmup):
-            flush.zero_()
-            s3.step(1)
-        ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(a.steps)]
-        for k in range(a.steps):
-            flush.zero_()
-            ev3[k][0].record(stream)
-            s3.step(1)
-            ev3[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms3 = sum(e0.elapsed_time(e1) for e0, e1 in ev3) / a.steps
-        neutral = float(np.mean([sc.types[t].charge == 0 for t in types]))
-        skip = {"ms_per_step": ms3, "neutral_fraction": neutral,
+        with P.Sim(dataclasses.replace(sc, sum_neutral=True), x, v, types, stream=stream) as s3:
+            s3.profile(True)
+            ms3, ap3 = _timed_steps(s3, torch, stream, flush, a.steps, a.warmup)
+            cfg3 = s3.allpairs_config()
+        ach3 = FLOPS_PER_PAIR * pairs_per_step / (ap3 * 1e-3) / 1e12
+        full = {"ms_per_step": ms3, "allpairs_ms": ap3,
                 "pair_interactions_per_s": world * pairs_per_step / (ms3 * 1e-3),
                 "particle_steps_per_s": world * n / (ms3 * 1e-3),
-                "allpairs_launch": s3.allpairs_config()}
-        s3.close()
+                "allpairs_launch": cfg3,
+                "roofline": {"bound": "alu", "achieved": ach3, "peak": peak_tflops,
+                             "unit": "TFLOP/s", "frac": ach3 / peak_tflops,
+                             "traffic": _traffic_from_profile(cfg3, full_sum=True),
+                             "work": f"{FLOPS_PER_PAIR} flops x N(N-1) = {pairs_per_step:.4g} "
+                                     f"ordered pairs per launch"}}
 
     ens = None
     if not a.no_ensemble and rank == 0:
-        ens = _ensemble_measure(P, torch, stream, max(3, a.steps // 2), a.warmup)
+        ens = _ensemble_measure(P, torch, stream, steps_per_droplet=a.ensemble_steps)
 
     surr = None
     cfg2 = None
@@ -642,6 +786,7 @@ def run_ours(a):
     if not a.no_hbm and rank == 0:
         hbm["integrator"] = _integrator_roofline(P, stream)
         hbm["cell_list"] = _cell_list_roofline(P, stream)
+        hbm["cell_list_dense"] = _cell_list_dense_roofline(P, stream)
 
     if not a.no_surrogate and rank == 0:
         surr = _surrogate_measure(P)
@@ -682,7 +827,7 @@ def run_ours(a):
             # the same oracle rate applied to the ensemble's pair count (context:
             # the oracle's LJ + Coulomb pairs cost about what its Coulomb pairs do)
             ens["oracle_droplets_per_s_extrapolated"] = (
-                cpu["value"] / (ens["pairs_per_step"] * ens["steps_per_droplet"]) *
+                cpu["value"] / (ens["pairs_per_step_initial"] * ens["steps_per_droplet"]) *
                 ens["droplets"])
 
     if rank == 0:
@@ -695,7 +840,8 @@ def run_ours(a):
                          "positions; f32 velocities",
             "data": "synthetic (seeded placement in the droplet, Maxwell velocities)",
             "config": {"workload": sc.name, "n_particles": n, "types": 3,
-                       "forces": "all-pairs Coulomb + cell-list LJ 2.5 sigma_ab",
+                       "forces": "all-pairs Coulomb (the 60 % neutral NPs left out of it: "
+                                 "their terms are exactly zero) + cell-list LJ 2.5 sigma_ab",
                        "l2": "flushed (256 MiB write) before every timed step, outside "
                              "the step's events",
                        "allpairs_launch": cfg, "parallelism": f"replicas{world}"},
@@ -705,12 +851,14 @@ def run_ours(a):
                           "cell_list": sum(cell_ms) / len(cell_ms)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": traffic,
-                         "peak_basis": f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x "
-                                       f"{max_mhz:.0f} MHz (max SM clock)",
-                         "frac_at_sampled_clock": (achieved / (peak_tflops * clk["sm_mhz"] /
-                                                               max_mhz)) if clk else None},
-            "skip_neutral": skip,
+                         "traffic": traffic, "peak_basis": peak_basis,
+                         "work": f"{FLOPS_PER_PAIR} flops x Nc(Nc-1) = {charged_pairs:.4g} "
+                                 f"charged ordered pairs per launch (Nc = {n_charged} charged "
+                                 f"NPs; the neutral NPs' Coulomb terms are exactly zero)",
+                         "nominal_peak": nominal_tflops,
+                         "frac_of_nominal": achieved / nominal_tflops},
+            "fp32_peak": peak,
+            "full_sum": full,
             "config2": cfg2,
             "truncated_coulomb": trunc,
             "ensemble": ens,
@@ -760,9 +908,9 @@ def run_dense_case(a, compress_steps=20000):
     """The paper-scale workload at its second structural point: the 250000 NPs
     compacted by the droplet's evaporation to R = 60 (packing fraction ~0.6).
     The run that compacts them follows the radius law from 200 to 60 over
-    `compress_steps` steps with the neutral NPs left out of the Coulomb sum
-    (their terms are exactly zero); the final state is then timed as in the
-    headline (all N(N-1) pairs, cell-list LJ) in a droplet held at R = 60."""
+    `compress_steps` steps; the final state is then timed as in the headline
+    (neutral NPs out of the Coulomb sum, cell-list LJ) in a droplet held at
+    R = 60."""
     import dataclasses
     import numpy as np
     import torch
@@ -772,7 +920,7 @@ def run_dense_case(a, compress_steps=20000):
     import paper_2501_04456_gb300 as P
     sc = _scenario(a.n, 0)
     Rf = 60.0 * (sc.n / 250000) ** (1.0 / 3.0)
-    comp = dataclasses.replace(sc, skip_neutral=True, n_steps=compress_steps,
+    comp = dataclasses.replace(sc, n_steps=compress_steps,
                                k_evap=(sc.R0 ** 2 - Rf ** 2) / (compress_steps * sc.dt))
     types, x, v = wl.initial_state(sc)
     stream = torch.cuda.current_stream()
@@ -818,8 +966,151 @@ def run_dense_case(a, compress_steps=20000):
           flush=True)
 
 
+def run_surrogate_train_case(a, n_train=2048, n_test=256, steps=10000, n_nets=4):
+    """The learned surrogate in the regime of the batched ensemble: training data
+    from n_train droplets (N log-uniform in [512, 8192], final R/R0 in
+    [0.2, 0.6], three types, 10000 steps each) generated by the ensemble kernel,
+    the deep ensemble of 4 MLPs trained on 90 % of them (the rest calibrates the
+    acceptance thresholds), and n_test held-out droplets simulated twice (two
+    seeds, for the simulation's own noise).  Acceptance: the spread of D_f
+    across the networks <= tau_Df and the relative spread of g(r) <= tau_g, both
+    calibrated so that >= 98 % of accepted validation predictions are within
+    0.05 in D_f and 0.1 ||g||_2 in g(r); the rest falls back to the simulation."""
+    import numpy as np
+    import torch
+    from paper_2501_04456_gb300 import build as _b
+    _b.build()
+    import paper_2501_04456_gb300 as P
+    from paper_2501_04456_gb300 import surrogate_pipeline as sp_
+    uuid = getattr(torch.cuda.get_device_properties(0), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    clocks.start()
+    rng = np.random.default_rng(0)
+    r = sp_.config5_ranges()
+    Xtr = sp_.sample_features(n_train, rng, steps, r)
+    Xte = sp_.sample_features(n_test, rng, steps, r)
+    t0 = time.perf_counter()
+    Ytr, t_tr = sp_.simulate(P, Xtr, steps, seed0=0)
+    wall_tr = time.perf_counter() - t0
+    Yte, t_te = sp_.simulate(P, Xte, steps, seed0=10 ** 6)
+    Yrep, _ = sp_.simulate(P, Xte, steps, seed0=2 * 10 ** 6)
+    nv = n_train // 10
+    model = sp_.SurrogateModel(P, n_nets=n_nets, seed=1)
+    try:
+        epochs, batch = 300, 256
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = model.fit(Xtr[nv:], Ytr[nv:], epochs=epochs, batch=batch, lr=1e-3)
+        t_fit = time.perf_counter() - t0
+        mv, sv = model.predict(Xtr[:nv])
+        tau_df = sp_.calibrate_tau(sv[:, 0], np.abs(mv[:, 0] - Ytr[:nv, 0]), tol=0.05)
+        tau_g = sp_.calibrate_tau(sp_.rdf_spread(mv, sv), sp_.rdf_rel_error(mv, Ytr[:nv]),
+                                  tol=0.1)
+        t0 = time.perf_counter()
+        m, s = model.predict(Xte)
+        t_pred = time.perf_counter() - t0
+    finally:
+        model.close()
+    clk = clocks.stop()
+    err = np.abs(m[:, 0] - Yte[:, 0])
+    gerr = sp_.rdf_rel_error(m, Yte)
+    acc = (s[:, 0] <= tau_df) & (sp_.rdf_spread(m, s) <= tau_g)
+    base = np.abs(Ytr[nv:, 0].mean() - Yte[:, 0])
+    gbase = sp_.rdf_rel_error(np.tile(Ytr[nv:].mean(0), (n_test, 1)), Yte)
+    rep = np.abs(Yrep[:, 0] - Yte[:, 0])
+    grep_ = sp_.rdf_rel_error(Yrep, Yte)
+
+    def q(v):
+        v = np.asarray(v)
+        if len(v) == 0:
+            return None
+        return {"mean": float(v.mean()), "median": float(np.median(v)),
+                "p95": float(np.percentile(v, 95)), "max": float(v.max())}
+    n_fit = n_train - nv
+    print(json.dumps({
+        "case": "surrogate_train", "droplets_train": n_train, "droplets_test": n_test,
+        "steps_per_droplet": steps,
+        "ranges": {"n": [r.n_min, r.n_max], "final_R_over_R0": list(r.shrink),
+                   "phi0": list(r.phi0), "kT": list(r.kT), "eps": list(r.eps), "q": list(r.q)},
+        "generation": {"simulate_s": t_tr, "wall_s_with_placement": wall_tr,
+                       "droplets_per_s": n_train / t_tr},
+        "training": {"samples": n_fit, "epochs": epochs, "minibatch": batch, "nets": n_nets,
+                     "s": t_fit, "network_samples_per_s": n_fit * epochs * n_nets / t_fit,
+                     "final_loss": loss},
+        "prediction": {"batch": n_test, "ms": 1e3 * t_pred,
+                       "simulation_ms_per_droplet": 1e3 * t_te / n_test},
+        "acceptance": {"tau_df": tau_df, "tau_rdf": tau_g, "accepted": int(acc.sum()),
+                       "fallback": int((~acc).sum()),
+                       "df_within_0.05": float(np.mean(err[acc] <= 0.05)) if acc.any() else None,
+                       "rdf_within_0.1": float(np.mean(gerr[acc] <= 0.1)) if acc.any() else None},
+        "df_abs_error": {"network_accepted": q(err[acc]), "network_all": q(err),
+                         "data_mean": q(base), "seed_to_seed": q(rep)},
+        "rdf_rel_l2_error": {"network_accepted": q(gerr[acc]), "network_all": q(gerr),
+                             "data_mean": q(gbase), "seed_to_seed": q(grep_)},
+        "clocks": clk}), flush=True)
+
+
+def run_config3_full_case(a, kTs=(0.5, 1.0, 2.0), n_steps=50000, segments=10):
+    """Config 3 as specified: the 250000-NP three-type droplet shrinking from
+    R = 200 to 60 over 50000 steps at each kT of the sweep, with the RDF (128
+    bins over [0, 10 sigma)) and both fractal dimensions at the end, and the
+    step time (kernel split, neighbour-list length) at the final, dense state."""
+    import torch
+    import workloads as wl
+    from paper_2501_04456_gb300 import build as _b
+    _b.build()
+    import paper_2501_04456_gb300 as P
+    stream = torch.cuda.current_stream()
+    uuid = getattr(torch.cuda.get_device_properties(0), "uuid", None)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = []
+    for kT in kTs:
+        sc = wl.config3(kT=kT, seed=0)
+        if a.n != 250000:
+            sc = wl.scaled(sc, a.n)
+        types, x, v = wl.initial_state(sc)
+        clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+        clocks.start()
+        with P.Sim(sc, x, v, types, stream=stream) as sim:
+            seg = n_steps // segments
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(segments + 1)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev[0].record(stream)
+            for k in range(segments):
+                sim.step(seg)
+                ev[k + 1].record(stream)
+            torch.cuda.synchronize()
+            t_run = time.perf_counter() - t0
+            seg_ms = [ev[k].elapsed_time(ev[k + 1]) / seg for k in range(segments)]
+            st = sim.stats(r_max=10.0, n_bins=128, boxcount=True)
+            # the final (dense) state timed like the headline
+            sim.profile(True)
+            _, _, b0 = sim.nbr_info()
+            ms, ap = _timed_steps(sim, torch, stream, flush, 20, 3)
+            kt, _ = sim.kernel_times()
+            cap, mean_len, b1 = sim.nbr_info()
+        clk = clocks.stop()
+        out.append({"kT": kT, "n": sc.n, "steps": n_steps, "run_s": t_run,
+                    "ms_per_step_by_segment": seg_ms, "R_final": st["R"],
+                    "Df_rg": st["Df_rg"], "Df_box": st["Df_box"], "Rg": st["Rg"],
+                    "n_surf": st["n_surf"], "rdf_g": [float(g) for g in st["rdf_g"]],
+                    "dense": {"ms_per_step": ms, "allpairs_ms": ap, "kernel_ms": kt,
+                              "pair_interactions_per_s": sc.n * (sc.n - 1) / (ms * 1e-3),
+                              "neighbour_lists": {"mean_length": mean_len, "capacity": cap,
+                                                  "rebuilds_per_step": (b1 - b0) / (20 + 3)}},
+                    "clocks": clk})
+    print(json.dumps({"case": "config3_full", "runs": out}), flush=True)
+
+
 def main():
     a = _args()
+    if a.case == "surrogate_train":
+        run_surrogate_train_case(a)
+        return
+    if a.case == "config3_full":
+        run_config3_full_case(a)
+        return
     if a.case == "dense":
         run_dense_case(a)
         return
@@ -834,7 +1125,18 @@ def main():
         stream = torch.cuda.current_stream()
         n = a.n if a.n != 250000 else 1 << 23  # --n sets the integrator's size (cell list: n/2)
         print(json.dumps({"case": "hbm", "integrator": _integrator_roofline(P, stream, n),
-                          "cell_list": _cell_list_roofline(P, stream, n // 2)}), flush=True)
+                          "cell_list": _cell_list_roofline(P, stream, n // 2),
+                          "cell_list_dense": _cell_list_dense_roofline(P, stream)}), flush=True)
+        return
+    if a.case == "dense_lj":  # profiling: the dense aggregate's cell-list path alone
+        import torch
+        from paper_2501_04456_gb300 import build as _b
+        _b.build()
+        import paper_2501_04456_gb300 as P
+        stream = torch.cuda.current_stream()
+        print(json.dumps({"case": "dense_lj", **_cell_list_dense_roofline(
+            P, stream, chunks=max(1, a.steps // 16), copies=max(1, round((a.n / 65536) ** (1 / 3)))
+            if a.n != 250000 else 4)}), flush=True)
         return
     if a.case == "surrogate":
         from paper_2501_04456_gb300 import build as _b

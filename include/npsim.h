@@ -71,8 +71,10 @@ typedef struct {
     int32_t integrator; /* 0: BAOAB Langevin; 1: overdamped (Brownian dynamics); 2: the
                            step (vi) as printed: v += dt (F/m - gamma v), then a random
                            velocity of magnitude v_kick in a uniform direction, x += dt v */
-    int32_t skip_neutral; /* 1: leave NPs of charge 0 out of the all-pairs Coulomb sum
-                             (their terms are exactly zero); 0: sum over all pairs */
+    int32_t sum_neutral;  /* 0 (default): NPs of charge 0 are left out of the all-pairs
+                             Coulomb sum, whose terms for them are exactly zero (the
+                             forces are those of the full sum, up to float32 summation
+                             order); 1: sum the Coulomb term over all N(N-1) pairs */
     int32_t reserved_;    /* set to 0 */
     uint64_t seed;      /* Philox key of the noise */
     double dt;          /* time step */
@@ -262,7 +264,7 @@ typedef struct npsim_ens *npsim_ens_t;
 
 /* One droplet: same meaning as the arguments of npsim_create.  params.lj_mode
  * must be 0 or 1 (the ensemble sums LJ inside the all-pairs kernel);
- * params.skip_neutral is ignored. */
+ * params.sum_neutral is ignored (the ensemble sums LJ and Coulomb in one pass). */
 typedef struct {
     int64_t n;
     const npsim_type_t *types; /* params.n_types entries */
@@ -371,6 +373,18 @@ int npsim_surr_predict(npsim_surr_t s, const float *X, int32_t B, float *Y_mean,
  * must be multiples of 16, n_tile <= 256. */
 int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
                     int32_t n_tile, float *C);
+
+/* Test hook of the failure path of the tensor-core kernels (no counterpart in the
+ * paper): every mbarrier wait of the GEMM kernel's main loop (TMA operand ring,
+ * MMA pipeline, accumulator ready) gives up after `cycles` SM clock cycles
+ * instead of the default 2^32 (~2 s), for every GEMM launched after the call
+ * from any thread (the surrogate's training and gradient passes and
+ * npsim_gemm_bf16); 0 restores the default.  A wait that gives up makes the
+ * kernel set its error flag, wait with the default bound for its copies and
+ * MMAs in flight, free its tensor memory and return without writing its
+ * output; the call that launched it returns NPSIM_ERR_TIMEOUT.  This lets a
+ * test drive that path without a stuck GPU.  Errors: INVALID_ARG (cycles < 0). */
+int npsim_test_wait_cycles(int64_t cycles);
 
 /*
  * All-pairs Coulomb forces without any device allocation.  The paper has no

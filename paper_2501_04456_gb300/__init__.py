@@ -42,7 +42,7 @@ class npsim_type_t(C.Structure):
 class npsim_params_t(C.Structure):
     _fields_ = [("n_types", C.c_int32), ("rot_mode", C.c_int32), ("lj_mode", C.c_int32),
                 ("coulomb", C.c_int32), ("wall", C.c_int32), ("integrator", C.c_int32),
-                ("skip_neutral", C.c_int32), ("reserved_", C.c_int32),
+                ("sum_neutral", C.c_int32), ("reserved_", C.c_int32),
                 ("seed", C.c_uint64), ("dt", C.c_double), ("kT", C.c_double),
                 ("R0", C.c_double), ("k_evap", C.c_double), ("g", C.c_double),
                 ("omega", C.c_double), ("bjerrum", C.c_double), ("lj_cut", C.c_double),
@@ -147,6 +147,7 @@ def lib():
             L.npsim_gemm_bf16.argtypes = [C.POINTER(C.c_uint16), C.POINTER(C.c_uint16),
                                           C.c_int32, C.c_int32, C.c_int32, C.c_int32, _f]
             L.npsim_chunk_steps.argtypes = [_h, _i32]
+            L.npsim_test_wait_cycles.argtypes = [C.c_int64]
             L.npsim_profile.argtypes = [_h, C.c_int]
             L.npsim_kernel_times.argtypes = [_h, _d, _i32]
             _lib = L
@@ -210,7 +211,7 @@ def params_from(sc):
     p.wall = 0 if not sc.wall else (2 if getattr(sc, "wall_band", False) else 1)
     p.integrator = sc.integrator
     p.v_kick = float(getattr(sc, "v_kick", 0.0))
-    p.skip_neutral = int(bool(getattr(sc, "skip_neutral", False)))
+    p.sum_neutral = int(bool(getattr(sc, "sum_neutral", False)))
     p.seed = sc.seed
     p.dt, p.kT, p.R0, p.k_evap = sc.dt, sc.kT, sc.R0, sc.k_evap
     p.g, p.omega, p.bjerrum, p.lj_cut = sc.g, sc.omega, sc.bjerrum, sc.lj_cut
@@ -666,6 +667,11 @@ def npsim_gemm_bf16(A_bits, B_bits, n_tile=64):
     _check(lib().npsim_gemm_bf16(_p(A, C.c_uint16), _p(B, C.c_uint16), M, N, K, n_tile,
                                  _p(Cm, C.c_float)))
     return Cm
+
+
+def npsim_test_wait_cycles(cycles):
+    """Bound (SM cycles) of the GEMM kernel's main-loop waits; 0 = default."""
+    _check(lib().npsim_test_wait_cycles(int(cycles)))
 
 
 class Surrogate:

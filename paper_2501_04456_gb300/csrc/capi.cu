@@ -130,7 +130,7 @@ int check_device(int *sms)
 }
 
 std::mutex g_tune_mu;
-// (n, lj, grouped length, skip_neutral) -> (launch shape, ranges per CTA)
+// (n, lj, grouped length, neutral NPs elided) -> (launch shape, ranges per CTA)
 std::map<std::array<long long, 4>, std::pair<int, int>> g_tune_cache;
 // Ranges per CTA the autotuner tries for the grouped kernels (dynamic
 // launches), and the one a forced shape gets by default.
@@ -303,17 +303,21 @@ struct npsim_sim {
 
 namespace {
 
+// Buffers of a cell list of n NPs over the g.tb * g.n_cells sort keys.  pos starts
+// at 0 so that every slot it names is in range before the first build.
 int alloc_cells(CellGrid &g, CellBufs &b, int n)
 {
+    const size_t m = (size_t)std::max(g.tb, 1) * (size_t)g.n_cells;
     NP_CUDA(dalloc(&b.key, n));
     NP_CUDA(dalloc(&b.rank, n));
-    NP_CUDA(dalloc(&b.count, g.n_cells));
-    NP_CUDA(dalloc(&b.start, (size_t)g.n_cells + 1));
+    NP_CUDA(dalloc(&b.count, m));
+    NP_CUDA(dalloc(&b.start, m + 1));
     NP_CUDA(dalloc(&b.arrived, n));
     NP_CUDA(dalloc(&b.sorted, n));
     NP_CUDA(dalloc(&b.pos, n));
+    NP_CUDA(cudaMemset(b.pos, 0, sizeof(int) * (size_t)(n > 0 ? n : 1)));
     NP_CUDA(dalloc(&b.sxq, n));
-    NP_CUDA(dalloc(&b.tile_sum, cell_scan_tiles(g.n_cells)));
+    NP_CUDA(dalloc(&b.tile_sum, cell_scan_tiles((int)m)));
     return NPSIM_OK;
 }
 
@@ -333,6 +337,7 @@ CellGrid make_grid(double L, double h_min, long long max_cells)
     g.n_cells = (int)(dim * dim * dim);
     g.inv_h = (float)(1.0 / h);
     g.L = (float)L;
+    g.tb = 1;
     return g;
 }
 
@@ -413,8 +418,8 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
                  cudaStream_t st, int prof_slot = -1)
 {
     const bool ap_lj = want_lj && s->P.lj_mode == 1;
-    // with every charged NP left out (skip_neutral and no charges) the grouped
-    // Coulomb sum is empty
+    // with the neutral NPs left out and no type charged, the grouped Coulomb
+    // sum is empty
     const bool ap_coul = want_coul && s->P.coulomb == 1 &&
                          !(shape_grouped(s->ap_idx) && s->grp_len == 0);
     // coulomb mode 2: Coulomb truncated at its cutoff, summed with LJ from the lists
@@ -466,6 +471,8 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     a.row_pos = grouped ? s->row_pos : nullptr;
     a.spring = s->d_spring;
     a.x_ref = s->cell ? s->nl.x_ref : nullptr;
+    a.sxq = s->cell ? s->cb.sxq : nullptr;
+    a.cell_pos = s->cell ? s->cb.pos : nullptr;
     a.nbr_gate = s->d_gate;
     a.half_skin2 = kHalfSkin2;
     a.step = s->d_step;
@@ -488,6 +495,8 @@ int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
     a.sk = s->sk;
     a.spring = s->d_spring;
     a.x_ref = s->cell ? s->nl.x_ref : nullptr;
+    a.sxq = s->cell ? s->cb.sxq : nullptr;
+    a.cell_pos = s->cell ? s->cb.pos : nullptr;
     a.nbr_gate = s->d_gate;
     a.half_skin2 = kHalfSkin2;
     a.step = s->d_step;
@@ -614,7 +623,7 @@ int autotune(npsim_sim *s)
         }
     }
     const std::array<long long, 4> key{s->n, lj ? 1 : 0, s->grp_len,
-                                       s->P.skip_neutral ? 1 : 0};
+                                       s->P.sum_neutral ? 0 : 1};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -741,9 +750,10 @@ void morton_sort(std::vector<int> &idx, const double *x)
 // at creation when LJ is in the pair sum (tiles of nearby NPs let the LJ kernel
 // skip tile pairs beyond the cutoff), else their index order; every group is
 // padded with -1 to a multiple of 512, so each
-// 256-position block has one type (and one charge).  With skip_neutral and no
-// LJ in the pair sum, the grouped kernels cover only the charged groups and
-// neutral NPs have no pair row.
+// 256-position block has one type (and one charge).  Unless sum_neutral is
+// set, and with no LJ in the pair sum, the grouped kernels cover only the
+// charged groups and neutral NPs have no pair row (their Coulomb terms are
+// exactly zero).
 int build_grouping(npsim_sim *s, const int32_t *type, const double *x0, const int32_t *rank)
 {
     std::vector<int> order;
@@ -787,7 +797,7 @@ int build_grouping(npsim_sim *s, const int32_t *type, const double *x0, const in
     }
     s->n_perm = (int)perm.size();
     s->h_rank.assign(pos.begin(), pos.end());
-    const bool skip = s->P.skip_neutral && s->P.lj_mode != 1;
+    const bool skip = !s->P.sum_neutral && s->P.lj_mode != 1;
     if (skip) {
         s->grp_len = charged_len;
         for (int i = 0; i < s->n; ++i)
@@ -1174,6 +1184,7 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
             L = std::max(L, std::fabs(x0[i]));
         L += rc_cell + kSkin;
         s->grid = make_grid(L, rc_cell + kSkin, std::max<long long>(4 * n + 4096, 1 << 16));
+        s->grid.tb = s->T; // cell order grouped by type (uniform list lengths per warp)
         rc = alloc_cells(s->grid, s->cb, s->n);
         if (rc)
             return bail(rc);
@@ -1767,13 +1778,13 @@ namespace {
 // also the neighbour-list state: the cell grid and list capacity (header), the
 // positions of the last build (float4[n]) and the rebuild gate (header), from
 // which a resumed run rebuilds exactly the list the saved run was using.
-const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '4'};
+const char kMagic[8] = {'N', 'P', 'S', 'I', 'M', 'C', 'K', '5'};
 
 struct CkptHeader {
     char magic[8];
     int32_t version, n_types;
     int64_t n, step;
-    int32_t rot_mode, lj_mode, coulomb, wall, integrator, has_ov, skip_neutral, pad_;
+    int32_t rot_mode, lj_mode, coulomb, wall, integrator, has_ov, sum_neutral, pad_;
     uint64_t seed;
     double dt, kT, R0, k_evap, g, omega, bjerrum, lj_cut, v_kick, coulomb_cut;
     double eps_ov[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
@@ -1797,6 +1808,7 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
     g.n_cells = h.grid_cells;
     g.inv_h = h.grid_inv_h;
     g.L = h.grid_L;
+    g.tb = s->T;
     if (!s->cb.key) {
         int rc = alloc_cells(g, s->cb, s->n);
         if (rc)
@@ -1817,6 +1829,8 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
     NP_CUDA(launch_nbr_build(s->grid, s->cb, s->n, s->tab_full, s->d_rcc2, kSkin, s->nl,
                              s->d_flags,
                              nullptr, s->user));
+    // the list kernel reads the current positions from the cell-ordered records
+    NP_CUDA(launch_cell_refresh(s->cb, s->xq, s->typ, s->n, s->user));
     NP_CUDA(cudaStreamSynchronize(s->user));
     return set_gate(s, h.gate);
 }
@@ -1878,7 +1892,7 @@ int npsim_save(npsim_sim_t s, const char *path)
     h.wall = s->P.wall;
     h.integrator = s->P.integrator;
     h.has_ov = s->has_ov ? 1 : 0;
-    h.skip_neutral = s->P.skip_neutral;
+    h.sum_neutral = s->P.sum_neutral;
     h.seed = s->P.seed;
     h.dt = s->P.dt;
     h.kT = s->P.kT;
@@ -1974,7 +1988,7 @@ int npsim_load(const char *path, const npsim_type_t *types_override,
     p.coulomb = h.coulomb;
     p.wall = h.wall;
     p.integrator = h.integrator;
-    p.skip_neutral = h.skip_neutral;
+    p.sum_neutral = h.sum_neutral;
     p.seed = h.seed;
     p.dt = h.dt;
     p.kT = h.kT;

@@ -4,14 +4,20 @@
 // cells (step (ii)):
 //   F_i = sum_{j != i, r < rc_ij} 24 eps_ij (2 (s_ij/r)^12 - (s_ij/r)^6) r_ij / r^2.
 //
-// Binning is a counting sort: hash (cell of each NP, its arrival rank from an
-// atomic counter), exclusive scan of the per-cell counts, scatter, then every
-// NP is placed at its rank by index inside its cell (one thread per NP counts
-// the members of its cell with a smaller index) so that the order inside a
+// Binning is a counting sort: hash (sort key of each NP, its arrival rank from
+// an atomic counter), exclusive scan of the per-key counts, scatter, then every
+// NP is placed at its rank by index inside its key (one thread per NP counts
+// the members of its key with a smaller index) so that the order inside a
 // cell -- and therefore the float summation order of the LJ kernel -- does not
-// depend on the atomic arrival order (runs are bit-reproducible).  A gather
-// writes the NP records (position, type in the fourth word) in cell order so
-// the LJ kernel reads neighbours from contiguous memory.
+// depend on the atomic arrival order (runs are bit-reproducible).  For the LJ
+// lists the key is type * n_cells + cell: the cell order lists the NPs of one
+// type cell by cell, then the next type, so that consecutive threads of the
+// list kernels hold NPs of one type (lists of similar length, read coalesced)
+// in nearby cells (their partners lie in the same few cells).  A gather writes
+// the NP records (position, type in the fourth word) in cell order so the
+// kernels read neighbours from contiguous memory; with a neighbour list the
+// integrator keeps these records current, so the per-step list kernel reads
+// every position in cell order and never gathers by particle index.
 //
 // The simulation keeps a Verlet neighbour list on top of the cells: the cell
 // edge is the largest cutoff plus a skin, a build lists for every NP the
@@ -48,16 +54,18 @@ __global__ void k_cell_zero(int *__restrict__ count, int m, const int *__restric
         count[c] = 0;
 }
 
-__global__ void k_cell_hash(CellGrid g, const float4 *__restrict__ xq, int n,
-                            int *__restrict__ key, int *__restrict__ rank,
-                            int *__restrict__ count, const int *__restrict__ gate)
+__global__ void k_cell_hash(CellGrid g, const float4 *__restrict__ xq,
+                            const int *__restrict__ typ, int n, int *__restrict__ key,
+                            int *__restrict__ rank, int *__restrict__ count,
+                            const int *__restrict__ gate)
 {
     if (gate_closed(gate))
         return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 p = xq[i];
-        const int c = (cell_coord(p.z, g) * g.dim + cell_coord(p.y, g)) * g.dim +
-                      cell_coord(p.x, g);
+        int c = (cell_coord(p.z, g) * g.dim + cell_coord(p.y, g)) * g.dim + cell_coord(p.x, g);
+        if (g.tb > 1)
+            c += typ[i] * g.n_cells;
         key[i] = c;
         rank[i] = atomicAdd(&count[c], 1);
     }
@@ -264,13 +272,14 @@ __device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab,
     __syncthreads();
 }
 
-// Neighbour lists (gated): for NP i (threads in the cell order, so that a
-// warp scans the same cells), the partners within (rc_ab + skin) in the 27
-// cells, in scan order, as (index << 3 | type) (unsigned: an index below 2^29
-// fits), column-major nbr[k * n + i] for k < cap; nnbr[i] = the full count (an
-// NP with more than cap partners is summed from the cells instead).  Lists are
-// written by particle so that the per-step force kernel reads them coalesced.
-// Records the positions of this build in x_ref.
+// Neighbour lists (gated): for the NP at cell-order slot p (threads in the cell
+// order, so that a warp scans the same cells), the partners within
+// (rc_ab + skin) in the 27 cells, type block by type block in scan order, as
+// (slot << 3 | type) (unsigned: a slot below 2^29 fits), column-major
+// nbr[k * n + p] for k < cap; nnbr[p] = the full count (an NP with more than
+// cap partners is summed from the cells instead).  Lists are written by slot
+// so that the per-step force kernel, which runs in the same order, reads them
+// coalesced.  Records the positions of this build in x_ref (by particle).
 __global__ void __launch_bounds__(128)
 k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
             const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab,
@@ -288,6 +297,7 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
     __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
     __shared__ float s_rmax[NPSIM_MAX_TYPES];
     load_tables(tab, rcc2, skin, s_tab, s_rl2, s_rmax);
+    const int tb = g.tb > 1 ? g.tb : 1;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const float4 pi = sxq[p];
         const int i = sorted[p];
@@ -296,33 +306,38 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
         const float rmax = s_rmax[ti];
         const int cx = cell_coord(pi.x, g), cy = cell_coord(pi.y, g), cz = cell_coord(pi.z, g);
         int cnt = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int z = cz + dz;
-            if (z < 0 || z >= g.dim)
-                continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int y = cy + dy;
-                if (y < 0 || y >= g.dim)
+        for (int t = 0; t < tb; ++t) {
+            if (tb > 1 && s_rl2[row + t] == 0.0f)
+                continue; // no term acts between these types
+            const int kofs = t * g.n_cells;
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int z = cz + dz;
+                if (z < 0 || z >= g.dim)
                     continue;
-                const int base = (z * g.dim + y) * g.dim;
-                const int b = start[base + max(cx - 1, 0)];
-                const int e = start[base + min(cx + 1, g.dim - 1) + 1];
-                for (int q = b; q < e; ++q) {
-                    const float4 pj = sxq[q];
-                    const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
-                    if (r2 >= rmax || q == p)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int y = cy + dy;
+                    if (y < 0 || y >= g.dim)
                         continue;
-                    const int tj = __float_as_int(pj.w);
-                    if (r2 < s_rl2[row + tj]) {
-                        if (cnt < cap)
-                            nbr[(size_t)cnt * n + i] = ((unsigned)sorted[q] << 3) | (unsigned)tj;
-                        ++cnt;
+                    const int base = kofs + (z * g.dim + y) * g.dim;
+                    const int b = start[base + max(cx - 1, 0)];
+                    const int e = start[base + min(cx + 1, g.dim - 1) + 1];
+                    for (int q = b; q < e; ++q) {
+                        const float4 pj = sxq[q];
+                        const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
+                        if (r2 >= rmax || q == p)
+                            continue;
+                        const int tj = __float_as_int(pj.w);
+                        if (r2 < s_rl2[row + tj]) {
+                            if (cnt < cap)
+                                nbr[(size_t)cnt * n + p] = ((unsigned)q << 3) | (unsigned)tj;
+                            ++cnt;
+                        }
                     }
                 }
             }
         }
-        nnbr[i] = cnt;
+        nnbr[p] = cnt;
         if (cnt > cap)
             atomicOr(flags, FLAG_NBR_OVERFLOW);
         x_ref[i] = make_float4(pi.x, pi.y, pi.z, 0.0f);
@@ -330,19 +345,20 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
 }
 
 // LJ forces (and, with rcc2, the truncated Coulomb term) from the neighbour
-// lists at the current positions xq, one thread per NP in particle index
-// order: the NP's own record, list column and force record are coalesced, the
-// partners' records are gathered.  An NP whose list overflowed sums over the
-// 27 cells of that build instead (a superset of its list).  Writes one 32-byte
-// (hi x, y, z, lo x, y, z, 0, 0) record per NP and closes the rebuild gate.
-// 10 CTAs of 128 per SM for the LJ-only kernel (48 registers): the partner
-// gathers are latency-bound, and more threads in flight help (0.114 -> 0.100 ms
-// per step on 4.2 M NPs; 12 CTAs spill).  The truncated-Coulomb variant keeps 8.
+// lists at the current positions, one thread per cell-order slot p: the NP's
+// own record sxq[p] (kept current by the integrator), its list column and its
+// partners' records are read in cell order -- coalesced, and for the partners
+// from the nearby cells -- and the 32-byte force record goes to the NP's index
+// i = sorted[p], where the integrator reads it.  An NP whose list overflowed
+// sums over the 27 cells of that build instead (a superset of its list).
+// Writes one 32-byte (hi x, y, z, lo x, y, z, 0, 0) record per NP and closes
+// the rebuild gate.  10 CTAs of 128 per SM for the LJ-only kernel: the partner
+// gathers are latency-bound, and more threads in flight help.  The
+// truncated-Coulomb variant keeps 8.
 template <bool COUL>
 __global__ void __launch_bounds__(128, COUL ? 8 : 10)
 k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
-         const int *__restrict__ pos, const float4 *__restrict__ sxq,
-         const float4 *__restrict__ xq, const int *__restrict__ typ, int n,
+         const int *__restrict__ key, const float4 *__restrict__ sxq, int n,
          const PairTab *__restrict__ tab, const float *__restrict__ rcc2, int cap,
          const unsigned *__restrict__ nbr, const int *__restrict__ nnbr,
          float *__restrict__ F_lj, int *__restrict__ gate)
@@ -354,11 +370,12 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
     load_tables(tab, COUL ? rcc2 : nullptr, 0.0f, s_tab, s_rl2, s_rmax, s_rcc2);
     if (gate && blockIdx.x == 0 && threadIdx.x == 0)
         *gate = 0; // every build kernel of this step has run; the integrator may reopen it
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
         return;
-    const float4 pi = xq[i];
-    const int ti = typ[i];
+    const float4 pi = sxq[p];
+    const int i = sorted[p];
+    const int ti = __float_as_int(pi.w);
     const int row = ti * NPSIM_MAX_TYPES;
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     // One pair's force added into (sx, sy, sz); 1/r^2 as rsqrt(r^2)^2, as in
@@ -388,12 +405,12 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
     // List entries are read four at a time, one block ahead of their use (rows
     // below cap exist whatever the count), so each block's partner positions
     // are gathered as soon as the count is known; the pairs are summed in
-    // list order.  Entries are index << 3 | type (index < 2^29).
+    // list order.  Entries are slot << 3 | type (slot < 2^29).
     unsigned e[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        e[u] = u < cap ? nbr[(size_t)u * n + i] : 0u;
-    const int cnt = nnbr[i];
+        e[u] = u < cap ? nbr[(size_t)u * n + p] : 0u;
+    const int cnt = nnbr[p];
     if (cnt <= cap) {
         int k = 0;
         for (; k + 4 <= cnt; k += 4) {
@@ -401,10 +418,10 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
             unsigned en[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                pj[u] = xq[e[u] >> 3];
+                pj[u] = sxq[e[u] >> 3];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                en[u] = k + 4 + u < cap ? nbr[(size_t)(k + 4 + u) * n + i] : 0u;
+                en[u] = k + 4 + u < cap ? nbr[(size_t)(k + 4 + u) * n + p] : 0u;
             float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -419,7 +436,7 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (k + u < cnt)
-                    pj[u] = xq[e[u] >> 3];
+                    pj[u] = sxq[e[u] >> 3];
             float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -428,26 +445,31 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
             flush(sx, sy, sz);
         }
     } else {
-        const int p = pos[i];
-        const float4 pb = sxq[p]; // cells of the build
-        const int cx = cell_coord(pb.x, g), cy = cell_coord(pb.y, g), cz = cell_coord(pb.z, g);
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int z = cz + dz;
-            if (z < 0 || z >= g.dim)
-                continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int y = cy + dy;
-                if (y < 0 || y >= g.dim)
+        // cells of the build: the NP's sort key holds its build cell
+        const int tb = g.tb > 1 ? g.tb : 1;
+        const int c = key[i] - (g.tb > 1 ? ti * g.n_cells : 0);
+        const int cx = c % g.dim, cy = (c / g.dim) % g.dim, cz = c / (g.dim * g.dim);
+        for (int t = 0; t < tb; ++t) {
+            const int kofs = t * g.n_cells;
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int z = cz + dz;
+                if (z < 0 || z >= g.dim)
                     continue;
-                const int base = (z * g.dim + y) * g.dim;
-                const int b = start[base + max(cx - 1, 0)];
-                const int e = start[base + min(cx + 1, g.dim - 1) + 1];
-                for (int q = b; q < e; ++q)
-                    if (q != p) {
-                        float sx = 0.f, sy = 0.f, sz = 0.f;
-                        pair(xq[sorted[q]], __float_as_int(sxq[q].w), sx, sy, sz);
-                        flush(sx, sy, sz);
-                    }
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int y = cy + dy;
+                    if (y < 0 || y >= g.dim)
+                        continue;
+                    const int base = kofs + (z * g.dim + y) * g.dim;
+                    const int b = start[base + max(cx - 1, 0)];
+                    const int e = start[base + min(cx + 1, g.dim - 1) + 1];
+                    for (int q = b; q < e; ++q)
+                        if (q != p) {
+                            const float4 pj = sxq[q];
+                            float sx = 0.f, sy = 0.f, sz = 0.f;
+                            pair(pj, __float_as_int(pj.w), sx, sy, sz);
+                            flush(sx, sy, sz);
+                        }
+                }
             }
         }
     }
@@ -479,17 +501,25 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
     // grid-stride kernels on at most kMaxGrid CTAs: when the gate is closed a
     // launch costs little more than its CTAs' start
     const int B = 256;
-    const int gn = grid_for(n, B), gc = grid_for(g.n_cells, B);
-    k_cell_zero<<<gc, B, 0, st>>>(b.count, g.n_cells, gate);
-    k_cell_hash<<<gn, B, 0, st>>>(g, xq, n, b.key, b.rank, b.count, gate);
-    const int nt = cell_scan_tiles(g.n_cells);
+    const int m = (g.tb > 1 ? g.tb : 1) * g.n_cells; // sort keys
+    const int gn = grid_for(n, B), gc = grid_for(m, B);
+    k_cell_zero<<<gc, B, 0, st>>>(b.count, m, gate);
+    k_cell_hash<<<gn, B, 0, st>>>(g, xq, typ, n, b.key, b.rank, b.count, gate);
+    const int nt = cell_scan_tiles(m);
     const int gt = nt < kMaxGrid ? nt : kMaxGrid;
-    k_scan_tiles<<<gt, kScanThreads, 0, st>>>(b.count, b.start, b.tile_sum, g.n_cells, gate);
-    k_scan_totals<<<1, kScanThreads, 0, st>>>(b.tile_sum, nt, b.start, g.n_cells, gate);
-    k_scan_add<<<gt, kScanThreads, 0, st>>>(b.start, b.tile_sum, g.n_cells, gate);
+    k_scan_tiles<<<gt, kScanThreads, 0, st>>>(b.count, b.start, b.tile_sum, m, gate);
+    k_scan_totals<<<1, kScanThreads, 0, st>>>(b.tile_sum, nt, b.start, m, gate);
+    k_scan_add<<<gt, kScanThreads, 0, st>>>(b.start, b.tile_sum, m, gate);
     k_cell_scatter<<<gn, B, 0, st>>>(b.key, b.rank, b.start, b.arrived, n, gate);
     k_cell_order<<<gn, B, 0, st>>>(b.arrived, b.key, b.start, b.sorted, b.pos, n, gate);
     k_cell_gather<<<gn, B, 0, st>>>(b.sorted, xq, typ, b.sxq, n, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_refresh(const CellBufs &b, const float4 *xq, const int *typ, int n,
+                                cudaStream_t st)
+{
+    k_cell_gather<<<grid_for(n, 256), 256, 0, st>>>(b.sorted, xq, typ, b.sxq, n, nullptr);
     return cudaGetLastError();
 }
 
@@ -511,14 +541,16 @@ cudaError_t launch_lj_nbr(const CellGrid &g, const CellBufs &b, const float4 *xq
                           const int *typ, int n, const PairTab *tab, const float *rcc2,
                           const NbrList &l, float *F_lj, int *gate, cudaStream_t st)
 {
+    (void)xq; // the current positions are the cell-ordered records b.sxq
+    (void)typ;
     const int B = 128;
     const int grid = (n + B - 1) / B;
     if (rcc2)
-        k_lj_nbr<true><<<grid, B, 0, st>>>(g, b.start, b.sorted, b.pos, b.sxq, xq, typ, n, tab,
-                                           rcc2, l.cap, l.nbr, l.nnbr, F_lj, gate);
+        k_lj_nbr<true><<<grid, B, 0, st>>>(g, b.start, b.sorted, b.key, b.sxq, n, tab, rcc2,
+                                           l.cap, l.nbr, l.nnbr, F_lj, gate);
     else
-        k_lj_nbr<false><<<grid, B, 0, st>>>(g, b.start, b.sorted, b.pos, b.sxq, xq, typ, n, tab,
-                                            nullptr, l.cap, l.nbr, l.nnbr, F_lj, gate);
+        k_lj_nbr<false><<<grid, B, 0, st>>>(g, b.start, b.sorted, b.key, b.sxq, n, tab, nullptr,
+                                            l.cap, l.nbr, l.nnbr, F_lj, gate);
     return cudaGetLastError();
 }
 

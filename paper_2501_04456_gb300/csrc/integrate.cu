@@ -142,7 +142,8 @@ k_integrate(IntArgs a, StepParams p)
 
         advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
                                step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq,
-                               a.flags, a.x_ref, a.nbr_gate, a.half_skin2);
+                               a.flags, a.x_ref, a.nbr_gate, a.half_skin2, a.sxq, a.cell_pos,
+                               ti);
     }
 }
 

@@ -73,12 +73,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait for the completion of the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+// Default bound of every mbarrier wait: 2^32 SM cycles, ~2 s at 2 GHz.
+constexpr long long kWaitCycles = 1ll << 32;
+
+// Bounded wait for the completion of the mbarrier phase with the given parity:
+// false once `budget` SM cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  long long budget = kWaitCycles)
 {
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > (1ll << 32)) // ~2 s at 2 GHz
+        if (clock64() - t0 > budget)
             return false;
     }
     return true;
@@ -164,6 +169,10 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const uint32_t sbytes = (uint32_t)stage_bytes(g.n_tile);
     const uint32_t a_bytes = kTileM * kChunkK * 2;
     const uint32_t done_bar = smem_addr(&done);
+    // bound of the main loop's waits (a test may shorten it); the drain after an
+    // abort always waits with the default bound, so copies and MMAs in flight
+    // land before the CTA frees its tensor memory and leaves
+    const long long wb = g.wait_cycles > 0 ? g.wait_cycles : kWaitCycles;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -191,7 +200,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int c = 0;
             for (; c < nchunks; ++c) {
                 const int s = c % stages, u = c / stages;
-                if (u > 0 && !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((u - 1) & 1))) {
+                if (u > 0 &&
+                    !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((u - 1) & 1), wb)) {
                     atomicExch(&s_abort, 1);
                     break;
                 }
@@ -212,7 +222,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const uint32_t idesc = idesc_bf16(kTileM, nt);
             for (int c = 0; c < nchunks; ++c) {
                 const int s = c % stages, u = c / stages;
-                if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)(u & 1))) {
+                if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)(u & 1), wb)) {
                     atomicExch(&s_abort, 1);
                     break;
                 }
@@ -239,7 +249,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 
     // wait for the accumulator (bounded), then the epilogue
-    if (!mbar_wait_bounded(done_bar, 0))
+    if (!mbar_wait_bounded(done_bar, 0, wb))
         atomicExch(&s_abort, 1);
     __syncthreads();
     const bool abort = s_abort != 0;

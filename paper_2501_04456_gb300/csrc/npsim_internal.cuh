@@ -642,6 +642,8 @@ struct CellGrid {
     int n_cells;    // dim^3
     float inv_h;    // 1 / cell edge
     float L;        // grid covers [-L, L)^3; coordinates outside are clamped
+    int tb;         // type blocks of the sort key: key = type * n_cells + cell when
+                    // tb > 1 (cell order grouped by type first), key = cell when tb == 1
 };
 
 // Record a message for npsim_last_error() on this thread and return `code`
@@ -710,6 +712,8 @@ struct IntArgs {
     const int *row_pos;      // grouped layout: position of particle i in the rows (-1:
                              // no Coulomb partial); NULL: row position = i
     const float4 *x_ref;     // positions at the last neighbour-list build (or NULL)
+    float4 *sxq;             // cell-ordered current positions of the neighbour-list
+    const int *cell_pos;     // kernel, and the slot of NP i (both NULL without one)
     int *nbr_gate;           // set to 1 when an NP has moved more than half the skin
     float half_skin2;        // (skin / 2)^2, with margin
     float4 *spring;          // spring radius per type (spring_entry), two buffers
@@ -737,7 +741,9 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
                                                  float *x_lo, float *v_, float *F, float4 *xq,
                                                  int *flags,
                                                  const float4 *x_ref = nullptr,
-                                                 int *nbr_gate = nullptr, float half_skin2 = 0.f)
+                                                 int *nbr_gate = nullptr, float half_skin2 = 0.f,
+                                                 float4 *sxq = nullptr,
+                                                 const int *cell_pos = nullptr, int ti = 0)
 {
     constexpr bool DO_B = (MODE == MODE_BA || MODE == MODE_B);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
@@ -789,6 +795,8 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
             }
         }
         xq[i] = make_float4(xhi[0], xhi[1], xhi[2], xh.w);
+        if (sxq) // the neighbour-list kernel's cell-ordered copy
+            sxq[cell_pos[i]] = make_float4(xhi[0], xhi[1], xhi[2], __int_as_float(ti));
         x_lo[i] = xlo[0];
         x_lo[n + i] = xlo[1];
         x_lo[2 * n + i] = xlo[2];
@@ -884,6 +892,7 @@ struct GemmArgs {
     __nv_bfloat16 *Cb;      // BF16 output or NULL
     float *Z;               // pre-activation (GEMM_ACT writes, GEMM_DACT reads), ldc
     int *flags;             // FLAG_TIMEOUT on a bounded wait that expired
+    long long wait_cycles;  // bound of the main loop's waits in SM cycles (0: 2^32)
 };
 
 struct AdamArgs {
@@ -921,18 +930,27 @@ cudaError_t launch_f32_to_bf16(const float *x, int n, void *y, cudaStream_t st);
 cudaError_t launch_weights_bf16(const float *w, int rows, int cols, void *wb, void *wt,
                                 cudaStream_t st);
 
-// Cell list (celllist.cu)
+// Cell list (celllist.cu).  The sort key of NP i is its cell (tb == 1) or
+// type * n_cells + cell (tb = the number of types): the cell order lists all NPs
+// of type 0 cell by cell, then those of type 1, and so on.  count and start
+// cover the tb * n_cells keys.
 struct CellBufs {
     int *key, *rank, *count, *start, *arrived, *sorted, *tile_sum;
     int *pos;    // cell-ordered position of NP i (the inverse of sorted)
-    float4 *sxq; // cell-ordered (x, y, z, type as int bits)
+    float4 *sxq; // cell-ordered (x, y, z, type as int bits): the positions of the
+                 // build, and with a neighbour list the current positions (the
+                 // integrator writes each new position to its NP's slot)
 };
 // Build the cell list of positions xq (gate: NULL = always, else only when *gate != 0).
 cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
                               CellBufs &b, const int *gate, cudaStream_t st);
+// Rewrite the cell-ordered records from positions xq in the order of the last build.
+cudaError_t launch_cell_refresh(const CellBufs &b, const float4 *xq, const int *typ, int n,
+                                cudaStream_t st);
 // Verlet neighbour list over the cells (celllist.cu): nbr [cap][n] column-major
-// (index << 3 | type), column i the list of NP i; nnbr [n] the full counts,
-// x_ref [n] the positions of the last build.
+// (cell-order slot << 3 | type), column p the list of the NP at cell-order slot
+// p; nnbr [n] the full counts by slot; x_ref [n] the positions of the last
+// build by particle index.
 struct NbrList {
     unsigned *nbr; // (index << 3 | type)
     int *nnbr;

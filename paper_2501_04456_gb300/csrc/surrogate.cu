@@ -14,6 +14,7 @@
 // Parameter layout of one network (npsim_surr_get_params): for each layer l
 // in order, W_l (out_pad x in_pad, row-major) then b_l (out_pad).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -154,6 +155,10 @@ namespace {
 
 int n_tile_for(int N) { return (N % 64 == 0) ? 64 : N; }
 
+// Bound of the GEMM kernel's main-loop waits set by npsim_test_wait_cycles
+// (0: the kernel's default).
+std::atomic<long long> g_wait_cycles{0};
+
 cudaError_t gemm(npsim_surr *s, int mode, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
                  int ldb, int M, int N, int K, const float *bias, float *Cf, __nv_bfloat16 *Cb,
                  int ldc, float *Z, int act)
@@ -176,6 +181,7 @@ cudaError_t gemm(npsim_surr *s, int mode, const __nv_bfloat16 *A, int lda, const
     g.Cb = Cb;
     g.Z = Z;
     g.flags = s->flags;
+    g.wait_cycles = g_wait_cycles.load();
     return launch_gemm(g, s->st);
 }
 
@@ -748,6 +754,14 @@ int npsim_surr_predict(npsim_surr_t s, const float *X, int32_t B, float *Y_mean,
     return check_flags(s);
 }
 
+int npsim_test_wait_cycles(int64_t cycles)
+{
+    if (cycles < 0)
+        return report_error(NPSIM_ERR_INVALID_ARG, "cycles must be >= 0");
+    g_wait_cycles.store((long long)cycles);
+    return NPSIM_OK;
+}
+
 // Test hook: C = A B^T for host BF16 matrices (bit patterns), C in FP32.
 int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
                     int32_t n_tile, float *C)
@@ -779,6 +793,7 @@ int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, 
     g.mode = GEMM_F32;
     g.Cf = dC;
     g.flags = dflag;
+    g.wait_cycles = g_wait_cycles.load();
     cudaError_t e = launch_gemm(g, 0);
     if (e == cudaSuccess)
         e = cudaDeviceSynchronize();

@@ -38,6 +38,33 @@ class Ranges:
     kT: tuple = (0.5, 2.0)
 
 
+def config5_ranges() -> Ranges:
+    """Scenario ranges of the surrogate's training data in the regime of the
+    batched ensemble: N log-uniform in [512, 8192], final R/R0 in [0.2, 0.6],
+    initial packing fraction in [0.006, 0.012] (the ensemble's 0.01 with some
+    spread), the other inputs as in Ranges."""
+    return Ranges(n_min=512, n_max=8192, phi0=(0.006, 0.012), shrink=(0.2, 0.6))
+
+
+def calibrate_tau(spread, err, tol=0.05, target=0.98):
+    """Largest spread threshold tau such that, on a validation set, at least
+    `target` of the predictions with spread <= tau are within `tol` of the
+    simulation (err = |prediction - simulation|).  Returns tau (0.0 if no
+    threshold qualifies: everything falls back to the simulation)."""
+    order = np.argsort(spread, kind="stable")
+    sp = np.asarray(spread)[order]
+    ok = (np.asarray(err)[order] <= tol).astype(np.float64)
+    frac = np.cumsum(ok) / np.arange(1, len(ok) + 1)
+    good = np.nonzero(frac >= target)[0]
+    if len(good) == 0:
+        return 0.0
+    k = good[-1]
+    # keep every prediction tied with the last accepted spread on the same side
+    while k + 1 < len(sp) and sp[k + 1] == sp[k] and frac[k + 1] >= target:
+        k += 1
+    return float(sp[k])
+
+
 def scenario_from(feat, steps, dt=5e-4, seed=0):
     """Scenario of one droplet: three types of diameters 1, 1.5, 3 (fractions f1,
     f2, 1 - f1 - f2), charges 0, +q, -q, LJ eps, Bjerrum length 0.7, all-pairs
@@ -96,6 +123,20 @@ def simulate(P, feats, steps, seed0=0, batch=256, stream=None, r_max=8.0):
     return Y, t_sim
 
 
+def rdf_spread(mean, spread):
+    """Relative spread of the predicted g(r) across the networks:
+    ||spread of the 64 bins||_2 / ||mean g||_2 per sample."""
+    g = np.asarray(mean)[:, 1:]
+    return np.linalg.norm(np.asarray(spread)[:, 1:], axis=1) / np.maximum(
+        np.linalg.norm(g, axis=1), 1e-30)
+
+
+def rdf_rel_error(pred, sim):
+    """||g_pred - g_sim||_2 / ||g_sim||_2 per sample (the 64 RDF bins)."""
+    a, b = np.asarray(pred)[:, 1:], np.asarray(sim)[:, 1:]
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-30)
+
+
 class SurrogateModel:
     """Deep ensemble of MLPs (8 -> 4 x 256 SiLU -> 65) with a spread-gated
     fallback to simulation."""
@@ -115,11 +156,14 @@ class SurrogateModel:
     def predict(self, X):
         return self.net.predict(X)
 
-    def predict_or_simulate(self, X, steps, tau, seed0=10 ** 6, stream=None):
+    def predict_or_simulate(self, X, steps, tau, seed0=10 ** 6, stream=None, tau_rdf=None):
         """Surrogate prediction where the spread of D_f across the networks is at
-        most tau; the plain simulation elsewhere.  Returns (Y, fallback mask)."""
+        most tau (and, with tau_rdf, the relative spread of g(r) at most
+        tau_rdf); the plain simulation elsewhere.  Returns (Y, fallback mask)."""
         m, sp = self.predict(X)
         fb = sp[:, 0] > tau
+        if tau_rdf is not None:
+            fb |= rdf_spread(m, sp) > tau_rdf
         Y = m.astype(np.float64)
         if fb.any():
             Ys, _ = simulate(self.P, X[fb], steps, seed0=seed0, stream=stream)

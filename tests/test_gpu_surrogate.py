@@ -121,3 +121,38 @@ def test_surrogate_learns_smooth_function(P):
     rmse = np.sqrt(((m - Yt) ** 2).mean(0))
     assert np.all(rmse <= 0.15 * Yt.std(0) + 1e-3)
     assert np.all(np.isfinite(sp)) and np.all(sp >= 0) and sp.mean() > 0
+
+
+def test_bounded_wait_expiry_reports_timeout_and_recovers(P):
+    """Failure path of the tensor-core kernels without a stuck GPU: with the
+    bound of the GEMM kernel's main-loop waits cut to one SM cycle, the waits
+    give up (a TMA copy or an MMA always takes longer), the kernel drains its
+    copies and MMAs in flight with the default bound, frees its tensor memory
+    and flags the timeout: npsim_gemm_bf16 and the surrogate's training return
+    NPSIM_ERR_TIMEOUT.  With the default bound back, the same GEMM is correct
+    and a fresh surrogate trains."""
+    rng = np.random.default_rng(9)
+    A = _bits(rng.standard_normal((256, 128)))
+    B = _bits(rng.standard_normal((64, 128)))
+    a, b = _val(A), _val(B)
+    ref, scale = a @ b.T, np.abs(a) @ np.abs(b).T
+    X = rng.standard_normal((256, 8)).astype(np.float32)
+    Y = rng.standard_normal((256, 16)).astype(np.float32)
+    try:
+        P.npsim_test_wait_cycles(1)
+        with pytest.raises(P.NpsimError) as e:
+            P.npsim_gemm_bf16(A, B, 64)
+        assert e.value.code == -4  # NPSIM_ERR_TIMEOUT
+        with P.Surrogate(n_in=8, n_hidden=64, n_layers=2, n_out=16, n_nets=1, seed=0) as s:
+            with pytest.raises(P.NpsimError) as e:
+                s.train(X, Y, epochs=1, batch=128)
+            assert e.value.code == -4
+    finally:
+        P.npsim_test_wait_cycles(0)
+    Cg = P.npsim_gemm_bf16(A, B, 64)
+    assert np.all(np.abs(Cg - ref) <= 2e-5 * scale + 1e-30)
+    with P.Surrogate(n_in=8, n_hidden=64, n_layers=2, n_out=16, n_nets=1, seed=0) as s:
+        loss = s.train(X, Y, epochs=2, batch=128)
+        assert np.isfinite(loss)
+    with pytest.raises(P.NpsimError):
+        P.npsim_test_wait_cycles(-1)

@@ -73,7 +73,8 @@ class Scenario:
     eps_override: Optional[np.ndarray] = None
     n_steps: int = 1000          # length of the full run
     min_gap: float = 0.9         # placement: no pair closer than min_gap*sigma_ab
-    skip_neutral: bool = False   # leave charge-0 NPs out of the Coulomb sum (exact)
+    sum_neutral: bool = False    # all-pairs Coulomb over all pairs, charge-0 NPs included
+                                 # (default: they are left out; their terms are exactly 0)
 
     @property
     def T(self) -> int:
