@@ -214,6 +214,7 @@ struct npsim_sim {
     CellGrid grid{};
     CellBufs cb{};
     bool cell = false;
+    double rlist[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES]{}; // list radius per type pair (0: none)
     NbrList nl{};          // Verlet list over the cells (cell-list LJ)
     int *d_gate = nullptr; // 1: rebuild the cell and neighbour lists at the next pass
 
@@ -303,6 +304,34 @@ struct npsim_sim {
 
 namespace {
 
+// List radius (largest acting cutoff + skin) of every type pair of a pair table,
+// as the list kernels form it in float32 (0: the pair is never listed), for
+// LJ (t.z = rc^2 where 24 eps = t.y != 0) and, with rcc2, the truncated
+// Coulomb term (where C q_a q_b = t.w != 0).
+void list_radii(const PairTab &tab, const float *rcc2, float skin, double *rl)
+{
+    for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) {
+        const float4 t = tab.e[k];
+        const float r_lj = t.y != 0.0f ? std::sqrt(t.z) : 0.0f;
+        const float r_c = (rcc2 && rcc2[k] > 0.0f && t.w != 0.0f) ? std::sqrt(rcc2[k]) : 0.0f;
+        const float r = std::max(r_lj, r_c);
+        rl[k] = r > 0.0f ? (double)r + (double)skin : 0.0;
+    }
+}
+
+// Stencil half-widths of a grid for the list radii rl: a partner within r of an
+// NP lies at most ceil(r / h) cells away along each axis (clamping coordinates
+// beyond the grid into the edge cells only shortens distances); a relative
+// margin of 1e-5 covers float32 rounding of the cell coordinates.
+void set_extents(CellGrid &g, const double *rl)
+{
+    const double h = 1.0 / (double)g.inv_h;
+    for (int k = 0; k < NPSIM_MAX_TYPES * NPSIM_MAX_TYPES; ++k) {
+        const double e = rl[k] > 0.0 ? std::ceil(rl[k] * (1.0 + 1e-5) / h) : 1.0;
+        g.ext[k] = (unsigned char)std::min(std::max(e, 1.0), 60.0);
+    }
+}
+
 // Buffers of a cell list of n NPs over the g.tb * g.n_cells sort keys.  pos starts
 // at 0 so that every slot it names is in range before the first build.
 int alloc_cells(CellGrid &g, CellBufs &b, int n)
@@ -316,7 +345,11 @@ int alloc_cells(CellGrid &g, CellBufs &b, int n)
     NP_CUDA(dalloc(&b.sorted, n));
     NP_CUDA(dalloc(&b.pos, n));
     NP_CUDA(cudaMemset(b.pos, 0, sizeof(int) * (size_t)(n > 0 ? n : 1)));
-    NP_CUDA(dalloc(&b.sxq, n));
+    // one record past the NPs: a position far from every NP (type 0), the
+    // partner that pads each neighbour list to whole blocks of four
+    NP_CUDA(dalloc(&b.sxq, (size_t)n + 1));
+    const float4 far = make_float4(kPairPad, kPairPad, kPairPad, 0.0f);
+    NP_CUDA(cudaMemcpy(b.sxq + n, &far, sizeof(far), cudaMemcpyHostToDevice));
     NP_CUDA(dalloc(&b.tile_sum, cell_scan_tiles((int)m)));
     return NPSIM_OK;
 }
@@ -338,6 +371,8 @@ CellGrid make_grid(double L, double h_min, long long max_cells)
     g.inv_h = (float)(1.0 / h);
     g.L = (float)L;
     g.tb = 1;
+    for (auto &e : g.ext)
+        e = 1;
     return g;
 }
 
@@ -558,7 +593,7 @@ int grow_neighbour_list(npsim_sim *s)
     const int mx = *std::max_element(cnt.begin(), cnt.end());
     if (mx <= s->nl.cap)
         return NPSIM_OK;
-    const int cap = mx + mx / 4 + 8;
+    const int cap = ((mx + mx / 4 + 8) + 3) & ~3; // whole blocks of four entries
     unsigned *nb = nullptr;
     cudaError_t e = dalloc(&nb, (size_t)cap * s->n);
     if (e != cudaSuccess)
@@ -1183,8 +1218,22 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
         for (int64_t i = 0; i < 3 * n; ++i)
             L = std::max(L, std::fabs(x0[i]));
         L += rc_cell + kSkin;
-        s->grid = make_grid(L, rc_cell + kSkin, std::max<long long>(4 * n + 4096, 1 << 16));
+        // cell edge: the smallest list radius of the acting type pairs (each pair
+        // scans as many cells as its own radius needs), the sort keys (types x
+        // cells) capped at about two per NP, so that the cell ranges stay in L2
+        // (the edge grows until the grid fits)
+        float rcc2h[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES] = {};
+        if (s->d_rcc2)
+            BAIL_CUDA(cudaMemcpy(rcc2h, s->d_rcc2, sizeof(rcc2h), cudaMemcpyDeviceToHost));
+        list_radii(tf, s->d_rcc2 ? rcc2h : nullptr, kSkin, s->rlist);
+        double h_min = rc_cell + kSkin;
+        for (int a = 0; a < s->T; ++a)
+            for (int b = 0; b < s->T; ++b)
+                if (s->rlist[a * NPSIM_MAX_TYPES + b] > 0.0)
+                    h_min = std::min(h_min, s->rlist[a * NPSIM_MAX_TYPES + b]);
+        s->grid = make_grid(L, h_min, std::max<long long>(2 * n / s->T + 4096, 1 << 16));
         s->grid.tb = s->T; // cell order grouped by type (uniform list lengths per warp)
+        set_extents(s->grid, s->rlist);
         rc = alloc_cells(s->grid, s->cb, s->n);
         if (rc)
             return bail(rc);
@@ -1809,6 +1858,7 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
     g.inv_h = h.grid_inv_h;
     g.L = h.grid_L;
     g.tb = s->T;
+    set_extents(g, s->rlist);
     if (!s->cb.key) {
         int rc = alloc_cells(g, s->cb, s->n);
         if (rc)

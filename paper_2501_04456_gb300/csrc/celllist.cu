@@ -280,8 +280,8 @@ __device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab,
 // cap partners is summed from the cells instead).  Lists are written by slot
 // so that the per-step force kernel, which runs in the same order, reads them
 // coalesced.  Records the positions of this build in x_ref (by particle).
-__global__ void __launch_bounds__(128)
-k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
+__global__ void __launch_bounds__(128, 8)
+k_nbr_build(const __grid_constant__ CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
             const float4 *__restrict__ sxq, int n, const PairTab *__restrict__ tab,
             const float *__restrict__ rcc2, float skin,
             int cap, unsigned *__restrict__ nbr, int *__restrict__ nnbr,
@@ -310,33 +310,44 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
             if (tb > 1 && s_rl2[row + t] == 0.0f)
                 continue; // no term acts between these types
             const int kofs = t * g.n_cells;
-            for (int dz = -1; dz <= 1; ++dz) {
+            // the cells this type pair's list radius can reach (with tb == 1, the
+            // widest stencil of the row type); with type blocks every candidate
+            // of block t has type t, so its squared list radius is fixed
+            int w = g.ext[row + t];
+            if (tb == 1)
+                for (int b = 1; b < NPSIM_MAX_TYPES; ++b)
+                    w = max(w, (int)g.ext[row + b]);
+            const float rl2_t = tb > 1 ? s_rl2[row + t] : rmax;
+            for (int dz = -w; dz <= w; ++dz) {
                 const int z = cz + dz;
                 if (z < 0 || z >= g.dim)
                     continue;
-                for (int dy = -1; dy <= 1; ++dy) {
+                for (int dy = -w; dy <= w; ++dy) {
                     const int y = cy + dy;
                     if (y < 0 || y >= g.dim)
                         continue;
                     const int base = kofs + (z * g.dim + y) * g.dim;
-                    const int b = start[base + max(cx - 1, 0)];
-                    const int e = start[base + min(cx + 1, g.dim - 1) + 1];
+                    const int b = start[base + max(cx - w, 0)];
+                    const int e = start[base + min(cx + w, g.dim - 1) + 1];
                     for (int q = b; q < e; ++q) {
                         const float4 pj = sxq[q];
                         const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
                         const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
-                        if (r2 >= rmax || q == p)
+                        if (r2 >= rl2_t || q == p)
                             continue;
                         const int tj = __float_as_int(pj.w);
-                        if (r2 < s_rl2[row + tj]) {
+                        if (tb > 1 || r2 < s_rl2[row + tj]) {
                             if (cnt < cap)
-                                nbr[(size_t)cnt * n + p] = ((unsigned)q << 3) | (unsigned)tj;
+                                nbr[nbr_index(cnt, p, n)] = ((unsigned)q << 3) | (unsigned)tj;
                             ++cnt;
                         }
                     }
                 }
             }
         }
+        // pad the last block with the far record (whole blocks of four partners)
+        for (int k = cnt; k < cap && (k & 3); ++k)
+            nbr[nbr_index(k, p, n)] = (unsigned)n << 3;
         nnbr[p] = cnt;
         if (cnt > cap)
             atomicOr(flags, FLAG_NBR_OVERFLOW);
@@ -352,12 +363,11 @@ k_nbr_build(CellGrid g, const int *__restrict__ start, const int *__restrict__ s
 // i = sorted[p], where the integrator reads it.  An NP whose list overflowed
 // sums over the 27 cells of that build instead (a superset of its list).
 // Writes one 32-byte (hi x, y, z, lo x, y, z, 0, 0) record per NP and closes
-// the rebuild gate.  10 CTAs of 128 per SM for the LJ-only kernel: the partner
-// gathers are latency-bound, and more threads in flight help.  The
-// truncated-Coulomb variant keeps 8.
+// the rebuild gate.  8 CTAs of 128 per SM (64 registers: each thread keeps
+// two blocks of partner records and entries in flight).
 template <bool COUL>
-__global__ void __launch_bounds__(128, COUL ? 8 : 10)
-k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
+__global__ void __launch_bounds__(128, 8)
+k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
          const int *__restrict__ key, const float4 *__restrict__ sxq, int n,
          const PairTab *__restrict__ tab, const float *__restrict__ rcc2, int cap,
          const unsigned *__restrict__ nbr, const int *__restrict__ nnbr,
@@ -402,47 +412,49 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
         two_sum_acc(hy, ly, sy);
         two_sum_acc(hz, lz, sz);
     };
-    // List entries are read four at a time, one block ahead of their use (rows
-    // below cap exist whatever the count), so each block's partner positions
-    // are gathered as soon as the count is known; the pairs are summed in
-    // list order.  Entries are slot << 3 | type (slot < 2^29).
-    unsigned e[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-        e[u] = u < cap ? nbr[(size_t)u * n + p] : 0u;
+    // List entries arrive four at a time (one 16-byte load per block of four,
+    // contiguous over the warp), two blocks ahead of their use, and a block's
+    // partner records are gathered one block ahead, so that each thread keeps
+    // the next block's gathers and the entries after it in flight while it
+    // computes.  A list's last block is padded with the far record, whose terms
+    // are exactly zero, so every block is four whole pairs.  Pairs are summed
+    // in list order, each block of four in float32 and then into the
+    // compensated (hi, lo) total.  The first block is read before the count is
+    // known (cap >= 4 entries exist for every slot).  Entries are
+    // slot << 3 | type (slot <= n < 2^29).
+    const uint4 *nb4 = reinterpret_cast<const uint4 *>(nbr);
+    const uint4 far4 = make_uint4((unsigned)n << 3, (unsigned)n << 3, (unsigned)n << 3,
+                                  (unsigned)n << 3);
+    uint4 cur = nb4[p];
     const int cnt = nnbr[p];
     if (cnt <= cap) {
-        int k = 0;
-        for (; k + 4 <= cnt; k += 4) {
-            float4 pj[4];
-            unsigned en[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                pj[u] = sxq[e[u] >> 3];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                en[u] = k + 4 + u < cap ? nbr[(size_t)(k + 4 + u) * n + p] : 0u;
+        const int nblk = (cnt + 3) >> 2;
+        uint4 nxt = nblk > 1 ? nb4[(size_t)n + p] : far4;
+        float4 pj[4];
+        pj[0] = sxq[cur.x >> 3];
+        pj[1] = sxq[cur.y >> 3];
+        pj[2] = sxq[cur.z >> 3];
+        pj[3] = sxq[cur.w >> 3];
+        for (int j = 0; j < nblk; ++j) {
+            const uint4 nn = j + 2 < nblk ? nb4[(size_t)(j + 2) * n + p] : far4;
+            float4 pn[4];
+            if (j + 1 < nblk) {
+                pn[0] = sxq[nxt.x >> 3];
+                pn[1] = sxq[nxt.y >> 3];
+                pn[2] = sxq[nxt.z >> 3];
+                pn[3] = sxq[nxt.w >> 3];
+            }
             float sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                pair(pj[u], (int)(e[u] & 7u), sx, sy, sz);
+            pair(pj[0], (int)(cur.x & 7u), sx, sy, sz);
+            pair(pj[1], (int)(cur.y & 7u), sx, sy, sz);
+            pair(pj[2], (int)(cur.z & 7u), sx, sy, sz);
+            pair(pj[3], (int)(cur.w & 7u), sx, sy, sz);
             flush(sx, sy, sz);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                e[u] = en[u];
-        }
-        if (k < cnt) { // the last cnt - k < 4 entries
-            float4 pj[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (k + u < cnt)
-                    pj[u] = sxq[e[u] >> 3];
-            float sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (k + u < cnt)
-                    pair(pj[u], (int)(e[u] & 7u), sx, sy, sz);
-            flush(sx, sy, sz);
+                pj[u] = pn[u];
+            cur = nxt;
+            nxt = nn;
         }
     } else {
         // cells of the build: the NP's sort key holds its build cell
@@ -451,17 +463,21 @@ k_lj_nbr(CellGrid g, const int *__restrict__ start, const int *__restrict__ sort
         const int cx = c % g.dim, cy = (c / g.dim) % g.dim, cz = c / (g.dim * g.dim);
         for (int t = 0; t < tb; ++t) {
             const int kofs = t * g.n_cells;
-            for (int dz = -1; dz <= 1; ++dz) {
+            int w = g.ext[row + t];
+            if (tb == 1)
+                for (int b = 1; b < NPSIM_MAX_TYPES; ++b)
+                    w = max(w, (int)g.ext[row + b]);
+            for (int dz = -w; dz <= w; ++dz) {
                 const int z = cz + dz;
                 if (z < 0 || z >= g.dim)
                     continue;
-                for (int dy = -1; dy <= 1; ++dy) {
+                for (int dy = -w; dy <= w; ++dy) {
                     const int y = cy + dy;
                     if (y < 0 || y >= g.dim)
                         continue;
                     const int base = kofs + (z * g.dim + y) * g.dim;
-                    const int b = start[base + max(cx - 1, 0)];
-                    const int e = start[base + min(cx + 1, g.dim - 1) + 1];
+                    const int b = start[base + max(cx - w, 0)];
+                    const int e = start[base + min(cx + w, g.dim - 1) + 1];
                     for (int q = b; q < e; ++q)
                         if (q != p) {
                             const float4 pj = sxq[q];

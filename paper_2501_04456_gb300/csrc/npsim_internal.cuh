@@ -644,6 +644,10 @@ struct CellGrid {
     float L;        // grid covers [-L, L)^3; coordinates outside are clamped
     int tb;         // type blocks of the sort key: key = type * n_cells + cell when
                     // tb > 1 (cell order grouped by type first), key = cell when tb == 1
+    // stencil half-width (in cells) per type pair: partners of type b of an NP of
+    // type a within its list radius lie within ext[a * 8 + b] cells along each
+    // axis (1 when the edge is at least every radius)
+    unsigned char ext[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
 };
 
 // Record a message for npsim_last_error() on this thread and return `code`
@@ -939,7 +943,9 @@ struct CellBufs {
     int *pos;    // cell-ordered position of NP i (the inverse of sorted)
     float4 *sxq; // cell-ordered (x, y, z, type as int bits): the positions of the
                  // build, and with a neighbour list the current positions (the
-                 // integrator writes each new position to its NP's slot)
+                 // integrator writes each new position to its NP's slot);
+                 // sxq[n] is a record far from every NP (type 0) that pads the
+                 // neighbour lists
 };
 // Build the cell list of positions xq (gate: NULL = always, else only when *gate != 0).
 cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *typ, int n,
@@ -947,10 +953,17 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
 // Rewrite the cell-ordered records from positions xq in the order of the last build.
 cudaError_t launch_cell_refresh(const CellBufs &b, const float4 *xq, const int *typ, int n,
                                 cudaStream_t st);
-// Verlet neighbour list over the cells (celllist.cu): nbr [cap][n] column-major
-// (cell-order slot << 3 | type), column p the list of the NP at cell-order slot
-// p; nnbr [n] the full counts by slot; x_ref [n] the positions of the last
-// build by particle index.
+// Verlet neighbour list over the cells (celllist.cu): entries (cell-order slot
+// << 3 | type); entry k of the NP at cell-order slot p at nbr[nbr_index(k, p, n)]
+// -- blocks of four entries, block j of all slots contiguous, so that a thread
+// reads its next four entries with one 16-byte load and a warp reads 512
+// contiguous bytes; cap (a multiple of 4) entries per slot; a list's last block
+// is padded with entries (n << 3) naming the far record sxq[n].  nnbr [n] the full
+// counts by slot; x_ref [n] the positions of the last build by particle index.
+__host__ __device__ __forceinline__ size_t nbr_index(int k, int p, int n)
+{
+    return ((size_t)(k >> 2) * (size_t)n + (size_t)p) * 4 + (size_t)(k & 3);
+}
 struct NbrList {
     unsigned *nbr; // (index << 3 | type)
     int *nnbr;
