@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--no-full-sum", action="store_true", help=argparse.SUPPRESS)
     # profiling: the headline step with the Coulomb sum over all N(N-1) pairs
     ap.add_argument("--sum-neutral", action="store_true", help=argparse.SUPPRESS)
+    # profiling: skip the FMA microbenchmark (the roofline then divides by the
+    # nominal FP32 peak)
+    ap.add_argument("--no-peak", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-ensemble", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--ensemble-steps", type=int, default=10000, help=argparse.SUPPRESS)
     ap.add_argument("--no-surrogate", action="store_true", help=argparse.SUPPRESS)
@@ -57,7 +60,7 @@ def _args():
     ap.add_argument("--no-cfg2", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--case", default="step",
                     choices=["step", "integrator", "surrogate", "hbm", "dense", "dense_lj",
-                             "surrogate_train", "config3_full"],
+                             "surrogate_train", "config3_full", "fma_peak", "lattice"],
                     help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -744,7 +747,8 @@ def run_ours(a):
     peaks = _peaks()
     max_mhz = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
     nominal_tflops = info["sm_count"] * 128 * 2 * max_mhz * 1e6 / 1e12
-    peak = _fp32_peak(P, stream, f"GPU-{uuid}" if uuid else None) if rank == 0 else None
+    peak = (_fp32_peak(P, stream, f"GPU-{uuid}" if uuid else None)
+            if rank == 0 and not a.no_peak else None)
     peak_tflops = peak["tflops"] if peak else nominal_tflops
     ap_avg = sum(ap_ms) / len(ap_ms)
     achieved = FLOPS_PER_PAIR * charged_pairs / (ap_avg * 1e-3) / 1e12
@@ -1132,6 +1136,17 @@ def main():
     if a.case == "config3_full":
         run_config3_full_case(a)
         return
+    if a.case == "fma_peak":  # the FP32 microbenchmark alone (profiling)
+        import torch
+        from paper_2501_04456_gb300 import build as _b
+        _b.build()
+        import paper_2501_04456_gb300 as P
+        uuid = getattr(torch.cuda.get_device_properties(0), "uuid", None)
+        print(json.dumps({"case": "fma_peak", **_fp32_peak(
+            P, torch.cuda.current_stream(), f"GPU-{uuid}" if uuid else None,
+            target_s=0.05 if a.steps < 20 else 0.25, reps=max(1, min(a.steps, 3)))}),
+            flush=True)
+        return
     if a.case == "dense":
         run_dense_case(a)
         return
@@ -1148,6 +1163,14 @@ def main():
         print(json.dumps({"case": "hbm", "integrator": _integrator_roofline(P, stream, n),
                           "cell_list": _cell_list_roofline(P, stream, n // 2),
                           "cell_list_dense": _cell_list_dense_roofline(P, stream)}), flush=True)
+        return
+    if a.case == "lattice":  # profiling: the jittered-lattice cell-list case alone
+        import torch
+        from paper_2501_04456_gb300 import build as _b
+        _b.build()
+        import paper_2501_04456_gb300 as P
+        print(json.dumps({"case": "lattice", **_cell_list_roofline(
+            P, torch.cuda.current_stream(), n=a.n if a.n != 250000 else 1 << 22)}), flush=True)
         return
     if a.case == "dense_lj":  # profiling: the dense aggregate's cell-list path alone
         import torch

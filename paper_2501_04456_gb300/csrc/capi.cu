@@ -215,6 +215,9 @@ struct npsim_sim {
     CellBufs cb{};
     bool cell = false;
     double rlist[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES]{}; // list radius per type pair (0: none)
+    double cell_h_min = 0.0; // smallest list radius (the cell edge the grid aims at)
+    double cell_rc = 0.0;    // largest cutoff of the cell-list terms
+    size_t cells_alloc = 0;  // sort keys the cell buffers hold
     NbrList nl{};          // Verlet list over the cells (cell-list LJ)
     int *d_gate = nullptr; // 1: rebuild the cell and neighbour lists at the next pass
 
@@ -375,6 +378,35 @@ CellGrid make_grid(double L, double h_min, long long max_cells)
         e = 1;
     return g;
 }
+
+// The LJ cell list's grid over [-L, L)^3: edge = the smallest list radius of
+// the acting type pairs (each pair scans as many cells as its own radius
+// needs), sort keys (types x cells) capped at about two per NP so that the
+// cell ranges stay in L2 (the edge grows until the grid fits), cell order
+// grouped by type.
+CellGrid lj_grid(const npsim_sim *s, double L)
+{
+    CellGrid g = make_grid(L, s->cell_h_min, std::max<long long>(2LL * s->n / s->T + 4096, 1 << 16));
+    g.tb = s->T; // cell order grouped by type (uniform list lengths per warp)
+    set_extents(g, s->rlist);
+    return g;
+}
+
+// Cell buffers large enough for grid g (reallocated only when it has more keys).
+int ensure_cells(npsim_sim *s, CellGrid &g)
+{
+    const size_t keys = (size_t)std::max(g.tb, 1) * (size_t)g.n_cells;
+    if (keys > s->cells_alloc || !s->cb.key) {
+        free_cells(s->cb);
+        s->cells_alloc = 0;
+        int rc = alloc_cells(g, s->cb, s->n);
+        if (rc)
+            return rc;
+        s->cells_alloc = keys;
+    }
+    return NPSIM_OK;
+}
+
 
 // Launch shapes of the all-pairs sum in one index space: [0, A) the
 // identity-order kernels of allpairs.cu (scalar and packed), then [A, A + G) the
@@ -1231,10 +1263,10 @@ int create_impl(const npsim_type_t *types, const npsim_params_t *params, int64_t
             for (int b = 0; b < s->T; ++b)
                 if (s->rlist[a * NPSIM_MAX_TYPES + b] > 0.0)
                     h_min = std::min(h_min, s->rlist[a * NPSIM_MAX_TYPES + b]);
-        s->grid = make_grid(L, h_min, std::max<long long>(2 * n / s->T + 4096, 1 << 16));
-        s->grid.tb = s->T; // cell order grouped by type (uniform list lengths per warp)
-        set_extents(s->grid, s->rlist);
-        rc = alloc_cells(s->grid, s->cb, s->n);
+        s->cell_h_min = h_min;
+        s->cell_rc = rc_cell;
+        s->grid = lj_grid(s, L);
+        rc = ensure_cells(s, s->grid);
         if (rc)
             return bail(rc);
         BAIL_CUDA(dalloc(&s->F_lj, 8 * (size_t)n)); // one 32-byte record per NP
@@ -1306,11 +1338,54 @@ void npsim_destroy(npsim_sim_t sim)
 
 namespace {
 // Queue n_steps steps as graph chunks of at most kChunk steps (no host wait).
+// The LJ cell grid follows the droplet.  With the interface spring on, the NPs
+// stay within about R(t) of the centre; at every step that is a multiple of
+// kRegridPeriod the grid's half-width L is compared with R(t) plus the largest
+// cutoff and the skin, and when that differs from L by more than a quarter
+// (the droplet has shrunk or grown) a new grid replaces the old one: the cell
+// buffers are resized if needed, the lists are rebuilt at the next pass and
+// the step graphs are captured again.  The decision depends on the step count
+// alone, and the steps are cut at those multiples whatever the calls' sizes,
+// so runs stay bit-reproducible (npsim_step(37) = 5 + 16 + 1 + 15 steps).
+constexpr int64_t kRegridPeriod = 1024;
+
+// Only the spring on every NP beyond its equilibrium point (wall 1) keeps the
+// NPs inside R(t); without a spring or with the band-only one they may leave.
+bool follows_droplet(const npsim_sim *s) { return s->cell && s->P.wall == 1; }
+
+int regrid_if_needed(npsim_sim *s)
+{
+    if (!follows_droplet(s) || s->step % kRegridPeriod != 0)
+        return NPSIM_OK;
+    const double t = (double)s->step * s->P.dt;
+    const double R2 = s->P.R0 * s->P.R0 - s->P.k_evap * t;
+    const double R = R2 > 0.0 ? std::sqrt(R2) : 0.0;
+    const double L_want = std::max(R, 1.0) + s->cell_rc + kSkin;
+    const double L = (double)s->grid.L;
+    if (L_want >= 0.75 * L && L_want <= L)
+        return NPSIM_OK;
+    NP_CUDA(cudaStreamSynchronize(s->user)); // nothing of the old grid in flight
+    CellGrid g = lj_grid(s, L_want);
+    int rc = ensure_cells(s, g);
+    if (rc)
+        return rc;
+    s->grid = g;
+    for (auto &e : s->graphs)
+        cudaGraphExecDestroy(e.second);
+    s->graphs.clear();
+    return set_gate(s, 1);
+}
+
 int enqueue_steps(npsim_sim *s, int64_t n_steps)
 {
     int64_t rem = n_steps;
     while (rem > 0) {
-        const int k = (int)std::min<int64_t>(rem, kChunk);
+        int rc0 = regrid_if_needed(s);
+        if (rc0)
+            return rc0;
+        int k = (int)std::min<int64_t>(rem, kChunk);
+        if (follows_droplet(s)) // stop at the next multiple of kRegridPeriod
+            k = (int)std::min<int64_t>(k, kRegridPeriod - s->step % kRegridPeriod);
         cudaGraphExec_t ex = nullptr;
         int rc = get_graph(s, k, &ex);
         if (rc)
@@ -1849,9 +1924,6 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
 {
     if (!s->cell || !h.cell)
         return NPSIM_OK;
-    if (h.grid_cells != s->grid.n_cells) {
-        free_cells(s->cb);
-    }
     CellGrid g{};
     g.dim = h.grid_dim;
     g.n_cells = h.grid_cells;
@@ -1859,11 +1931,9 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
     g.L = h.grid_L;
     g.tb = s->T;
     set_extents(g, s->rlist);
-    if (!s->cb.key) {
-        int rc = alloc_cells(g, s->cb, s->n);
-        if (rc)
-            return rc;
-    }
+    int rc0 = ensure_cells(s, g);
+    if (rc0)
+        return rc0;
     s->grid = g;
     if (h.nbr_cap != s->nl.cap) {
         dfree(s->nl.nbr);

@@ -422,21 +422,24 @@ k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, cons
     // compensated (hi, lo) total.  The first block is read before the count is
     // known (cap >= 4 entries exist for every slot).  Entries are
     // slot << 3 | type (slot <= n < 2^29).
+    // The lists stream through once per step: they are read with the
+    // evict-first (streaming) policy so that they do not push the partner
+    // records out of L1 and L2.
     const uint4 *nb4 = reinterpret_cast<const uint4 *>(nbr);
     const uint4 far4 = make_uint4((unsigned)n << 3, (unsigned)n << 3, (unsigned)n << 3,
                                   (unsigned)n << 3);
-    uint4 cur = nb4[p];
+    uint4 cur = __ldcs(nb4 + p);
     const int cnt = nnbr[p];
     if (cnt <= cap) {
         const int nblk = (cnt + 3) >> 2;
-        uint4 nxt = nblk > 1 ? nb4[(size_t)n + p] : far4;
+        uint4 nxt = nblk > 1 ? __ldcs(nb4 + (size_t)n + p) : far4;
         float4 pj[4];
         pj[0] = sxq[cur.x >> 3];
         pj[1] = sxq[cur.y >> 3];
         pj[2] = sxq[cur.z >> 3];
         pj[3] = sxq[cur.w >> 3];
         for (int j = 0; j < nblk; ++j) {
-            const uint4 nn = j + 2 < nblk ? nb4[(size_t)(j + 2) * n + p] : far4;
+            const uint4 nn = j + 2 < nblk ? __ldcs(nb4 + (size_t)(j + 2) * n + p) : far4;
             float4 pn[4];
             if (j + 1 < nblk) {
                 pn[0] = sxq[nxt.x >> 3];

@@ -691,3 +691,30 @@ def test_nonfinite_position_is_reported(P):
         with pytest.raises(P.NpsimError) as e:
             sim.step(2)
         assert e.value.code == -3
+
+
+def test_cell_grid_follows_the_shrinking_droplet(P):
+    """The droplet of config 1 shrinks from R = 30 to 20: at step 1024 the cell
+    grid (sized at creation for R0) is more than a quarter too wide and is
+    replaced by one sized for R(t).  After the regrid the LJ forces still equal
+    the oracle's at the same float32 positions, and the steps are cut at the
+    regrid period whatever the calls' sizes, so 1500 steps in one call equal
+    700 + 800 bit for bit."""
+    sc = wl.config1()
+    types, x, v = wl.initial_state(sc)
+    with P.Sim(sc, x, v, types) as a:
+        dim0, _ = a.cell_grid()
+        a.step(1500)
+        dim1, _ = a.cell_grid()
+        xa, va, _, st = a.state()
+        F = a.forces(2)
+        xh = _hi_words(P, a, sc.n)
+    assert st == 1500 and dim1 < dim0
+    ref = _oracle_pair(sc, xh, types, coul=False)
+    amb = cutoff_ambiguous(xh, types, sc)
+    assert force_error(F, ref)[~amb].max() <= FORCE_TOL
+    with P.Sim(sc, x, v, types) as b:
+        b.step(700)
+        b.step(800)
+        xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
