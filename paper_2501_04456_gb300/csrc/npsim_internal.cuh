@@ -544,7 +544,13 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
                                                float &fy, float &fz)
 {
     fx = fy = fz = 0.0f;
-    if (wall) {
+    // the spring acts only beyond R_eff (s > 0): an NP whose float32 |x|^2 from
+    // the hi words lies below (R_eff - 0.01)^2 is certainly inside (the lo words
+    // and the rounding of that sum move |x| by far less than 0.01), so the
+    // exact distance is formed only near the surface
+    const float reff_in = spring.z - 0.01f;
+    const float r2_cheap = __fmaf_rn(xh.x, xh.x, __fmaf_rn(xh.y, xh.y, __fmul_rn(xh.z, xh.z)));
+    if (wall && !(reff_in > 0.0f && r2_cheap < reff_in * reff_in)) {
         float r2h = 0.0f, r2l = 0.0f;
         const float hh[3] = {xh.x, xh.y, xh.z}, ll[3] = {lx, ly, lz};
 #pragma unroll
@@ -774,13 +780,15 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
         normals3(seed, noise_idx, step, 0u, nz[0], nz[1], nz[2]);
         float xhi[3] = {xh.x, xh.y, xh.z}, xlo[3] = {lx, ly, lz};
         if (baoab) {
+            // the two A half steps around the O step add dt/2 (v' + v'') to the
+            // position (the O step does not depend on x): one compensated add
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 v[d] = __fmaf_rn(tc.hdt_m, f[d], v[d]);               // B
-                df_add(xhi[d], xlo[d], __fmul_rn(hdt, v[d]));         // A
+                const float va = v[d];                                // A (first half)
                 v[d] = __fmaf_rn(tc.c1f, v[d],
                                  __fmaf_rn(tc.c1lo, v[d], __fmul_rn(tc.sd_of, nz[d]))); // O
-                df_add(xhi[d], xlo[d], __fmul_rn(hdt, v[d]));         // A
+                df_add(xhi[d], xlo[d], __fmul_rn(hdt, __fadd_rn(va, v[d]))); // A + A
             }
         } else if (integrator == 1) {
 #pragma unroll
