@@ -345,8 +345,11 @@ k_nbr_build(const __grid_constant__ CellGrid g, const int *__restrict__ start, c
                 }
             }
         }
-        // pad the last block with the far record (whole blocks of four partners)
-        for (int k = cnt; k < cap && (k & 3); ++k)
+        // pad the last block with the far record (whole blocks of four
+        // partners); an empty list gets one block of it, so that the first
+        // block, which the force kernel reads before the count, always names
+        // valid records
+        for (int k = cnt; k < cap && (k < 4 || (k & 3)); ++k)
             nbr[nbr_index(k, p, n)] = (unsigned)n << 3;
         nnbr[p] = cnt;
         if (cnt > cap)

@@ -156,3 +156,13 @@ def test_ensemble_stats_match_oracle(P, drops):
         if np.isfinite(Dfb):
             assert st["Df_box"] == pytest.approx(Dfb, rel=1e-10)
         assert st["n_surf"] == oracle.surface_count(xg, types, sig, st["R"])
+
+
+def test_ensemble_stats_rejects_a_bad_droplet_index(P, drops):
+    with P.Ensemble(drops[:2]) as ens:
+        for d in (-1, 2):
+            with pytest.raises(P.NpsimError) as e:
+                ens.stats(d, r_max=8.0, n_bins=16)
+            assert e.value.code == -1  # NPSIM_ERR_INVALID_ARG
+        with pytest.raises(P.NpsimError):
+            ens.stats(0, r_max=-1.0, n_bins=16)  # bins need a positive range

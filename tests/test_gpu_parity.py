@@ -343,12 +343,17 @@ def test_chunking_and_runs_are_bit_identical(P):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(Fa, Fb)
 
 
-@pytest.mark.parametrize("which", ["lj_allpairs", "cell_list", "printed_cell"])
+@pytest.mark.parametrize("which", ["lj_allpairs", "cell_list", "printed_cell", "full_sum"])
 def test_checkpoint_resume_is_bit_exact(P, tmp_path, which):
     # the cell-list case carries neighbour lists (and their rebuilds) across the
-    # checkpoint: kT = 4 makes the NPs fast enough to rebuild several times
+    # checkpoint: kT = 4 makes the NPs fast enough to rebuild several times;
+    # full_sum: the Coulomb sum over all pairs (sum_neutral) travels with the
+    # file (resumed with the default neutral elision, the summation order and
+    # so the bits would differ)
     sc = (small(wl.config2(), 1500) if which == "lj_allpairs"
           else with_(small(wl.config3(), 3000), kT=4.0))
+    if which == "full_sum":
+        sc = with_(sc, sum_neutral=True)
     if which == "printed_cell":  # the printed variants' parameters travel with the file
         sc = with_(sc, coulomb_cut=4.0, integrator=2, v_kick=0.05, wall_band=True)
     types, x, v = wl.initial_state(sc)
