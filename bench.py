@@ -240,13 +240,20 @@ def _peaks():
 
 def kernel_source_hash(packed):
     """sha256[:16] of the all-pairs kernel source a launch shape runs (its .cu file
-    followed by the shared device header)."""
+    followed by the shared device header), comments and blank lines left out so
+    that only code changes count."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2501_04456_gb300", "csrc")
     name = "allpairs_grouped.cu" if packed in (2, 3) else "allpairs.cu"
-    src = b"".join(open(os.path.join(csrc, f), "rb").read()
-                   for f in (name, "npsim_internal.cuh"))
-    return hashlib.sha256(src).hexdigest()[:16]
+    code = []
+    for f in (name, "npsim_internal.cuh"):
+        txt = open(os.path.join(csrc, f), encoding="utf-8").read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)  # block comments
+        for ln in txt.splitlines():
+            ln = ln.split("//", 1)[0].rstrip()
+            if ln.strip():
+                code.append(ln)
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def _traffic_from_profile(cfg, full_sum):

@@ -18,9 +18,10 @@
 //    took <256,4,256> from 22.2 to 20.3 ms; with one row per thread the
 //    registers of a fourfold unroll would halve the CTAs per SM.
 //    The result is the field sum_j q_j r_ij / r^3 (the integrator multiplies
-//    by C q_i).  Neutral types form the last groups; with `skip neutral` the
-//    caller limits rows and columns to the charged groups, since every
-//    Coulomb term with a neutral particle is exactly zero.
+//    by C q_i).  Neutral types form the last groups; unless the caller asks
+//    for the sum over all pairs (sum_neutral), it limits rows and columns to
+//    the charged groups, since every Coulomb term with a neutral particle is
+//    exactly zero.
 //  * k_ljc_grp (LJ + Coulomb): the type-pair constants of a row and a tile are
 //    loaded once per tile (ljc_tile_sweep); the result is the force.
 //

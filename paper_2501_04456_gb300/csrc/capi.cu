@@ -666,7 +666,9 @@ int read_flags(npsim_sim *s)
 }
 
 // Pick the all-pairs launch shape (and, for the grouped kernels, the ranges
-// per CTA): time each candidate on the current positions.
+// per CTA): time each candidate on the current positions, together with the
+// integrator's sum over its partial slots (more ranges mean more slots per
+// row: the all-pairs launch can gain less than the sum loses).
 int autotune(npsim_sim *s)
 {
     const bool lj = s->ap_lj;
@@ -713,8 +715,10 @@ int autotune(npsim_sim *s)
             shape_streamk(s, c, occ * s->sms, kRangesPerCta[n_m - 1], sk);
             need = std::max(need, slots_floats(sk));
         }
+        const size_t out_floats = 6 * (size_t)std::max(s->n, s->grp_len);
         float *tmp = nullptr;
-        NP_CUDA(dalloc(&tmp, need));
+        NP_CUDA(dalloc(&tmp, need + out_floats));
+        float *sum_out = tmp + need;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -731,12 +735,16 @@ int autotune(npsim_sim *s)
                 shape_streamk(s, c, occ * s->sms, m, sk);
                 if (shape_grouped(c) && mi > 0 && sk.grid == sk.ctas)
                     break; // no more ranges than CTAs: the same launch as m = 1
-                if (shape_launch(s, c, lj, coul, sk, tmp, s->user) != cudaSuccess)
+                const int n_pos = shape_grouped(c) ? s->grp_len : s->n;
+                if (shape_launch(s, c, lj, coul, sk, tmp, s->user) != cudaSuccess ||
+                    launch_slot_sum(tmp, sk, n_pos, sum_out, s->user) != cudaSuccess)
                     continue;
                 const int reps = s->n > 100000 ? 2 : 5;
                 cudaEventRecord(e0, s->user);
-                for (int r = 0; r < reps; ++r)
+                for (int r = 0; r < reps; ++r) {
                     shape_launch(s, c, lj, coul, sk, tmp, s->user);
+                    launch_slot_sum(tmp, sk, n_pos, sum_out, s->user);
+                }
                 cudaEventRecord(e1, s->user);
                 if (cudaEventSynchronize(e1) != cudaSuccess)
                     continue;

@@ -40,6 +40,40 @@ namespace npsim {
 
 namespace {
 
+// Add the all-pairs partial slots of position `pos` (row pos / itile of the
+// stream-K order) into (Fh, Fl): the ranges that met the row, in range order.
+// Four ranges per pass, their twelve loads issued before the adds.
+__device__ __forceinline__ void sum_row_slots(const float *__restrict__ slots,
+                                              const StreamK &sk, int pos, float Fh[3],
+                                              float Fl[3])
+{
+    const int r = pos / sk.itile;
+    const int idx = pos - r * sk.itile;
+    const long long u0 = (long long)r * sk.n_jt;
+    const int c0 = sk_cta_of(sk, u0);
+    const int c1 = sk_cta_of(sk, u0 + sk.n_jt - 1);
+    const size_t stride = 6 * (size_t)sk.itile; // floats per slot
+    const float *slot = slots + (size_t)(r + c0) * stride + idx;
+    int c = c0;
+    for (; c + 3 <= c1; c += 4, slot += 4 * stride) {
+        float w[4][6];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 0; e < 6; ++e)
+                w[k][e] = __ldcs(slot + k * stride + e * sk.itile);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                df_add_df(Fh[d], Fl[d], w[k][d], w[k][3 + d]);
+    }
+    for (; c <= c1; ++c, slot += stride)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            df_add_df(Fh[d], Fl[d], __ldcs(slot + d * sk.itile), __ldcs(slot + (3 + d) * sk.itile));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256, 5)
 k_integrate(IntArgs a, StepParams p)
@@ -99,20 +133,11 @@ k_integrate(IntArgs a, StepParams p)
         const TypeCoef &tc = s_tc[ti];
         float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
         if (ASSEMBLE) {
+            bool any = false; // some force term is in (Fh, Fl) already
             const int pos = a.row_pos ? a.row_pos[i] : i;
             if (a.slots && pos >= 0) {
-                const StreamK &sk = a.sk;
-                const int r = pos / sk.itile;
-                const int idx = pos - r * sk.itile;
-                const long long u0 = (long long)r * sk.n_jt;
-                const int c0 = sk_cta_of(sk, u0);
-                const int c1 = sk_cta_of(sk, u0 + sk.n_jt - 1);
-                for (int c = c0; c <= c1; ++c) {
-                    const float *slot = a.slots + (size_t)(r + c) * 6 * sk.itile + idx;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        df_add_df(Fh[d], Fl[d], slot[d * sk.itile], slot[(3 + d) * sk.itile]);
-                }
+                any = true;
+                sum_row_slots(a.slots, a.sk, pos, Fh, Fl);
                 if (a.field_slots) { // the Coulomb-only kernels return sum_j q_j r_ij / r^3
 #pragma unroll
                     for (int d = 0; d < 3; ++d)
@@ -120,6 +145,7 @@ k_integrate(IntArgs a, StepParams p)
                 }
             }
             if (a.F_lj) {
+                any = true;
                 df_add_df(Fh[0], Fl[0], flj0.x, flj0.w);
                 df_add_df(Fh[1], Fl[1], flj0.y, flj1.x);
                 df_add_df(Fh[2], Fl[2], flj0.z, flj1.y);
@@ -128,9 +154,15 @@ k_integrate(IntArgs a, StepParams p)
                 float ex, ey, ez;
                 external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, spring[ti], p.wall,
                                p.rot_mode, ex, ey, ez);
-                df_add(Fh[0], Fl[0], ex);
-                df_add(Fh[1], Fl[1], ey);
-                df_add(Fh[2], Fl[2], ez);
+                if (any) {
+                    df_add(Fh[0], Fl[0], ex);
+                    df_add(Fh[1], Fl[1], ey);
+                    df_add(Fh[2], Fl[2], ez);
+                } else { // the first term: (x, 0), as the compensated add into zero gives
+                    Fh[0] = ex;
+                    Fh[1] = ey;
+                    Fh[2] = ez;
+                }
             }
         } else {
 #pragma unroll
@@ -205,6 +237,24 @@ __global__ void k_state_aos(const float4 *__restrict__ xq, const float *__restri
     }
 }
 
+// The integrator's read of the all-pairs partial slots on its own (the
+// autotuner charges it to each launch shape): position p's sum to
+// out[d * n_pos + p] (hi) and out[(3 + d) * n_pos + p] (lo).
+__global__ void k_slot_sum(const float *__restrict__ slots, StreamK sk, int n_pos,
+                           float *__restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pos)
+        return;
+    float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
+    sum_row_slots(slots, sk, p, Fh, Fl);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        out[d * (size_t)n_pos + p] = Fh[d];
+        out[(3 + d) * (size_t)n_pos + p] = Fl[d];
+    }
+}
+
 } // namespace
 
 cudaError_t launch_state_aos(const float4 *xq, const float *x_lo, const float *v, const float *F,
@@ -235,6 +285,15 @@ cudaError_t launch_positions_f64_ld(const float4 *xq, const float *x_lo, int n, 
                                     double *x, cudaStream_t st)
 {
     k_positions_f64<<<(n + 255) / 256, 256, 0, st>>>(xq, x_lo, n, ld, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_sum(const float *slots, const StreamK &sk, int n_pos, float *out,
+                            cudaStream_t st)
+{
+    if (n_pos <= 0)
+        return cudaSuccess;
+    k_slot_sum<<<(n_pos + 255) / 256, 256, 0, st>>>(slots, sk, n_pos, out);
     return cudaGetLastError();
 }
 

@@ -828,6 +828,11 @@ __device__ __forceinline__ void advance_particle(int i, int n, uint32_t noise_id
 
 cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
                              cudaStream_t st);
+// The integrator's sum of the all-pairs partial slots alone, for positions
+// 0 .. n_pos - 1 of the stream-K order, to out (6 n_pos floats: hi x, y, z,
+// lo x, y, z planes).
+cudaError_t launch_slot_sum(const float *slots, const StreamK &sk, int n_pos, float *out,
+                            cudaStream_t st);
 
 // Ensemble of droplets (ensemble.cu).  Each droplet's particles are listed in a
 // type-grouped order (groups padded to 256 positions) at positions [gpos0,
