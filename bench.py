@@ -476,8 +476,10 @@ def _dense_lj_state(P, stream, n_copy=65536, copies=4, compress_steps=20000, see
     T = np.tile(types, len(offs))
     perm = np.random.default_rng(seed + 1).permutation(len(X))
     X, T = X[perm], T[perm].astype(np.int32)
-    R_all = float(np.linalg.norm(X, axis=1).max()) + 10.0
-    held = dataclasses.replace(sc, n=len(X), R0=R_all, k_evap=0.0, wall=False,
+    # with the wall off R0 only bounds the cell grid's half-width from below:
+    # the copies' bounding cube (the grid is a cube)
+    R_box = float(np.abs(X).max()) + 1.0
+    held = dataclasses.replace(sc, n=len(X), R0=R_box, k_evap=0.0, wall=False,
                                name=f"dense_lj{len(X)}")
     return held, X, T, phi
 

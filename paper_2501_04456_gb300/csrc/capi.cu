@@ -477,12 +477,13 @@ cudaError_t shape_launch(const npsim_sim *s, int k, bool lj, bool coul, const St
                            slots, st);
 }
 
-// Queue the pair forces of the current positions and one integrator pass.
-// Kernel groups timed by npsim_kernel_times.
+// Queue the pair forces of the current positions and one integrator pass at
+// step (device counter) + step_ofs; step_commit: this pass ends a chunk of
+// steps and moves the counter on.  Kernel groups timed by npsim_kernel_times.
 enum { KG_ALLPAIRS = 0, KG_CELL_BUILD = 1, KG_CELL_LJ = 2, KG_INTEGRATE = 3 };
 
 int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext, float *Fout,
-                 cudaStream_t st, int prof_slot = -1)
+                 cudaStream_t st, int prof_slot = -1, int step_ofs = 0, bool step_commit = false)
 {
     const bool ap_lj = want_lj && s->P.lj_mode == 1;
     // with the neutral NPs left out and no type charged, the grouped Coulomb
@@ -543,6 +544,8 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     a.nbr_gate = s->d_gate;
     a.half_skin2 = kHalfSkin2;
     a.step = s->d_step;
+    a.step_ofs = step_ofs;
+    a.step_commit = step_commit ? 1 : 0;
     a.flags = s->d_flags;
     a.done = s->d_done;
     NP_CUDA(mark(KG_INTEGRATE, 0));
@@ -551,6 +554,9 @@ int enqueue_pass(npsim_sim *s, int mode, bool want_lj, bool want_coul, bool ext,
     return NPSIM_OK;
 }
 
+// Queue k >= 1 steps from the step in the device counter: A, (pairs, BA) x
+// (k - 1), pairs, B; the launches carry their offsets from the counter, and
+// the last one moves it on by k.
 int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
 {
     IntArgs a{};
@@ -566,12 +572,16 @@ int enqueue_chunk(npsim_sim *s, int k, cudaStream_t st)
     a.cell_pos = s->cell ? s->cb.pos : nullptr;
     a.nbr_gate = s->d_gate;
     a.half_skin2 = kHalfSkin2;
-    a.step = s->d_step;
+    a.step = s->d_step; // the chunk's first step; launch j + 1 below is at step + j + 1
+    a.step_ofs = 0;
+    a.step_commit = 0;
     a.flags = s->d_flags;
     a.done = s->d_done;
     NP_CUDA(launch_integrate(MODE_A, a, s->sp, st));
     for (int j = 0; j < k; ++j) {
-        int rc = enqueue_pass(s, j + 1 < k ? MODE_BA : MODE_B, true, true, true, s->F, st, j);
+        // the last pass (B at step + k) moves the counter on to step + k
+        int rc = enqueue_pass(s, j + 1 < k ? MODE_BA : MODE_B, true, true, true, s->F, st, j,
+                              j + 1, j + 1 == k);
         if (rc)
             return rc;
     }

@@ -22,7 +22,7 @@
 // interface distance |x| - (R - sigma/2), a difference of two nearly equal
 // numbers, is formed from |x|^2 - R_eff^2 (see external_force); R(t) and
 // R_eff^2 come from a per-type table evaluated once per step in float64 (by
-// the first CTA of the launch that advances the step, for the next step).
+// the first CTA of each launch that takes the A part, for the next step).
 //
 // One kernel serves four modes (see IntMode): it sums the stream-K partials of
 // the all-pairs kernel (and the list forces: LJ, and the truncated Coulomb term
@@ -30,10 +30,12 @@
 // t = step*dt, and applies the B half kick and/or the BAOA part of the next
 // step (or the overdamped step, or step (vi) as printed).  The step counter
 // lives in device memory so that a captured CUDA graph replays without
-// parameter updates: thread 0 of every CTA reads it into shared memory before
-// the CTA's one barrier and counts the CTA in right after, so the CTA that
-// counts last -- every CTA has the step by then -- advances it, and threads
-// then run to completion without waiting for one another.
+// parameter updates.  It holds the first step of the current chunk of steps
+// and no launch of the chunk changes it but the last: a launch's step is the
+// counter plus its offset within the chunk (a launch parameter), read by every
+// thread together with its state, with no barrier in between.  The chunk's
+// last launch counts its CTAs in once each has finished with the step, and
+// the CTA that counts last moves the counter on to the next chunk.
 #include "npsim_internal.cuh"
 
 namespace npsim {
@@ -79,13 +81,13 @@ __global__ void __launch_bounds__(256, 5)
 k_integrate(IntArgs a, StepParams p)
 {
     __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
-    __shared__ long long s_step;
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
     const int n = p.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    // this thread's state first: its loads do not depend on the step, so they
-    // are in flight while the CTA waits for the counter at the barrier
+    // positions are x_step at t = step * dt; the counter is read with this
+    // thread's state, all of it in flight at once
+    const long long step = *a.step + a.step_ofs;
     int ti = 0;
     float4 xh = make_float4(0.f, 0.f, 0.f, 0.f);
     float lx = 0.f, ly = 0.f, lz = 0.f;
@@ -108,21 +110,9 @@ k_integrate(IntArgs a, StepParams p)
             flj1 = r[1]; // (ly, lz, -, -)
         }
     }
-    if (threadIdx.x == 0)
-        s_step = *a.step;
     if (threadIdx.x < NPSIM_MAX_TYPES)
         s_tc[threadIdx.x] = p.tc[threadIdx.x];
     __syncthreads();
-    const long long step = s_step; // positions are x_step at t = step * dt
-    if (DO_A && threadIdx.x == 0) { // this CTA has the step: count it in
-        __threadfence();
-        const unsigned prev = atomicAdd(a.done, 1u);
-        if (prev == gridDim.x - 1) { // the last: advance the step
-            *a.step = step + 1;
-            *a.done = 0u;
-            __threadfence();
-        }
-    }
     if (DO_A && blockIdx.x == 0 && threadIdx.x < p.n_types) // spring radius of step + 1
         a.spring[((step + 1) & 1) * NPSIM_MAX_TYPES + threadIdx.x] =
             spring_entry(p.R0, p.k_evap, p.dt, step + 1, p.tc[threadIdx.x].half_sigma);
@@ -176,6 +166,20 @@ k_integrate(IntArgs a, StepParams p)
                                step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq,
                                a.flags, a.x_ref, a.nbr_gate, a.half_skin2, a.sxq, a.cell_pos,
                                ti);
+    }
+    if (a.step_commit) {
+        // the chunk's last launch: once every thread of the CTA is past its use
+        // of the step, count the CTA in; the last one sets the counter to the
+        // first step of the next chunk
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(a.done, 1u) == gridDim.x - 1) {
+                *a.step = DO_A ? step + 1 : step;
+                *a.done = 0u;
+                __threadfence();
+            }
+        }
     }
 }
 

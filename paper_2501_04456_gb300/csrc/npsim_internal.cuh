@@ -43,7 +43,7 @@ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
 
 // Three standard normals of particle i at step `step` (counter (i, step_lo,
 // step_hi, purpose), key = seed).  Uniforms u = (k + 1/2) 2^-32, rounded to
-// float; Box-Muller in float32 with the accurate logf / sincospif.
+// float; Box-Muller in float32 with the accurate logf, sincospif and cospif.
 __device__ __forceinline__ void normals3(uint64_t seed, uint32_t i, int64_t step,
                                          uint32_t purpose, float &n0, float &n1, float &n2)
 {
@@ -57,9 +57,9 @@ __device__ __forceinline__ void normals3(uint64_t seed, uint32_t i, int64_t step
     float u3 = fmaf(__uint2float_rn(r.w), sc, 0.5f * sc);
     float rho1 = sqrtf(-2.0f * logf(u0));
     float rho2 = sqrtf(-2.0f * logf(u2));
-    float s1, c1, s3, c3;
+    float s1, c1;
     sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s3, &c3);
+    const float c3 = cospif(2.0f * u3); // the sine of this angle is not used
     n0 = rho1 * c1;
     n1 = rho1 * s1;
     n2 = rho2 * c3;
@@ -732,9 +732,13 @@ struct IntArgs {
                              // the other one for step + 1
     int ext_on;              // add external forces
     int field_slots;         // slots hold sum_j q_j r_ij/r^3 (Coulomb-only kernel): scale by C q_i
-    long long *step;         // device step counter
+    long long *step;         // device step counter: the first step of the current chunk
+    int step_ofs;            // this launch's step = *step + step_ofs
+    int step_commit;         // last launch of a chunk: set *step to this launch's step
+                             // (+ 1 in the modes that take the A part) once every CTA
+                             // has read it
     int *flags;
-    unsigned *done;          // last-block counter
+    unsigned *done;          // CTAs counted in by the committing launch (zero between)
 };
 
 // One particle's update after its force (Fh + Fl) has been assembled: store F
