@@ -117,8 +117,8 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
             v[2] = a.v[2 * n_total + i];
         }
     }
-    // the step counter as in k_integrate: read by thread 0 before the CTA's
-    // one barrier, the CTA counted in right after, the last one advances it
+    // the device step counter: read by thread 0 before the CTA's one barrier,
+    // the CTA counted in right after, and the last CTA to count advances it
     __shared__ long long s_step;
     if (threadIdx.x == 0)
         s_step = *a.step;
