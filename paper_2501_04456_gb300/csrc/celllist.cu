@@ -275,9 +275,10 @@ __device__ __forceinline__ void load_tables(const PairTab *__restrict__ tab,
 // Neighbour lists (gated): for the NP at cell-order slot p (threads in the cell
 // order, so that a warp scans the same cells), the partners within
 // (rc_ab + skin) in the 27 cells, type block by type block in scan order, as
-// (slot << 3 | type) (unsigned: a slot below 2^29 fits), column-major
-// nbr[k * n + p] for k < cap; nnbr[p] = the full count (an NP with more than
-// cap partners is summed from the cells instead).  Lists are written by slot
+// their cell-order slots (the partner's type is the fourth word of its
+// record), in blocks of four at nbr[nbr_index(k, p, n)] for k < cap;
+// nnbr[p] = the full count (an NP with more than cap partners is summed from
+// the cells instead).  Lists are written by slot
 // so that the per-step force kernel, which runs in the same order, reads them
 // coalesced.  Records the positions of this build in x_ref (by particle).
 __global__ void __launch_bounds__(128, 8)
@@ -338,7 +339,7 @@ k_nbr_build(const __grid_constant__ CellGrid g, const int *__restrict__ start, c
                         const int tj = __float_as_int(pj.w);
                         if (tb > 1 || r2 < s_rl2[row + tj]) {
                             if (cnt < cap)
-                                nbr[nbr_index(cnt, p, n)] = ((unsigned)q << 3) | (unsigned)tj;
+                                nbr[nbr_index(cnt, p, n)] = (unsigned)q;
                             ++cnt;
                         }
                     }
@@ -350,7 +351,7 @@ k_nbr_build(const __grid_constant__ CellGrid g, const int *__restrict__ start, c
         // block, which the force kernel reads before the count, always names
         // valid records
         for (int k = cnt; k < cap && (k < 4 || (k & 3)); ++k)
-            nbr[nbr_index(k, p, n)] = (unsigned)n << 3;
+            nbr[nbr_index(k, p, n)] = (unsigned)n;
         nnbr[p] = cnt;
         if (cnt > cap)
             atomicOr(flags, FLAG_NBR_OVERFLOW);
@@ -358,34 +359,87 @@ k_nbr_build(const __grid_constant__ CellGrid g, const int *__restrict__ start, c
     }
 }
 
-// LJ forces (and, with rcc2, the truncated Coulomb term) from the neighbour
-// lists at the current positions, one thread per cell-order slot p: the NP's
-// own record sxq[p] (kept current by the integrator), its list column and its
-// partners' records are read in cell order -- coalesced, and for the partners
-// from the nearby cells -- and the 32-byte force record goes to the NP's index
-// i = sorted[p], where the integrator reads it.  An NP whose list overflowed
-// sums over the 27 cells of that build instead (a superset of its list).
-// Writes one 32-byte (hi x, y, z, lo x, y, z, 0, 0) record per NP and closes
-// the rebuild gate.  8 CTAs of 128 per SM (64 registers: each thread keeps
-// two blocks of partner records and entries in flight).
+// The forces of the NP at slot p whose list overflowed: every NP of the cells of
+// its build (the NP's sort key holds its build cell; a superset of its list),
+// summed pair by pair into the compensated totals.  Kept out of line so that
+// it takes no registers from the list loops.
 template <bool COUL>
-__global__ void __launch_bounds__(128, 8)
-k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
-         const int *__restrict__ key, const float4 *__restrict__ sxq, int n,
-         const PairTab *__restrict__ tab, const float *__restrict__ rcc2, int cap,
-         const unsigned *__restrict__ nbr, const int *__restrict__ nnbr,
-         float *__restrict__ F_lj, int *__restrict__ gate)
+__device__ __noinline__ void cell_slot_forces(int p, const CellGrid g, const int *__restrict__ start,
+                                              const int *__restrict__ sorted,
+                                              const int *__restrict__ key,
+                                              const float4 *__restrict__ sxq,
+                                              float *__restrict__ F_lj, const float4 *s_tab,
+                                              const float *s_rcc2)
 {
-    __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
-    __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
-    __shared__ float s_rcc2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
-    __shared__ float s_rmax[NPSIM_MAX_TYPES];
-    load_tables(tab, COUL ? rcc2 : nullptr, 0.0f, s_tab, s_rl2, s_rmax, s_rcc2);
-    if (gate && blockIdx.x == 0 && threadIdx.x == 0)
-        *gate = 0; // every build kernel of this step has run; the integrator may reopen it
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
-        return;
+    const float4 pi = sxq[p];
+    const int i = sorted[p];
+    const int ti = __float_as_int(pi.w);
+    const int row = ti * NPSIM_MAX_TYPES;
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    const int tb = g.tb > 1 ? g.tb : 1;
+    const int c = key[i] - (g.tb > 1 ? ti * g.n_cells : 0);
+    const int cx = c % g.dim, cy = (c / g.dim) % g.dim, cz = c / (g.dim * g.dim);
+    for (int t = 0; t < tb; ++t) {
+        const int kofs = t * g.n_cells;
+        int w = g.ext[row + t];
+        if (tb == 1)
+            for (int b = 1; b < NPSIM_MAX_TYPES; ++b)
+                w = max(w, (int)g.ext[row + b]);
+        for (int dz = -w; dz <= w; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= g.dim)
+                continue;
+            for (int dy = -w; dy <= w; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= g.dim)
+                    continue;
+                const int base = kofs + (z * g.dim + y) * g.dim;
+                const int b = start[base + max(cx - w, 0)];
+                const int e = start[base + min(cx + w, g.dim - 1) + 1];
+                for (int q = b; q < e; ++q)
+                    if (q != p) {
+                        const float4 pj = sxq[q];
+                        const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
+                        const int tj = __float_as_int(pj.w);
+                        const float4 tt = s_tab[row + tj];
+                        const float ri = rsqrtf(r2);
+                        const float rinv2 = ri * ri;
+                        const float s2 = tt.x * rinv2;
+                        const float s6 = s2 * s2 * s2;
+                        float f = r2 < tt.z ? tt.y * rinv2 * s6 * fmaf(2.0f, s6, -1.0f) : 0.0f;
+                        if (COUL && r2 < s_rcc2[row + tj])
+                            f = fmaf(tt.w * ri, rinv2, f);
+                        two_sum_acc(hx, lx, f * dx);
+                        two_sum_acc(hy, ly, f * dy2);
+                        two_sum_acc(hz, lz, f * dz2);
+                    }
+            }
+        }
+    }
+    float4 *o = reinterpret_cast<float4 *>(F_lj + 8 * (size_t)i);
+    o[0] = make_float4(hx, hy, hz, lx);
+    o[1] = make_float4(ly, lz, 0.0f, 0.0f);
+}
+
+// LJ forces (and, with rcc2, the truncated Coulomb term) from the neighbour
+// lists at the current positions for the NP at cell-order slot p: its own
+// record sxq[p] (kept current by the integrator), its list column and its
+// partners' records are read in cell order -- coalesced over consecutive
+// slots, and for the partners from the nearby cells -- and the 32-byte force
+// record goes to the NP's index i = sorted[p], where the integrator reads it.
+// An NP whose list overflowed sums over the cells of that build instead (a
+// superset of its list).  Writes one (hi x, y, z, lo x, y, z, 0, 0) record.
+template <bool COUL>
+__device__ __forceinline__ void slot_forces(int p, const CellGrid &g, const int *__restrict__ start,
+                                            const int *__restrict__ sorted,
+                                            const int *__restrict__ key,
+                                            const float4 *__restrict__ sxq, int n, int cap,
+                                            const unsigned *__restrict__ nbr,
+                                            const int *__restrict__ nnbr,
+                                            float *__restrict__ F_lj, const float4 *s_tab,
+                                            const float *s_rcc2)
+{
     const float4 pi = sxq[p];
     const int i = sorted[p];
     const int ti = __float_as_int(pi.w);
@@ -394,9 +448,10 @@ k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, cons
     // One pair's force added into (sx, sy, sz); 1/r^2 as rsqrt(r^2)^2, as in
     // the all-pairs kernels.  The block sums go into the compensated (hi, lo)
     // totals by flush(), once per block of up to four partners.
-    auto pair = [&](const float4 pj, int tj, float &sx, float &sy, float &sz) {
+    auto pair = [&](const float4 pj, float &sx, float &sy, float &sz) {
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const int tj = __float_as_int(pj.w);
         const float4 t = s_tab[row + tj];
         const float ri = rsqrtf(r2);
         const float rinv2 = ri * ri;
@@ -416,45 +471,48 @@ k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, cons
         two_sum_acc(hz, lz, sz);
     };
     // List entries arrive four at a time (one 16-byte load per block of four,
-    // contiguous over the warp), two blocks ahead of their use, and a block's
-    // partner records are gathered one block ahead, so that each thread keeps
-    // the next block's gathers and the entries after it in flight while it
-    // computes.  A list's last block is padded with the far record, whose terms
-    // are exactly zero, so every block is four whole pairs.  Pairs are summed
-    // in list order, each block of four in float32 and then into the
+    // contiguous over consecutive slots), two blocks ahead of their use, and a
+    // block's partner records are gathered one block ahead, so that each thread
+    // keeps the next block's gathers and the entries after it in flight while
+    // it computes.  A list's last block is padded with the far record, whose
+    // terms are exactly zero, so every block is four whole pairs.  Pairs are
+    // summed in list order, each block of four in float32 and then into the
     // compensated (hi, lo) total.  The first block is read before the count is
-    // known (cap >= 4 entries exist for every slot).  Entries are
-    // slot << 3 | type (slot <= n < 2^29).
+    // known (cap >= 4 entries exist for every slot).  Entries are the
+    // partners' slots; a partner's type is the fourth word of its record.
     // The lists stream through once per step: they are read with the
     // evict-first (streaming) policy so that they do not push the partner
     // records out of L1 and L2.
     const uint4 *nb4 = reinterpret_cast<const uint4 *>(nbr);
-    const uint4 far4 = make_uint4((unsigned)n << 3, (unsigned)n << 3, (unsigned)n << 3,
-                                  (unsigned)n << 3);
+    const uint4 far4 = make_uint4((unsigned)n, (unsigned)n, (unsigned)n, (unsigned)n);
     uint4 cur = __ldcs(nb4 + p);
     const int cnt = nnbr[p];
-    if (cnt <= cap) {
+    if (cnt > cap) {
+        cell_slot_forces<COUL>(p, g, start, sorted, key, sxq, F_lj, s_tab, s_rcc2);
+        return;
+    }
+    {
         const int nblk = (cnt + 3) >> 2;
         uint4 nxt = nblk > 1 ? __ldcs(nb4 + (size_t)n + p) : far4;
         float4 pj[4];
-        pj[0] = sxq[cur.x >> 3];
-        pj[1] = sxq[cur.y >> 3];
-        pj[2] = sxq[cur.z >> 3];
-        pj[3] = sxq[cur.w >> 3];
+        pj[0] = sxq[cur.x];
+        pj[1] = sxq[cur.y];
+        pj[2] = sxq[cur.z];
+        pj[3] = sxq[cur.w];
         for (int j = 0; j < nblk; ++j) {
             const uint4 nn = j + 2 < nblk ? __ldcs(nb4 + (size_t)(j + 2) * n + p) : far4;
             float4 pn[4];
             if (j + 1 < nblk) {
-                pn[0] = sxq[nxt.x >> 3];
-                pn[1] = sxq[nxt.y >> 3];
-                pn[2] = sxq[nxt.z >> 3];
-                pn[3] = sxq[nxt.w >> 3];
+                pn[0] = sxq[nxt.x];
+                pn[1] = sxq[nxt.y];
+                pn[2] = sxq[nxt.z];
+                pn[3] = sxq[nxt.w];
             }
             float sx = 0.f, sy = 0.f, sz = 0.f;
-            pair(pj[0], (int)(cur.x & 7u), sx, sy, sz);
-            pair(pj[1], (int)(cur.y & 7u), sx, sy, sz);
-            pair(pj[2], (int)(cur.z & 7u), sx, sy, sz);
-            pair(pj[3], (int)(cur.w & 7u), sx, sy, sz);
+            pair(pj[0], sx, sy, sz);
+            pair(pj[1], sx, sy, sz);
+            pair(pj[2], sx, sy, sz);
+            pair(pj[3], sx, sy, sz);
             flush(sx, sy, sz);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -462,43 +520,39 @@ k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, cons
             cur = nxt;
             nxt = nn;
         }
-    } else {
-        // cells of the build: the NP's sort key holds its build cell
-        const int tb = g.tb > 1 ? g.tb : 1;
-        const int c = key[i] - (g.tb > 1 ? ti * g.n_cells : 0);
-        const int cx = c % g.dim, cy = (c / g.dim) % g.dim, cz = c / (g.dim * g.dim);
-        for (int t = 0; t < tb; ++t) {
-            const int kofs = t * g.n_cells;
-            int w = g.ext[row + t];
-            if (tb == 1)
-                for (int b = 1; b < NPSIM_MAX_TYPES; ++b)
-                    w = max(w, (int)g.ext[row + b]);
-            for (int dz = -w; dz <= w; ++dz) {
-                const int z = cz + dz;
-                if (z < 0 || z >= g.dim)
-                    continue;
-                for (int dy = -w; dy <= w; ++dy) {
-                    const int y = cy + dy;
-                    if (y < 0 || y >= g.dim)
-                        continue;
-                    const int base = kofs + (z * g.dim + y) * g.dim;
-                    const int b = start[base + max(cx - w, 0)];
-                    const int e = start[base + min(cx + w, g.dim - 1) + 1];
-                    for (int q = b; q < e; ++q)
-                        if (q != p) {
-                            const float4 pj = sxq[q];
-                            float sx = 0.f, sy = 0.f, sz = 0.f;
-                            pair(pj, __float_as_int(pj.w), sx, sy, sz);
-                            flush(sx, sy, sz);
-                        }
-                }
-            }
-        }
     }
     // one 32-byte record per NP, a whole DRAM sector: (hi x, y, z, lo x), (lo y, z)
     float4 *o = reinterpret_cast<float4 *>(F_lj + 8 * (size_t)i);
     o[0] = make_float4(hx, hy, hz, lx);
     o[1] = make_float4(ly, lz, 0.0f, 0.0f);
+}
+
+// List forces, one thread per cell-order slot (slot_forces), and closes the
+// rebuild gate.  The CTAs take the 128-slot tiles from the last one back: the
+// cell order lists the types one after another, so the last tiles hold the
+// largest NPs, whose lists are the longest (several times the mean in a
+// polydisperse aggregate); started first, they no longer run alone at the end
+// of the launch while the short ones fill the tail.  8 CTAs of 128 per SM (64
+// registers: each thread keeps two blocks of partner records and entries in
+// flight).
+template <bool COUL>
+__global__ void __launch_bounds__(128, 8)
+k_lj_nbr(const __grid_constant__ CellGrid g, const int *__restrict__ start, const int *__restrict__ sorted,
+         const int *__restrict__ key, const float4 *__restrict__ sxq, int n,
+         const PairTab *__restrict__ tab, const float *__restrict__ rcc2, int cap,
+         const unsigned *__restrict__ nbr, const int *__restrict__ nnbr,
+         float *__restrict__ F_lj, int *__restrict__ gate)
+{
+    __shared__ float4 s_tab[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rl2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rcc2[NPSIM_MAX_TYPES * NPSIM_MAX_TYPES];
+    __shared__ float s_rmax[NPSIM_MAX_TYPES];
+    load_tables(tab, COUL ? rcc2 : nullptr, 0.0f, s_tab, s_rl2, s_rmax, s_rcc2);
+    if (gate && blockIdx.x == 0 && threadIdx.x == 0)
+        *gate = 0; // every build kernel of this step has run; the integrator may reopen it
+    const int p = (int)(gridDim.x - 1 - blockIdx.x) * (int)blockDim.x + (int)threadIdx.x;
+    if (p < n)
+        slot_forces<COUL>(p, g, start, sorted, key, sxq, n, cap, nbr, nnbr, F_lj, s_tab, s_rcc2);
 }
 
 } // namespace

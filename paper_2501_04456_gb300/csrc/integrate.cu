@@ -76,101 +76,121 @@ __device__ __forceinline__ void sum_row_slots(const float *__restrict__ slots,
             df_add_df(Fh[d], Fl[d], __ldcs(slot + d * sk.itile), __ldcs(slot + (3 + d) * sk.itile));
 }
 
+// The state one particle's update reads: type, position (hi + lo), velocity
+// and the list force record.
+struct PartState {
+    int ti;
+    float4 xh;
+    float lx, ly, lz;
+    float v[3];
+    float4 flj0, flj1;
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(256, 5)
-k_integrate(IntArgs a, StepParams p)
+__device__ __forceinline__ void load_state(const IntArgs &a, int n, int i, PartState &s)
 {
-    __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
     constexpr bool ASSEMBLE = (MODE != MODE_A);
-    constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
+    s.ti = a.typ[i];
+    s.xh = a.xq[i];
+    s.lx = a.x_lo[i];
+    s.ly = a.x_lo[n + i];
+    s.lz = a.x_lo[2 * n + i];
+    if (MODE != MODE_FORCES) {
+        s.v[0] = a.v[i];
+        s.v[1] = a.v[n + i];
+        s.v[2] = a.v[2 * n + i];
+    } else {
+        s.v[0] = s.v[1] = s.v[2] = 0.f;
+    }
+    if (ASSEMBLE && a.F_lj) {
+        const float4 *r = reinterpret_cast<const float4 *>(a.F_lj + 8 * (size_t)i);
+        s.flj0 = r[0]; // (hx, hy, hz, lx)
+        s.flj1 = r[1]; // (ly, lz, -, -)
+    } else {
+        s.flj0 = s.flj1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Assemble particle i's force (partials, list forces, external forces) and
+// apply the mode's part of the step.
+template <int MODE>
+__device__ __forceinline__ void update_particle(const IntArgs &a, const StepParams &p,
+                                                const TypeCoef *s_tc, const float4 *spring,
+                                                long long step, int i, const PartState &st)
+{
+    constexpr bool ASSEMBLE = (MODE != MODE_A);
     const int n = p.n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    // positions are x_step at t = step * dt; the counter is read with this
-    // thread's state, all of it in flight at once
-    const long long step = *a.step + a.step_ofs;
-    int ti = 0;
-    float4 xh = make_float4(0.f, 0.f, 0.f, 0.f);
-    float lx = 0.f, ly = 0.f, lz = 0.f;
-    float v[3] = {0.f, 0.f, 0.f};
-    float4 flj0 = make_float4(0.f, 0.f, 0.f, 0.f), flj1 = flj0;
-    if (i < n) {
-        ti = a.typ[i];
-        xh = a.xq[i];
-        lx = a.x_lo[i];
-        ly = a.x_lo[n + i];
-        lz = a.x_lo[2 * n + i];
-        if (MODE != MODE_FORCES) {
-            v[0] = a.v[i];
-            v[1] = a.v[n + i];
-            v[2] = a.v[2 * n + i];
+    const int ti = st.ti;
+    const TypeCoef &tc = s_tc[ti];
+    float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
+    if (ASSEMBLE) {
+        bool any = false; // some force term is in (Fh, Fl) already
+        const int pos = a.row_pos ? a.row_pos[i] : i;
+        if (a.slots && pos >= 0) {
+            any = true;
+            sum_row_slots(a.slots, a.sk, pos, Fh, Fl);
+            if (a.field_slots) { // the Coulomb-only kernels return sum_j q_j r_ij / r^3
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    df_mul(Fh[d], Fl[d], tc.qc);
+            }
         }
-        if (ASSEMBLE && a.F_lj) {
-            const float4 *r = reinterpret_cast<const float4 *>(a.F_lj + 8 * (size_t)i);
-            flj0 = r[0]; // (hx, hy, hz, lx)
-            flj1 = r[1]; // (ly, lz, -, -)
+        if (a.F_lj) {
+            any = true;
+            df_add_df(Fh[0], Fl[0], st.flj0.x, st.flj0.w);
+            df_add_df(Fh[1], Fl[1], st.flj0.y, st.flj1.x);
+            df_add_df(Fh[2], Fl[2], st.flj0.z, st.flj1.y);
+        }
+        if (a.ext_on) {
+            float ex, ey, ez;
+            external_force(st.xh, st.lx, st.ly, st.lz, tc.kw, tc.mg, tc.mw2, spring[ti], p.wall,
+                           p.rot_mode, ex, ey, ez);
+            if (any) {
+                df_add(Fh[0], Fl[0], ex);
+                df_add(Fh[1], Fl[1], ey);
+                df_add(Fh[2], Fl[2], ez);
+            } else { // the first term: (x, 0), as the compensated add into zero gives
+                Fh[0] = ex;
+                Fh[1] = ey;
+                Fh[2] = ez;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            Fh[d] = a.F[d * n + i];
+            Fl[d] = a.F[(3 + d) * n + i];
         }
     }
+    advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
+                           step, st.xh, st.lx, st.ly, st.lz, Fh, Fl, st.v, a.x_lo, a.v, a.F,
+                           a.xq, a.flags, a.x_ref, a.nbr_gate, a.half_skin2, a.sxq, a.cell_pos,
+                           ti);
+}
+
+// The per-type coefficients in shared memory and, by the first CTA of a launch
+// that takes the A part, the spring radius of step + 1.
+template <int MODE>
+__device__ __forceinline__ void integrate_prologue(const IntArgs &a, const StepParams &p,
+                                                   TypeCoef *s_tc, long long step)
+{
+    constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
     if (threadIdx.x < NPSIM_MAX_TYPES)
         s_tc[threadIdx.x] = p.tc[threadIdx.x];
     __syncthreads();
     if (DO_A && blockIdx.x == 0 && threadIdx.x < p.n_types) // spring radius of step + 1
         a.spring[((step + 1) & 1) * NPSIM_MAX_TYPES + threadIdx.x] =
             spring_entry(p.R0, p.k_evap, p.dt, step + 1, p.tc[threadIdx.x].half_sigma);
+}
 
-    const float4 *spring = a.spring + (step & 1) * NPSIM_MAX_TYPES;
-
-    if (i < n) {
-        const TypeCoef &tc = s_tc[ti];
-        float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
-        if (ASSEMBLE) {
-            bool any = false; // some force term is in (Fh, Fl) already
-            const int pos = a.row_pos ? a.row_pos[i] : i;
-            if (a.slots && pos >= 0) {
-                any = true;
-                sum_row_slots(a.slots, a.sk, pos, Fh, Fl);
-                if (a.field_slots) { // the Coulomb-only kernels return sum_j q_j r_ij / r^3
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        df_mul(Fh[d], Fl[d], tc.qc);
-                }
-            }
-            if (a.F_lj) {
-                any = true;
-                df_add_df(Fh[0], Fl[0], flj0.x, flj0.w);
-                df_add_df(Fh[1], Fl[1], flj0.y, flj1.x);
-                df_add_df(Fh[2], Fl[2], flj0.z, flj1.y);
-            }
-            if (a.ext_on) {
-                float ex, ey, ez;
-                external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2, spring[ti], p.wall,
-                               p.rot_mode, ex, ey, ez);
-                if (any) {
-                    df_add(Fh[0], Fl[0], ex);
-                    df_add(Fh[1], Fl[1], ey);
-                    df_add(Fh[2], Fl[2], ez);
-                } else { // the first term: (x, 0), as the compensated add into zero gives
-                    Fh[0] = ex;
-                    Fh[1] = ey;
-                    Fh[2] = ez;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                Fh[d] = a.F[d * n + i];
-                Fl[d] = a.F[(3 + d) * n + i];
-            }
-        }
-
-        advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
-                               step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq,
-                               a.flags, a.x_ref, a.nbr_gate, a.half_skin2, a.sxq, a.cell_pos,
-                               ti);
-    }
+// The chunk's last launch: once every thread of the CTA is past its use of the
+// step, count the CTA in; the last one sets the counter to the first step of
+// the next chunk.
+template <int MODE>
+__device__ __forceinline__ void integrate_commit(const IntArgs &a, long long step)
+{
+    constexpr bool DO_A = (MODE == MODE_A || MODE == MODE_BA);
     if (a.step_commit) {
-        // the chunk's last launch: once every thread of the CTA is past its use
-        // of the step, count the CTA in; the last one sets the counter to the
-        // first step of the next chunk
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -181,6 +201,37 @@ k_integrate(IntArgs a, StepParams p)
             }
         }
     }
+}
+
+// A grid of resident CTAs (at most SMs x 4 of 256 threads) striding over the
+// particles: each thread has the next particle's state in flight while it
+// updates the current one, and reads the step counter and the per-type
+// coefficients once for all of its particles.  (One particle per thread, one
+// CTA per 256, measured 1.4 % slower on 8.4 M free NPs.)
+template <int MODE>
+__global__ void __launch_bounds__(256, 4)
+k_integrate(IntArgs a, StepParams p)
+{
+    __shared__ TypeCoef s_tc[NPSIM_MAX_TYPES];
+    const int n = p.n;
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long step = *a.step + a.step_ofs;
+    PartState st{};
+    if (i < n)
+        load_state<MODE>(a, n, i, st);
+    integrate_prologue<MODE>(a, p, s_tc, step);
+    const float4 *spring = a.spring + (step & 1) * NPSIM_MAX_TYPES;
+    while (i < n) {
+        const int inext = i + stride;
+        PartState nx{};
+        if (inext < n)
+            load_state<MODE>(a, n, inext, nx);
+        update_particle<MODE>(a, p, s_tc, spring, step, i, st);
+        st = nx;
+        i = inext;
+    }
+    integrate_commit<MODE>(a, step);
 }
 
 // hi = float(x), lo = float(x - hi): the nearest float and the remainder.
@@ -305,7 +356,30 @@ cudaError_t launch_integrate(int mode, const IntArgs &a, const StepParams &p,
                              cudaStream_t st)
 {
     const int block = 256;
-    const int grid = (p.n + block - 1) / block;
+    // resident CTAs per device (every mode has the same register bound)
+    constexpr int kMaxDev = 64;
+    static int resident[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    int gmax = dev < kMaxDev ? resident[dev] : 0;
+    if (gmax == 0) {
+        int sms = 0, occ = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_integrate<MODE_BA>, block, 0);
+        if (e != cudaSuccess)
+            return e;
+        gmax = sms * (occ > 0 ? occ : 1);
+        if (dev < kMaxDev)
+            resident[dev] = gmax;
+    }
+    int grid = (p.n + block - 1) / block;
+    if (grid > gmax)
+        grid = gmax;
+    if (grid < 1)
+        grid = 1;
     switch (mode) {
     case MODE_FORCES: k_integrate<MODE_FORCES><<<grid, block, 0, st>>>(a, p); break;
     case MODE_A: k_integrate<MODE_A><<<grid, block, 0, st>>>(a, p); break;

@@ -559,33 +559,35 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
             const float e = __fmaf_rn(hh[d], hh[d], -p);
             df_add_df(r2h, r2l, p, __fmaf_rn(2.0f * hh[d], ll[d], e));
         }
-        // |x| and 1/|x| from one rsqrt (a few ulp: far below the force tolerance)
+        // |x| and 1/|x| from one rsqrt (a few ulp: far below the force tolerance);
+        // every operation below is rounded explicitly, so the force does not
+        // depend on how the compiler fuses operations in each kernel that
+        // inlines this (the integrator's modes must agree bit for bit)
         const float rinv = rsqrtf(r2h);
-        const float rr = r2h * rinv;
         const float reff = spring.z;
         float s;
         if (reff > 0.0f) {
             float dh = r2h, dl = r2l;
             df_add_df(dh, dl, -spring.x, -spring.y);
-            s = __fdividef(dh, rr + reff);
+            s = __fdividef(dh, __fmaf_rn(r2h, rinv, reff)); // (|x|^2 - R_eff^2) / (|x| + R_eff)
         } else {
-            s = rr - reff;
+            s = __fmaf_rn(r2h, rinv, -reff);
         }
         if (s > 0.0f && r2h > 0.0f && (wall != 2 || s < spring.w)) {
-            const float f = -kw * s * rinv;
-            fx = f * xh.x;
-            fy = f * xh.y;
-            fz = f * xh.z;
+            const float f = __fmul_rn(__fmul_rn(-kw, s), rinv);
+            fx = __fmul_rn(f, xh.x);
+            fy = __fmul_rn(f, xh.y);
+            fz = __fmul_rn(f, xh.z);
         }
     }
-    fz -= mg;
+    fz = __fsub_rn(fz, mg);
     if (rot_mode == 1) {
-        fx += mw2 * xh.x;
-        fy += mw2 * xh.y;
+        fx = __fmaf_rn(mw2, xh.x, fx);
+        fy = __fmaf_rn(mw2, xh.y, fy);
     } else if (rot_mode == 2) {
-        fx += mw2 * xh.x;
-        fy += mw2 * xh.y;
-        fz += mw2 * xh.z;
+        fx = __fmaf_rn(mw2, xh.x, fx);
+        fy = __fmaf_rn(mw2, xh.y, fy);
+        fz = __fmaf_rn(mw2, xh.z, fz);
     }
 }
 
@@ -970,19 +972,19 @@ cudaError_t launch_cell_build(const CellGrid &g, const float4 *xq, const int *ty
 // Rewrite the cell-ordered records from positions xq in the order of the last build.
 cudaError_t launch_cell_refresh(const CellBufs &b, const float4 *xq, const int *typ, int n,
                                 cudaStream_t st);
-// Verlet neighbour list over the cells (celllist.cu): entries (cell-order slot
-// << 3 | type); entry k of the NP at cell-order slot p at nbr[nbr_index(k, p, n)]
+// Verlet neighbour list over the cells (celllist.cu): entries are cell-order
+// slots; entry k of the NP at cell-order slot p at nbr[nbr_index(k, p, n)]
 // -- blocks of four entries, block j of all slots contiguous, so that a thread
 // reads its next four entries with one 16-byte load and a warp reads 512
 // contiguous bytes; cap (a multiple of 4) entries per slot; a list's last block
-// is padded with entries (n << 3) naming the far record sxq[n].  nnbr [n] the full
+// is padded with entries n naming the far record sxq[n].  nnbr [n] the full
 // counts by slot; x_ref [n] the positions of the last build by particle index.
 __host__ __device__ __forceinline__ size_t nbr_index(int k, int p, int n)
 {
     return ((size_t)(k >> 2) * (size_t)n + (size_t)p) * 4 + (size_t)(k & 3);
 }
 struct NbrList {
-    unsigned *nbr; // (index << 3 | type)
+    unsigned *nbr; // partner slots
     int *nnbr;
     float4 *x_ref;
     unsigned long long *builds; // number of builds run (device counter)
