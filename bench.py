@@ -484,10 +484,12 @@ def _dense_lj_state(P, stream, n_copy=65536, copies=4, compress_steps=20000, see
     return held, X, T, phi
 
 
-def _cell_list_dense_roofline(P, stream, chunks=4, **kw):
+def _cell_list_dense_roofline(P, stream, chunks=16, **kw):
     """The cell-list LJ path on the dense aggregate of _dense_lj_state (4.2 M
     NPs, ~0.6 packing fraction, random index order): bytes per step as in
-    _cell_list_roofline (list forces every step, builds at the rate they ran)."""
+    _cell_list_roofline (list forces every step, builds at the rate they ran,
+    over 16 graph chunks so that the ~one rebuild per ten steps is averaged
+    over some 25 of them)."""
     hs, X, T, phi = _dense_lj_state(P, stream, **kw)
     n = len(X)
     with P.Sim(hs, X, None, T, stream=stream) as sim:

@@ -55,8 +55,10 @@ __device__ __forceinline__ void normals3(uint64_t seed, uint32_t i, int64_t step
     float u1 = fmaf(__uint2float_rn(r.y), sc, 0.5f * sc);
     float u2 = fmaf(__uint2float_rn(r.z), sc, 0.5f * sc);
     float u3 = fmaf(__uint2float_rn(r.w), sc, 0.5f * sc);
-    float rho1 = sqrtf(-2.0f * logf(u0));
-    float rho2 = sqrtf(-2.0f * logf(u2));
+    // the radii sqrt(-2 ln u) as x rsqrt(x) (within two ulp of sqrt; 0 at u = 1)
+    const float x1 = -2.0f * logf(u0), x2 = -2.0f * logf(u2);
+    const float rho1 = x1 > 0.0f ? x1 * rsqrtf(x1) : 0.0f;
+    const float rho2 = x2 > 0.0f ? x2 * rsqrtf(x2) : 0.0f;
     float s1, c1;
     sincospif(2.0f * u1, &s1, &c1);
     const float c3 = cospif(2.0f * u3); // the sine of this angle is not used
