@@ -43,7 +43,11 @@ enum {
     NPSIM_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
     NPSIM_ERR_OOM = -5,         /* device allocation failed */
     NPSIM_ERR_IO = -6,          /* checkpoint file could not be written or read */
-    NPSIM_ERR_NO_DEVICE = -7    /* no CUDA device, or not an sm_103 device */
+    NPSIM_ERR_NO_DEVICE = -7,   /* no CUDA device, or not an sm_103 device */
+    NPSIM_ERR_ESCAPED = -8      /* with the full interface spring on (wall 1), an NP was
+                                   farther than 2 R(t) from the droplet centre: a step
+                                   went unstable (the paper has no such check; its
+                                   runs rely on strong damping) */
 };
 
 /* Per-type NP properties (Sec. 2.1: each NP type has its own size, mass and
@@ -124,7 +128,9 @@ void npsim_destroy(npsim_sim_t sim);
  * keyed by (seed) and counted by (particle, step, 0).  Steps are replayed from
  * captured CUDA graphs.  Returns after one device-to-host read of the error
  * word: NONFINITE if any position became non-finite, TIMEOUT if a bounded wait
- * expired.  n_steps = 0 is a no-op.
+ * expired, ESCAPED if (wall 1) an NP was farther than 2 R(t) from the centre at
+ * the start of some step.  The steps were taken in every case; the word is
+ * cleared by the read.  n_steps = 0 is a no-op.
  */
 int npsim_step(npsim_sim_t sim, int64_t n_steps);
 
@@ -280,7 +286,8 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
                      npsim_ens_t *out);
 
 /* Advance every droplet by n_steps steps (all droplets share the step counter);
- * one device-to-host read of the error word at the end. */
+ * one device-to-host read of the error word at the end: NONFINITE or ESCAPED
+ * (per droplet, as npsim_step). */
 int npsim_ens_step(npsim_ens_t ens, int64_t n_steps);
 
 /* State of droplet d (host arrays, any may be NULL; n_d x 3). */

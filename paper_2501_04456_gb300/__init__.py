@@ -25,7 +25,7 @@ MAX_SCALES = 32
 
 NPSIM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NONFINITE", -4: "TIMEOUT", -5: "OOM",
-          -6: "IO", -7: "NO_DEVICE"}
+          -6: "IO", -7: "NO_DEVICE", -8: "ESCAPED"}
 
 
 class NpsimError(RuntimeError):

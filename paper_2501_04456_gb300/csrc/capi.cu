@@ -670,6 +670,9 @@ int read_flags(npsim_sim *s)
             return set_err(NPSIM_ERR_NONFINITE, "a position became non-finite");
         if (h & FLAG_TIMEOUT)
             return set_err(NPSIM_ERR_TIMEOUT, "a bounded device wait expired");
+        if (h & FLAG_ESCAPED)
+            return set_err(NPSIM_ERR_ESCAPED,
+                           "an NP was farther than 2 R(t) from the droplet centre");
         return set_err(NPSIM_ERR_CUDA, "device error word 0x%x", h);
     }
     return NPSIM_OK;
@@ -1341,11 +1344,13 @@ int npsim_create(const npsim_type_t *types, const npsim_params_t *params, int64_
                  const double *x0, const double *v0, const int32_t *type, void *stream,
                  npsim_sim_t *out)
 {
+    NP_TRACE();
     return create_impl(types, params, n, x0, v0, type, stream, nullptr, out);
 }
 
 void npsim_destroy(npsim_sim_t sim)
 {
+    NP_TRACE();
     if (!sim)
         return;
     cudaStreamSynchronize(sim->user);
@@ -1421,6 +1426,7 @@ extern "C" {
 
 int npsim_step(npsim_sim_t s, int64_t n_steps)
 {
+    NP_TRACE();
     NP_REQUIRE(s, "sim is NULL");
     NP_REQUIRE(n_steps >= 0, "n_steps must be >= 0");
     int rc = enqueue_steps(s, n_steps);
@@ -1432,6 +1438,7 @@ int npsim_step(npsim_sim_t s, int64_t n_steps)
 int npsim_step_record(npsim_sim_t s, int64_t n_steps, int64_t every, float *frames,
                       int64_t n_frames)
 {
+    NP_TRACE();
     NP_REQUIRE(s && frames, "sim and frames are required");
     NP_REQUIRE(n_steps >= 0 && every >= 1, "n_steps >= 0 and every >= 1 are required");
     const int64_t nf = n_steps / every;
@@ -1497,6 +1504,7 @@ int npsim_step_record(npsim_sim_t s, int64_t n_steps, int64_t every, float *fram
 
 int npsim_get_state(npsim_sim_t s, double *x, double *v, double *F, int64_t *step)
 {
+    NP_TRACE();
     NP_REQUIRE(s, "sim is NULL");
     if (x || v || F) {
         int rc = copy_state_out(s, s->F, x, v, F);
@@ -1517,6 +1525,7 @@ int npsim_set_state(npsim_sim_t s, const double *x, const double *v, int64_t ste
 
 int npsim_forces(npsim_sim_t s, int what, double *F)
 {
+    NP_TRACE();
     NP_REQUIRE(s && F, "sim and F are required");
     NP_REQUIRE(what >= 0 && what <= 3, "what must be 0..3");
     const bool lj = what == 0 || what == 1 || what == 2;
@@ -1892,6 +1901,7 @@ extern "C" {
 int npsim_stats(npsim_sim_t s, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
                 double *rdf_g, int64_t *radial_counts, double *radial_c, npsim_stats_t *out)
 {
+    NP_TRACE();
     NP_REQUIRE(s && cfg && out, "sim, cfg and out are required");
     int rc = check_stats_cfg(cfg);
     if (rc)
@@ -1977,6 +1987,7 @@ int restore_lists(npsim_sim *s, const CkptHeader &h, const float4 *x_ref_host)
 int npsim_scattering(const double *g, int32_t n_bins, double r_max, double n_surf, double Rg,
                      double Df, const double *q, int32_t n_q, double *I, double *I_frac)
 {
+    NP_TRACE();
     NP_REQUIRE(g && q && I, "g, q and I are required");
     NP_REQUIRE(n_bins >= 1 && n_q >= 1, "n_bins and n_q must be >= 1");
     NP_REQUIRE(r_max > 0 && std::isfinite(r_max), "r_max must be positive");
@@ -2017,6 +2028,7 @@ int npsim_scattering(const double *g, int32_t n_bins, double r_max, double n_sur
 
 int npsim_save(npsim_sim_t s, const char *path)
 {
+    NP_TRACE();
     NP_REQUIRE(s && path, "sim and path are required");
     CkptHeader h{};
     memcpy(h.magic, kMagic, 8);
@@ -2090,6 +2102,7 @@ int npsim_save(npsim_sim_t s, const char *path)
 int npsim_load(const char *path, const npsim_type_t *types_override,
                const npsim_params_t *params_override, void *stream, npsim_sim_t *out)
 {
+    NP_TRACE();
     NP_REQUIRE(path && out, "path and out are required");
     *out = nullptr;
     FILE *f = fopen(path, "rb");
@@ -2493,6 +2506,7 @@ extern "C" {
 int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream,
                      npsim_ens_t *out)
 {
+    NP_TRACE();
     NP_REQUIRE(out, "out is NULL");
     *out = nullptr;
     NP_REQUIRE(drops && n_drops >= 1, "need at least one droplet");
@@ -2705,6 +2719,7 @@ int npsim_ens_create(const npsim_droplet_t *drops, int32_t n_drops, void *stream
 
 void npsim_ens_destroy(npsim_ens_t e)
 {
+    NP_TRACE();
     if (!e)
         return;
     cudaStreamSynchronize(e->user);
@@ -2713,6 +2728,7 @@ void npsim_ens_destroy(npsim_ens_t e)
 
 int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
 {
+    NP_TRACE();
     NP_REQUIRE(e, "ensemble is NULL");
     NP_REQUIRE(n_steps >= 0, "n_steps must be >= 0");
     int64_t rem = n_steps;
@@ -2731,6 +2747,9 @@ int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
     NP_CUDA(cudaStreamSynchronize(e->user));
     if (h) {
         NP_CUDA(cudaMemsetAsync(e->d_flags, 0, sizeof(int), e->user));
+        if (!(h & FLAG_NONFINITE) && (h & FLAG_ESCAPED))
+            return set_err(NPSIM_ERR_ESCAPED,
+                           "an NP was farther than 2 R(t) from its droplet's centre");
         return set_err(NPSIM_ERR_NONFINITE, "a position became non-finite");
     }
     return NPSIM_OK;
@@ -2739,6 +2758,7 @@ int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
 int npsim_ens_get_state(npsim_ens_t e, int32_t d, double *x, double *v, double *F,
                         int64_t *step)
 {
+    NP_TRACE();
     NP_REQUIRE(e && d >= 0 && d < e->D, "bad ensemble or droplet index");
     NP_CUDA(cudaStreamSynchronize(e->user));
     const int n = e->cnt[d], off = e->off[d];
@@ -2779,6 +2799,7 @@ int npsim_ens_get_state(npsim_ens_t e, int32_t d, double *x, double *v, double *
 
 int npsim_ens_forces(npsim_ens_t e, int32_t d, double *F)
 {
+    NP_TRACE();
     NP_REQUIRE(e && F && d >= 0 && d < e->D, "bad ensemble, droplet index or F");
     int rc = ens_pass(e, MODE_FORCES, true, e->F_tmp, e->user);
     if (rc)
@@ -2801,6 +2822,7 @@ int npsim_ens_forces(npsim_ens_t e, int32_t d, double *F)
 int npsim_ens_stats(npsim_ens_t e, int32_t d, const npsim_stats_cfg_t *cfg, int64_t *rdf_counts,
                     double *rdf_g, int64_t *radial_counts, double *radial_c, npsim_stats_t *out)
 {
+    NP_TRACE();
     NP_REQUIRE(e && cfg && out && d >= 0 && d < e->D,
                "bad ensemble, droplet index, cfg or out");
     int rc = check_stats_cfg(cfg);

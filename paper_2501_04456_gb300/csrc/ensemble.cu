@@ -181,6 +181,8 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 Fl[k] = a.F[(3 + k) * n + i];
             }
         }
+        if (DO_A)
+            check_escape(xh, spring[d * NPSIM_MAX_TYPES + ti], D.wall, a.flags);
         advance_particle<MODE>(i, n, (uint32_t)li, tc, D.integrator, 0.5f * (float)D.dt, D.seed,
                                step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq, a.flags);
     }

@@ -4,6 +4,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/npsim.h"
@@ -17,6 +18,7 @@ enum : int {
     FLAG_TIMEOUT = 2,
     FLAG_BAD_CELL = 4,
     FLAG_NBR_OVERFLOW = 8, // some NP had more list partners than the list holds (not an error)
+    FLAG_ESCAPED = 16,     // an NP farther than 2 R(t) from the centre with the full spring on
 };
 
 // ---------------------------------------------------------------------------
@@ -593,6 +595,23 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
     }
 }
 
+// Failure check of the interface (no counterpart in the paper, whose runs rely
+// on strong damping for stability): with the full spring on (wall 1) no NP can
+// get farther than 2 R(t) from the centre unless a step went unstable; R(t) =
+// R_eff + sigma/2 from the step's spring entry.  Sets FLAG_ESCAPED.
+__device__ __forceinline__ void check_escape(const float4 &xh, const float4 &spring, int wall,
+                                             int *flags)
+{
+    if (wall != 1)
+        return;
+    const float R = __fmaf_rn(0.5f, spring.w, spring.z);
+    if (!(R > 0.0f))
+        return;
+    const float r2 = __fmaf_rn(xh.x, xh.x, __fmaf_rn(xh.y, xh.y, __fmul_rn(xh.z, xh.z)));
+    if (r2 > __fmul_rn(4.0f, __fmul_rn(R, R)))
+        atomicOr(flags, FLAG_ESCAPED);
+}
+
 struct StepParams {
     int n;
     int n_types;
@@ -663,6 +682,17 @@ struct CellGrid {
 // Record a message for npsim_last_error() on this thread and return `code`
 // (defined in capi.cu).
 int report_error(int code, const char *fmt, ...);
+
+// An NVTX range named after the C-ABI entry point it is declared in, for the
+// length of the call: the calls show on Nsight Systems timelines above the
+// kernels they launch (the NVTX calls do nothing when no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define NP_TRACE() ::npsim::TraceRange np_trace_range_(__func__)
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the .cu files).

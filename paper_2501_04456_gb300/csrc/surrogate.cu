@@ -381,6 +381,7 @@ extern "C" {
 int npsim_surr_create(int32_t n_in, int32_t n_hidden, int32_t n_layers, int32_t n_out,
                       int32_t n_nets, uint64_t seed, npsim_surr_t *out)
 {
+    NP_TRACE();
     if (!out)
         return report_error(NPSIM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -622,6 +623,7 @@ int npsim_surr_train(npsim_surr_t s, const float *X, const float *Y, int32_t n_s
                      int32_t epochs, int32_t batch, float lr, float wd, uint64_t shuffle_seed,
                      float *final_loss)
 {
+    NP_TRACE();
     if (!s || !X || !Y || n_samples < 1 || epochs < 0 || batch < 1 || batch > 8192)
         return report_error(NPSIM_ERR_INVALID_ARG, "bad training arguments");
     const int bp = (batch + 127) / 128 * 128;
@@ -705,6 +707,7 @@ int npsim_surr_train(npsim_surr_t s, const float *X, const float *Y, int32_t n_s
 
 int npsim_surr_predict(npsim_surr_t s, const float *X, int32_t B, float *Y_mean, float *Y_spread)
 {
+    NP_TRACE();
     if (!s || !X || !Y_mean || B < 1 || B > 65536)
         return report_error(NPSIM_ERR_INVALID_ARG, "bad prediction arguments");
     const int bp = (B + 127) / 128 * 128;
@@ -766,6 +769,7 @@ int npsim_test_wait_cycles(int64_t cycles)
 int npsim_gemm_bf16(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
                     int32_t n_tile, float *C)
 {
+    NP_TRACE();
     if (!A || !B || !C || M < 1 || N < 16 || K < 16 || N % 16 || K % 16 || n_tile % 16 ||
         n_tile < 16 || n_tile > 256)
         return report_error(NPSIM_ERR_INVALID_ARG, "gemm shape: N, K, n_tile multiples of 16");

@@ -100,3 +100,14 @@ def test_no_device_is_an_error_not_a_crash(libpath):
     with pytest.raises(P.NpsimError) as e:
         P.npsim_philox(1, [0, 0, 0, 0], 4)
     assert e.value.code == -7
+
+
+def test_binding_error_names_match_the_header():
+    """Every NPSIM_ERR_* code of include/npsim.h has its name in the binding's
+    error map, and the map names no code the header lacks."""
+    txt = open(os.path.join(HEADER_DIR, "npsim.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    codes = {int(v): k for k, v in re.findall(r"NPSIM_ERR_([A-Z_]+)\s*=\s*(-?\d+)", txt)}
+    import paper_2501_04456_gb300 as P
+    assert codes == P.ERRORS
+    assert codes[-8] == "ESCAPED"

@@ -166,3 +166,20 @@ def test_ensemble_stats_rejects_a_bad_droplet_index(P, drops):
             assert e.value.code == -1  # NPSIM_ERR_INVALID_ARG
         with pytest.raises(P.NpsimError):
             ens.stats(0, r_max=-1.0, n_bins=16)  # bins need a positive range
+
+
+def test_ensemble_reports_an_escaped_np(P, drops):
+    """An NP of one droplet farther than 2 R(t) from its centre (spring on)
+    makes npsim_ens_step return NPSIM_ERR_ESCAPED; the other droplets' NPs
+    are inside theirs, and an ensemble without it steps without error."""
+    sc, x, v, types = drops[1]
+    xb = x.copy()
+    xb[3] = [0.0, 0.0, -3.0 * sc.R0]
+    bad = list(drops[:3])
+    bad[1] = (sc, xb, v, types)
+    with P.Ensemble(bad) as ens:
+        with pytest.raises(P.NpsimError) as e:
+            ens.step(2)
+        assert e.value.code == -8
+    with P.Ensemble(drops[:3]) as ens:
+        ens.step(2)

@@ -698,6 +698,29 @@ def test_nonfinite_position_is_reported(P):
         assert e.value.code == -3
 
 
+def test_escaped_np_is_reported(P):
+    """With the full interface spring on, an NP farther than 2 R(t) from the
+    centre (where only an unstable step could have left it) makes npsim_step
+    return NPSIM_ERR_ESCAPED; the steps were still taken and the word is
+    cleared, so the next steps (the spring pulling the NP back in) succeed.
+    Without the spring the same position is no error."""
+    sc = wl.config1()
+    types, x, v = wl.initial_state(sc)
+    xb = x.copy()
+    xb[7] = [3.0 * sc.R0, 0.0, 0.0]
+    with P.Sim(sc, x, v, types) as sim:
+        sim.set_state(xb, v, 0)
+        with pytest.raises(P.NpsimError) as e:
+            sim.step(2)
+        assert e.value.code == -8
+        assert sim.state()[3] == 2
+        x2 = sim.state()[0]
+        assert np.linalg.norm(x2[7]) < 3.0 * sc.R0  # pulled back towards the droplet
+    with P.Sim(with_(sc, wall=False), xb, v, types) as sim:
+        sim.step(2)
+        assert sim.state()[3] == 2
+
+
 def test_cell_grid_follows_the_shrinking_droplet(P):
     """The droplet of config 1 shrinks from R = 30 to 20: at step 1024 the cell
     grid (sized at creation for R0) is more than a quarter too wide and is
