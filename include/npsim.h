@@ -45,9 +45,9 @@ enum {
     NPSIM_ERR_IO = -6,          /* checkpoint file could not be written or read */
     NPSIM_ERR_NO_DEVICE = -7,   /* no CUDA device, or not an sm_103 device */
     NPSIM_ERR_ESCAPED = -8      /* with the full interface spring on (wall 1), an NP was
-                                   farther than 2 R(t) from the droplet centre: a step
-                                   went unstable (the paper has no such check; its
-                                   runs rely on strong damping) */
+                                   farther than twice the larger of R0 and R(t) from the
+                                   droplet centre: a step went unstable (the paper has
+                                   no such check; its runs rely on strong damping) */
 };
 
 /* Per-type NP properties (Sec. 2.1: each NP type has its own size, mass and
@@ -128,8 +128,8 @@ void npsim_destroy(npsim_sim_t sim);
  * keyed by (seed) and counted by (particle, step, 0).  Steps are replayed from
  * captured CUDA graphs.  Returns after one device-to-host read of the error
  * word: NONFINITE if any position became non-finite, TIMEOUT if a bounded wait
- * expired, ESCAPED if (wall 1) an NP was farther than 2 R(t) from the centre at
- * the start of some step.  The steps were taken in every case; the word is
+ * expired, ESCAPED if (wall 1) an NP was farther than 2 max(R0, R(t)) from the
+ * centre at the start of some step.  The steps were taken in every case; the word is
  * cleared by the read.  n_steps = 0 is a no-op.
  */
 int npsim_step(npsim_sim_t sim, int64_t n_steps);
@@ -411,11 +411,12 @@ int npsim_test_wait_cycles(int64_t cycles);
  * [1, 32768]; larger n is rejected with NPSIM_ERR_INVALID_ARG.  The first call
  * on a device looks up the array's device address for that device (set-up,
  * once per device, with that device current); make that first call before any
- * stream capture.  The address is kept for the life of the process: after a
- * cudaDeviceReset (or anything else that destroys the device's primary context)
- * the kept address is stale, so do not call this entry point again in that
- * process.  Every call on a device shares the array: calls that overlap on the
- * GPU (different streams without ordering) race and give wrong forces.  Each
+ * stream capture.  The address is kept while the calling thread's current
+ * context stays the one the set-up ran in, and looked up again when it changes
+ * (after a cudaDeviceReset, for instance, the array lives at a new address in
+ * the new context).  Every call on a device shares the array: calls that
+ * overlap on the GPU (different streams without ordering) race and give wrong
+ * forces.  Each
  * call writes every partial it reads, so nothing carries over from the previous
  * call.  Allocates nothing (no cudaMalloc/cudaFree).
  */

@@ -672,7 +672,7 @@ int read_flags(npsim_sim *s)
             return set_err(NPSIM_ERR_TIMEOUT, "a bounded device wait expired");
         if (h & FLAG_ESCAPED)
             return set_err(NPSIM_ERR_ESCAPED,
-                           "an NP was farther than 2 R(t) from the droplet centre");
+                           "an NP was farther than 2 max(R0, R(t)) from the droplet centre");
         return set_err(NPSIM_ERR_CUDA, "device error word 0x%x", h);
     }
     return NPSIM_OK;
@@ -2749,7 +2749,7 @@ int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
         NP_CUDA(cudaMemsetAsync(e->d_flags, 0, sizeof(int), e->user));
         if (!(h & FLAG_NONFINITE) && (h & FLAG_ESCAPED))
             return set_err(NPSIM_ERR_ESCAPED,
-                           "an NP was farther than 2 R(t) from its droplet's centre");
+                           "an NP was farther than 2 max(R0, R(t)) from its droplet's centre");
         return set_err(NPSIM_ERR_NONFINITE, "a position became non-finite");
     }
     return NPSIM_OK;

@@ -182,7 +182,7 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
             }
         }
         if (DO_A)
-            check_escape(xh, spring[d * NPSIM_MAX_TYPES + ti], D.wall, a.flags);
+            check_escape(xh, spring[d * NPSIM_MAX_TYPES + ti], (float)D.R0, D.wall, a.flags);
         advance_particle<MODE>(i, n, (uint32_t)li, tc, D.integrator, 0.5f * (float)D.dt, D.seed,
                                step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq, a.flags);
     }

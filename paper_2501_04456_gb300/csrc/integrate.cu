@@ -163,7 +163,7 @@ __device__ __forceinline__ void update_particle(const IntArgs &a, const StepPara
         }
     }
     if (MODE == MODE_A || MODE == MODE_BA) // the positions this launch moves on
-        check_escape(st.xh, spring[ti], p.wall, a.flags);
+        check_escape(st.xh, spring[ti], (float)p.R0, p.wall, a.flags);
     advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
                            step, st.xh, st.lx, st.ly, st.lz, Fh, Fl, st.v, a.x_lo, a.v, a.F,
                            a.xq, a.flags, a.x_ref, a.nbr_gate, a.half_skin2, a.sxq, a.cell_pos,

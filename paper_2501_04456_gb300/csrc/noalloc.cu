@@ -15,6 +15,8 @@
 //   F_i = C q_i sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3,
 // using the packed float32x2 all-pairs kernel of allpairs.cu, followed by a
 // reduction of each row's partials in CTA order (deterministic).
+#include <cuda.h>
+
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -40,6 +42,7 @@ constexpr int kMaxDevices = 64;
 
 struct DeviceSetup {
     bool done = false;
+    CUcontext ctx = nullptr;   // the context the set-up was done in
     float *scratch = nullptr;  // device address of g_scratch on this device
     int shape = -1;            // all-pairs launch shape (index in the autotuner table)
     int grid_cap = 0;          // CTAs: min(kMaxGrid, resident CTAs of the shape)
@@ -48,16 +51,39 @@ struct DeviceSetup {
 std::mutex g_mu;
 DeviceSetup g_setup[kMaxDevices];
 
-// Once per device, with that device current: the device address of g_scratch
-// (in host code the array's name is only a host-side stand-in) and the launch
-// shape.  The first call on a device runs this; the result is kept for the
-// life of the process, so it goes stale if the device's primary context is
-// destroyed (cudaDeviceReset), which the header tells callers not to do.
+// The calling thread's current driver context (NULL if none yet, or if the
+// driver entry point is unavailable), through the runtime's driver entry point
+// lookup so that the library does not link the driver library.
+CUcontext current_context()
+{
+    using Fn = CUresult (*)(CUcontext *);
+    static const Fn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return reinterpret_cast<Fn>(p);
+        return static_cast<Fn>(nullptr);
+    }();
+    CUcontext c = nullptr;
+    if (fn && fn(&c) != CUDA_SUCCESS)
+        c = nullptr;
+    return c;
+}
+
+// Once per device and context, with that device current: the device address
+// of g_scratch (in host code the array's name is only a host-side stand-in)
+// and the launch shape.  The first call on a device runs this; the result is
+// kept and reused while the calling thread's current context is the one it was
+// made in, and made again when that changes (after a cudaDeviceReset the
+// module is loaded again in a new primary context, at a new address).
 int setup_device(int dev, DeviceSetup &out)
 {
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceSetup &s = g_setup[dev];
-    if (!s.done) {
+    const CUcontext ctx = current_context();
+    if (!s.done || ctx == nullptr || ctx != s.ctx) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
         if (e != cudaSuccess)
@@ -83,6 +109,7 @@ int setup_device(int dev, DeviceSetup &out)
         s.scratch = (float *)ptr;
         s.shape = shape;
         s.grid_cap = cap;
+        s.ctx = current_context(); // made current by the symbol lookup if it was not
         s.done = true;
     }
     out = s;

@@ -18,7 +18,7 @@ enum : int {
     FLAG_TIMEOUT = 2,
     FLAG_BAD_CELL = 4,
     FLAG_NBR_OVERFLOW = 8, // some NP had more list partners than the list holds (not an error)
-    FLAG_ESCAPED = 16,     // an NP farther than 2 R(t) from the centre with the full spring on
+    FLAG_ESCAPED = 16,     // an NP farther than 2 max(R0, R(t)) from the centre, full spring on
 };
 
 // ---------------------------------------------------------------------------
@@ -596,17 +596,17 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
 }
 
 // Failure check of the interface (no counterpart in the paper, whose runs rely
-// on strong damping for stability): with the full spring on (wall 1) no NP can
-// get farther than 2 R(t) from the centre unless a step went unstable; R(t) =
+// on strong damping for stability): with the full spring on (wall 1) no NP gets
+// farther than twice the larger of R0 and R(t) from the centre unless a step
+// went unstable.  (Twice R(t) alone is not a bound: under a fast compression
+// a heavy NP can lag the moving interface by more than R(t) itself.)  R(t) =
 // R_eff + sigma/2 from the step's spring entry.  Sets FLAG_ESCAPED.
-__device__ __forceinline__ void check_escape(const float4 &xh, const float4 &spring, int wall,
-                                             int *flags)
+__device__ __forceinline__ void check_escape(const float4 &xh, const float4 &spring, float R0,
+                                             int wall, int *flags)
 {
     if (wall != 1)
         return;
-    const float R = __fmaf_rn(0.5f, spring.w, spring.z);
-    if (!(R > 0.0f))
-        return;
+    const float R = fmaxf(__fmaf_rn(0.5f, spring.w, spring.z), R0);
     const float r2 = __fmaf_rn(xh.x, xh.x, __fmaf_rn(xh.y, xh.y, __fmul_rn(xh.z, xh.z)));
     if (r2 > __fmul_rn(4.0f, __fmul_rn(R, R)))
         atomicOr(flags, FLAG_ESCAPED);

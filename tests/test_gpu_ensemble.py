@@ -169,8 +169,8 @@ def test_ensemble_stats_rejects_a_bad_droplet_index(P, drops):
 
 
 def test_ensemble_reports_an_escaped_np(P, drops):
-    """An NP of one droplet farther than 2 R(t) from its centre (spring on)
-    makes npsim_ens_step return NPSIM_ERR_ESCAPED; the other droplets' NPs
+    """An NP of one droplet farther than 2 max(R0, R(t)) from its centre (spring
+    on) makes npsim_ens_step return NPSIM_ERR_ESCAPED; the other droplets' NPs
     are inside theirs, and an ensemble without it steps without error."""
     sc, x, v, types = drops[1]
     xb = x.copy()

@@ -699,8 +699,8 @@ def test_nonfinite_position_is_reported(P):
 
 
 def test_escaped_np_is_reported(P):
-    """With the full interface spring on, an NP farther than 2 R(t) from the
-    centre (where only an unstable step could have left it) makes npsim_step
+    """With the full interface spring on, an NP farther than 2 max(R0, R(t))
+    from the centre (where only an unstable step could have left it) makes npsim_step
     return NPSIM_ERR_ESCAPED; the steps were still taken and the word is
     cleared, so the next steps (the spring pulling the NP back in) succeed.
     Without the spring the same position is no error."""
