@@ -129,7 +129,7 @@ void npsim_destroy(npsim_sim_t sim);
  * captured CUDA graphs.  Returns after one device-to-host read of the error
  * word: NONFINITE if any position became non-finite, TIMEOUT if a bounded wait
  * expired, ESCAPED if (wall 1) an NP was farther than 2 max(R0, R(t)) from the
- * centre at the start of some step.  The steps were taken in every case; the word is
+ * centre during some step.  The steps were taken in every case; the word is
  * cleared by the read.  n_steps = 0 is a no-op.
  */
 int npsim_step(npsim_sim_t sim, int64_t n_steps);

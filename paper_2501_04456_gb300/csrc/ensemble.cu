@@ -169,7 +169,7 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 float ex, ey, ez;
                 external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2,
                                spring[d * NPSIM_MAX_TYPES + ti], D.wall, D.rot_mode, ex, ey,
-                               ez);
+                               ez, (float)D.R0, a.flags);
                 df_add(Fh[0], Fl[0], ex);
                 df_add(Fh[1], Fl[1], ey);
                 df_add(Fh[2], Fl[2], ez);
@@ -181,8 +181,6 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 Fl[k] = a.F[(3 + k) * n + i];
             }
         }
-        if (DO_A)
-            check_escape(xh, spring[d * NPSIM_MAX_TYPES + ti], (float)D.R0, D.wall, a.flags);
         advance_particle<MODE>(i, n, (uint32_t)li, tc, D.integrator, 0.5f * (float)D.dt, D.seed,
                                step, xh, lx, ly, lz, Fh, Fl, v, a.x_lo, a.v, a.F, a.xq, a.flags);
     }

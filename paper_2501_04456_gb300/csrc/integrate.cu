@@ -116,7 +116,8 @@ __device__ __forceinline__ void load_state(const IntArgs &a, int n, int i, PartS
 template <int MODE>
 __device__ __forceinline__ void update_particle(const IntArgs &a, const StepParams &p,
                                                 const TypeCoef *s_tc, const float4 *spring,
-                                                long long step, int i, const PartState &st)
+                                                float R0f, long long step, int i,
+                                                const PartState &st)
 {
     constexpr bool ASSEMBLE = (MODE != MODE_A);
     const int n = p.n;
@@ -144,7 +145,7 @@ __device__ __forceinline__ void update_particle(const IntArgs &a, const StepPara
         if (a.ext_on) {
             float ex, ey, ez;
             external_force(st.xh, st.lx, st.ly, st.lz, tc.kw, tc.mg, tc.mw2, spring[ti], p.wall,
-                           p.rot_mode, ex, ey, ez);
+                           p.rot_mode, ex, ey, ez, R0f, a.flags);
             if (any) {
                 df_add(Fh[0], Fl[0], ex);
                 df_add(Fh[1], Fl[1], ey);
@@ -162,8 +163,6 @@ __device__ __forceinline__ void update_particle(const IntArgs &a, const StepPara
             Fl[d] = a.F[(3 + d) * n + i];
         }
     }
-    if (MODE == MODE_A || MODE == MODE_BA) // the positions this launch moves on
-        check_escape(st.xh, spring[ti], (float)p.R0, p.wall, a.flags);
     advance_particle<MODE>(i, n, (uint32_t)i, tc, p.integrator, 0.5f * (float)p.dt, p.seed,
                            step, st.xh, st.lx, st.ly, st.lz, Fh, Fl, st.v, a.x_lo, a.v, a.F,
                            a.xq, a.flags, a.x_ref, a.nbr_gate, a.half_skin2, a.sxq, a.cell_pos,
@@ -224,12 +223,13 @@ k_integrate(IntArgs a, StepParams p)
         load_state<MODE>(a, n, i, st);
     integrate_prologue<MODE>(a, p, s_tc, step);
     const float4 *spring = a.spring + (step & 1) * NPSIM_MAX_TYPES;
+    const float R0f = (float)p.R0; // bound of the escape check
     while (i < n) {
         const int inext = i + stride;
         PartState nx{};
         if (inext < n)
             load_state<MODE>(a, n, inext, nx);
-        update_particle<MODE>(a, p, s_tc, spring, step, i, st);
+        update_particle<MODE>(a, p, s_tc, spring, R0f, step, i, st);
         st = nx;
         i = inext;
     }

@@ -542,10 +542,19 @@ __host__ __device__ inline float4 spring_entry(double R0, double k_evap, double 
 // (the lo^2 terms lie below the precision kept), so s keeps float32 relative
 // precision however large |x| is.  wall = 2 limits the spring to the band
 // (-r, r) about the surface, 0 < s < 2 r (spring.w = 2 r).
+//
+// With flags given, the failure check of the interface (no counterpart in the
+// paper, whose runs rely on strong damping for stability) runs on the NPs near
+// or beyond the surface: with the full spring on (wall 1) no NP gets farther
+// than twice the larger of R0 and R(t) from the centre unless a step went
+// unstable (twice R(t) alone is not a bound: under a fast compression a heavy
+// NP can lag the moving interface by more than R(t) itself); R(t) = R_eff +
+// sigma/2 from the spring entry.  Sets FLAG_ESCAPED.
 __device__ __forceinline__ void external_force(const float4 &xh, float lx, float ly, float lz,
                                                float kw, float mg, float mw2, float4 spring,
                                                int wall, int rot_mode, float &fx,
-                                               float &fy, float &fz)
+                                               float &fy, float &fz, float R0 = 0.0f,
+                                               int *flags = nullptr)
 {
     fx = fy = fz = 0.0f;
     // the spring acts only beyond R_eff (s > 0): an NP whose float32 |x|^2 from
@@ -555,6 +564,11 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
     const float reff_in = spring.z - 0.01f;
     const float r2_cheap = __fmaf_rn(xh.x, xh.x, __fmaf_rn(xh.y, xh.y, __fmul_rn(xh.z, xh.z)));
     if (wall && !(reff_in > 0.0f && r2_cheap < reff_in * reff_in)) {
+        if (flags && wall == 1) {
+            const float R = fmaxf(__fmaf_rn(0.5f, spring.w, spring.z), R0);
+            if (r2_cheap > __fmul_rn(4.0f, __fmul_rn(R, R)))
+                atomicOr(flags, FLAG_ESCAPED);
+        }
         float r2h = 0.0f, r2l = 0.0f;
         const float hh[3] = {xh.x, xh.y, xh.z}, ll[3] = {lx, ly, lz};
 #pragma unroll
@@ -593,23 +607,6 @@ __device__ __forceinline__ void external_force(const float4 &xh, float lx, float
         fy = __fmaf_rn(mw2, xh.y, fy);
         fz = __fmaf_rn(mw2, xh.z, fz);
     }
-}
-
-// Failure check of the interface (no counterpart in the paper, whose runs rely
-// on strong damping for stability): with the full spring on (wall 1) no NP gets
-// farther than twice the larger of R0 and R(t) from the centre unless a step
-// went unstable.  (Twice R(t) alone is not a bound: under a fast compression
-// a heavy NP can lag the moving interface by more than R(t) itself.)  R(t) =
-// R_eff + sigma/2 from the step's spring entry.  Sets FLAG_ESCAPED.
-__device__ __forceinline__ void check_escape(const float4 &xh, const float4 &spring, float R0,
-                                             int wall, int *flags)
-{
-    if (wall != 1)
-        return;
-    const float R = fmaxf(__fmaf_rn(0.5f, spring.w, spring.z), R0);
-    const float r2 = __fmaf_rn(xh.x, xh.x, __fmaf_rn(xh.y, xh.y, __fmul_rn(xh.z, xh.z)));
-    if (r2 > __fmul_rn(4.0f, __fmul_rn(R, R)))
-        atomicOr(flags, FLAG_ESCAPED);
 }
 
 struct StepParams {
