@@ -169,7 +169,8 @@ k_ens_integrate(EnsIntArgs a, int n_total, int n_drops, StreamK sk)
                 float ex, ey, ez;
                 external_force(xh, lx, ly, lz, tc.kw, tc.mg, tc.mw2,
                                spring[d * NPSIM_MAX_TYPES + ti], D.wall, D.rot_mode, ex, ey,
-                               ez, (float)D.R0, a.flags);
+                               ez, (float)D.R0,
+                               MODE == MODE_FORCES ? nullptr : a.flags); // steps only
                 df_add(Fh[0], Fl[0], ex);
                 df_add(Fh[1], Fl[1], ey);
                 df_add(Fh[2], Fl[2], ez);

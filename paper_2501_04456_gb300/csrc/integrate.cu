@@ -145,7 +145,8 @@ __device__ __forceinline__ void update_particle(const IntArgs &a, const StepPara
         if (a.ext_on) {
             float ex, ey, ez;
             external_force(st.xh, st.lx, st.ly, st.lz, tc.kw, tc.mg, tc.mw2, spring[ti], p.wall,
-                           p.rot_mode, ex, ey, ez, R0f, a.flags);
+                           p.rot_mode, ex, ey, ez, R0f,
+                           MODE == MODE_FORCES ? nullptr : a.flags); // steps only
             if (any) {
                 df_add(Fh[0], Fl[0], ex);
                 df_add(Fh[1], Fl[1], ey);
