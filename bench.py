@@ -279,7 +279,50 @@ def _traffic_from_profile(cfg, full_sum):
     return None
 
 
-def _ensemble_measure(P, torch, stream, n_plain=16, steps_per_droplet=10000, segments=10):
+# Algorithmic bytes per NP of the ensemble's integrator launch in mode BA: read
+# the position hi words with the charge (16), lo words (12), velocity (12),
+# type (4), droplet index (4) and row position (4); write the position (28) and
+# velocity (12).  Plus the partial slots of the all-pairs launch, read once:
+# 24 bytes per row and work item (6 floats), n_items x itile rows.
+ENS_INT_BYTES_BA = 16 + 12 + 12 + 4 + 4 + 4 + 28 + 12
+
+
+def _ensemble_kernels(P, drops, stream, n_tot, pairs, peak_tflops, chunks=4):
+    """The ensemble's two launches per step timed apart (CUDA event records in the
+    step graph, npsim_ens_profile) over `chunks` graph chunks of a fresh
+    ensemble at the initial state: the all-pairs launch against the measured
+    FP32 rate (17 flops per ordered pair, the Coulomb count; the LJ segments it
+    evaluates near the rows add work that is not credited) and the integrator
+    launch against the measured copy bandwidth (ENS_INT_BYTES_BA per NP plus
+    24 bytes per row of every work item's partial slot)."""
+    with P.Ensemble(drops, stream=stream) as ens:
+        n_items, itile = ens.work()
+        ens.profile(True)
+        ens.step(32)  # warm-up, graphs captured
+        ap, it = [], []
+        for _ in range(chunks):
+            ens.step(16)
+            kt, _ = ens.kernel_times()
+            ap.append(kt["allpairs"])
+            it.append(kt["integrate"])
+    ap_ms, int_ms = sum(ap) / len(ap), sum(it) / len(it)
+    ach = FLOPS_PER_PAIR * pairs / (ap_ms * 1e-3) / 1e12
+    int_bytes = ENS_INT_BYTES_BA * n_tot + 24 * n_items * itile
+    gbs = int_bytes / (int_ms * 1e-3) / 1e9
+    hbm = _hbm_peak()
+    return {"allpairs_ms": ap_ms, "integrate_ms": int_ms,
+            "allpairs_roofline": {"bound": "alu", "achieved": ach, "peak": peak_tflops,
+                                  "unit": "TFLOP/s", "frac": ach / peak_tflops,
+                                  "work": f"{FLOPS_PER_PAIR} flops x {pairs:.4g} ordered pairs "
+                                          f"per launch (sum over droplets of N(N-1))"},
+            "integrator_roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm,
+                                    "unit": "GB/s", "frac": gbs / hbm,
+                                    "bytes_per_launch": int_bytes,
+                                    "work_items": n_items, "rows_per_item": itile}}
+
+
+def _ensemble_measure(P, torch, stream, n_plain=16, steps_per_droplet=10000, segments=10,
+                      peak_tflops=None):
     """Droplets/s of the 256-droplet ensemble (N log-uniform in [512, 32768]) over
     whole runs: the batched ensemble is created from host arrays and advanced
     through all 10000 steps of every droplet (the step time is recorded per
@@ -324,6 +367,8 @@ def _ensemble_measure(P, torch, stream, n_plain=16, steps_per_droplet=10000, seg
             torch.cuda.synchronize()
         t_plain += time.perf_counter() - t1
     t_plain_all = t_plain * len(scs) / len(sample)
+    kernels = (_ensemble_kernels(P, drops, stream, n_tot, pairs, peak_tflops)
+               if peak_tflops else None)
     ens_dps = len(scs) / t_run
     plain_dps = len(scs) / t_plain_all
     run_ms = sum(seg_ms)
@@ -339,7 +384,8 @@ def _ensemble_measure(P, torch, stream, n_plain=16, steps_per_droplet=10000, seg
                       "sample": f"{len(sample)} of {len(scs)} droplets, every {stride}-th by N, "
                                 f"each created and run for {steps_per_droplet} steps; summed "
                                 f"wall time x {len(scs) / len(sample):.0f}"},
-            "speedup_vs_plain": ens_dps / plain_dps}
+            "speedup_vs_plain": ens_dps / plain_dps,
+            "kernels": kernels}
 
 
 # Algorithmic bytes per NP of the integrator launches (float32 words): mode BA
@@ -793,7 +839,8 @@ def run_ours(a):
 
     ens = None
     if not a.no_ensemble and rank == 0:
-        ens = _ensemble_measure(P, torch, stream, steps_per_droplet=a.ensemble_steps)
+        ens = _ensemble_measure(P, torch, stream, steps_per_droplet=a.ensemble_steps,
+                                peak_tflops=peak_tflops)
 
     surr = None
     cfg2 = None

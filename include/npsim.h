@@ -319,6 +319,25 @@ int npsim_ens_config(npsim_ens_t ens, int *block, int *i_per_thread, int *j_tile
 /* Total NPs and ordered pairs sum_d n_d (n_d - 1) per step. */
 int npsim_ens_info(npsim_ens_t ens, int64_t *n_total, double *pairs_per_step);
 
+/* Work items of one all-pairs launch (row tile x run of j-tiles, over all
+ * droplets) and rows per tile (either pointer may be NULL): each item writes
+ * one partial slot of 6 x itile floats that the integrator reads (measurement
+ * hook: the integrator's bytes). */
+int npsim_ens_work(npsim_ens_t ens, int64_t *n_items, int32_t *itile);
+
+/*
+ * Per-kernel timing of the ensemble (measurement hook).  enable = 1 re-captures
+ * the step graphs with CUDA event records around the all-pairs launch and the
+ * integrator launch of every step of a chunk; enable = 0 removes them (results
+ * do not depend on it).  After an npsim_ens_step, npsim_ens_kernel_times writes
+ * the mean duration in milliseconds of the all-pairs launch (ms[0]) and of the
+ * integrator launch (ms[1]) over the steps of the last replayed graph chunk,
+ * and the number of steps averaged.  ms must hold 2 doubles.  Errors:
+ * INVALID_ARG (NULL ensemble or ms, profiling not enabled), CUDA.
+ */
+int npsim_ens_profile(npsim_ens_t ens, int enable);
+int npsim_ens_kernel_times(npsim_ens_t ens, double *ms, int *samples);
+
 void npsim_ens_destroy(npsim_ens_t ens);
 
 /* ------------------------------------------------------------------------

@@ -129,6 +129,7 @@ def lib():
             L.npsim_ens_stats.argtypes = [_h, C.c_int32, C.POINTER(npsim_stats_cfg_t), _i64,
                                           _d, _i64, _d, C.POINTER(npsim_stats_t)]
             L.npsim_ens_info.argtypes = [_h, _i64, _d]
+            L.npsim_ens_work.argtypes = [_h, _i64, _i32]
             L.npsim_ens_destroy.argtypes = [_h]
             L.npsim_ens_destroy.restype = None
             _f = C.POINTER(C.c_float)
@@ -150,6 +151,8 @@ def lib():
             L.npsim_test_wait_cycles.argtypes = [C.c_int64]
             L.npsim_profile.argtypes = [_h, C.c_int]
             L.npsim_kernel_times.argtypes = [_h, _d, _i32]
+            L.npsim_ens_profile.argtypes = [_h, C.c_int]
+            L.npsim_ens_kernel_times.argtypes = [_h, _d, _i32]
             _lib = L
         return _lib
 
@@ -601,8 +604,29 @@ def npsim_ens_info(h):
     return n.value, p.value
 
 
+def npsim_ens_work(h):
+    n = C.c_int64()
+    t = C.c_int32()
+    _check(lib().npsim_ens_work(h, C.byref(n), C.byref(t)))
+    return n.value, t.value
+
+
 def npsim_ens_destroy(h):
     lib().npsim_ens_destroy(h)
+
+
+def npsim_ens_profile(h, enable=True):
+    _check(lib().npsim_ens_profile(h, int(bool(enable))))
+
+
+ENS_KERNEL_GROUPS = ("allpairs", "integrate")
+
+
+def npsim_ens_kernel_times(h):
+    ms = np.zeros(2)
+    k = C.c_int32()
+    _check(lib().npsim_ens_kernel_times(h, _p(ms, C.c_double), C.byref(k)))
+    return dict(zip(ENS_KERNEL_GROUPS, ms.tolist())), k.value
 
 
 class Ensemble:
@@ -629,6 +653,15 @@ class Ensemble:
 
     def info(self):
         return npsim_ens_info(self.h)
+
+    def work(self):
+        return npsim_ens_work(self.h)
+
+    def profile(self, enable=True):
+        npsim_ens_profile(self.h, enable)
+
+    def kernel_times(self):
+        return npsim_ens_kernel_times(self.h)
 
     def close(self):
         if getattr(self, "h", None):

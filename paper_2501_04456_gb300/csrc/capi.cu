@@ -2213,6 +2213,11 @@ struct npsim_ens {
     long long n_items = 0;  // work items of one all-pairs launch
     std::map<int, cudaGraphExec_t> graphs;
     int64_t step = 0;
+    // kernel timing (npsim_ens_profile): events around the all-pairs launch
+    // (group 0) and the integrator launch (group 1) of every pass of a chunk
+    bool profiling = false;
+    int last_chunk = 0;
+    cudaEvent_t ev[kChunk][2][2]{};
 
     std::vector<double> d_mean; // number-mean NP diameter of each droplet
     StatsWork sw{};             // statistics of one droplet at a time (lazy)
@@ -2222,6 +2227,11 @@ struct npsim_ens {
         free_stats(sw);
         for (auto &g : graphs)
             cudaGraphExecDestroy(g.second);
+        for (auto &a : ev)
+            for (auto &b : a)
+                for (auto &x : b)
+                    if (x)
+                        cudaEventDestroy(x);
         dfree(x_lo);
         dfree(v);
         dfree(F);
@@ -2324,9 +2334,20 @@ EnsAllpairsArgs ens_ap_args(npsim_ens *e, float *slots)
     return a;
 }
 
-int ens_pass(npsim_ens *e, int mode, bool ext, float *Fout, cudaStream_t st)
+int ens_pass(npsim_ens *e, int mode, bool ext, float *Fout, cudaStream_t st,
+             int prof_slot = -1)
 {
+    const bool prof = prof_slot >= 0 && e->profiling;
+    // inside stream capture the External flag makes each record a real
+    // event-record node of the graph
+    auto mark = [&](int group, int edge) -> cudaError_t {
+        return prof ? cudaEventRecordWithFlags(e->ev[prof_slot][group][edge], st,
+                                               cudaEventRecordExternal)
+                    : cudaSuccess;
+    };
+    NP_CUDA(mark(0, 0));
     NP_CUDA(launch_ens_allpairs(e->shape, e->sk, ens_ap_args(e, e->slots), st));
+    NP_CUDA(mark(0, 1));
     EnsIntArgs a{};
     a.x_lo = e->x_lo;
     a.v = e->v;
@@ -2342,7 +2363,9 @@ int ens_pass(npsim_ens *e, int mode, bool ext, float *Fout, cudaStream_t st)
     a.step = e->d_step;
     a.flags = e->d_flags;
     a.done = e->d_done;
+    NP_CUDA(mark(1, 0));
     NP_CUDA(launch_ens_integrate(mode, a, e->n_total, e->D, e->sk, st));
+    NP_CUDA(mark(1, 1));
     return NPSIM_OK;
 }
 
@@ -2363,7 +2386,7 @@ int ens_chunk(npsim_ens *e, int k, cudaStream_t st)
     a.done = e->d_done;
     NP_CUDA(launch_ens_integrate(MODE_A, a, e->n_total, e->D, e->sk, st));
     for (int j = 0; j < k; ++j) {
-        int rc = ens_pass(e, j + 1 < k ? MODE_BA : MODE_B, true, e->F, st);
+        int rc = ens_pass(e, j + 1 < k ? MODE_BA : MODE_B, true, e->F, st, j);
         if (rc)
             return rc;
     }
@@ -2741,6 +2764,7 @@ int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
         NP_CUDA(cudaGraphLaunch(ex, e->user));
         rem -= k;
         e->step += k;
+        e->last_chunk = k;
     }
     int h = 0;
     NP_CUDA(cudaMemcpyAsync(&h, e->d_flags, sizeof(int), cudaMemcpyDeviceToHost, e->user));
@@ -2752,6 +2776,46 @@ int npsim_ens_step(npsim_ens_t e, int64_t n_steps)
                            "an NP was farther than 2 max(R0, R(t)) from its droplet's centre");
         return set_err(NPSIM_ERR_NONFINITE, "a position became non-finite");
     }
+    return NPSIM_OK;
+}
+
+int npsim_ens_profile(npsim_ens_t e, int enable)
+{
+    NP_REQUIRE(e, "ensemble is NULL");
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    if (enable && !e->ev[0][0][0]) {
+        for (auto &a : e->ev)
+            for (auto &b : a)
+                for (auto &x : b)
+                    NP_CUDA(cudaEventCreate(&x));
+    }
+    if ((enable != 0) != e->profiling) {
+        for (auto &g : e->graphs)
+            cudaGraphExecDestroy(g.second);
+        e->graphs.clear();
+        e->profiling = enable != 0;
+        e->last_chunk = 0;
+    }
+    return NPSIM_OK;
+}
+
+int npsim_ens_kernel_times(npsim_ens_t e, double *ms, int *samples)
+{
+    NP_REQUIRE(e && ms, "ensemble and ms are required");
+    NP_REQUIRE(e->profiling, "profiling is not enabled (npsim_ens_profile)");
+    NP_CUDA(cudaStreamSynchronize(e->user));
+    const int k = e->last_chunk;
+    for (int g = 0; g < 2; ++g) {
+        double tot = 0.0;
+        for (int j = 0; j < k; ++j) {
+            float t = 0.f;
+            NP_CUDA(cudaEventElapsedTime(&t, e->ev[j][g][0], e->ev[j][g][1]));
+            tot += t;
+        }
+        ms[g] = k > 0 ? tot / k : 0.0;
+    }
+    if (samples)
+        *samples = k;
     return NPSIM_OK;
 }
 
@@ -2872,6 +2936,16 @@ int npsim_ens_config(npsim_ens_t e, int *block, int *i_per_thread, int *j_tile, 
         *grid = e->sk.grid;
     if (index)
         *index = e->shape;
+    return NPSIM_OK;
+}
+
+int npsim_ens_work(npsim_ens_t e, int64_t *n_items, int32_t *itile)
+{
+    NP_REQUIRE(e, "ensemble is NULL");
+    if (n_items)
+        *n_items = e->n_items;
+    if (itile)
+        *itile = e->sk.itile;
     return NPSIM_OK;
 }
 

@@ -183,3 +183,27 @@ def test_ensemble_reports_an_escaped_np(P, drops):
         assert e.value.code == -8
     with P.Ensemble(drops[:3]) as ens:
         ens.step(2)
+
+
+def test_ensemble_kernel_times_leave_results_unchanged(P, drops):
+    """The measurement hook: with CUDA event records in its step graphs an
+    ensemble gives the same states bit for bit as one without, and reports
+    positive durations of its all-pairs and integrator launches over the
+    steps of the last chunk; without profiling the hook is refused."""
+    with P.Ensemble(drops[:3]) as a, P.Ensemble(drops[:3]) as b:
+        with pytest.raises(P.NpsimError) as e:
+            a.kernel_times()
+        assert e.value.code == -1
+        b.profile(True)
+        a.step(20)
+        b.step(20)  # a chunk of 16 steps, then one of 4
+        kt, k = b.kernel_times()
+        assert k == 4 and kt["allpairs"] > 0.0 and kt["integrate"] > 0.0
+        n_items, itile = b.work()
+        assert itile == b.config()["block"] * b.config()["i_per_thread"]
+        rows = sum(-(-n // itile) for n in b.sizes)  # row tiles, at least one item each
+        assert n_items >= rows
+        for d in range(3):
+            xa, va, _, _ = a.state(d)
+            xb, vb, _, _ = b.state(d)
+            assert np.array_equal(xa, xb) and np.array_equal(va, vb)
